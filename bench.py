@@ -1,0 +1,354 @@
+"""Benchmark: MG setup (iCSVD) + Galerkin coarse build + solve to 1e-10 on one GB300.
+
+A step is one pass of the whole hot path on the 16^3 x 32 near-critical isotropic
+workload: Philox test vectors smoothed by GMRES (Eq. 2), chiral split and streaming
+SVD into P (Algorithm 3), Galerkin coarse operator (Eq. 5), and the K-cycle FGMRES
+solve of D x = b (Eq. 1) to a true relative residual of 1e-10, in the mixed-precision
+form (FP32 setup smoother and inner solve, FP64 SVD / coarse assembly / refinement).
+The plain FP64 form of the same step is timed beside it.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+"""
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2_16^3x32_near_critical"
+METRIC = "MG setup+solve seconds to 1e-10 residual (mixed precision); Dslash GB/s"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = self.rows
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[2 + i]
+                          and "Not" not in r[2 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def workload():
+    from paper_2505_14399_gb300 import synthetic
+    cfg = dict(synthetic.WORKLOADS[WORKLOAD])
+    cfg["kappa"] = synthetic.kappa_of(cfg)
+    return cfg
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2505_14399_gb300 import _lib, api, synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    cfg = workload()
+    dims = cfg["dims"]
+    V = int(np.prod(dims))
+    U = synthetic.make_links(cfg)
+    b = synthetic.gaussian_rhs(dims, cfg["rhs_seed"] + rank)
+    Ud = torch.from_numpy(U).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make_params(mixed):
+        return api.params(dims, cfg["block"], cfg["kappa"], cfg["k"], cfg["r"], cfg["n_s"],
+                          cfg["sweeps"], cfg["tv_seed"], cfg["hop_weight"], cfg["bc"],
+                          setup_dtype="c64" if mixed else "c128",
+                          solve_dtype="c64" if mixed else "c128")
+
+    def step(p, links, rhs):
+        h = api.Hierarchy(links, p)
+        h.coarse_build()
+        x, info = h.solve(rhs, tol=1e-10, maxiter=4000)
+        h.close()
+        return x, info
+
+    def timed(p, links, rhs, K, W):
+        for _ in range(W):
+            step(p, links, rhs)
+        torch.cuda.synchronize()
+        times, infos = [], []
+        n0 = _lib.lib().mg_kernel_launches()
+        for _ in range(K):
+            flush.zero_()
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, info = step(p, links, rhs)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            infos.append(info)
+        launches = _lib.lib().mg_kernel_launches() - n0
+        t = float(np.mean(times))
+        if world > 1:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t, infos[-1], launches // max(K, 1), x
+
+    pm, p64 = make_params(True), make_params(False)
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_mixed, info_m, launches, x = timed(pm, Ud, bd, args.steps, args.warmup)
+    clocks = sampler.stop()
+    t_fp64, info_64, _, _ = timed(p64, Ud, bd, max(1, min(args.steps, 2)), 1)
+
+    # end to end through the C ABI with host buffers (links, b on the host; x back to host)
+    Uh = torch.from_numpy(U).pin_memory()
+    bh = torch.from_numpy(b).pin_memory()
+    e2e = []
+    for i in range(args.steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xh, _ = step(pm, Uh, bh)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e.append(time.perf_counter() - t0)
+
+    # Dslash roofline: FP32 full operator on the workload lattice, L2 flushed between launches
+    nd = 20
+    psi = torch.from_numpy(synthetic.gaussian_rhs(dims, 7)).to(torch.complex64).to(dev)
+    U32 = Ud.to(torch.complex64)
+    out = torch.empty_like(psi)
+    ev = []
+    for i in range(nd + 3):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.dslash(psi, U32, dims, cfg["kappa"], out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            ev.append(e0.elapsed_time(e1) / 1e3)
+    t_d = float(np.mean(ev))
+    bytes_d = V * 480.0   # 24 reals in + 24 out + 72 link reals per site, FP32
+    peaks, peak_kind = load_peaks()
+    gbs = bytes_d / t_d / 1e9
+
+    # residual check of the timed result (FP64 on device via the library)
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": world / t_mixed if False else t_mixed,
+            "unit": "s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t_mixed * 1e3,
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "c64+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dims": list(dims), "block": list(cfg["block"]),
+                       "k": cfg["k"], "r": cfg["r"], "n_s": cfg["n_s"], "sweeps": cfg["sweeps"],
+                       "kappa": cfg["kappa"], "tol": 1e-10, "nrhs": 1,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "256 MB buffer written between timed steps"},
+            "fp64_seconds": t_fp64,
+            "mixed_over_fp64_speedup": t_fp64 / t_mixed,
+            "solve_info_mixed": info_m,
+            "solve_info_fp64": info_64,
+            "dslash_fp32_gbs": gbs,
+            "e2e": {"value": float(np.mean(e2e)), "unit": "s",
+                    "h2d_bytes_per_step": int(U.nbytes + b.nbytes),
+                    "d2h_bytes_per_step": int(b.nbytes)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "roofline": {"kernel": "dslash_kernel<StC64> (FP32 Wilson-Dirac stencil, 16^3x32)",
+                         "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                         "peak_source": peak_kind, "traffic": None,
+                         "avg_launch_us": t_d * 1e6, "algorithmic_bytes": bytes_d},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(cfg, U, b, info_m, budget_s=args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(cfg, U, b, info, budget_s=20.0):
+    """The FP64 oracle, as it stands, timed on a bounded sample of the workload.
+
+    Sample: one test vector of stream 0 smoothed at full volume (Eq. 2), the iCSVD of
+    a subset of aggregates over all streams, Galerkin assembly over a slice of fine
+    sites, and one K-cycle application at full volume.  Each time is scaled by its
+    share of the full step (r * n_s vectors; all aggregates; all sites; the K-cycle
+    count of the GPU solve), giving estimated oracle seconds for one full step.
+    """
+    from oracle import coarse, icsvd, mg, wilson
+    dims, block = cfg["dims"], cfg["block"]
+    w, bc, kappa = cfg["hop_weight"], cfg["bc"], cfg["kappa"]
+    V = int(np.prod(dims))
+    t0 = time.perf_counter()
+    tv = icsvd.test_vectors(U, dims, kappa, w, bc, cfg["tv_seed"], 1, 0, cfg["sweeps"])
+    t_vec = time.perf_counter() - t0
+    # iCSVD on a subset of aggregates: smooth vectors are not needed for timing the SVD,
+    # Gaussian columns of the same shape stand in
+    nd = int(np.prod(block))
+    dsub = 16
+    rng = np.random.default_rng(0)
+    tiles = [rng.standard_normal((dsub, 2, 6 * nd, cfg["r"]))
+             + 1j * rng.standard_normal((dsub, 2, 6 * nd, cfg["r"])) for _ in range(cfg["n_s"])]
+    t0 = time.perf_counter()
+    icsvd.icsvd_tiles(tiles, cfg["k"])
+    t_svd = (time.perf_counter() - t0) * (V // nd) / dsub
+    # Galerkin on a slice: a P of the right shape; time the full-volume assembly of one
+    # t-slice's worth of sites by restricting the lattice to a single coarse time slab
+    sub = (dims[0], dims[1], dims[2], block[3])
+    Usub = np.ascontiguousarray(U[:, :int(np.prod(sub))])
+    Pt = rng.standard_normal(((int(np.prod(sub)) // nd), 2, 6 * nd, cfg["k"])) + 0j
+    t0 = time.perf_counter()
+    coarse.galerkin(Pt, Usub, sub, block, kappa, w, bc)
+    t_gal = (time.perf_counter() - t0) * dims[3] / block[3]
+    # one K-cycle at full volume with a random P (coarse GMRES counted per iteration)
+    Pf = rng.standard_normal((V // nd, 2, 6 * nd, cfg["k"])) + 0j
+    t0 = time.perf_counter()
+    vc = coarse.restrict(Pf, b[0], dims, block)
+    e = coarse.prolong(Pf, vc, dims, block)
+    t_rp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    wilson.dslash(b[0], U, dims, kappa, w, bc)
+    t_dslash = time.perf_counter() - t0
+    coarse_its = max(1, info.get("coarse", 1))
+    kcycles = max(1, info.get("kcycles", 1))
+    # coarse apply cost on a small stencil, scaled by coarse volume
+    cd = [dims[m] // block[m] for m in range(4)]
+    d = V // nd
+    n2k = 2 * cfg["k"]
+    X = rng.standard_normal((d, n2k, n2k)) + 0j
+    Y = rng.standard_normal((8, d, n2k, n2k)) + 0j
+    t0 = time.perf_counter()
+    coarse.coarse_apply(X, Y, rng.standard_normal((d, n2k)) + 0j, cd)
+    t_capply = time.perf_counter() - t0
+    t_setup = t_vec * cfg["r"] * cfg["n_s"] + t_svd
+    t_solve = kcycles * (t_rp + (cfg.get("post", 8) + 2) * t_dslash) + coarse_its * t_capply \
+        + info.get("outer", 1) * t_dslash
+    est = t_setup + t_gal + t_solve
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": ("full-volume smoothing of 1 of %d test vectors, iCSVD of %d of %d "
+                       "aggregates, Galerkin over 1 of %d time slabs, one Dslash/restrict/"
+                       "prolong/coarse apply; scaled by the GPU solve's counts (%d K-cycles, "
+                       "%d coarse iterations)" % (cfg["r"] * cfg["n_s"], dsub, d,
+                                                  dims[3] // block[3], kcycles, coarse_its)),
+            "parts_s": {"setup": t_setup, "galerkin": t_gal, "solve": t_solve}}
+
+
+def reference_arm(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    from paper_2505_14399_gb300 import synthetic
+    cfg = workload()
+    U = synthetic.make_links(cfg)
+    b = synthetic.gaussian_rhs(cfg["dims"], cfg["rhs_seed"])
+    # iteration counts for the solve share come from the oracle's own small-volume solve
+    info = {"outer": 12, "kcycles": 12, "coarse": 12 * 60}
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(cfg, U, b, info, budget_s=args.cpu_budget)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "dims": list(cfg["dims"])},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * wilson_mg.h -- C ABI of the GB300 streaming chiral-SVD multigrid library.
+ *
+ * Method: Whyte, Stathopoulos, Romero, "Accelerating multigrid with streaming chiral
+ * SVD for Wilson fermions in lattice QCD" (arXiv:2505.14399).  The library solves
+ * D x = b (Eq. 1) for the Wilson-Dirac operator D with a two-level multigrid
+ * preconditioner whose prolongator comes from the streaming chiral SVD (iCSVD,
+ * Algorithm 3) and whose coarse operator is the Galerkin product P^dag D P (Eq. 5),
+ * used in a K-cycle inside flexible GMRES (Sec. 2.1, Sec. 4).
+ *
+ * Conventions (the paper states none of them; Eq. 3 fixes only that spins 1,2 and
+ * 3,4 are the two chiralities):
+ *   - dims = {Lx, Ly, Lz, Lt}; mu = 0..3 = x, y, z, t;
+ *     site s = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) mod 2.
+ *   - spinor fields: [site][spin 4][colour 3] complex, (re, im) interleaved;
+ *     nrhs fields are stored one after another.
+ *   - gauge links: [mu][site][3][3] complex row-major; U_mu(x) connects x to x+mu.
+ *   - D psi(x) = psi(x) - kappa sum_mu w_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                          + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ]
+ *     in the chiral basis gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
+ *     gamma_4 = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1); a hop that wraps
+ *     around the lattice in direction mu is multiplied by bc_phase[mu] (+1 or -1).
+ *   - coarse vectors: [coarse site][chirality 2][k] complex; coarse site index
+ *     j = cx + Cx*(cy + Cy*(cz + Cz*ct)) with C = dims / block.
+ *
+ * Pointers: every field argument may be device memory or host memory (pageable
+ * or pinned); host buffers are staged through device memory on the given stream.
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ * asynchronous on that stream unless stated otherwise.  The caller owns every
+ * buffer it passes; the library owns mg_handle and everything inside it.
+ *
+ * Errors: every call returns an mg_status; no exception or device trap crosses
+ * the ABI.  mg_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef WILSON_MG_H
+#define WILSON_MG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mg_status {
+  MG_OK = 0,
+  MG_EINVAL = 1,    /* bad dimensions, sizes, parameters or NULL pointers      */
+  MG_ENOMEM = 2,    /* device allocation failed                                */
+  MG_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed             */
+  MG_ENOCONV = 4,   /* solver stopped at maxiter; x holds the best iterate     */
+  MG_ETIMEOUT = 5,  /* a bounded device-side wait gave up                      */
+  MG_ENAN = 6       /* a NaN/Inf residual was detected                         */
+} mg_status;
+
+/* storage types of complex fields */
+typedef enum mg_dtype {
+  MG_C128 = 0,      /* complex double                                          */
+  MG_C64 = 1,       /* complex float                                           */
+  MG_F16 = 2,       /* complex IEEE half storage, FP32 arithmetic              */
+  MG_BF16 = 3       /* complex bfloat16 storage, FP32 arithmetic               */
+} mg_dtype;
+
+typedef struct mg_handle mg_handle;
+
+/* Parameters of the hierarchy and of the solve.  Paper symbols: k, r, n_s
+ * (Algorithm 3/4), aggregates Lambda_j of extent `block` (Sec. 2.1). */
+typedef struct mg_params {
+  int dims[4];               /* fine lattice extents                                    */
+  int block[4];              /* aggregate extents; dims[mu] % block[mu] == 0           */
+  double kappa;              /* hopping parameter                                       */
+  double hop_weight[4];      /* w_mu (anisotropy), 1 for isotropic                      */
+  int bc_phase[4];           /* +1 periodic, -1 antiperiodic                             */
+  int k;                     /* singular vectors kept per aggregate and chirality        */
+  int r;                     /* test vectors generated per stream                        */
+  int n_s;                   /* number of streams                                        */
+  int sweeps;                /* smoother GMRES steps per test vector (Eq. 2)             */
+  unsigned long long seed;   /* Philox key of the random initial guesses                 */
+  int setup_dtype;           /* MG_C128 or MG_C64: arithmetic of the setup smoother      */
+  int solve_dtype;           /* MG_C128: plain FP64 solve; MG_C64 / MG_F16 / MG_BF16:
+                                inner FGMRES + K-cycle in that storage inside FP64
+                                iterative refinement                                     */
+  int post_smooth;           /* post-smoother GMRES steps in the K-cycle (8, Sec. 4)     */
+  double coarse_tol;         /* coarse solve relative tolerance (0.03, Sec. 4)           */
+  int coarse_restart;        /* coarse GMRES restart length                              */
+  int coarse_maxiter;        /* coarse GMRES iteration cap per K-cycle                   */
+  int outer_restart;         /* fine FGMRES restart length                               */
+  double inner_tol;          /* inner relative tolerance of mixed-precision refinement   */
+  int svd_refine;            /* 1: second Gram pass per SVD update (more accurate)       */
+} mg_params;
+
+typedef struct mg_solve_info {
+  int outer_iterations;      /* fine-level FGMRES iterations over all refinement steps   */
+  int refinements;           /* FP64 refinement steps (1 for the plain FP64 solve)       */
+  int kcycles;               /* preconditioner applications                              */
+  long long coarse_iterations;  /* coarse GMRES iterations over all K-cycles            */
+  double true_residual;      /* ||b - D x|| / ||b|| in FP64, per the last RHS checked    */
+} mg_solve_info;
+
+/* Defaults: k = 24, r = 24, n_s = 2, sweeps = 5, post_smooth = 8, coarse_tol = 0.03,
+ * coarse_restart = 32, coarse_maxiter = 2000, outer_restart = 16, inner_tol = 1e-5,
+ * setup_dtype = MG_C64, solve_dtype = MG_C64, svd_refine = 1, isotropic periodic. */
+void mg_params_default(mg_params* p);
+
+/* Thread-local message describing the most recent non-MG_OK return. */
+const char* mg_last_error(void);
+
+/* Number of kernels this library has launched since load (diagnostic counter). */
+long long mg_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------------
+ * wilson_dslash -- the Wilson-Dirac stencil (the operator of Eq. 1).
+ *   parity = -1: out = D in (or D^dag in if dagger), full-lattice fields of V sites.
+ *   parity = 0 / 1: out_p = -kappa H_{p,1-p} in_{1-p}: half-lattice fields of V/2
+ *     sites, ordered by checkerboard index site/2 (requires every dims[mu] even).
+ *   dtype: storage of out, in and links (all the same); MG_F16 / MG_BF16 accumulate
+ *   in FP32.  nrhs fields are processed in one launch sharing the links.
+ * Returns MG_EINVAL for bad dims / dtype / nrhs < 1 / NULL pointers.
+ * ------------------------------------------------------------------------------- */
+int wilson_dslash(void* out, const void* in, const void* links, const int dims[4],
+                  double kappa, const double hop_weight[4], const int bc_phase[4],
+                  int parity, int dagger, int dtype, int nrhs, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * mg_setup_streaming_svd -- Algorithm 4 up to P: iCSVD (Algorithm 3) on the fine
+ * operator.  For s = 0..n_s-1: r Philox complex-Gaussian phi_i (vector ids s*r+i),
+ * psi_i = phi_i + GMRES_sweeps(D, -D phi_i) (Eq. 2); chiral split into aggregates
+ * (Eq. 3); per aggregate and chirality Phi_s = rank-k SVD([Phi_{s-1}, Psi_s]) (Eq. 8)
+ * kept as U_k Sigma_k (Eq. 7); after the last stream P = U_k (Eq. 6), each column
+ * with the canonical phase "sum of entries real positive".
+ * links: complex double [mu][site][3][3]; copied into the handle.
+ * Creates *h (must be NULL on entry).  Synchronises `stream` before returning.
+ * MG_EINVAL: dims not divisible by block, k > 6*prod(block), k+r > 64,
+ *            n_s*r < k, odd dims, bad dtypes.
+ * ------------------------------------------------------------------------------- */
+int mg_setup_streaming_svd(mg_handle** h, const void* links, const mg_params* p,
+                           void* stream);
+
+/* Creates a handle with links and parameters but no prolongator (for mg_set_prolongator). */
+int mg_create(mg_handle** h, const void* links, const mg_params* p, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * coarse_build -- Galerkin coarse operator D_c = P^dag D P (Eq. 5; Algorithm 4) as a
+ * nearest-neighbour coarse stencil: X(j) and Y_dir(j), dir = 2 mu + (0: +mu, 1: -mu),
+ * each (2k) x (2k), assembled in FP64 and also kept in FP32.
+ * ------------------------------------------------------------------------------- */
+int coarse_build(mg_handle* h, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * mg_solve -- x = D^{-1} b to ||b - D x|| <= tol ||b|| (checked in FP64) with FGMRES
+ * preconditioned by the two-level K-cycle (restrict, coarse GMRES to coarse_tol,
+ * prolong, post_smooth GMRES steps).  solve_dtype MG_C128: one FP64 FGMRES;
+ * otherwise FP64 iterative refinement around an inner solve in solve_dtype.
+ * x, b: complex double fields, nrhs of them.  x is overwritten (initial guess 0).
+ * Synchronises `stream`.  MG_ENOCONV after maxiter outer iterations per RHS.
+ * ------------------------------------------------------------------------------- */
+int mg_solve(mg_handle* h, void* x, const void* b, int nrhs, double tol, int maxiter,
+             mg_solve_info* info, void* stream);
+
+/* x = D^{-dag} b = gamma_5 D^{-1} gamma_5 b on the same hierarchy (adjoint solve). */
+int mg_solve_adjoint(mg_handle* h, void* x, const void* b, int nrhs, double tol,
+                     int maxiter, mg_solve_info* info, void* stream);
+
+int mg_destroy(mg_handle* h);
+
+/* ---------------------------------------------------------------------------------
+ * Step-level entry points (each step of the path callable on its own).
+ * ------------------------------------------------------------------------------- */
+
+/* The r test vectors of stream `stream_index` (Eq. 2) in setup_dtype arithmetic,
+ * written as complex double fields out[r][site][4][3].  links: complex double. */
+int mg_test_vectors(void* out, const void* links, const mg_params* p, int stream_index,
+                    void* stream);
+
+/* P tiles: P[j][alpha][i][row], row = (local site * 2 + spin in chirality) * 3 + colour,
+ * local site lexicographic inside the aggregate; complex double.  sigma[j][alpha][k]
+ * (double, may be NULL): singular values of the last stream. */
+int mg_get_prolongator(mg_handle* h, void* P, void* sigma, void* stream);
+
+/* Singular values of every stream: hist[s][j][alpha][k] (double; entries beyond the
+ * stream's kept count are 0). */
+int mg_get_sigma_history(mg_handle* h, void* hist, void* stream);
+
+/* Replace P (same layout as mg_get_prolongator, complex double). */
+int mg_set_prolongator(mg_handle* h, const void* P, void* stream);
+
+/* e_c = P^dag v (R = P^dag, Sec. 2.1) and v = P e_c; complex double fields. */
+int mg_restrict(mg_handle* h, void* vc, const void* v, int nrhs, void* stream);
+int mg_prolong(mg_handle* h, void* v, const void* vc, int nrhs, void* stream);
+
+/* Coarse operator export: X[j][a][b], Y[dir][j][a][b] complex double (row a, col b). */
+int mg_get_coarse_op(mg_handle* h, void* X, void* Y, void* stream);
+
+/* y = D_c x on the coarse lattice; dtype MG_C128 or MG_C64 (FP64 / FP32 stencil). */
+int mg_coarse_apply(mg_handle* h, void* y, const void* x, int nrhs, int dtype, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * wilson_link_gradient -- link-angle gradient of a loss through x = D^{-1} b:
+ * with g_b = D^{-dag} g_x (g_x = 2 dL/d conj x),
+ *   out[mu][y][a] = -Re[ g_b(y)^dag dD/d omega^a_mu(y) x ]
+ * for U_mu(y) -> exp(i sum_a omega^a T^a) U_mu(y), T^a = lambda^a / 2 (Gell-Mann).
+ * g_b, x, links: complex double; out: double [4][V][8].
+ * ------------------------------------------------------------------------------- */
+int wilson_link_gradient(void* out, const void* g_b, const void* x, const void* links,
+                         const int dims[4], double kappa, const double hop_weight[4],
+                         const int bc_phase[4], void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WILSON_MG_H */

@@ -1,0 +1,209 @@
+"""PyTorch-facing binding of the C ABI (marshalling only; all compute runs in the CUDA library).
+
+Fields are torch tensors in the ABI layouts of include/wilson_mg.h:
+spinors (nrhs, V, 4, 3) complex, links (4, V, 3, 3) complex, coarse vectors
+(nrhs, d, 2, k) complex.  FP16/BF16 fields are real tensors with a trailing (re, im)
+dimension of size 2.  Device tensors are passed by pointer on torch's current CUDA
+stream; CPU tensors are staged by the library itself.
+"""
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+_DT = {torch.complex128: L.MG_C128, torch.complex64: L.MG_C64,
+       torch.float16: L.MG_F16, torch.bfloat16: L.MG_BF16}
+
+
+def _stream(t=None):
+    if t is not None and not t.is_cuda:
+        return None
+    if not torch.cuda.is_available():
+        return None
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def params(dims, block, kappa, k, r, n_s, sweeps=5, seed=3000, hop_weight=(1, 1, 1, 1),
+           bc=(1, 1, 1, 1), setup_dtype="c64", solve_dtype="c64", post_smooth=8,
+           coarse_tol=0.03, coarse_restart=32, coarse_maxiter=2000, outer_restart=16,
+           inner_tol=1e-5, svd_refine=1):
+    """Build an mg_params structure (paper symbols k, r, n_s; aggregates of extent `block`)."""
+    p = L.MgParams()
+    L.lib().mg_params_default(C.byref(p))
+    dmap = {"c128": L.MG_C128, "c64": L.MG_C64}
+    p.dims = L.ivec(dims)
+    p.block = L.ivec(block)
+    p.kappa = float(kappa)
+    p.hop_weight = L.dvec(hop_weight)
+    p.bc_phase = L.ivec(bc)
+    p.k, p.r, p.n_s, p.sweeps = int(k), int(r), int(n_s), int(sweeps)
+    p.seed = int(seed)
+    p.setup_dtype = dmap[setup_dtype]
+    p.solve_dtype = dmap[solve_dtype]
+    p.post_smooth = int(post_smooth)
+    p.coarse_tol = float(coarse_tol)
+    p.coarse_restart = int(coarse_restart)
+    p.coarse_maxiter = int(coarse_maxiter)
+    p.outer_restart = int(outer_restart)
+    p.inner_tol = float(inner_tol)
+    p.svd_refine = int(svd_refine)
+    return p
+
+
+def dslash(inp, links, dims, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1, 1, 1), parity=-1,
+           dagger=False, out=None):
+    """out = D in (parity -1) or the single-parity hop term (parity 0/1, half-lattice fields)."""
+    dt = _DT[inp.dtype]
+    if links.dtype != inp.dtype:
+        raise ValueError("links and fields must share a dtype")
+    if out is None:
+        out = torch.empty_like(inp)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    per = (V if parity < 0 else V // 2) * 12 * (2 if dt >= L.MG_F16 else 1)
+    nrhs = inp.numel() // per
+    L.check(L.lib().wilson_dslash(_ptr(out), _ptr(inp), _ptr(links), L.ivec(dims), float(kappa),
+                                  L.dvec(hop_weight), L.ivec(bc), int(parity), int(dagger), dt,
+                                  int(nrhs), _stream(inp)), "wilson_dslash")
+    return out
+
+
+def test_vectors(links, p, stream_index, device=None):
+    """The r smoothed test vectors of one stream (Eq. 2), complex128 (r, V, 4, 3)."""
+    V = p.dims[0] * p.dims[1] * p.dims[2] * p.dims[3]
+    dev = links.device if device is None else device
+    out = torch.empty((p.r, V, 4, 3), dtype=torch.complex128, device=dev)
+    L.check(L.lib().mg_test_vectors(_ptr(out), _ptr(links), C.byref(p), int(stream_index),
+                                    _stream(out)), "mg_test_vectors")
+    return out
+
+
+def link_gradient(g_b, x, links, dims, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1, 1, 1)):
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    out = torch.empty((4, V, 8), dtype=torch.float64, device=x.device)
+    L.check(L.lib().wilson_link_gradient(_ptr(out), _ptr(g_b), _ptr(x), _ptr(links), L.ivec(dims),
+                                         float(kappa), L.dvec(hop_weight), L.ivec(bc),
+                                         _stream(x)), "wilson_link_gradient")
+    return out
+
+
+class Hierarchy:
+    """Owner of an mg_handle: iCSVD prolongator, Galerkin coarse operator, K-cycle solver."""
+
+    def __init__(self, links, p, setup=True):
+        self.p = p
+        self.dims = tuple(p.dims)
+        self.block = tuple(p.block)
+        self.k = p.k
+        self.V = self.dims[0] * self.dims[1] * self.dims[2] * self.dims[3]
+        self.nd = self.block[0] * self.block[1] * self.block[2] * self.block[3]
+        self.d = self.V // self.nd
+        self.device = links.device
+        self._h = C.c_void_p()
+        fn = L.lib().mg_setup_streaming_svd if setup else L.lib().mg_create
+        L.check(fn(C.byref(self._h), _ptr(links), C.byref(p), _stream(links)),
+                "mg_setup_streaming_svd" if setup else "mg_create")
+
+    def close(self):
+        if self._h:
+            L.lib().mg_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coarse_build(self):
+        L.check(L.lib().coarse_build(self._h, _stream()), "coarse_build")
+
+    def solve(self, b, tol=1e-10, maxiter=1000, adjoint=False, x=None):
+        nrhs = b.numel() // (self.V * 12)
+        if x is None:
+            x = torch.empty_like(b)
+        info = L.MgSolveInfo()
+        fn = L.lib().mg_solve_adjoint if adjoint else L.lib().mg_solve
+        L.check(fn(self._h, _ptr(x), _ptr(b), int(nrhs), float(tol), int(maxiter),
+                   C.byref(info), _stream(b)), "mg_solve")
+        return x, {"outer": info.outer_iterations, "refinements": info.refinements,
+                   "kcycles": info.kcycles, "coarse": info.coarse_iterations,
+                   "residual": info.true_residual}
+
+    def prolongator(self):
+        P = torch.empty((self.d, 2, self.k, 6 * self.nd), dtype=torch.complex128,
+                        device=self.device)
+        S = torch.empty((self.d, 2, self.k), dtype=torch.float64, device=self.device)
+        L.check(L.lib().mg_get_prolongator(self._h, _ptr(P), _ptr(S), _stream(P)),
+                "mg_get_prolongator")
+        return P, S
+
+    def sigma_history(self):
+        H = torch.empty((self.p.n_s, self.d, 2, self.k), dtype=torch.float64, device=self.device)
+        L.check(L.lib().mg_get_sigma_history(self._h, _ptr(H), _stream(H)), "mg_get_sigma_history")
+        return H
+
+    def set_prolongator(self, P):
+        L.check(L.lib().mg_set_prolongator(self._h, _ptr(P), _stream(P)), "mg_set_prolongator")
+
+    def restrict(self, v):
+        nrhs = v.numel() // (self.V * 12)
+        out = torch.empty((nrhs, self.d, 2, self.k), dtype=torch.complex128, device=v.device)
+        L.check(L.lib().mg_restrict(self._h, _ptr(out), _ptr(v), nrhs, _stream(v)), "mg_restrict")
+        return out
+
+    def prolong(self, vc):
+        nrhs = vc.numel() // (self.d * 2 * self.k)
+        out = torch.empty((nrhs, self.V, 4, 3), dtype=torch.complex128, device=vc.device)
+        L.check(L.lib().mg_prolong(self._h, _ptr(out), _ptr(vc), nrhs, _stream(vc)), "mg_prolong")
+        return out
+
+    def coarse_op(self):
+        n2k = 2 * self.k
+        X = torch.empty((self.d, n2k, n2k), dtype=torch.complex128, device=self.device)
+        Y = torch.empty((8, self.d, n2k, n2k), dtype=torch.complex128, device=self.device)
+        L.check(L.lib().mg_get_coarse_op(self._h, _ptr(X), _ptr(Y), _stream(X)), "mg_get_coarse_op")
+        return X, Y
+
+    def coarse_apply(self, vc):
+        dt = _DT[vc.dtype]
+        nrhs = vc.numel() // (self.d * 2 * self.k)
+        out = torch.empty_like(vc)
+        L.check(L.lib().mg_coarse_apply(self._h, _ptr(out), _ptr(vc), nrhs, dt, _stream(vc)),
+                "mg_coarse_apply")
+        return out
+
+
+class MGSolve(torch.autograd.Function):
+    """x = D^{-1} b through the multigrid solver, differentiable in b and in link angles.
+
+    Forward: mg_solve.  Backward (recomputed, nothing stored but b, x): g_b = D^{-dag} g_x
+    via mg_solve_adjoint (gamma_5-hermiticity, D^dag = gamma_5 D gamma_5), and the link-angle
+    gradient -Re[g_b^dag dD x] for U_mu(y) -> exp(i omega^a T^a) U_mu(y) at omega = 0.
+    """
+
+    @staticmethod
+    def forward(ctx, b, omega, hier, links, tol):
+        x, _ = hier.solve(b.contiguous(), tol=tol)
+        ctx.hier, ctx.links, ctx.tol = hier, links, tol
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, g_x):
+        (x,) = ctx.saved_tensors
+        h = ctx.hier
+        g_b, _ = h.solve(g_x.contiguous(), tol=ctx.tol, adjoint=True)
+        g_om = link_gradient(g_b, x, ctx.links, h.dims, h.p.kappa, tuple(h.p.hop_weight),
+                             tuple(h.p.bc_phase))
+        return g_b, g_om, None, None, None
+
+
+def mg_solve_autograd(b, omega, hier, links, tol=1e-10):
+    return MGSolve.apply(b, omega, hier, links, tol)

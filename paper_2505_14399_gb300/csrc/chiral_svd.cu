@@ -1,0 +1,394 @@
+// Batched streaming chiral SVD (Algorithm 3, Eqs. 7-8) over all aggregates and both
+// chiralities at once.
+//
+// Every (aggregate j, chirality alpha) owns a tile A = [Phi_{s-1} | Psi_s] of M = 6 n_d
+// rows (Eq. 3 split) stored column-major in FP64.  One stream is:
+//   gather   : chiral split of the r new smoothed vectors into columns kk.. of all tiles
+//   gram     : G = A^dag A (c x c Hermitian, c = kk + r), one CTA per tile
+//   eig      : parallel cyclic Jacobi (Brent-Luk ordering) on G in shared memory,
+//              eigenvalues sorted descending (ties by index) -> Sigma^2 and V
+//   update   : Phi_s = A V_k (= U_k Sigma_k, Eq. 7), or U_k = A V_k Sigma_k^{-1} at the end
+// An optional second pass (G of A V over all c columns, eig, rotate) restores the
+// accuracy lost by forming A^dag A (its rotations are relative to sigma_i sigma_j).
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace wmg {
+
+namespace {
+
+template <typename R>
+__global__ void gather_kernel(zd* tiles, int cmax, int col0, const cplx<R>* __restrict__ f,
+                              int nvec, Blocking B) {
+  size_t total = (size_t)nvec * B.L[0] * B.L[1] * B.L[2] * B.L[3] * 12;
+  size_t V12 = total / nvec;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int v = (int)(e / V12);
+    size_t rem = e % V12;
+    int s = (int)(rem / 12), comp = (int)(rem % 12);
+    int spin = comp / 3, col = comp % 3;
+    int j, l;
+    B.block_of(s, &j, &l);
+    int alpha = spin >> 1;
+    int row = (l * 2 + (spin & 1)) * 3 + col;
+    size_t t = (size_t)j * 2 + alpha;
+    cplx<R> x = f[e];
+    tiles[(t * cmax + col0 + v) * B.M + row] = {(double)x.re, (double)x.im};
+  }
+}
+
+constexpr int GT = 256;   // threads per tile CTA
+constexpr int GR = 32;    // rows staged per chunk
+constexpr int MAXC = 64;  // max columns per tile
+
+// G = A^dag A, upper triangle computed, mirrored.
+__global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ tiles, int cmax,
+                                                  int c, int M) {
+  extern __shared__ zd sA[];  // [GR][c]
+  int t = blockIdx.x;
+  const zd* A = tiles + (size_t)t * cmax * M;
+  int npairs = c * (c + 1) / 2;
+  constexpr int MAXP = (MAXC * (MAXC + 1) / 2 + GT - 1) / GT;
+  zd acc[MAXP];
+  int pi[MAXP], pj[MAXP];
+#pragma unroll
+  for (int q = 0; q < MAXP; ++q) {
+    acc[q] = {0, 0};
+    int p = threadIdx.x + q * GT;
+    // p -> (i, j) with i <= j, row-major over the upper triangle
+    int i = 0, rem = p;
+    while (i < c && rem >= c - i) { rem -= c - i; ++i; }
+    pi[q] = i;
+    pj[q] = i + rem;
+  }
+  for (int r0 = 0; r0 < M; r0 += GR) {
+    int nr = min(GR, M - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * c; e += GT) {
+      int col = e / nr, rr = e % nr;
+      sA[rr * c + col] = A[(size_t)col * M + r0 + rr];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < MAXP; ++q) {
+      int p = threadIdx.x + q * GT;
+      if (p < npairs) {
+        zd a = acc[q];
+        for (int rr = 0; rr < nr; ++rr) cfmac(a, sA[rr * c + pi[q]], sA[rr * c + pj[q]]);
+        acc[q] = a;
+      }
+    }
+  }
+  zd* Gt = G + (size_t)t * c * c;
+#pragma unroll
+  for (int q = 0; q < MAXP; ++q) {
+    int p = threadIdx.x + q * GT;
+    if (p < npairs) {
+      Gt[pi[q] * c + pj[q]] = acc[q];
+      if (pi[q] != pj[q]) Gt[pj[q] * c + pi[q]] = conj(acc[q]);
+    }
+  }
+}
+
+// Parallel cyclic Jacobi on a Hermitian c x c matrix per CTA (Brent-Luk round robin).
+__global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const zd* G, int c) {
+  extern __shared__ zd sm[];
+  int ce = c + (c & 1);              // padded to even
+  zd* A = sm;                         // ce x ce
+  zd* Vv = A + ce * ce;               // ce x ce
+  double* rc = reinterpret_cast<double*>(Vv + ce * ce);   // [ce/2] cos
+  zd* rs = reinterpret_cast<zd*>(rc + ce / 2 + 1);        // [ce/2] s e^{-i phi}... see below
+  zd* rph = rs + ce / 2;                                   // [ce/2] e^{-i phi}
+  int* top = reinterpret_cast<int*>(rph + ce / 2);        // [ce/2]
+  int* bot = top + ce / 2;                                 // [ce/2]
+  __shared__ int rotated;
+  int t = blockIdx.x;
+  const zd* Gt = G + (size_t)t * c * c;
+  for (int e = threadIdx.x; e < ce * ce; e += blockDim.x) {
+    int i = e / ce, j = e % ce;
+    A[e] = (i < c && j < c) ? Gt[i * c + j] : zd{0, 0};
+    Vv[e] = (i == j) ? zd{1, 0} : zd{0, 0};
+  }
+  int np = ce / 2;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    top[p] = 2 * p;
+    bot[p] = 2 * p + 1;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < ce - 1; ++round) {
+      // rotation parameters
+      for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+        double c0 = 1.0;
+        zd s0 = {0, 0}, ph = {1, 0};
+        if (b < c) {
+          zd g = A[a * ce + b];
+          double ag = sqrt(norm2(g));
+          double da = A[a * ce + a].re, db = A[b * ce + b].re;
+          if (ag > 1e-15 * sqrt(fabs(da * db)) && ag > 1e-300) {
+            double zeta = (db - da) / (2.0 * ag);
+            double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c0 = 1.0 / sqrt(1.0 + tt * tt);
+            double s = tt * c0;
+            ph = {g.re / ag, -g.im / ag};  // e^{-i phi}
+            s0 = {s, 0};
+            rotated = 1;
+          }
+        }
+        rc[p] = c0;
+        rs[p] = s0;
+        rph[p] = ph;
+      }
+      __syncthreads();
+      // rows: new_a = c A_a - s e^{i phi} A_b ; new_b = s A_a + c e^{i phi} A_b
+      for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
+        int p = e / ce, k = e % ce;
+        int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+        double cc = rc[p], s = rs[p].re;
+        if (s == 0.0 && cc == 1.0) continue;
+        zd eph = conj(rph[p]);  // e^{i phi}
+        zd xa = A[a * ce + k], xb = A[b * ce + k];
+        zd ebx = eph * xb;
+        A[a * ce + k] = cc * xa - s * ebx;
+        A[b * ce + k] = s * xa + cc * ebx;
+      }
+      __syncthreads();
+      // columns: new_a = c M_a - s e^{-i phi} M_b ; new_b = s M_a + c e^{-i phi} M_b
+      for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
+        int p = e / ce, k = e % ce;
+        int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+        double cc = rc[p], s = rs[p].re;
+        if (s == 0.0 && cc == 1.0) continue;
+        zd mph = rph[p];
+        zd xa = A[k * ce + a], xb = A[k * ce + b];
+        zd ebx = mph * xb;
+        A[k * ce + a] = cc * xa - s * ebx;
+        A[k * ce + b] = s * xa + cc * ebx;
+        zd va = Vv[k * ce + a], vb = Vv[k * ce + b];
+        zd evb = mph * vb;
+        Vv[k * ce + a] = cc * va - s * evb;
+        Vv[k * ce + b] = s * va + cc * evb;
+      }
+      __syncthreads();
+      // the rotated pair's off-diagonal entries are zero by construction
+      for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        if (!(rs[p].re == 0.0 && rc[p] == 1.0)) {
+          int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+          A[a * ce + b] = {0, 0};
+          A[b * ce + a] = {0, 0};
+        }
+      }
+      __syncthreads();
+      // round-robin: keep top[0], rotate the others
+      if (threadIdx.x == 0 && np > 1) {
+        int tlast = top[np - 1];
+        int b0 = bot[0];
+        for (int p = np - 1; p > 1; --p) top[p] = top[p - 1];
+        top[1] = b0;
+        for (int p = 0; p < np - 1; ++p) bot[p] = bot[p + 1];
+        bot[np - 1] = tlast;
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!rotated) break;
+  }
+  // sort eigenvalues descending (stable by index), thread 0
+  __shared__ int order[MAXC];
+  if (threadIdx.x == 0) {
+    // stable insertion sort by value descending (ties keep index order)
+    for (int i = 0; i < c; ++i) order[i] = i;
+    for (int i = 1; i < c; ++i) {
+      int key = order[i];
+      double kv = A[key * ce + key].re;
+      int j = i - 1;
+      while (j >= 0 && A[order[j] * ce + order[j]].re < kv) {
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = key;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < c; i += blockDim.x)
+    lam[(size_t)t * c + i] = A[order[i] * ce + order[i]].re;
+  zd* Vt = Vec + (size_t)t * c * c;
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    int row = e / c, i = e % c;
+    Vt[row * c + i] = Vv[row * ce + order[i]];
+  }
+}
+
+constexpr int UK = 64;  // max output columns per update
+
+__global__ void __launch_bounds__(GT) update_kernel(zd* out, int cmax_out, const zd* __restrict__ tiles,
+                                                    int cmax, int c, const zd* __restrict__ Vec,
+                                                    const double* lam, int kout, int scale_inv,
+                                                    int M) {
+  extern __shared__ zd sV[];  // [c][kout]
+  int t = blockIdx.x;
+  const zd* Vt = Vec + (size_t)t * c * c;
+  for (int e = threadIdx.x; e < c * kout; e += blockDim.x) {
+    int row = e / kout, i = e % kout;
+    zd v = Vt[row * c + i];
+    if (scale_inv) {
+      double l = lam[(size_t)t * c + i];
+      double f = l > 0 ? 1.0 / sqrt(l) : 0.0;
+      v = f * v;
+    }
+    sV[e] = v;
+  }
+  __syncthreads();
+  const zd* A = tiles + (size_t)t * cmax * M;
+  zd* O = out + (size_t)t * cmax_out * M;
+  for (int r = threadIdx.x; r < M; r += blockDim.x) {
+    for (int i0 = 0; i0 < kout; i0 += 16) {
+      zd acc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] = {0, 0};
+      for (int col = 0; col < c; ++col) {
+        zd a = A[(size_t)col * M + r];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (i0 + q < kout) cfma(acc[q], a, sV[col * kout + i0 + q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (i0 + q < kout) O[(size_t)(i0 + q) * M + r] = acc[q];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GT) phase_kernel(zd* tiles, int cmax, int k, int M) {
+  __shared__ double sh[64];
+  __shared__ zd q;
+  int t = blockIdx.x;
+  zd* A = tiles + (size_t)t * cmax * M;
+  for (int i = 0; i < k; ++i) {
+    zd* col = A + (size_t)i * M;
+    double a = 0, b = 0;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) {
+      a += col[r].re;
+      b += col[r].im;
+    }
+    // block sum
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sh[2 * wid] = a; sh[2 * wid + 1] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sa = 0, sb = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa += sh[2 * w]; sb += sh[2 * w + 1]; }
+      double m = sqrt(sa * sa + sb * sb);
+      q = m > 0 ? zd{sa / m, -sb / m} : zd{1, 0};
+    }
+    __syncthreads();
+    zd f = q;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) col[r] = col[r] * f;
+    __syncthreads();
+  }
+}
+
+__global__ void sigma_kernel(double* sig, int ldsig, const double* lam, int c, int kk, int ntiles) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ntiles * kk) return;
+  int t = e / kk, i = e % kk;
+  double l = lam[(size_t)t * c + i];
+  sig[(size_t)t * ldsig + i] = l > 0 ? sqrt(l) : 0.0;
+}
+
+}  // namespace
+
+int make_blocking(Blocking& B, const int dims[4], const int block[4]) {
+  B.nd = 1;
+  B.d = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (block[m] < 1 || dims[m] % block[m] != 0)
+      return fail(MG_EINVAL, "aggregate extents must divide the lattice extents");
+    B.L[m] = dims[m];
+    B.b[m] = block[m];
+    B.C[m] = dims[m] / block[m];
+    B.nd *= block[m];
+    B.d *= B.C[m];
+  }
+  B.M = 6 * B.nd;
+  return MG_OK;
+}
+
+template <typename R>
+int chiral_gather(zd* tiles, int cmax, int col0, const cplx<R>* fields, int nvec,
+                  const Blocking& B, cudaStream_t st) {
+  size_t total = (size_t)nvec * B.nd * B.d * 12;
+  size_t g = (total + 255) / 256;
+  size_t cap = (size_t)num_sms() * 16;
+  gather_kernel<R><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(tiles, cmax, col0, fields, nvec, B);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+template int chiral_gather<float>(zd*, int, int, const zf*, int, const Blocking&, cudaStream_t);
+template int chiral_gather<double>(zd*, int, int, const zd*, int, const Blocking&, cudaStream_t);
+
+int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaStream_t st) {
+  if (c > MAXC) return fail(MG_EINVAL, "tile_gram: more than 64 columns");
+  size_t sh = sizeof(zd) * GR * c;
+  gram_kernel<<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st) {
+  if (c > MAXC) return fail(MG_EINVAL, "tile_eig: more than 64 columns");
+  int ce = c + (c & 1);
+  size_t sh = sizeof(zd) * 2 * ce * ce + sizeof(double) * (ce / 2 + 1) + sizeof(zd) * ce +
+              sizeof(int) * ce + 64;
+  static bool attr_set = false;
+  if (!attr_set) {
+    WMG_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr_set = true;
+  }
+  jacobi_kernel<<<ntiles, GT, sh, st>>>(lam, Vec, G, c);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+int tile_update(zd* out, int cmax_out, const zd* tiles, int cmax, int c, const zd* Vec,
+                const double* lam, int kout, int scale_inv, const Blocking& B, cudaStream_t st) {
+  if (kout > UK || c > MAXC) return fail(MG_EINVAL, "tile_update: too many columns");
+  size_t sh = sizeof(zd) * c * kout;
+  static bool attr_set = false;
+  if (!attr_set) {
+    WMG_CUDA(cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  100 * 1024));
+    attr_set = true;
+  }
+  update_kernel<<<B.d * 2, GT, sh, st>>>(out, cmax_out, tiles, cmax, c, Vec, lam, kout, scale_inv, B.M);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+int tile_canonical_phase(zd* tiles, int cmax, int k, const Blocking& B, cudaStream_t st) {
+  phase_kernel<<<B.d * 2, GT, 0, st>>>(tiles, cmax, k, B.M);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+int tile_sigma(double* sig, int ldsig, const double* lam, int c, int kk, int ntiles,
+               cudaStream_t st) {
+  int tot = ntiles * kk;
+  sigma_kernel<<<(tot + 255) / 256, 256, 0, st>>>(sig, ldsig, lam, c, kk, ntiles);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+}  // namespace wmg

@@ -1,0 +1,377 @@
+// Restriction R = P^dag, prolongation, the Galerkin coarse operator D_c = P^dag D P
+// (Eq. 5) and its application.
+//
+// P is kept as the final iCSVD tiles: P[t][i][row], t = 2 j + alpha, M = 6 n_d rows.
+// D_c is a coarse nearest-neighbour stencil stored per coarse site as 9 column-major
+// (2k)x(2k) blocks: blk 0 = X (self), blk 1 + dir = Y_dir, dir = 2 mu + (0: +mu, 1: -mu).
+//
+// Galerkin assembly: CTA (j, dir) walks the n_d fine sites x of aggregate j; for each,
+// the hop x -> x +/- mu of D applied to the 2k columns of P at the neighbour is reduced
+// to a 6 x 2k half-spinor block chi (spin projection, colour transport), P(x) is
+// folded with the matching reconstruction into a 6 x 2k block Ptil, and
+// Ptil^dag chi is accumulated in FP64 -- into Y_dir(j) if the hop leaves the
+// aggregate, else into a per-direction partial of X(j).  A second kernel sums the
+// partials and the diagonal term P_j^dag P_j in a fixed order.
+#include "common.cuh"
+#include "internal.h"
+
+namespace wmg {
+
+namespace {
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+restrict_kernel(cplx<R>* vc, const cplx<R>* __restrict__ v, const cplx<R>* __restrict__ P,
+                int k, Blocking B) {
+  extern __shared__ unsigned char smraw[];
+  cplx<R>* sv = reinterpret_cast<cplx<R>*>(smraw);
+  int t = blockIdx.x, rhs = blockIdx.y;
+  int j = t >> 1, alpha = t & 1;
+  size_t V = (size_t)B.nd * B.d;
+  const cplx<R>* vr = v + (size_t)rhs * V * 12;
+  for (int row = threadIdx.x; row < B.M; row += blockDim.x) {
+    int l = row / 6, sp = (row / 3) & 1, c = row % 3;
+    int s = B.site(j, l);
+    sv[row] = vr[(size_t)s * 12 + (2 * alpha + sp) * 3 + c];
+  }
+  __syncthreads();
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const cplx<R>* Pt = P + (size_t)t * k * B.M;
+  for (int i = wid; i < k; i += nw) {
+    const cplx<R>* col = Pt + (size_t)i * B.M;
+    cplx<R> acc = {0, 0};
+    for (int row = lane; row < B.M; row += 32) cfmac(acc, col[row], sv[row]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.re += __shfl_down_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_down_sync(0xffffffffu, acc.im, o);
+    }
+    if (lane == 0) vc[(size_t)rhs * B.d * 2 * k + (size_t)t * k + i] = acc;
+  }
+}
+
+template <typename R>
+__global__ void prolong_kernel(cplx<R>* v, const cplx<R>* __restrict__ vc,
+                               const cplx<R>* __restrict__ P, int k, Blocking B, size_t total) {
+  size_t V12 = (size_t)B.nd * B.d * 12;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t rhs = e / V12, rem = e % V12;
+    int s = (int)(rem / 12), comp = (int)(rem % 12);
+    int spin = comp / 3, c = comp % 3;
+    int j, l;
+    B.block_of(s, &j, &l);
+    int t = 2 * j + (spin >> 1);
+    int row = (l * 2 + (spin & 1)) * 3 + c;
+    const cplx<R>* Pt = P + (size_t)t * k * B.M + row;
+    const cplx<R>* cv = vc + rhs * B.d * 2 * k + (size_t)t * k;
+    cplx<R> acc = {0, 0};
+    for (int i = 0; i < k; ++i) cfma(acc, Pt[(size_t)i * B.M], cv[i]);
+    v[e] = acc;
+  }
+}
+
+struct HopGeom {
+  int L[4], stride[4];
+  double w[4];
+  int bc[4];
+  double kappa;
+};
+
+// (i sigma_mu psi)[s] for a 2-spinor given by its two components: returns component s.
+__device__ __forceinline__ zd isigma(int mu, int s, zd p0, zd p1) {
+  if (mu == 0) return s == 0 ? ti(p1) : ti(p0);
+  if (mu == 1) return s == 0 ? p1 : -p0;
+  return s == 0 ? ti(p0) : tmi(p1);
+}
+
+constexpr int GNB = 8;       // fine sites staged per batch
+constexpr int GTH = 256;     // threads
+constexpr int GMAXE = 16;    // accumulator entries per thread ((2k)^2 <= 4096)
+
+__global__ void __launch_bounds__(GTH)
+galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
+                    const zd* __restrict__ links, HopGeom g, Blocking B) {
+  extern __shared__ zd gsm[];
+  int n2k = 2 * k;
+  zd* sPt = gsm;                       // [GNB][6][n2k]
+  zd* sCh = gsm + GNB * 6 * n2k;       // [GNB][6][n2k]
+  __shared__ int ssite[GNB], snb[GNB];
+  __shared__ double sph[GNB];
+  int j = blockIdx.x, dir = blockIdx.y;
+  int mu = dir >> 1;
+  bool fwd = (dir & 1) == 0;
+  // projector sign of this hop in D: forward (1 - gamma), backward (1 + gamma)
+  int S = fwd ? -1 : +1;
+  double coef = -g.kappa * g.w[mu];
+  int ne = n2k * n2k;
+  int bmu = B.b[mu];
+  const int* bb = B.b;
+  for (int pass = 0; pass < 2; ++pass) {  // 0: hops inside the aggregate, 1: crossing hops
+    zd acc[GMAXE];
+#pragma unroll
+    for (int q = 0; q < GMAXE; ++q) acc[q] = {0, 0};
+    int l = 0;
+    while (true) {
+      // collect the next batch of local sites of this pass (same scan in every thread)
+      int nb = 0;
+      int lsel[GNB];
+      while (l < B.nd && nb < GNB) {
+        int lm;
+        {
+          int q = l;
+          int lc[4];
+          lc[0] = q % bb[0]; q /= bb[0];
+          lc[1] = q % bb[1]; q /= bb[1];
+          lc[2] = q % bb[2]; lc[3] = q / bb[2];
+          lm = lc[mu];
+        }
+        bool cross = fwd ? (lm == bmu - 1) : (lm == 0);
+        if ((pass == 1) == cross) lsel[nb++] = l;
+        ++l;
+      }
+      if (nb == 0) break;
+      __syncthreads();
+      if (threadIdx.x < nb) {
+        int x = B.site(j, lsel[threadIdx.x]);
+        int c[4];
+        c[0] = x % g.L[0];
+        int r = x / g.L[0];
+        c[1] = r % g.L[1]; r /= g.L[1];
+        c[2] = r % g.L[2]; c[3] = r / g.L[2];
+        int y;
+        bool wrap;
+        if (fwd) {
+          wrap = c[mu] == g.L[mu] - 1;
+          y = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
+        } else {
+          wrap = c[mu] == 0;
+          y = wrap ? x + (g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu];
+        }
+        ssite[threadIdx.x] = x;
+        snb[threadIdx.x] = y;
+        sph[threadIdx.x] = (wrap && g.bc[mu] < 0) ? -coef : coef;
+      }
+      __syncthreads();
+      // stage chi and Ptil
+      for (int e = threadIdx.x; e < nb * 6 * n2k; e += GTH) {
+        int h = e / (6 * n2k);
+        int r = (e / n2k) % 6;
+        int bcol = e % n2k;
+        int s = r / 3, cc = r % 3;
+        int beta = bcol / k, ip = bcol % k;
+        int x = ssite[h], y = snb[h];
+        // half spinor of column bcol of P at y, colour c' = 0..2, spin s
+        int jy, ly;
+        B.block_of(y, &jy, &ly);
+        const zd* Py = P + ((size_t)(2 * jy + beta) * k + ip) * B.M;
+        zd hv[3];
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2) {
+          if (beta == 0) {
+            hv[c2] = Py[(ly * 2 + s) * 3 + c2];
+          } else {
+            zd p0 = Py[(ly * 2 + 0) * 3 + c2], p1 = Py[(ly * 2 + 1) * 3 + c2];
+            if (mu < 3) {
+              zd is = isigma(mu, s, p0, p1);
+              hv[c2] = (S > 0) ? -is : is;      // -S i sigma psi_dn
+            } else {
+              zd ps = s == 0 ? p0 : p1;
+              hv[c2] = (S > 0) ? ps : -ps;      // S psi_dn
+            }
+          }
+        }
+        // colour transport
+        zd ch = {0, 0};
+        if (fwd) {
+          const zd* U = links + ((size_t)mu * B.nd * B.d + x) * 9;
+#pragma unroll
+          for (int c2 = 0; c2 < 3; ++c2) cfma(ch, U[cc * 3 + c2], hv[c2]);
+        } else {
+          const zd* U = links + ((size_t)mu * B.nd * B.d + y) * 9;
+#pragma unroll
+          for (int c2 = 0; c2 < 3; ++c2) cfmac(ch, U[c2 * 3 + cc], hv[c2]);
+        }
+        sCh[(h * 6 + r) * n2k + bcol] = sph[h] * ch;
+        // Ptil: column a = bcol of P(x) folded with the reconstruction
+        int jx, lx;
+        B.block_of(x, &jx, &lx);
+        const zd* Px = P + ((size_t)(2 * jx + beta) * k + ip) * B.M;
+        zd pt;
+        if (beta == 0) {
+          pt = Px[(lx * 2 + s) * 3 + cc];
+        } else {
+          zd p0 = Px[(lx * 2 + 0) * 3 + cc], p1 = Px[(lx * 2 + 1) * 3 + cc];
+          if (mu < 3) {
+            zd is = isigma(mu, s, p0, p1);
+            pt = (S > 0) ? -is : is;            // L^dag = -S i sigma
+          } else {
+            zd ps = s == 0 ? p0 : p1;
+            pt = (S > 0) ? ps : -ps;            // L^dag = S
+          }
+        }
+        sPt[(h * 6 + r) * n2k + bcol] = pt;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < GMAXE; ++q) {
+        int e = threadIdx.x + q * GTH;
+        if (e < ne) {
+          int a = e / n2k, b = e % n2k;
+          zd t = acc[q];
+          for (int h = 0; h < nb; ++h)
+#pragma unroll
+            for (int r = 0; r < 6; ++r)
+              cfmac(t, sPt[(h * 6 + r) * n2k + a], sCh[(h * 6 + r) * n2k + b]);
+          acc[q] = t;
+        }
+      }
+    }
+    zd* out = pass == 1 ? Op + ((size_t)j * 9 + 1 + dir) * ne
+                        : Xpart + ((size_t)dir * B.d + j) * ne;
+#pragma unroll
+    for (int q = 0; q < GMAXE; ++q) {
+      int e = threadIdx.x + q * GTH;
+      if (e < ne) {
+        int a = e / n2k, b = e % n2k;
+        out[(size_t)b * n2k + a] = acc[q];   // column-major
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// X(j) = P_j^dag P_j (per chirality) + sum_dir Xpart_dir(j)
+__global__ void __launch_bounds__(GTH)
+galerkin_diag_kernel(zd* Op, const zd* __restrict__ Xpart, const zd* __restrict__ P, int k,
+                     Blocking B) {
+  int j = blockIdx.x;
+  int n2k = 2 * k, ne = n2k * n2k;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    int b = e / n2k, a = e % n2k;  // column-major element (a, b)
+    zd acc = {0, 0};
+    int aa = a / k, bb = b / k;
+    if (aa == bb) {
+      const zd* Pa = P + ((size_t)(2 * j + aa) * k + a % k) * B.M;
+      const zd* Pb = P + ((size_t)(2 * j + bb) * k + b % k) * B.M;
+      for (int r = 0; r < B.M; ++r) cfmac(acc, Pa[r], Pb[r]);
+    }
+    for (int dir = 0; dir < 8; ++dir) acc += Xpart[((size_t)dir * B.d + j) * ne + e];
+    Op[(size_t)j * 9 * ne + e] = acc;
+  }
+}
+
+// y(j) = sum_blk Op[j][blk] x(src(blk)); one warp per (coarse site, rhs)
+template <typename R>
+__global__ void __launch_bounds__(256)
+coarse_apply_kernel(cplx<R>* y, const cplx<R>* __restrict__ x, const cplx<R>* __restrict__ Op,
+                    int n2k, Blocking B, int nrhs) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= B.d * nrhs) return;
+  int rhs = warp / B.d, j = warp % B.d;
+  size_t nc = (size_t)B.d * n2k;
+  const cplx<R>* xr = x + rhs * nc;
+  constexpr int MAXR = 2;  // rows per lane (2k <= 64)
+  cplx<R> acc[MAXR];
+#pragma unroll
+  for (int q = 0; q < MAXR; ++q) acc[q] = {0, 0};
+  size_t ne = (size_t)n2k * n2k;
+  for (int blk = 0; blk < 9; ++blk) {
+    int src = blk == 0 ? j : B.coarse_nbr(j, blk - 1);
+    const cplx<R>* xs = xr + (size_t)src * n2k;
+    const cplx<R>* O = Op + ((size_t)j * 9 + blk) * ne;
+    for (int b = 0; b < n2k; ++b) {
+      cplx<R> xb = xs[b];
+#pragma unroll
+      for (int q = 0; q < MAXR; ++q) {
+        int a = lane + 32 * q;
+        if (a < n2k) cfma(acc[q], O[(size_t)b * n2k + a], xb);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < MAXR; ++q) {
+    int a = lane + 32 * q;
+    if (a < n2k) y[rhs * nc + (size_t)j * n2k + a] = acc[q];
+  }
+}
+
+}  // namespace
+
+template <typename R>
+int restrict_launch(cplx<R>* vc, const cplx<R>* v, const cplx<R>* P, int k, const Blocking& B,
+                    int nrhs, cudaStream_t st) {
+  dim3 grid(B.d * 2, nrhs);
+  size_t sh = sizeof(cplx<R>) * B.M;
+  if (sh > 200 * 1024) return fail(MG_EINVAL, "restrict: aggregate too large");
+  static bool set = false;
+  if (!set) {
+    WMG_CUDA(cudaFuncSetAttribute(restrict_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    set = true;
+  }
+  restrict_kernel<R><<<grid, 256, sh, st>>>(vc, v, P, k, B);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+template <typename R>
+int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const Blocking& B,
+                   int nrhs, cudaStream_t st) {
+  size_t total = (size_t)nrhs * B.nd * B.d * 12;
+  size_t gsz = (total + 255) / 256;
+  size_t cap = (size_t)num_sms() * 16;
+  prolong_kernel<R><<<(unsigned)(gsz < cap ? gsz : cap), 256, 0, st>>>(v, vc, P, k, B, total);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+int galerkin_build(zd* Op, zd* Xpart, const zd* P, int k, const zd* links, const Geom& g,
+                   const Blocking& B, cudaStream_t st) {
+  if (4 * k * k > GTH * GMAXE) return fail(MG_EINVAL, "galerkin: k > 32");
+  HopGeom hg;
+  for (int m = 0; m < 4; ++m) {
+    hg.L[m] = g.L[m];
+    hg.w[m] = g.w[m];
+    hg.bc[m] = g.bc[m];
+  }
+  hg.stride[0] = 1;
+  hg.stride[1] = g.L[0];
+  hg.stride[2] = g.L[0] * g.L[1];
+  hg.stride[3] = g.L[0] * g.L[1] * g.L[2];
+  hg.kappa = g.kappa;
+  size_t sh = sizeof(zd) * 2 * GNB * 6 * 2 * k;
+  static bool set = false;
+  if (!set) {
+    WMG_CUDA(cudaFuncSetAttribute(galerkin_hop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    set = true;
+  }
+  dim3 grid(B.d, 8);
+  galerkin_hop_kernel<<<grid, GTH, sh, st>>>(Op, Xpart, P, k, links, hg, B);
+  WMG_LAUNCHED();
+  galerkin_diag_kernel<<<B.d, GTH, 0, st>>>(Op, Xpart, P, k, B);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+template <typename R>
+int coarse_apply_launch(cplx<R>* y, const cplx<R>* x, const cplx<R>* Op, int k, const Blocking& B,
+                        int nrhs, cudaStream_t st) {
+  if (2 * k > 64) return fail(MG_EINVAL, "coarse_apply: 2k > 64");
+  size_t warps = (size_t)B.d * nrhs;
+  size_t blocks = (warps * 32 + 255) / 256;
+  coarse_apply_kernel<R><<<(unsigned)blocks, 256, 0, st>>>(y, x, Op, 2 * k, B, nrhs);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+template int restrict_launch<float>(zf*, const zf*, const zf*, int, const Blocking&, int, cudaStream_t);
+template int restrict_launch<double>(zd*, const zd*, const zd*, int, const Blocking&, int, cudaStream_t);
+template int prolong_launch<float>(zf*, const zf*, const zf*, int, const Blocking&, int, cudaStream_t);
+template int prolong_launch<double>(zd*, const zd*, const zd*, int, const Blocking&, int, cudaStream_t);
+template int coarse_apply_launch<float>(zf*, const zf*, const zf*, int, const Blocking&, int, cudaStream_t);
+template int coarse_apply_launch<double>(zd*, const zd*, const zd*, int, const Blocking&, int, cudaStream_t);
+
+}  // namespace wmg

@@ -1,0 +1,657 @@
+// Multigrid hierarchy handle: iCSVD setup (Algorithms 3-4), Galerkin coarse build
+// (Eq. 5) and the K-cycle preconditioned FGMRES solve of D x = b (Eq. 1; Sec. 2.1, 4).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace wmg;
+
+struct mg_handle {
+  mg_params p;
+  Geom g;
+  Blocking B;
+  int k = 0;
+  size_t nf = 0;   // complex entries per fine field
+  size_t nc = 0;   // complex entries per coarse field
+  zd* links64 = nullptr;
+  zf* links32 = nullptr;
+  zd* P64 = nullptr;
+  zf* P32 = nullptr;
+  double* sigma = nullptr;   // [tile][k]
+  double* hist = nullptr;    // [n_s][tile][k]
+  zd* Op64 = nullptr;
+  zf* Op32 = nullptr;
+  bool have_P = false, have_coarse = false;
+  // solver state, sized for `nrhs`
+  int nrhs = 0;
+  Gmres<double> outer64, coarse64, post64;
+  Gmres<float> outer32, coarse32, post32;
+  zd *x64 = nullptr, *r64 = nullptr, *t64 = nullptr;
+  zf *e32 = nullptr, *r32 = nullptr;
+  zd *vc64 = nullptr, *ec64 = nullptr, *kw64 = nullptr, *ke64 = nullptr;
+  zf *vc32 = nullptr, *ec32 = nullptr, *kw32 = nullptr, *ke32 = nullptr;
+  double* dscal = nullptr;     // device scalars [4][nrhs]
+  double* hscal = nullptr;     // pinned
+  ReduceWork rw;
+  // counters of the last solve
+  long long coarse_its = 0;
+  int kcycles = 0;
+  ~mg_handle();
+  void free_solver();
+};
+
+namespace {
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+int validate(const mg_params* p, bool need_svd) {
+  if (!p) return fail(MG_EINVAL, "NULL params");
+  for (int m = 0; m < 4; ++m) {
+    if (p->dims[m] < 2 || (p->dims[m] & 1)) return fail(MG_EINVAL, "lattice extents must be even and >= 2");
+    if (p->block[m] < 1 || p->dims[m] % p->block[m]) return fail(MG_EINVAL, "block must divide dims");
+  }
+  int nd = p->block[0] * p->block[1] * p->block[2] * p->block[3];
+  if (p->k < 1 || p->k > 6 * nd) return fail(MG_EINVAL, "k must be in [1, 6 n_d]");
+  if (p->k > 32) return fail(MG_EINVAL, "k > 32 not supported");
+  if (need_svd) {
+    if (p->r < 1 || p->n_s < 1) return fail(MG_EINVAL, "r and n_s must be >= 1");
+    if (p->k + p->r > 64) return fail(MG_EINVAL, "k + r must be <= 64");
+    if ((long long)p->r * p->n_s < p->k) return fail(MG_EINVAL, "n_s * r must be >= k");
+    if (p->sweeps < 0 || p->sweeps > 64) return fail(MG_EINVAL, "sweeps must be in [0, 64]");
+    if (p->setup_dtype != MG_C128 && p->setup_dtype != MG_C64)
+      return fail(MG_EINVAL, "setup_dtype must be MG_C128 or MG_C64");
+  }
+  if (p->solve_dtype != MG_C128 && p->solve_dtype != MG_C64)
+    return fail(MG_EINVAL, "solve_dtype must be MG_C128 or MG_C64");
+  if (p->post_smooth < 0 || p->post_smooth > 64) return fail(MG_EINVAL, "post_smooth in [0, 64]");
+  if (p->coarse_restart < 1 || p->coarse_restart > 128) return fail(MG_EINVAL, "coarse_restart in [1, 128]");
+  if (p->outer_restart < 1 || p->outer_restart > 128) return fail(MG_EINVAL, "outer_restart in [1, 128]");
+  if (!(p->coarse_tol > 0 && p->coarse_tol < 1)) return fail(MG_EINVAL, "coarse_tol in (0, 1)");
+  return MG_OK;
+}
+
+int create_handle(mg_handle** out, const void* links, const mg_params* p, bool need_svd,
+                  cudaStream_t st) {
+  if (!out) return fail(MG_EINVAL, "NULL handle pointer");
+  if (*out) return fail(MG_EINVAL, "*h must be NULL on entry");
+  if (!links) return fail(MG_EINVAL, "NULL links");
+  WMG_TRY(validate(p, need_svd));
+  std::unique_ptr<mg_handle> h(new mg_handle());
+  h->p = *p;
+  WMG_TRY(make_geom(h->g, p->dims, p->kappa, p->hop_weight, p->bc_phase, true));
+  WMG_TRY(make_blocking(h->B, p->dims, p->block));
+  h->k = p->k;
+  h->nf = (size_t)h->g.V * 12;
+  h->nc = (size_t)h->B.d * 2 * h->k;
+  size_t lb = (size_t)4 * h->g.V * 9;
+  WMG_CUDA(cudaMalloc(&h->links64, lb * sizeof(zd)));
+  WMG_CUDA(cudaMalloc(&h->links32, lb * sizeof(zf)));
+  Staged sl;
+  WMG_TRY(stage_in(sl, links, lb * sizeof(zd), st));
+  WMG_CUDA(cudaMemcpyAsync(h->links64, sl.dev, lb * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+  WMG_TRY((convert<float, double>(h->links32, h->links64, nullptr, 0, lb, 1, st)));
+  size_t ntile = (size_t)h->B.d * 2;
+  WMG_CUDA(cudaMalloc(&h->P64, ntile * h->k * h->B.M * sizeof(zd)));
+  WMG_CUDA(cudaMalloc(&h->P32, ntile * h->k * h->B.M * sizeof(zf)));
+  WMG_CUDA(cudaMalloc(&h->sigma, ntile * h->k * sizeof(double)));
+  WMG_CUDA(cudaMemsetAsync(h->sigma, 0, ntile * h->k * sizeof(double), st));
+  int ns = p->n_s > 0 ? p->n_s : 1;
+  WMG_CUDA(cudaMalloc(&h->hist, (size_t)ns * ntile * h->k * sizeof(double)));
+  WMG_CUDA(cudaMemsetAsync(h->hist, 0, (size_t)ns * ntile * h->k * sizeof(double), st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  *out = h.release();
+  return MG_OK;
+}
+
+// b = -D phi ; psi = phi + GMRES_sweeps(D, b)   (Eq. 2) for r fields, in precision R
+template <typename R>
+int smooth_stream(mg_handle* h, cplx<R>* psi, cplx<R>* phi, cplx<R>* tmp, Gmres<R>& gm, int s,
+                  cudaStream_t st) {
+  const mg_params& p = h->p;
+  int r = p.r;
+  WMG_TRY(gaussian_fill<R>(phi, p.seed, (unsigned)(s * r), r, h->g.V, st));
+  int dt = sizeof(R) == 8 ? MG_C128 : MG_C64;
+  const void* L = sizeof(R) == 8 ? (const void*)h->links64 : (const void*)h->links32;
+  Op<R> D = [h, dt, L, r](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
+    return dslash_launch(dt, out, in, L, h->g, -1, 0, r, s2, h->nf, h->nf);
+  };
+  WMG_TRY(D(tmp, phi, st));
+  WMG_TRY(axpby<R>(tmp, 0.0, tmp, -1.0, h->nf * r, 1, st));   // tmp = -D phi
+  WMG_TRY(gm.alloc(h->nf, r, p.sweeps > 0 ? p.sweeps : 1, false));
+  WMG_TRY(gm.fixed(D, psi, tmp, p.sweeps, st));
+  WMG_TRY(axpby<R>(psi, 1.0, phi, 1.0, h->nf * r, 1, st));     // psi = phi + psi'
+  return MG_OK;
+}
+
+template <typename R>
+int run_setup(mg_handle* h, cudaStream_t st) {
+  const mg_params& p = h->p;
+  int r = p.r, k = h->k;
+  int cmax = k + r;
+  size_t ntile = (size_t)h->B.d * 2;
+  size_t M = h->B.M;
+  size_t fr = h->nf * r;
+  cplx<R>*phi = nullptr, *psi = nullptr, *tmp = nullptr;
+  zd *T0 = nullptr, *T1 = nullptr, *G = nullptr, *Vec = nullptr;
+  double* lam = nullptr;
+  Gmres<R> gm;
+  int status = MG_OK;
+  auto cleanup = [&]() {
+    dfree(phi); dfree(psi); dfree(tmp); dfree(T0); dfree(T1); dfree(G); dfree(Vec); dfree(lam);
+  };
+#define STEP(x) do { status = (x); if (status != MG_OK) { cleanup(); return status; } } while (0)
+#define CSTEP(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { cleanup(); return fail(e_ == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); } } while (0)
+  CSTEP(cudaMalloc(&phi, fr * sizeof(cplx<R>)));
+  CSTEP(cudaMalloc(&psi, fr * sizeof(cplx<R>)));
+  CSTEP(cudaMalloc(&tmp, fr * sizeof(cplx<R>)));
+  CSTEP(cudaMalloc(&T0, ntile * cmax * M * sizeof(zd)));
+  CSTEP(cudaMalloc(&T1, ntile * cmax * M * sizeof(zd)));
+  CSTEP(cudaMalloc(&G, ntile * cmax * cmax * sizeof(zd)));
+  CSTEP(cudaMalloc(&Vec, ntile * cmax * cmax * sizeof(zd)));
+  CSTEP(cudaMalloc(&lam, ntile * cmax * sizeof(double)));
+  zd* cur = T0;
+  zd* oth = T1;
+  int kk = 0;
+  for (int s = 0; s < p.n_s; ++s) {
+    STEP(smooth_stream<R>(h, psi, phi, tmp, gm, s, st));
+    STEP(chiral_gather<R>(cur, cmax, kk, psi, r, h->B, st));
+    int c = kk + r;
+    int kn = c < k ? c : k;
+    bool last = s == p.n_s - 1;
+    STEP(tile_gram(G, cur, cmax, c, h->B, st));
+    STEP(tile_eig(lam, Vec, G, c, (int)ntile, st));
+    if (p.svd_refine) {
+      // B = A V (all c columns), then a second Gram/eig pass on B
+      STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, c, 0, h->B, st));
+      STEP(tile_gram(G, oth, cmax, c, h->B, st));
+      STEP(tile_eig(lam, Vec, G, c, (int)ntile, st));
+      STEP(tile_update(cur, cmax, oth, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st));
+    } else {
+      STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st));
+      zd* t = cur; cur = oth; oth = t;
+    }
+    STEP(tile_sigma(h->hist + (size_t)s * ntile * k, k, lam, c, kn, (int)ntile, st));
+    kk = kn;
+  }
+  STEP(tile_canonical_phase(cur, cmax, k, h->B, st));
+  CSTEP(cudaMemcpy2DAsync(h->P64, (size_t)k * M * sizeof(zd), cur, (size_t)cmax * M * sizeof(zd),
+                          (size_t)k * M * sizeof(zd), ntile, cudaMemcpyDeviceToDevice, st));
+  STEP((convert<float, double>(h->P32, h->P64, nullptr, 0, ntile * k * M, 1, st)));
+  CSTEP(cudaMemcpyAsync(h->sigma, h->hist + (size_t)(p.n_s - 1) * ntile * k,
+                        ntile * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CSTEP(cudaStreamSynchronize(st));
+  cleanup();
+  h->have_P = true;
+  h->have_coarse = false;
+#undef STEP
+#undef CSTEP
+  return MG_OK;
+}
+
+int ensure_solver(mg_handle* h, int nrhs) {
+  if (h->nrhs == nrhs) return MG_OK;
+  h->free_solver();
+  size_t f = h->nf * nrhs, c = h->nc * nrhs;
+  const mg_params& p = h->p;
+  WMG_CUDA(cudaMalloc(&h->x64, f * sizeof(zd)));
+  WMG_CUDA(cudaMalloc(&h->r64, f * sizeof(zd)));
+  WMG_CUDA(cudaMalloc(&h->t64, f * sizeof(zd)));
+  WMG_CUDA(cudaMalloc(&h->dscal, 8 * nrhs * sizeof(double)));
+  WMG_CUDA(cudaMallocHost(&h->hscal, 8 * nrhs * sizeof(double)));
+  WMG_TRY(h->rw.alloc(h->nf, nrhs, 2));
+  if (p.solve_dtype == MG_C128) {
+    WMG_CUDA(cudaMalloc(&h->vc64, c * sizeof(zd)));
+    WMG_CUDA(cudaMalloc(&h->ec64, c * sizeof(zd)));
+    WMG_CUDA(cudaMalloc(&h->kw64, f * sizeof(zd)));
+    WMG_CUDA(cudaMalloc(&h->ke64, f * sizeof(zd)));
+    WMG_TRY(h->outer64.alloc(h->nf, nrhs, p.outer_restart, true));
+    WMG_TRY(h->coarse64.alloc(h->nc, nrhs, p.coarse_restart, false));
+    WMG_TRY(h->post64.alloc(h->nf, nrhs, p.post_smooth > 0 ? p.post_smooth : 1, false));
+  } else {
+    WMG_CUDA(cudaMalloc(&h->e32, f * sizeof(zf)));
+    WMG_CUDA(cudaMalloc(&h->r32, f * sizeof(zf)));
+    WMG_CUDA(cudaMalloc(&h->vc32, c * sizeof(zf)));
+    WMG_CUDA(cudaMalloc(&h->ec32, c * sizeof(zf)));
+    WMG_CUDA(cudaMalloc(&h->kw32, f * sizeof(zf)));
+    WMG_CUDA(cudaMalloc(&h->ke32, f * sizeof(zf)));
+    WMG_TRY(h->outer32.alloc(h->nf, nrhs, p.outer_restart, true));
+    WMG_TRY(h->coarse32.alloc(h->nc, nrhs, p.coarse_restart, false));
+    WMG_TRY(h->post32.alloc(h->nf, nrhs, p.post_smooth > 0 ? p.post_smooth : 1, false));
+  }
+  h->nrhs = nrhs;
+  return MG_OK;
+}
+
+// Typed views of the handle's precision-dependent members.
+template <typename R> struct Lvl;
+template <> struct Lvl<double> {
+  static const void* links(mg_handle* h) { return h->links64; }
+  static const zd* P(mg_handle* h) { return h->P64; }
+  static const zd* Op(mg_handle* h) { return h->Op64; }
+  static Gmres<double>& coarse(mg_handle* h) { return h->coarse64; }
+  static Gmres<double>& post(mg_handle* h) { return h->post64; }
+  static Gmres<double>& outer(mg_handle* h) { return h->outer64; }
+  static zd* vc(mg_handle* h) { return h->vc64; }
+  static zd* ec(mg_handle* h) { return h->ec64; }
+  static zd* kw(mg_handle* h) { return h->kw64; }
+  static zd* ke(mg_handle* h) { return h->ke64; }
+  static constexpr int dtype = MG_C128;
+};
+template <> struct Lvl<float> {
+  static const void* links(mg_handle* h) { return h->links32; }
+  static const zf* P(mg_handle* h) { return h->P32; }
+  static const zf* Op(mg_handle* h) { return h->Op32; }
+  static Gmres<float>& coarse(mg_handle* h) { return h->coarse32; }
+  static Gmres<float>& post(mg_handle* h) { return h->post32; }
+  static Gmres<float>& outer(mg_handle* h) { return h->outer32; }
+  static zf* vc(mg_handle* h) { return h->vc32; }
+  static zf* ec(mg_handle* h) { return h->ec32; }
+  static zf* kw(mg_handle* h) { return h->kw32; }
+  static zf* ke(mg_handle* h) { return h->ke32; }
+  static constexpr int dtype = MG_C64;
+};
+
+template <typename R>
+Op<R> fine_op(mg_handle* h, int nrhs) {
+  return [h, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t st) -> int {
+    return dslash_launch(Lvl<R>::dtype, out, in, Lvl<R>::links(h), h->g, -1, 0, nrhs, st, h->nf, h->nf);
+  };
+}
+
+template <typename R>
+Op<R> coarse_op(mg_handle* h, int nrhs) {
+  return [h, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t st) -> int {
+    return coarse_apply_launch<R>(out, in, Lvl<R>::Op(h), h->k, h->B, nrhs, st);
+  };
+}
+
+// z = M v: restrict, coarse GMRES to coarse_tol, prolong, post-smooth (Sec. 2.1 K-cycle, Sec. 4)
+template <typename R>
+Op<R> kcycle_op(mg_handle* h, int nrhs) {
+  return [h, nrhs](cplx<R>* z, const cplx<R>* v, cudaStream_t st) -> int {
+    const mg_params& p = h->p;
+    cplx<R>* vc = Lvl<R>::vc(h);
+    cplx<R>* ec = Lvl<R>::ec(h);
+    cplx<R>* kw = Lvl<R>::kw(h);
+    cplx<R>* ke = Lvl<R>::ke(h);
+    WMG_TRY(restrict_launch<R>(vc, v, Lvl<R>::P(h), h->k, h->B, nrhs, st));
+    Op<R> Dc = coarse_op<R>(h, nrhs);
+    int its = 0;
+    int s = Lvl<R>::coarse(h).solve(Dc, nullptr, ec, vc, p.coarse_tol, p.coarse_restart,
+                                    p.coarse_maxiter, &its, st);
+    if (s != MG_OK && s != MG_ENOCONV) return s;
+    h->coarse_its += its;
+    h->kcycles += 1;
+    WMG_TRY(prolong_launch<R>(z, ec, Lvl<R>::P(h), h->k, h->B, nrhs, st));
+    if (p.post_smooth > 0) {
+      Op<R> D = fine_op<R>(h, nrhs);
+      WMG_TRY(D(kw, z, st));
+      WMG_TRY(axpby<R>(kw, 1.0, v, -1.0, h->nf * nrhs, 1, st));   // kw = v - D z
+      WMG_TRY(Lvl<R>::post(h).fixed(D, ke, kw, p.post_smooth, st));
+      WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, h->nf * nrhs, 1, st));    // z += e
+    }
+    return MG_OK;
+  };
+}
+
+int host_norms(mg_handle* h, const zd* v, int nrhs, double* out, cudaStream_t st) {
+  WMG_TRY(norm2<double>(h->dscal, 1, v, h->nf, nrhs, h->rw, st));
+  WMG_CUDA(cudaMemcpyAsync(h->hscal, h->dscal, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  for (int r = 0; r < nrhs; ++r) out[r] = h->hscal[r];
+  return MG_OK;
+}
+
+int solve_impl(mg_handle* h, zd* x, const zd* b, int nrhs, double tol, int maxiter,
+               mg_solve_info* info, cudaStream_t st) {
+  const mg_params& p = h->p;
+  WMG_TRY(ensure_solver(h, nrhs));
+  h->coarse_its = 0;
+  h->kcycles = 0;
+  std::vector<double> bn(nrhs), rn(nrhs);
+  WMG_TRY(host_norms(h, b, nrhs, bn.data(), st));
+  int outer = 0, refinements = 0;
+  int status = MG_OK;
+  Op<double> D64 = fine_op<double>(h, nrhs);
+  if (p.solve_dtype == MG_C128) {
+    Op<double> M = kcycle_op<double>(h, nrhs);
+    int its = 0;
+    status = h->outer64.solve(D64, &M, x, b, tol, p.outer_restart, maxiter, &its, st);
+    outer = its;
+    refinements = 1;
+    if (status != MG_OK && status != MG_ENOCONV) return status;
+  } else {
+    // FP64 iterative refinement around the FP32 inner K-cycle FGMRES
+    Op<float> D32 = fine_op<float>(h, nrhs);
+    Op<float> M = kcycle_op<float>(h, nrhs);
+    WMG_TRY(fill_zero<double>(x, h->nf * nrhs, st));
+    WMG_CUDA(cudaMemcpyAsync(h->r64, b, h->nf * nrhs * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+    double inner = p.inner_tol > 0 ? p.inner_tol : 1e-5;
+    status = MG_ENOCONV;
+    while (outer < maxiter && refinements < 100) {
+      WMG_TRY(norm2<double>(h->dscal, 1, h->r64, h->nf, nrhs, h->rw, st));
+      WMG_CUDA(cudaMemcpyAsync(h->hscal, h->dscal, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+      WMG_CUDA(cudaStreamSynchronize(st));
+      bool done = true;
+      double worst = 0;
+      for (int r = 0; r < nrhs; ++r) {
+        rn[r] = h->hscal[r];
+        if (!std::isfinite(rn[r])) return fail(MG_ENAN, "mg_solve: non-finite residual");
+        done &= rn[r] <= tol * bn[r];
+        worst = std::fmax(worst, rn[r] / (bn[r] > 0 ? bn[r] : 1));
+      }
+      if (done) { status = MG_OK; break; }
+      // inner tolerance: reach the target in this step if FP32 allows it
+      double want = inner;
+      if (worst > 0 && tol / worst > want) want = std::fmin(0.5, tol / worst);
+      WMG_TRY((convert<float, double>(h->r32, h->r64, h->dscal, 1, h->nf, nrhs, st)));
+      int its = 0;
+      int s = h->outer32.solve(D32, &M, h->e32, h->r32, want, p.outer_restart, maxiter - outer, &its, st);
+      if (s != MG_OK && s != MG_ENOCONV) return s;
+      outer += its;
+      ++refinements;
+      WMG_TRY(accumulate_scaled<float>(x, h->e32, h->dscal, h->nf, nrhs, st));
+      WMG_TRY(D64(h->t64, x, st));
+      WMG_CUDA(cudaMemcpyAsync(h->r64, b, h->nf * nrhs * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+      WMG_TRY(axpby<double>(h->r64, -1.0, h->t64, 1.0, h->nf * nrhs, 1, st));
+    }
+  }
+  // true residual in FP64
+  WMG_TRY(D64(h->t64, x, st));
+  WMG_CUDA(cudaMemcpyAsync(h->r64, b, h->nf * nrhs * sizeof(zd), cudaMemcpyDeviceToDevice, st));
+  WMG_TRY(axpby<double>(h->r64, -1.0, h->t64, 1.0, h->nf * nrhs, 1, st));
+  WMG_TRY(host_norms(h, h->r64, nrhs, rn.data(), st));
+  double worst = 0;
+  for (int r = 0; r < nrhs; ++r) worst = std::fmax(worst, rn[r] / (bn[r] > 0 ? bn[r] : 1));
+  if (info) {
+    info->outer_iterations = outer;
+    info->refinements = refinements;
+    info->kcycles = h->kcycles;
+    info->coarse_iterations = h->coarse_its;
+    info->true_residual = worst;
+  }
+  if (!(worst <= tol)) return fail(MG_ENOCONV, "mg_solve: tolerance not reached");
+  return MG_OK;
+}
+
+int check_ready(mg_handle* h, bool need_coarse) {
+  if (!h) return fail(MG_EINVAL, "NULL handle");
+  if (!h->have_P) return fail(MG_EINVAL, "handle has no prolongator");
+  if (need_coarse && !h->have_coarse) return fail(MG_EINVAL, "coarse_build has not run");
+  return MG_OK;
+}
+
+}  // namespace
+
+mg_handle::~mg_handle() {
+  free_solver();
+  dfree(links64); dfree(links32); dfree(P64); dfree(P32); dfree(sigma); dfree(hist);
+  dfree(Op64); dfree(Op32);
+}
+
+void mg_handle::free_solver() {
+  outer64.release(); coarse64.release(); post64.release();
+  outer32.release(); coarse32.release(); post32.release();
+  dfree(x64); dfree(r64); dfree(t64); dfree(e32); dfree(r32);
+  dfree(vc64); dfree(ec64); dfree(kw64); dfree(ke64);
+  dfree(vc32); dfree(ec32); dfree(kw32); dfree(ke32);
+  dfree(dscal);
+  if (hscal) cudaFreeHost(hscal);
+  hscal = nullptr;
+  rw.release();
+  nrhs = 0;
+}
+
+// ============================================================================ C ABI
+extern "C" int mg_create(mg_handle** h, const void* links, const mg_params* p, void* stream) {
+  return create_handle(h, links, p, false, (cudaStream_t)stream);
+}
+
+extern "C" int mg_setup_streaming_svd(mg_handle** h, const void* links, const mg_params* p,
+                                      void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  WMG_TRY(create_handle(h, links, p, true, st));
+  int s = p->setup_dtype == MG_C128 ? run_setup<double>(*h, st) : run_setup<float>(*h, st);
+  if (s != MG_OK) {
+    std::string msg = mg_last_error();
+    delete *h;
+    *h = nullptr;
+    return fail(s, msg);
+  }
+  return MG_OK;
+}
+
+extern "C" int coarse_build(mg_handle* h, void* stream) {
+  WMG_TRY(check_ready(h, false));
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t ne = (size_t)4 * h->k * h->k;
+  if (!h->Op64) {
+    WMG_CUDA(cudaMalloc(&h->Op64, (size_t)h->B.d * 9 * ne * sizeof(zd)));
+    WMG_CUDA(cudaMalloc(&h->Op32, (size_t)h->B.d * 9 * ne * sizeof(zf)));
+  }
+  zd* Xpart = nullptr;
+  WMG_CUDA(cudaMallocAsync(&Xpart, (size_t)8 * h->B.d * ne * sizeof(zd), st));
+  int s = galerkin_build(h->Op64, Xpart, h->P64, h->k, h->links64, h->g, h->B, st);
+  cudaFreeAsync(Xpart, st);
+  WMG_TRY(s);
+  WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  h->have_coarse = true;
+  return MG_OK;
+}
+
+static int solve_entry(mg_handle* h, void* x, const void* b, int nrhs, double tol, int maxiter,
+                       mg_solve_info* info, void* stream, bool adjoint) {
+  WMG_TRY(check_ready(h, true));
+  if (!x || !b) return fail(MG_EINVAL, "mg_solve: NULL field");
+  if (nrhs < 1 || nrhs > 64) return fail(MG_EINVAL, "mg_solve: nrhs in [1, 64]");
+  if (!(tol > 0)) return fail(MG_EINVAL, "mg_solve: tol must be > 0");
+  if (maxiter < 1) return fail(MG_EINVAL, "mg_solve: maxiter < 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t fb = h->nf * nrhs * sizeof(zd);
+  Staged sb, sx;
+  WMG_TRY(stage_in(sb, b, fb, st));
+  WMG_TRY(stage_out_alloc(sx, x, fb, st));
+  const zd* bb = (const zd*)sb.dev;
+  zd* gb = nullptr;
+  if (adjoint) {
+    WMG_CUDA(cudaMallocAsync(&gb, fb, st));
+    WMG_TRY(apply_gamma5<double>(gb, bb, (size_t)h->g.V * nrhs, st));
+    bb = gb;
+  }
+  int s = solve_impl(h, (zd*)sx.dev, bb, nrhs, tol, maxiter, info, st);
+  if (adjoint) {
+    if (s == MG_OK || s == MG_ENOCONV) {
+      int s2 = apply_gamma5<double>((zd*)sx.dev, (const zd*)sx.dev, (size_t)h->g.V * nrhs, st);
+      if (s2 != MG_OK) s = s2;
+    }
+    cudaFreeAsync(gb, st);
+  }
+  if (s != MG_OK && s != MG_ENOCONV) return s;
+  std::string msg = s == MG_ENOCONV ? std::string(mg_last_error()) : std::string();
+  WMG_TRY(stage_out_finish(sx, x, fb, st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  if (s == MG_ENOCONV) return fail(s, msg);
+  return MG_OK;
+}
+
+extern "C" int mg_solve(mg_handle* h, void* x, const void* b, int nrhs, double tol, int maxiter,
+                        mg_solve_info* info, void* stream) {
+  return solve_entry(h, x, b, nrhs, tol, maxiter, info, stream, false);
+}
+
+extern "C" int mg_solve_adjoint(mg_handle* h, void* x, const void* b, int nrhs, double tol,
+                                int maxiter, mg_solve_info* info, void* stream) {
+  return solve_entry(h, x, b, nrhs, tol, maxiter, info, stream, true);
+}
+
+extern "C" int mg_destroy(mg_handle* h) {
+  if (!h) return MG_OK;
+  cudaDeviceSynchronize();
+  delete h;
+  return MG_OK;
+}
+
+extern "C" int mg_test_vectors(void* out, const void* links, const mg_params* p, int stream_index,
+                               void* stream) {
+  if (!out) return fail(MG_EINVAL, "mg_test_vectors: NULL output");
+  if (!p || stream_index < 0 || stream_index >= p->n_s)
+    return fail(MG_EINVAL, "mg_test_vectors: stream index out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  mg_handle* h = nullptr;
+  WMG_TRY(create_handle(&h, links, p, true, st));
+  std::unique_ptr<mg_handle> guard(h);
+  size_t fr = h->nf * p->r;
+  Staged so;
+  WMG_TRY(stage_out_alloc(so, out, fr * sizeof(zd), st));
+  if (p->setup_dtype == MG_C128) {
+    zd *phi, *tmp;
+    WMG_CUDA(cudaMallocAsync(&phi, fr * sizeof(zd), st));
+    WMG_CUDA(cudaMallocAsync(&tmp, fr * sizeof(zd), st));
+    Gmres<double> gm;
+    int s = smooth_stream<double>(h, (zd*)so.dev, phi, tmp, gm, stream_index, st);
+    cudaStreamSynchronize(st);
+    cudaFreeAsync(phi, st);
+    cudaFreeAsync(tmp, st);
+    WMG_TRY(s);
+  } else {
+    zf *phi, *tmp, *psi;
+    WMG_CUDA(cudaMallocAsync(&phi, fr * sizeof(zf), st));
+    WMG_CUDA(cudaMallocAsync(&tmp, fr * sizeof(zf), st));
+    WMG_CUDA(cudaMallocAsync(&psi, fr * sizeof(zf), st));
+    Gmres<float> gm;
+    int s = smooth_stream<float>(h, psi, phi, tmp, gm, stream_index, st);
+    if (s == MG_OK) s = convert<double, float>((zd*)so.dev, psi, nullptr, 0, fr, 1, st);
+    cudaStreamSynchronize(st);
+    cudaFreeAsync(phi, st);
+    cudaFreeAsync(tmp, st);
+    cudaFreeAsync(psi, st);
+    WMG_TRY(s);
+  }
+  WMG_TRY(stage_out_finish(so, out, fr * sizeof(zd), st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+extern "C" int mg_get_prolongator(mg_handle* h, void* P, void* sigma, void* stream) {
+  WMG_TRY(check_ready(h, false));
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t pb = (size_t)h->B.d * 2 * h->k * h->B.M * sizeof(zd);
+  if (P) WMG_CUDA(cudaMemcpyAsync(P, h->P64, pb, cudaMemcpyDefault, st));
+  if (sigma)
+    WMG_CUDA(cudaMemcpyAsync(sigma, h->sigma, (size_t)h->B.d * 2 * h->k * sizeof(double),
+                             cudaMemcpyDefault, st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+extern "C" int mg_get_sigma_history(mg_handle* h, void* hist, void* stream) {
+  WMG_TRY(check_ready(h, false));
+  if (!hist) return fail(MG_EINVAL, "NULL output");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t n = (size_t)h->p.n_s * h->B.d * 2 * h->k * sizeof(double);
+  WMG_CUDA(cudaMemcpyAsync(hist, h->hist, n, cudaMemcpyDefault, st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+extern "C" int mg_set_prolongator(mg_handle* h, const void* P, void* stream) {
+  if (!h || !P) return fail(MG_EINVAL, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t ne = (size_t)h->B.d * 2 * h->k * h->B.M;
+  WMG_CUDA(cudaMemcpyAsync(h->P64, P, ne * sizeof(zd), cudaMemcpyDefault, st));
+  WMG_TRY((convert<float, double>(h->P32, h->P64, nullptr, 0, ne, 1, st)));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  h->have_P = true;
+  h->have_coarse = false;
+  return MG_OK;
+}
+
+extern "C" int mg_restrict(mg_handle* h, void* vc, const void* v, int nrhs, void* stream) {
+  WMG_TRY(check_ready(h, false));
+  if (!vc || !v || nrhs < 1) return fail(MG_EINVAL, "mg_restrict: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged si, so;
+  WMG_TRY(stage_in(si, v, h->nf * nrhs * sizeof(zd), st));
+  WMG_TRY(stage_out_alloc(so, vc, h->nc * nrhs * sizeof(zd), st));
+  WMG_TRY(restrict_launch<double>((zd*)so.dev, (const zd*)si.dev, h->P64, h->k, h->B, nrhs, st));
+  WMG_TRY(stage_out_finish(so, vc, h->nc * nrhs * sizeof(zd), st));
+  return MG_OK;
+}
+
+extern "C" int mg_prolong(mg_handle* h, void* v, const void* vc, int nrhs, void* stream) {
+  WMG_TRY(check_ready(h, false));
+  if (!vc || !v || nrhs < 1) return fail(MG_EINVAL, "mg_prolong: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  Staged si, so;
+  WMG_TRY(stage_in(si, vc, h->nc * nrhs * sizeof(zd), st));
+  WMG_TRY(stage_out_alloc(so, v, h->nf * nrhs * sizeof(zd), st));
+  WMG_TRY(prolong_launch<double>((zd*)so.dev, (const zd*)si.dev, h->P64, h->k, h->B, nrhs, st));
+  WMG_TRY(stage_out_finish(so, v, h->nf * nrhs * sizeof(zd), st));
+  return MG_OK;
+}
+
+namespace {
+__global__ void export_coarse_kernel(zd* X, zd* Y, const zd* Op, int n2k, int d) {
+  size_t ne = (size_t)n2k * n2k;
+  size_t total = (size_t)d * 9 * ne;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t j = e / (9 * ne), rem = e % (9 * ne);
+    int blk = (int)(rem / ne);
+    size_t q = rem % ne;
+    int b = (int)(q / n2k), a = (int)(q % n2k);   // Op is column-major
+    zd v = Op[e];
+    if (blk == 0) X[j * ne + (size_t)a * n2k + b] = v;
+    else Y[((size_t)(blk - 1) * d + j) * ne + (size_t)a * n2k + b] = v;
+  }
+}
+}  // namespace
+
+extern "C" int mg_get_coarse_op(mg_handle* h, void* X, void* Y, void* stream) {
+  WMG_TRY(check_ready(h, true));
+  if (!X || !Y) return fail(MG_EINVAL, "NULL output");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t ne = (size_t)4 * h->k * h->k;
+  Staged sx, sy;
+  WMG_TRY(stage_out_alloc(sx, X, (size_t)h->B.d * ne * sizeof(zd), st));
+  WMG_TRY(stage_out_alloc(sy, Y, (size_t)8 * h->B.d * ne * sizeof(zd), st));
+  export_coarse_kernel<<<256, 256, 0, st>>>((zd*)sx.dev, (zd*)sy.dev, h->Op64, 2 * h->k, h->B.d);
+  WMG_LAUNCHED();
+  WMG_TRY(stage_out_finish(sx, X, (size_t)h->B.d * ne * sizeof(zd), st));
+  WMG_TRY(stage_out_finish(sy, Y, (size_t)8 * h->B.d * ne * sizeof(zd), st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+extern "C" int mg_coarse_apply(mg_handle* h, void* y, const void* x, int nrhs, int dtype,
+                               void* stream) {
+  WMG_TRY(check_ready(h, true));
+  if (!x || !y || nrhs < 1) return fail(MG_EINVAL, "mg_coarse_apply: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t n = h->nc * nrhs;
+  if (dtype == MG_C128) {
+    Staged si, so;
+    WMG_TRY(stage_in(si, x, n * sizeof(zd), st));
+    WMG_TRY(stage_out_alloc(so, y, n * sizeof(zd), st));
+    WMG_TRY(coarse_apply_launch<double>((zd*)so.dev, (const zd*)si.dev, h->Op64, h->k, h->B, nrhs, st));
+    WMG_TRY(stage_out_finish(so, y, n * sizeof(zd), st));
+  } else if (dtype == MG_C64) {
+    Staged si, so;
+    WMG_TRY(stage_in(si, x, n * sizeof(zf), st));
+    WMG_TRY(stage_out_alloc(so, y, n * sizeof(zf), st));
+    WMG_TRY(coarse_apply_launch<float>((zf*)so.dev, (const zf*)si.dev, h->Op32, h->k, h->B, nrhs, st));
+    WMG_TRY(stage_out_finish(so, y, n * sizeof(zf), st));
+  } else {
+    return fail(MG_EINVAL, "mg_coarse_apply: dtype must be MG_C128 or MG_C64");
+  }
+  return MG_OK;
+}

@@ -1,0 +1,73 @@
+// Complex-Gaussian random fields from Philox4x32-10 (random initial guesses of Eq. 2).
+//
+// Philox4x32-10 follows its published definition (Salmon, Moraes, Dror, Shaw, SC'11):
+// 10 rounds of two 32x32->64-bit multiplies of counter words 0 and 2 by fixed odd
+// constants, hi/lo halves permuted and xored with the key, key bumped by the Weyl
+// constants between rounds.  Counter (site, component, vector id, 0), key (seed low,
+// seed high); the four words make two 53-bit uniforms and Box-Muller gives
+// Re = sqrt(-2 ln(1 - u_a)) cos(2 pi u_b), Im = sqrt(-2 ln(1 - u_a)) sin(2 pi u_b).
+#include "common.cuh"
+#include "internal.h"
+
+namespace wmg {
+
+namespace {
+
+__device__ __forceinline__ void philox_round(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  uint32_t lo0 = M0 * c[0], hi0 = __umulhi(M0, c[0]);
+  uint32_t lo1 = M1 * c[2], hi1 = __umulhi(M1, c[2]);
+  uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+  c[0] = n0;
+  c[1] = lo1;
+  c[2] = n2;
+  c[3] = lo0;
+}
+
+__device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    philox_round(c, k0, k1);
+  }
+}
+
+template <typename R>
+__global__ void gaussian_kernel(cplx<R>* out, uint32_t k0, uint32_t k1, unsigned id0, int V,
+                                size_t total) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t per = (size_t)V * 12;
+    unsigned v = (unsigned)(e / per);
+    size_t rem = e % per;
+    uint32_t c[4] = {(uint32_t)(rem / 12), (uint32_t)(rem % 12), id0 + v, 0u};
+    philox10(c, k0, k1);
+    const double s53 = 1.1102230246251565e-16;  // 2^-53
+    double ua = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6)) * s53;
+    double ub = ((double)(c[2] >> 5) * 67108864.0 + (double)(c[3] >> 6)) * s53;
+    double rho = sqrt(-2.0 * log(1.0 - ua));
+    double sn, cs;
+    sincos(2.0 * 3.141592653589793 * ub, &sn, &cs);
+    out[e] = {(R)(rho * cs), (R)(rho * sn)};
+  }
+}
+
+}  // namespace
+
+template <typename R>
+int gaussian_fill(cplx<R>* out, unsigned long long seed, unsigned id0, int nvec, int V,
+                  cudaStream_t st) {
+  size_t total = (size_t)nvec * V * 12;
+  size_t g = (total + 255) / 256;
+  size_t cap = (size_t)num_sms() * 16;
+  gaussian_kernel<R><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(
+      out, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), id0, V, total);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+template int gaussian_fill<float>(zf*, unsigned long long, unsigned, int, int, cudaStream_t);
+template int gaussian_fill<double>(zd*, unsigned long long, unsigned, int, int, cudaStream_t);
+
+}  // namespace wmg

@@ -1,0 +1,135 @@
+// Error reporting, geometry validation and host/device staging of ABI arguments.
+#include <atomic>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace wmg {
+
+static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int make_geom(Geom& g, const int dims[4], double kappa, const double w[4], const int bc[4],
+              bool need_even) {
+  long long V = 1;
+  for (int m = 0; m < 4; ++m) {
+    if (dims[m] < 1) return fail(MG_EINVAL, "lattice extent < 1");
+    if (need_even && (dims[m] & 1)) return fail(MG_EINVAL, "parity form needs even extents");
+    if (bc[m] != 1 && bc[m] != -1) return fail(MG_EINVAL, "bc_phase must be +1 or -1");
+    g.L[m] = dims[m];
+    g.w[m] = w[m];
+    g.bc[m] = bc[m];
+    V *= dims[m];
+  }
+  if (V > (1LL << 30)) return fail(MG_EINVAL, "lattice volume too large");
+  g.V = (int)V;
+  g.kappa = kappa;
+  return MG_OK;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 148;
+  }
+  return n;
+}
+
+int is_device_pointer(const void* p, bool* dev) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *dev = false;
+    return MG_OK;
+  }
+  *dev = (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+  return MG_OK;
+}
+
+Staged::~Staged() {
+  if (owned && dev) cudaFreeAsync(dev, stream);
+}
+
+int stage_in(Staged& s, const void* p, size_t bytes, cudaStream_t st) {
+  bool dev = false;
+  WMG_TRY(is_device_pointer(p, &dev));
+  s.stream = st;
+  if (dev) {
+    s.dev = const_cast<void*>(p);
+    s.owned = false;
+    return MG_OK;
+  }
+  WMG_CUDA(cudaMallocAsync(&s.dev, bytes, st));
+  s.owned = true;
+  WMG_CUDA(cudaMemcpyAsync(s.dev, p, bytes, cudaMemcpyHostToDevice, st));
+  return MG_OK;
+}
+
+int stage_out_alloc(Staged& s, void* p, size_t bytes, cudaStream_t st) {
+  bool dev = false;
+  WMG_TRY(is_device_pointer(p, &dev));
+  s.stream = st;
+  if (dev) {
+    s.dev = p;
+    s.owned = false;
+    return MG_OK;
+  }
+  WMG_CUDA(cudaMallocAsync(&s.dev, bytes, st));
+  s.owned = true;
+  return MG_OK;
+}
+
+int stage_out_finish(Staged& s, void* p, size_t bytes, cudaStream_t st) {
+  if (!s.owned) return MG_OK;
+  WMG_CUDA(cudaMemcpyAsync(p, s.dev, bytes, cudaMemcpyDeviceToHost, st));
+  // host destination: the caller reads it after return
+  WMG_CUDA(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+}  // namespace wmg
+
+extern "C" const char* mg_last_error(void) { return wmg::g_last_error.c_str(); }
+
+extern "C" long long mg_kernel_launches(void) { return wmg::g_launches.load(); }
+
+extern "C" void mg_params_default(mg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  for (int m = 0; m < 4; ++m) {
+    p->dims[m] = 4;
+    p->block[m] = 2;
+    p->hop_weight[m] = 1.0;
+    p->bc_phase[m] = 1;
+  }
+  p->kappa = 0.12;
+  p->k = 24;
+  p->r = 24;
+  p->n_s = 2;
+  p->sweeps = 5;
+  p->seed = 3000;
+  p->setup_dtype = MG_C64;
+  p->solve_dtype = MG_C64;
+  p->post_smooth = 8;
+  p->coarse_tol = 0.03;
+  p->coarse_restart = 32;
+  p->coarse_maxiter = 2000;
+  p->outer_restart = 16;
+  p->inner_tol = 1e-5;
+  p->svd_refine = 1;
+}

@@ -92,6 +92,31 @@ WORKLOADS = {
 }
 
 
+# 1 / Re(lambda_max) of the hopping matrix on each seeded field, from ARPACK applied to
+# the FP64 oracle's hopping term (oracle/critical_kappa.py).  The 32^3 x 64 field is too
+# large for that run; it reuses the 16^3 x 32 value (same link distribution).
+KAPPA_CRIT = {
+    "c2_16^3x32_near_critical": None,
+    "c3_16^3x64_aniso": None,
+}
+KAPPA_CRIT["c4_32^3x64_12rhs"] = KAPPA_CRIT["c2_16^3x32_near_critical"]
+
+
+def kappa_of(cfg_or_name):
+    """The hopping parameter of a workload (near-critical ones: factor * kappa_crit)."""
+    if isinstance(cfg_or_name, str):
+        name, cfg = cfg_or_name, WORKLOADS[cfg_or_name]
+    else:
+        cfg = cfg_or_name
+        name = next(n for n, c in WORKLOADS.items() if c["link_seed"] == cfg["link_seed"])
+    if cfg.get("kappa") is not None:
+        return cfg["kappa"]
+    kc = KAPPA_CRIT.get(name)
+    if kc is None:
+        raise KeyError("kappa_crit of %s has not been computed" % name)
+    return cfg["kappa_factor"] * kc
+
+
 def make_links(cfg):
     if cfg["links"] == "haar":
         return haar_links(cfg["dims"], cfg["link_seed"])

@@ -1,0 +1,99 @@
+"""GPU test vectors (Eq. 2) and streaming chiral SVD (Algorithm 3) vs the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import icsvd, philox, wilson
+from paper_2505_14399_gb300 import api, synthetic
+from gpu_common import links_for, params_for, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+C1 = synthetic.WORKLOADS["c1_4^4_haar"]
+C5 = synthetic.WORKLOADS["c5_8^4_autograd"]
+
+
+def test_gaussian_fields_match_philox():
+    """sweeps = 0: psi = phi, the raw Philox complex-Gaussian field."""
+    U = links_for(C1)
+    p = params_for(C1, sweeps=0, setup_dtype="c128")
+    for s in range(2):
+        tv = api.test_vectors(to_dev(U), p, s).cpu().numpy()
+        ref = philox.gaussian_vectors(C1["tv_seed"], np.arange(s * C1["r"], (s + 1) * C1["r"]),
+                                      wilson.volume(C1["dims"]))
+        assert np.abs(tv - ref).max() < 1e-14 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("setup_dtype,tol", [("c128", 1e-12), ("c64", 1e-5)])
+def test_test_vectors(setup_dtype, tol):
+    U = links_for(C1)
+    p = params_for(C1, setup_dtype=setup_dtype)
+    tv = api.test_vectors(to_dev(U), p, 1).cpu().numpy()
+    ref = icsvd.test_vectors(U, C1["dims"], C1["kappa"], C1["hop_weight"], C1["bc"], C1["tv_seed"],
+                             C1["r"], 1, C1["sweeps"])
+    for i in range(C1["r"]):
+        assert rel(tv[i], ref[i]) < tol
+
+
+def _compare_icsvd(cfg, tol_sigma, tol_proj, **kw):
+    U = links_for(cfg)
+    p = params_for(cfg, setup_dtype="c128", **kw)
+    h = api.Hierarchy(to_dev(U), p)
+    P, S = h.prolongator()
+    H = h.sigma_history().cpu().numpy()
+    P = P.cpu().numpy()
+    S = S.cpu().numpy()
+    Pt, S_o, hist = icsvd.icsvd(U, cfg["dims"], cfg["kappa"], cfg["hop_weight"], cfg["bc"],
+                                cfg["block"], cfg["k"], cfg["r"], cfg["n_s"], cfg["sweeps"],
+                                cfg["tv_seed"])
+    assert np.abs(S - S_o).max() < tol_sigma * np.abs(S_o).max()
+    for s, hs in enumerate(hist):
+        kk = hs.shape[-1]
+        assert np.abs(H[s][..., :kk] - hs).max() < tol_sigma * np.abs(hs).max()
+    d = P.shape[0]
+    worst_col = 0.0
+    for j in range(d):
+        for a in range(2):
+            Ug = P[j, a].T                 # (rows, k)
+            Uo = Pt[j, a]
+            assert np.abs(Ug.conj().T @ Ug - np.eye(cfg["k"])).max() < 1e-12
+            assert np.abs(Ug @ Ug.conj().T - Uo @ Uo.conj().T).max() < tol_proj
+            q = Ug.sum(axis=0)
+            assert np.all(np.abs(q.imag) < 1e-10 * np.abs(q)) and np.all(q.real > 0)
+            worst_col = max(worst_col, np.abs(Ug - Uo).max())
+    h.close()
+    return worst_col
+
+
+def test_icsvd_c1():
+    worst = _compare_icsvd(C1, 1e-11, 1e-10)
+    assert worst < 1e-8
+
+
+def test_icsvd_c5_without_refinement_pass():
+    worst = _compare_icsvd(C5, 1e-10, 1e-8, svd_refine=0)
+    assert worst < 1e-6
+
+
+def test_icsvd_c5():
+    worst = _compare_icsvd(C5, 1e-11, 1e-10)
+    assert worst < 1e-8
+
+
+def test_single_stream_r_equals_k_is_regular_span():
+    """n_s = 1, r = k spans the block-orthonormalised test vectors (Algorithm 1)."""
+    cfg = dict(C1)
+    p = params_for(cfg, n_s=1, r=4, k=4, setup_dtype="c128")
+    U = links_for(cfg)
+    h = api.Hierarchy(to_dev(U), p)
+    P, _ = h.prolongator()
+    P = P.cpu().numpy()
+    tv = icsvd.test_vectors(U, cfg["dims"], cfg["kappa"], cfg["hop_weight"], cfg["bc"],
+                            cfg["tv_seed"], 4, 0, cfg["sweeps"])
+    T = icsvd.chiral_split(tv, cfg["dims"], cfg["block"])
+    for j in range(P.shape[0]):
+        for a in range(2):
+            Q = np.linalg.qr(T[j, a])[0]
+            Ug = P[j, a].T
+            assert np.abs(Q @ Q.conj().T - Ug @ Ug.conj().T).max() < 1e-10
+    h.close()
