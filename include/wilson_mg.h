@@ -82,20 +82,31 @@ typedef struct mg_params {
   int coarse_maxiter;        /* coarse GMRES iteration cap per K-cycle                   */
   int outer_restart;         /* fine FGMRES restart length                               */
   double inner_tol;          /* inner relative tolerance of mixed-precision refinement   */
-  int svd_refine;            /* 1: second Gram pass per SVD update (more accurate)       */
+  int svd_refine;            /* 1: second Gram pass per SVD update (accuracy of the Gram
+                                route restored to that of a direct SVD); 0: one pass;
+                                -1: second pass only when setup_dtype is MG_C128 (FP32
+                                test vectors carry 1e-7 of their own error)              */
+  int coarse_persistent;     /* 1: coarse GMRES as one persistent cooperative kernel
+                                (bounded grid barriers); 0: one launch per operation     */
+  int fp64_emulation;        /* sums of products of the SVD Gram/update and the Galerkin
+                                contraction: 1 double-float on FP32 units (~2^-48
+                                relative), 0 native FP64; -1 double-float only in the
+                                mixed form (setup / solve dtype MG_C64)                  */
 } mg_params;
 
 typedef struct mg_solve_info {
   int outer_iterations;      /* fine-level FGMRES iterations over all refinement steps   */
   int refinements;           /* FP64 refinement steps (1 for the plain FP64 solve)       */
   int kcycles;               /* preconditioner applications                              */
-  long long coarse_iterations;  /* coarse GMRES iterations over all K-cycles            */
+  long long coarse_iterations;  /* coarse GMRES iterations, summed over K-cycles and RHS */
   double true_residual;      /* ||b - D x|| / ||b|| in FP64, per the last RHS checked    */
 } mg_solve_info;
 
 /* Defaults: k = 24, r = 24, n_s = 2, sweeps = 5, post_smooth = 8, coarse_tol = 0.03,
  * coarse_restart = 32, coarse_maxiter = 2000, outer_restart = 16, inner_tol = 1e-5,
- * setup_dtype = MG_C64, solve_dtype = MG_C64, svd_refine = 1, isotropic periodic. */
+ * setup_dtype = MG_C64, solve_dtype = MG_C64, svd_refine = -1, coarse_persistent = 1,
+ * fp64_emulation = -1,
+ * isotropic periodic. */
 void mg_params_default(mg_params* p);
 
 /* Thread-local message describing the most recent non-MG_OK return. */
@@ -103,6 +114,16 @@ const char* mg_last_error(void);
 
 /* Number of kernels this library has launched since load (diagnostic counter). */
 long long mg_kernel_launches(void);
+
+/* JSON list of the launch shapes the autotuner has chosen so far (library-owned string,
+ * valid until the next call). */
+const char* mg_autotune_report(void);
+
+/* Failure-path self-test: runs the grid barrier used by the persistent coarse solver with
+ * an arrival count that is never reached, so its bounded wait expires (a few ms).  Returns
+ * MG_ETIMEOUT when the timeout is reported to the host as designed; the CUDA context stays
+ * usable.  No fault, trap or unbounded wait is involved. */
+int mg_selftest_barrier_timeout(void* stream);
 
 /* ---------------------------------------------------------------------------------
  * wilson_dslash -- the Wilson-Dirac stencil (the operator of Eq. 1).

@@ -37,6 +37,8 @@ class MgParams(C.Structure):
         ("outer_restart", C.c_int),
         ("inner_tol", C.c_double),
         ("svd_refine", C.c_int),
+        ("coarse_persistent", C.c_int),
+        ("fp64_emulation", C.c_int),
     ]
 
 
@@ -58,6 +60,8 @@ SIGNATURES = {
     "mg_params_default": (None, [C.POINTER(MgParams)]),
     "mg_last_error": (C.c_char_p, []),
     "mg_kernel_launches": (C.c_longlong, []),
+    "mg_autotune_report": (C.c_char_p, []),
+    "mg_selftest_barrier_timeout": (I, [P]),
     "wilson_dslash": (I, [P, P, P, C.POINTER(C.c_int), D, C.POINTER(C.c_double),
                           C.POINTER(C.c_int), I, I, I, I, P]),
     "mg_setup_streaming_svd": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),

@@ -33,7 +33,7 @@ def _ptr(t):
 def params(dims, block, kappa, k, r, n_s, sweeps=5, seed=3000, hop_weight=(1, 1, 1, 1),
            bc=(1, 1, 1, 1), setup_dtype="c64", solve_dtype="c64", post_smooth=8,
            coarse_tol=0.03, coarse_restart=32, coarse_maxiter=2000, outer_restart=16,
-           inner_tol=1e-5, svd_refine=1):
+           inner_tol=1e-5, svd_refine=-1, coarse_persistent=1, fp64_emulation=-1):
     """Build an mg_params structure (paper symbols k, r, n_s; aggregates of extent `block`)."""
     p = L.MgParams()
     L.lib().mg_params_default(C.byref(p))
@@ -54,6 +54,8 @@ def params(dims, block, kappa, k, r, n_s, sweeps=5, seed=3000, hop_weight=(1, 1,
     p.outer_restart = int(outer_restart)
     p.inner_tol = float(inner_tol)
     p.svd_refine = int(svd_refine)
+    p.coarse_persistent = int(coarse_persistent)
+    p.fp64_emulation = int(fp64_emulation)
     return p
 
 

@@ -19,6 +19,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // CTA sum of (a, b); result valid in thread 0.
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
   a = warp_sum(a);
@@ -60,28 +67,53 @@ __global__ void __launch_bounds__(RT)
 multi_dot_kernel(zd* out, int ldo, const cplx<R>* __restrict__ V, size_t vstride, int nv,
                  const cplx<R>* __restrict__ w, size_t n, double* partial, unsigned* counter,
                  int nblk, int maxvec) {
-  __shared__ double sh[64];
+  __shared__ double sh[(RT / 32) * 8 * 2];
   __shared__ bool last;
   int rhs = blockIdx.y;
   size_t chunk = (n + nblk - 1) / nblk;
   size_t k0 = (size_t)blockIdx.x * chunk;
   size_t k1 = min(n, k0 + chunk);
   const cplx<R>* wr = w + (size_t)rhs * n;
-  for (int i = 0; i < nv; ++i) {
-    const cplx<R>* vr = V + (size_t)i * vstride + (size_t)rhs * n;
-    R ar = 0, ai = 0;
+  // groups of G basis vectors share one pass over w (G independent loads per element)
+  constexpr int G = 8;
+  for (int i0 = 0; i0 < nv; i0 += G) {
+    int ni = min(G, nv - i0);
+    R ar[G], ai[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) { ar[q] = 0; ai[q] = 0; }
+    const cplx<R>* vb = V + (size_t)i0 * vstride + (size_t)rhs * n;
     for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
-      cplx<R> a = vr[k], b = wr[k];
-      ar = fma(a.re, b.re, ar); ar = fma(a.im, b.im, ar);
-      ai = fma(a.re, b.im, ai); ai = fma(-a.im, b.re, ai);
+      cplx<R> b = wr[k];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        if (q < ni) {
+          cplx<R> a = vb[(size_t)q * vstride + k];
+          ar[q] = fma(a.re, b.re, ar[q]); ar[q] = fma(a.im, b.im, ar[q]);
+          ai[q] = fma(a.re, b.im, ai[q]); ai[q] = fma(-a.im, b.re, ai[q]);
+        }
+      }
     }
-    double dr = ar, di = ai;
-    block_sum2(dr, di, sh);
-    if (threadIdx.x == 0) {
-      double* p = partial + (((size_t)rhs * maxvec + i) * nblk + blockIdx.x) * 2;
-      p[0] = dr;
-      p[1] = di;
+    // CTA reduction of the ni pairs in the vectors' own precision (FP64 arithmetic is
+    // scarce on this GPU): warp shuffles, then one shared-memory pass; only the CTA
+    // partial is widened to FP64 for the cross-CTA sum.
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    R* shg = reinterpret_cast<R*>(sh);  // [RT/32][G][2]
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      if (q < ni) {
+        R dr = warp_sum_r(ar[q]);
+        R di = warp_sum_r(ai[q]);
+        if (lane == 0) { shg[(wid * G + q) * 2] = dr; shg[(wid * G + q) * 2 + 1] = di; }
+      }
     }
+    __syncthreads();
+    if (threadIdx.x < 2 * ni) {
+      int q = threadIdx.x >> 1, part = threadIdx.x & 1;
+      R s = 0;
+      for (int wv = 0; wv < RT / 32; ++wv) s += shg[(wv * G + q) * 2 + part];
+      partial[(((size_t)rhs * maxvec + i0 + q) * nblk + blockIdx.x) * 2 + part] = (double)s;
+    }
+    __syncthreads();
   }
   __threadfence();
   if (threadIdx.x == 0) last = (atomicAdd(counter + rhs, 1u) == (unsigned)nblk - 1);
@@ -109,11 +141,16 @@ norm_kernel(double* nrm, int ldn, const cplx<R>* __restrict__ w, size_t n, doubl
     acc = fma(a.re, a.re, acc);
     acc = fma(a.im, a.im, acc);
   }
-  double d = acc, z = 0;
-  block_sum2(d, z, sh);
+  // CTA tree in the vectors' precision, FP64 only across CTAs
+  acc = warp_sum_r(acc);
+  R* shr = reinterpret_cast<R*>(sh);
+  if ((threadIdx.x & 31) == 0) shr[threadIdx.x >> 5] = acc;
+  __syncthreads();
   if (threadIdx.x == 0) {
+    R s = 0;
+    for (int wv = 0; wv < RT / 32; ++wv) s += shr[wv];
     double* p = partial + ((size_t)rhs * maxvec * nblk + blockIdx.x) * 2;
-    p[0] = d;
+    p[0] = (double)s;
     p[1] = 0;
   }
   __threadfence();
@@ -214,7 +251,7 @@ inline int grid_for(size_t n) {
 int ReduceWork::alloc(size_t n, int nrhs, int mv) {
   release();
   size_t nb = (n + 4 * RT - 1) / (4 * RT);
-  size_t cap = (size_t)num_sms() * 2;
+  size_t cap = (size_t)num_sms() * 6;
   nblk = (int)(nb < 1 ? 1 : (nb > cap ? cap : nb));
   maxvec = mv;
   nrhs_cap = nrhs;

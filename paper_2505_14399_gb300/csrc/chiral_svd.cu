@@ -11,8 +11,10 @@
 // An optional second pass (G of A V over all c columns, eig, rotate) restores the
 // accuracy lost by forming A^dag A (its rotations are relative to sigma_i sigma_j).
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "internal.h"
 
 namespace wmg {
@@ -44,19 +46,24 @@ constexpr int GT = 256;   // threads per tile CTA
 constexpr int GR = 32;    // rows staged per chunk
 constexpr int MAXC = 64;  // max columns per tile
 
-// G = A^dag A, upper triangle computed, mirrored.
+// G = A^dag A, upper triangle computed, mirrored.  DF: df64 arithmetic (FP32 units,
+// error-free transformations) instead of FP64.
+template <bool DF>
 __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ tiles, int cmax,
                                                   int c, int M) {
-  extern __shared__ zd sA[];  // [GR][c]
+  typedef typename std::conditional<DF, zdf, zd>::type T;
+  typedef typename std::conditional<DF, zdfacc, zd>::type TA;
+  extern __shared__ zd smraw_g[];
+  T* sA = reinterpret_cast<T*>(smraw_g);  // [GR][c]
   int t = blockIdx.x;
   const zd* A = tiles + (size_t)t * cmax * M;
   int npairs = c * (c + 1) / 2;
   constexpr int MAXP = (MAXC * (MAXC + 1) / 2 + GT - 1) / GT;
-  zd acc[MAXP];
+  TA acc[MAXP];
   int pi[MAXP], pj[MAXP];
 #pragma unroll
   for (int q = 0; q < MAXP; ++q) {
-    acc[q] = {0, 0};
+    acc[q] = TA{};
     int p = threadIdx.x + q * GT;
     // p -> (i, j) with i <= j, row-major over the upper triangle
     int i = 0, rem = p;
@@ -69,15 +76,20 @@ __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ 
     __syncthreads();
     for (int e = threadIdx.x; e < nr * c; e += GT) {
       int col = e / nr, rr = e % nr;
-      sA[rr * c + col] = A[(size_t)col * M + r0 + rr];
+      zd v = A[(size_t)col * M + r0 + rr];
+      if constexpr (DF) sA[rr * c + col] = zdf_from(v);
+      else sA[rr * c + col] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < MAXP; ++q) {
       int p = threadIdx.x + q * GT;
       if (p < npairs) {
-        zd a = acc[q];
-        for (int rr = 0; rr < nr; ++rr) cfmac(a, sA[rr * c + pi[q]], sA[rr * c + pj[q]]);
+        TA a = acc[q];
+        for (int rr = 0; rr < nr; ++rr) {
+          if constexpr (DF) zdf_fmac(a, sA[rr * c + pi[q]], sA[rr * c + pj[q]]);
+          else cfmac(a, sA[rr * c + pi[q]], sA[rr * c + pj[q]]);
+        }
         acc[q] = a;
       }
     }
@@ -87,8 +99,11 @@ __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ 
   for (int q = 0; q < MAXP; ++q) {
     int p = threadIdx.x + q * GT;
     if (p < npairs) {
-      Gt[pi[q] * c + pj[q]] = acc[q];
-      if (pi[q] != pj[q]) Gt[pj[q] * c + pi[q]] = conj(acc[q]);
+      zd v;
+      if constexpr (DF) v = zdf_result(acc[q]);
+      else v = acc[q];
+      Gt[pi[q] * c + pj[q]] = v;
+      if (pi[q] != pj[q]) Gt[pj[q] * c + pi[q]] = conj(v);
     }
   }
 }
@@ -227,11 +242,15 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
 
 constexpr int UK = 64;  // max output columns per update
 
+template <bool DF>
 __global__ void __launch_bounds__(GT) update_kernel(zd* out, int cmax_out, const zd* __restrict__ tiles,
                                                     int cmax, int c, const zd* __restrict__ Vec,
                                                     const double* lam, int kout, int scale_inv,
                                                     int M) {
-  extern __shared__ zd sV[];  // [c][kout]
+  typedef typename std::conditional<DF, zdf, zd>::type T;
+  typedef typename std::conditional<DF, zdfacc, zd>::type TA;
+  extern __shared__ zd smraw_u[];
+  T* sV = reinterpret_cast<T*>(smraw_u);  // [c][kout]
   int t = blockIdx.x;
   const zd* Vt = Vec + (size_t)t * c * c;
   for (int e = threadIdx.x; e < c * kout; e += blockDim.x) {
@@ -242,25 +261,37 @@ __global__ void __launch_bounds__(GT) update_kernel(zd* out, int cmax_out, const
       double f = l > 0 ? 1.0 / sqrt(l) : 0.0;
       v = f * v;
     }
-    sV[e] = v;
+    if constexpr (DF) sV[e] = zdf_from(v);
+    else sV[e] = v;
   }
   __syncthreads();
   const zd* A = tiles + (size_t)t * cmax * M;
   zd* O = out + (size_t)t * cmax_out * M;
   for (int r = threadIdx.x; r < M; r += blockDim.x) {
     for (int i0 = 0; i0 < kout; i0 += 16) {
-      zd acc[16];
+      TA acc[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = {0, 0};
+      for (int q = 0; q < 16; ++q) acc[q] = TA{};
       for (int col = 0; col < c; ++col) {
-        zd a = A[(size_t)col * M + r];
+        zd a0 = A[(size_t)col * M + r];
+        if constexpr (DF) {
+          zdf a = zdf_from(a0);
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (i0 + q < kout) cfma(acc[q], a, sV[col * kout + i0 + q]);
+          for (int q = 0; q < 16; ++q)
+            if (i0 + q < kout) zdf_fma(acc[q], a, sV[col * kout + i0 + q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q)
+            if (i0 + q < kout) cfma(acc[q], a0, sV[col * kout + i0 + q]);
+        }
       }
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (i0 + q < kout) O[(size_t)(i0 + q) * M + r] = acc[q];
+      for (int q = 0; q < 16; ++q) {
+        if (i0 + q < kout) {
+          if constexpr (DF) O[(size_t)(i0 + q) * M + r] = zdf_result(acc[q]);
+          else O[(size_t)(i0 + q) * M + r] = acc[q];
+        }
+      }
     }
   }
 }
@@ -338,10 +369,12 @@ int chiral_gather(zd* tiles, int cmax, int col0, const cplx<R>* fields, int nvec
 template int chiral_gather<float>(zd*, int, int, const zf*, int, const Blocking&, cudaStream_t);
 template int chiral_gather<double>(zd*, int, int, const zd*, int, const Blocking&, cudaStream_t);
 
-int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaStream_t st) {
+int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaStream_t st,
+              bool df64) {
   if (c > MAXC) return fail(MG_EINVAL, "tile_gram: more than 64 columns");
   size_t sh = sizeof(zd) * GR * c;
-  gram_kernel<<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+  if (df64) gram_kernel<true><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+  else gram_kernel<false><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
   WMG_LAUNCHED();
   return MG_OK;
 }
@@ -363,16 +396,24 @@ int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st) {
 }
 
 int tile_update(zd* out, int cmax_out, const zd* tiles, int cmax, int c, const zd* Vec,
-                const double* lam, int kout, int scale_inv, const Blocking& B, cudaStream_t st) {
+                const double* lam, int kout, int scale_inv, const Blocking& B, cudaStream_t st,
+                bool df64) {
   if (kout > UK || c > MAXC) return fail(MG_EINVAL, "tile_update: too many columns");
   size_t sh = sizeof(zd) * c * kout;
   static bool attr_set = false;
   if (!attr_set) {
-    WMG_CUDA(cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    WMG_CUDA(cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  100 * 1024));
+    WMG_CUDA(cudaFuncSetAttribute(update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   100 * 1024));
     attr_set = true;
   }
-  update_kernel<<<B.d * 2, GT, sh, st>>>(out, cmax_out, tiles, cmax, c, Vec, lam, kout, scale_inv, B.M);
+  if (df64)
+    update_kernel<true><<<B.d * 2, GT, sh, st>>>(out, cmax_out, tiles, cmax, c, Vec, lam, kout,
+                                                 scale_inv, B.M);
+  else
+    update_kernel<false><<<B.d * 2, GT, sh, st>>>(out, cmax_out, tiles, cmax, c, Vec, lam, kout,
+                                                  scale_inv, B.M);
   WMG_LAUNCHED();
   return MG_OK;
 }

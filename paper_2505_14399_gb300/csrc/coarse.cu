@@ -5,14 +5,20 @@
 // D_c is a coarse nearest-neighbour stencil stored per coarse site as 9 column-major
 // (2k)x(2k) blocks: blk 0 = X (self), blk 1 + dir = Y_dir, dir = 2 mu + (0: +mu, 1: -mu).
 //
-// Galerkin assembly: CTA (j, dir) walks the n_d fine sites x of aggregate j; for each,
-// the hop x -> x +/- mu of D applied to the 2k columns of P at the neighbour is reduced
-// to a 6 x 2k half-spinor block chi (spin projection, colour transport), P(x) is
-// folded with the matching reconstruction into a 6 x 2k block Ptil, and
-// Ptil^dag chi is accumulated in FP64 -- into Y_dir(j) if the hop leaves the
-// aggregate, else into a per-direction partial of X(j).  A second kernel sums the
-// partials and the diagonal term P_j^dag P_j in a fixed order.
+// Galerkin assembly: CTA (j, mu) walks the n_d fine sites x of aggregate j; for each,
+// the forward hop x -> x + mu of D applied to the 2k columns of P at the neighbour is
+// reduced to a 6 x 2k half-spinor block chi (spin projection, colour transport), P(x)
+// is folded with the matching reconstruction into a 6 x 2k block Ptil, and
+// Ptil^dag chi is accumulated in FP64 -- into Y_+mu(j) if the hop leaves the
+// aggregate, else into a per-direction partial of X(j).  Backward hops are not
+// computed: gamma_5 D gamma_5 = D^dag and gamma_5 P = P sigma_3 make each backward
+// contribution sigma_3 C^dag sigma_3 of a forward one C (exactly, up to rounding), which
+// halves the FP64 work.  A second kernel adds the diagonal term P_j^dag P_j and the
+// mirrored blocks in a fixed order.
+#include <type_traits>
+
 #include "common.cuh"
+#include "df64.cuh"
 #include "internal.h"
 
 namespace wmg {
@@ -89,18 +95,21 @@ constexpr int GNB = 8;       // fine sites staged per batch
 constexpr int GTH = 256;     // threads
 constexpr int GMAXE = 16;    // accumulator entries per thread ((2k)^2 <= 4096)
 
+template <bool DF>
 __global__ void __launch_bounds__(GTH)
 galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
                     const zd* __restrict__ links, HopGeom g, Blocking B) {
-  extern __shared__ zd gsm[];
+  typedef typename std::conditional<DF, zdf, zd>::type T;
+  typedef typename std::conditional<DF, zdfacc, zd>::type TA;
+  extern __shared__ zd gsm_raw[];
+  T* gsm = reinterpret_cast<T*>(gsm_raw);
   int n2k = 2 * k;
-  zd* sPt = gsm;                       // [GNB][6][n2k]
-  zd* sCh = gsm + GNB * 6 * n2k;       // [GNB][6][n2k]
+  T* sPt = gsm;                        // [GNB][6][n2k]
+  T* sCh = gsm + GNB * 6 * n2k;        // [GNB][6][n2k]
   __shared__ int ssite[GNB], snb[GNB];
   __shared__ double sph[GNB];
-  int j = blockIdx.x, dir = blockIdx.y;
-  int mu = dir >> 1;
-  bool fwd = (dir & 1) == 0;
+  int j = blockIdx.x, mu = blockIdx.y, dir = 2 * mu;
+  const bool fwd = true;
   // projector sign of this hop in D: forward (1 - gamma), backward (1 + gamma)
   int S = fwd ? -1 : +1;
   double coef = -g.kappa * g.w[mu];
@@ -108,9 +117,9 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
   int bmu = B.b[mu];
   const int* bb = B.b;
   for (int pass = 0; pass < 2; ++pass) {  // 0: hops inside the aggregate, 1: crossing hops
-    zd acc[GMAXE];
+    TA acc[GMAXE];
 #pragma unroll
-    for (int q = 0; q < GMAXE; ++q) acc[q] = {0, 0};
+    for (int q = 0; q < GMAXE; ++q) acc[q] = TA{};
     int l = 0;
     while (true) {
       // collect the next batch of local sites of this pass (same scan in every thread)
@@ -192,7 +201,8 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
 #pragma unroll
           for (int c2 = 0; c2 < 3; ++c2) cfmac(ch, U[c2 * 3 + cc], hv[c2]);
         }
-        sCh[(h * 6 + r) * n2k + bcol] = sph[h] * ch;
+        if constexpr (DF) sCh[(h * 6 + r) * n2k + bcol] = zdf_from(sph[h] * ch);
+        else sCh[(h * 6 + r) * n2k + bcol] = sph[h] * ch;
         // Ptil: column a = bcol of P(x) folded with the reconstruction
         int jx, lx;
         B.block_of(x, &jx, &lx);
@@ -210,7 +220,8 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
             pt = (S > 0) ? ps : -ps;            // L^dag = S
           }
         }
-        sPt[(h * 6 + r) * n2k + bcol] = pt;
+        if constexpr (DF) sPt[(h * 6 + r) * n2k + bcol] = zdf_from(pt);
+        else sPt[(h * 6 + r) * n2k + bcol] = pt;
       }
       __syncthreads();
 #pragma unroll
@@ -218,82 +229,96 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
         int e = threadIdx.x + q * GTH;
         if (e < ne) {
           int a = e / n2k, b = e % n2k;
-          zd t = acc[q];
+          TA t = acc[q];
           for (int h = 0; h < nb; ++h)
 #pragma unroll
             for (int r = 0; r < 6; ++r)
-              cfmac(t, sPt[(h * 6 + r) * n2k + a], sCh[(h * 6 + r) * n2k + b]);
+            {
+              if constexpr (DF) zdf_fmac(t, sPt[(h * 6 + r) * n2k + a], sCh[(h * 6 + r) * n2k + b]);
+              else cfmac(t, sPt[(h * 6 + r) * n2k + a], sCh[(h * 6 + r) * n2k + b]);
+            }
           acc[q] = t;
         }
       }
     }
     zd* out = pass == 1 ? Op + ((size_t)j * 9 + 1 + dir) * ne
-                        : Xpart + ((size_t)dir * B.d + j) * ne;
+                        : Xpart + ((size_t)mu * B.d + j) * ne;
 #pragma unroll
     for (int q = 0; q < GMAXE; ++q) {
       int e = threadIdx.x + q * GTH;
       if (e < ne) {
         int a = e / n2k, b = e % n2k;
-        out[(size_t)b * n2k + a] = acc[q];   // column-major
+        if constexpr (DF) out[(size_t)b * n2k + a] = zdf_result(acc[q]);   // column-major
+        else out[(size_t)b * n2k + a] = acc[q];
       }
     }
     __syncthreads();
   }
 }
 
-// X(j) = P_j^dag P_j (per chirality) + sum_dir Xpart_dir(j)
+// Completes D_c from the forward hops.  gamma_5-hermiticity of D with gamma_5 P = P sigma_3
+// gives, hop by hop, backward contribution = sigma_3 (forward contribution)^dag sigma_3, so
+//   X(j)      = P_j^dag P_j + sum_mu [F_mu(j) + sigma_3 F_mu(j)^dag sigma_3]
+//   Y_-mu(j)  = sigma_3 Y_+mu(j - mu)^dag sigma_3
+// with F_mu(j) the forward hops that stay inside aggregate j.  Element (a, b) of
+// sigma_3 M^dag sigma_3 is s_a s_b conj(M(b, a)), s = +1 / -1 for chirality 0 / 1.
 __global__ void __launch_bounds__(GTH)
-galerkin_diag_kernel(zd* Op, const zd* __restrict__ Xpart, const zd* __restrict__ P, int k,
-                     Blocking B) {
+galerkin_finish_kernel(zd* Op, const zd* __restrict__ Xpart, const zd* __restrict__ P, int k,
+                       Blocking B) {
   int j = blockIdx.x;
   int n2k = 2 * k, ne = n2k * n2k;
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     int b = e / n2k, a = e % n2k;  // column-major element (a, b)
-    zd acc = {0, 0};
+    int et = a * n2k + b;          // element (b, a)
     int aa = a / k, bb = b / k;
+    double sab = (aa == bb) ? 1.0 : -1.0;
+    zd acc = {0, 0};
     if (aa == bb) {
       const zd* Pa = P + ((size_t)(2 * j + aa) * k + a % k) * B.M;
       const zd* Pb = P + ((size_t)(2 * j + bb) * k + b % k) * B.M;
       for (int r = 0; r < B.M; ++r) cfmac(acc, Pa[r], Pb[r]);
     }
-    for (int dir = 0; dir < 8; ++dir) acc += Xpart[((size_t)dir * B.d + j) * ne + e];
+    for (int mu = 0; mu < 4; ++mu) {
+      const zd* F = Xpart + ((size_t)mu * B.d + j) * ne;
+      acc += F[e];
+      acc += sab * conj(F[et]);
+      int jm = B.coarse_nbr(j, 2 * mu + 1);
+      zd yv = Op[((size_t)jm * 9 + 1 + 2 * mu) * ne + et];
+      Op[((size_t)j * 9 + 2 + 2 * mu) * ne + e] = sab * conj(yv);
+    }
     Op[(size_t)j * 9 * ne + e] = acc;
   }
 }
 
-// y(j) = sum_blk Op[j][blk] x(src(blk)); one warp per (coarse site, rhs)
+// y(j) = sum_blk Op[j][blk] x(src(blk)).  One CTA per (coarse site, rhs) with 9 x 2k
+// threads: thread (blk, a) stages x(src(blk))[a] in shared memory, forms row a of
+// block blk times that vector (column-major blocks: coalesced over a), and the nine
+// partial rows are summed in a fixed order.
 template <typename R>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(576)
 coarse_apply_kernel(cplx<R>* y, const cplx<R>* __restrict__ x, const cplx<R>* __restrict__ Op,
-                    int n2k, Blocking B, int nrhs) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= B.d * nrhs) return;
-  int rhs = warp / B.d, j = warp % B.d;
+                    int n2k, Blocking B) {
+  extern __shared__ unsigned char csm[];
+  cplx<R>* sx = reinterpret_cast<cplx<R>*>(csm);     // [9][n2k]
+  cplx<R>* sp = sx + 9 * n2k;                         // [9][n2k] partial rows
+  int j = blockIdx.x, rhs = blockIdx.y;
+  int blk = threadIdx.x / n2k, a = threadIdx.x % n2k;
   size_t nc = (size_t)B.d * n2k;
-  const cplx<R>* xr = x + rhs * nc;
-  constexpr int MAXR = 2;  // rows per lane (2k <= 64)
-  cplx<R> acc[MAXR];
+  const cplx<R>* xr = x + (size_t)rhs * nc;
+  int src = blk == 0 ? j : B.coarse_nbr(j, blk - 1);
+  sx[threadIdx.x] = xr[(size_t)src * n2k + a];
+  __syncthreads();
+  const cplx<R>* O = Op + ((size_t)j * 9 + blk) * n2k * n2k + a;
+  const cplx<R>* xs = sx + blk * n2k;
+  cplx<R> acc = {0, 0};
+  for (int b = 0; b < n2k; ++b) cfma(acc, O[(size_t)b * n2k], xs[b]);
+  sp[threadIdx.x] = acc;
+  __syncthreads();
+  if (blk == 0) {
+    cplx<R> t = sp[a];
 #pragma unroll
-  for (int q = 0; q < MAXR; ++q) acc[q] = {0, 0};
-  size_t ne = (size_t)n2k * n2k;
-  for (int blk = 0; blk < 9; ++blk) {
-    int src = blk == 0 ? j : B.coarse_nbr(j, blk - 1);
-    const cplx<R>* xs = xr + (size_t)src * n2k;
-    const cplx<R>* O = Op + ((size_t)j * 9 + blk) * ne;
-    for (int b = 0; b < n2k; ++b) {
-      cplx<R> xb = xs[b];
-#pragma unroll
-      for (int q = 0; q < MAXR; ++q) {
-        int a = lane + 32 * q;
-        if (a < n2k) cfma(acc[q], O[(size_t)b * n2k + a], xb);
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < MAXR; ++q) {
-    int a = lane + 32 * q;
-    if (a < n2k) y[rhs * nc + (size_t)j * n2k + a] = acc[q];
+    for (int q = 1; q < 9; ++q) t += sp[q * n2k + a];
+    y[(size_t)rhs * nc + (size_t)j * n2k + a] = t;
   }
 }
 
@@ -328,7 +353,7 @@ int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const
 }
 
 int galerkin_build(zd* Op, zd* Xpart, const zd* P, int k, const zd* links, const Geom& g,
-                   const Blocking& B, cudaStream_t st) {
+                   const Blocking& B, cudaStream_t st, bool df64) {
   if (4 * k * k > GTH * GMAXE) return fail(MG_EINVAL, "galerkin: k > 32");
   HopGeom hg;
   for (int m = 0; m < 4; ++m) {
@@ -344,14 +369,17 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, int k, const zd* links, const
   size_t sh = sizeof(zd) * 2 * GNB * 6 * 2 * k;
   static bool set = false;
   if (!set) {
-    WMG_CUDA(cudaFuncSetAttribute(galerkin_hop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
+    WMG_CUDA(cudaFuncSetAttribute(galerkin_hop_kernel<false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    WMG_CUDA(cudaFuncSetAttribute(galerkin_hop_kernel<true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     set = true;
   }
-  dim3 grid(B.d, 8);
-  galerkin_hop_kernel<<<grid, GTH, sh, st>>>(Op, Xpart, P, k, links, hg, B);
+  dim3 grid(B.d, 4);
+  if (df64) galerkin_hop_kernel<true><<<grid, GTH, sh, st>>>(Op, Xpart, P, k, links, hg, B);
+  else galerkin_hop_kernel<false><<<grid, GTH, sh, st>>>(Op, Xpart, P, k, links, hg, B);
   WMG_LAUNCHED();
-  galerkin_diag_kernel<<<B.d, GTH, 0, st>>>(Op, Xpart, P, k, B);
+  galerkin_finish_kernel<<<B.d, GTH, 0, st>>>(Op, Xpart, P, k, B);
   WMG_LAUNCHED();
   return MG_OK;
 }
@@ -360,9 +388,9 @@ template <typename R>
 int coarse_apply_launch(cplx<R>* y, const cplx<R>* x, const cplx<R>* Op, int k, const Blocking& B,
                         int nrhs, cudaStream_t st) {
   if (2 * k > 64) return fail(MG_EINVAL, "coarse_apply: 2k > 64");
-  size_t warps = (size_t)B.d * nrhs;
-  size_t blocks = (warps * 32 + 255) / 256;
-  coarse_apply_kernel<R><<<(unsigned)blocks, 256, 0, st>>>(y, x, Op, 2 * k, B, nrhs);
+  dim3 grid(B.d, nrhs);
+  size_t sh = sizeof(cplx<R>) * 18 * 2 * k;
+  coarse_apply_kernel<R><<<grid, 9 * 2 * k, sh, st>>>(y, x, Op, 2 * k, B);
   WMG_LAUNCHED();
   return MG_OK;
 }

@@ -1,0 +1,78 @@
+// Double-float ("df64") arithmetic: a value is hi + lo with two FP32 numbers.
+//
+// GB300 runs FP32 FMA about 64x faster than FP64, so sums of products that need close
+// to FP64 accuracy are formed with error-free transformations on FP32 units:
+//   TwoProd(a, b):  p = a*b, e = fma(a, b, -p)             (a*b = p + e exactly)
+//   TwoSum(a, b):   s = a+b, bb = s-a, e = (a-(s-bb))+(b-bb) (a+b = s + e exactly)
+// (Dekker 1971; Knuth TAOCP vol. 2, Sec. 4.2.2; Ogita, Rump, Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, 2005 -- the "Dot2" scheme).  A product of df64 numbers
+// keeps hi*hi exactly plus the cross terms hi*lo + lo*hi; an accumulator is an unnormalised
+// pair (s, e) whose e collects the rounding errors, so a K-term dot product carries a
+// relative error of order K * 2^-48 (about 1e-13 for K ~ 10^3) instead of FP64's K * 2^-53.
+#pragma once
+
+#include "common.cuh"
+
+namespace wmg {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_from(double x) {
+  float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ df df_from(float x) { return {x, 0.0f}; }
+__device__ __forceinline__ double df_to_double(float s, float e) { return (double)s + (double)e; }
+
+// accumulator for sums of products
+struct dfacc {
+  float s, e;
+};
+
+// acc += a * b  (a, b df64).  The _rn intrinsics are never contracted into FMAs by the
+// compiler, which the error-free transformations rely on.
+__device__ __forceinline__ void df_fma(dfacc& acc, df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float pe = fmaf(a.hi, b.hi, -p);
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  float s = __fadd_rn(acc.s, p);
+  float bb = __fsub_rn(s, acc.s);
+  float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.s = s;
+  acc.e = __fadd_rn(acc.e, __fadd_rn(err, pe));
+}
+
+// complex df64 value and accumulator
+struct zdf {
+  df re, im;
+};
+struct zdfacc {
+  dfacc re, im;
+};
+
+__device__ __forceinline__ zdf zdf_from(zd x) { return {df_from(x.re), df_from(x.im)}; }
+__device__ __forceinline__ zdf zdf_from(zf x) { return {df_from(x.re), df_from(x.im)}; }
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+// acc += conj(a) * b
+__device__ __forceinline__ void zdf_fmac(zdfacc& acc, zdf a, zdf b) {
+  df_fma(acc.re, a.re, b.re);
+  df_fma(acc.re, a.im, b.im);
+  df_fma(acc.im, a.re, b.im);
+  df_fma(acc.im, df_neg(a.im), b.re);
+}
+// acc += a * b
+__device__ __forceinline__ void zdf_fma(zdfacc& acc, zdf a, zdf b) {
+  df_fma(acc.re, a.re, b.re);
+  df_fma(acc.re, df_neg(a.im), b.im);
+  df_fma(acc.im, a.re, b.im);
+  df_fma(acc.im, a.im, b.re);
+}
+__device__ __forceinline__ zd zdf_result(const zdfacc& acc) {
+  return {df_to_double(acc.re.s, acc.re.e), df_to_double(acc.im.s, acc.im.e)};
+}
+
+}  // namespace wmg

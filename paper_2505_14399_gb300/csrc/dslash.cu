@@ -198,8 +198,8 @@ __device__ __forceinline__ void hop_pair(const KGeom& g, int site, const int c[4
 
 // parity < 0: out = in - kappa H in (full lattice).  parity p >= 0: out_p = -kappa H in_{1-p}
 // on half-lattice (checkerboard-indexed) fields.
-template <typename S, int DAG>
-__global__ void __launch_bounds__(128)
+template <typename S, int DAG, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB)
 dslash_kernel(typename S::elem* __restrict__ out, const typename S::elem* __restrict__ in,
               const typename S::elem* __restrict__ links, KGeom g, int parity, int nsites,
               size_t in_stride, size_t out_stride) {
@@ -270,20 +270,49 @@ KGeom to_kgeom(const Geom& g) {
   return k;
 }
 
+// Launch shapes: threads per CTA and the minimum resident CTAs per SM requested from
+// the register allocator (register cap = 64K / (TPB * MINB)).  The autotuner below
+// picks one per (dtype, parity, dagger, volume, nrhs).
+struct Shape {
+  int tpb, minb;
+};
+constexpr Shape kShapes[] = {{128, 1}, {128, 6}, {128, 8}, {256, 4}, {64, 16}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <typename S, int DAG, int TPB, int MINB>
+void launch_shape(void* out, const void* in, const void* links, const KGeom& k, int parity,
+                  int nsites, int nrhs, cudaStream_t st, size_t in_stride, size_t out_stride) {
+  typedef typename S::elem E;
+  dim3 grid((nsites + TPB - 1) / TPB, nrhs);
+  dslash_kernel<S, DAG, TPB, MINB><<<grid, TPB, 0, st>>>((E*)out, (const E*)in, (const E*)links, k,
+                                                         parity, nsites, in_stride, out_stride);
+}
+
+template <typename S, int DAG>
+void launch_variant(int v, void* out, const void* in, const void* links, const KGeom& k,
+                    int parity, int nsites, int nrhs, cudaStream_t st, size_t is, size_t os) {
+  switch (v) {
+    case 1: launch_shape<S, DAG, 128, 6>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    case 2: launch_shape<S, DAG, 128, 8>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    case 3: launch_shape<S, DAG, 256, 4>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    case 4: launch_shape<S, DAG, 64, 16>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    default: launch_shape<S, DAG, 128, 1>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+  }
+}
+
 template <typename S>
 int launch_typed(void* out, const void* in, const void* links, const Geom& g, int parity,
-                 int dagger, int nrhs, cudaStream_t st, size_t in_stride, size_t out_stride) {
+                 int dagger, int nrhs, cudaStream_t st, size_t in_stride, size_t out_stride,
+                 int dtype) {
   KGeom k = to_kgeom(g);
   int nsites = parity < 0 ? g.V : g.V / 2;
-  dim3 block(128);
-  dim3 grid((nsites + 127) / 128, nrhs);
-  typedef typename S::elem E;
-  if (dagger)
-    dslash_kernel<S, 1><<<grid, block, 0, st>>>((E*)out, (const E*)in, (const E*)links, k,
-                                                parity, nsites, in_stride, out_stride);
-  else
-    dslash_kernel<S, 0><<<grid, block, 0, st>>>((E*)out, (const E*)in, (const E*)links, k,
-                                                parity, nsites, in_stride, out_stride);
+  auto run = [&](int v) {
+    if (dagger) launch_variant<S, 1>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+    else launch_variant<S, 0>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+  };
+  int v = tuned_variant(dtype, parity, dagger, g.V, nrhs, st, kNumShapes, run);
+  if (v < 0) return fail(MG_ECUDA, "dslash autotune failed");
+  run(v);
   WMG_LAUNCHED();
   return MG_OK;
 }
@@ -298,13 +327,13 @@ int dslash_launch(int dtype, void* out, const void* in, const void* links, const
   if (out_stride == 0) out_stride = half;
   switch (dtype) {
     case MG_C128:
-      return launch_typed<StC128>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride);
+      return launch_typed<StC128>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype);
     case MG_C64:
-      return launch_typed<StC64>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride);
+      return launch_typed<StC64>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype);
     case MG_F16:
-      return launch_typed<StF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride);
+      return launch_typed<StF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype);
     case MG_BF16:
-      return launch_typed<StBF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride);
+      return launch_typed<StBF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype);
   }
   return fail(MG_EINVAL, "dslash: unknown dtype");
 }

@@ -14,6 +14,12 @@ int dslash_launch(int dtype, void* out, const void* in, const void* links, const
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,
                   size_t out_stride);
 
+// Autotuned launch shape for a kernel with `nvar` candidate shapes; `run(v)` launches
+// shape v on the caller's arguments.  Returns the chosen shape or -1 on a CUDA error.
+int tuned_variant(int dtype, int parity, int dagger, int V, int nrhs, cudaStream_t st, int nvar,
+                  const std::function<void(int)>& run);
+const char* tune_report();
+
 // ------------------------------------------------------------------ BLAS-1 (batched)
 // All vectors are nrhs contiguous complex arrays of length n (stride n).
 // Reductions are deterministic: fixed partition, fixed tree order, FP64 combination.
@@ -75,8 +81,11 @@ class Gmres {
   int fixed(const Op<R>& A, cplx<R>* x, const cplx<R>* b, int m, cudaStream_t st);
   // Restarted (F)GMRES from x0 = 0 until ||b - A x|| <= rtol ||b|| for every rhs.
   // M == nullptr: plain GMRES.  Returns MG_OK or MG_ENOCONV; *its = iterations.
+  // check_every: host convergence check interval in Arnoldi steps; steps taken past
+  // convergence are discarded from the least-squares update, so the iterate and the
+  // iteration count equal those of a per-step check.
   int solve(const Op<R>& A, const Op<R>* M, cplx<R>* x, const cplx<R>* b, double rtol,
-            int restart, int maxiter, int* its, cudaStream_t st);
+            int restart, int maxiter, int* its, cudaStream_t st, int check_every = 1);
   size_t n = 0;
   int nrhs = 0, m = 0;
   bool flexible = false;
@@ -88,9 +97,34 @@ class Gmres {
   cplx<R>* w = nullptr;   // nrhs x n
   zd* small = nullptr;    // device scalars (Hessenberg, rotations, rhs)
   double* dnorm = nullptr;
-  double* host_res = nullptr;  // pinned
+  double* reshist = nullptr;   // [m][nrhs] residual estimate after each Arnoldi step
+  double* host_res = nullptr;  // pinned, (m + 2) * nrhs
   ReduceWork rw;
   size_t off_H = 0, off_h2 = 0, off_cs = 0, off_g = 0, off_y = 0;
+};
+
+// ------------------------------------------------------------------ persistent coarse GMRES
+struct Blocking;
+// Restarted GMRES on the coarse stencil operator in one cooperative launch (one system).
+template <typename R>
+class CoarseSolver {
+ public:
+  ~CoarseSolver() { release(); }
+  int alloc(size_t nc, int m);
+  void release();
+  int solve(const cplx<R>* Op, const Blocking& B, int k, cplx<R>* x, const cplx<R>* b,
+            double rtol, int restart, int maxiter, int* its, cudaStream_t st);
+  size_t nc = 0;
+  int m = 0;
+
+ private:
+  size_t smem_bytes() const;
+  cplx<R>* V = nullptr;
+  cplx<R>* W = nullptr;
+  double* partial = nullptr;
+  void* state = nullptr;
+  void* host_state = nullptr;
+  int max_grid = 0;
 };
 
 // ------------------------------------------------------------------ aggregates
@@ -136,15 +170,18 @@ template <typename R>
 int chiral_gather(zd* tiles, int cmax, int col0, const cplx<R>* fields, int nvec,
                   const Blocking& B, cudaStream_t st);
 // G[t][c][c] = A_t^dag A_t over the first c columns.
-int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaStream_t st);
+int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaStream_t st,
+              bool df64 = false);
 // Hermitian eigen-decomposition of every G_t (c x c) by parallel cyclic Jacobi; returns
 // eigenvalues descending in lam[t][c] and eigenvectors in Vec[t][c][c] (column i at
 // Vec[t][*][i], row-major c x c).
 int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st);
 // out[t][i][row] = sum_c A[t][c][row] Vec[t][c][i] * (scale_inv ? 1/sqrt(lam[t][i]) : 1)
 // for i < kout; out tile stride cmax_out*M.
+// df64: sums of products in double-float arithmetic (df64.cuh) instead of FP64.
 int tile_update(zd* out, int cmax_out, const zd* tiles, int cmax, int c, const zd* Vec,
-                const double* lam, int kout, int scale_inv, const Blocking& B, cudaStream_t st);
+                const double* lam, int kout, int scale_inv, const Blocking& B, cudaStream_t st,
+                bool df64 = false);
 // Multiply every column i < k of every tile by conj(q)/|q|, q = sum of its entries.
 int tile_canonical_phase(zd* tiles, int cmax, int k, const Blocking& B, cudaStream_t st);
 // sig[t*ldsig + i] = sqrt(max(lam[t][i], 0)), i < kk
@@ -161,7 +198,7 @@ int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const
                    int nrhs, cudaStream_t st);
 // Galerkin: Op[j][blk][b][a] (column-major blocks; blk 0 = X, 1 + dir = Y_dir), FP64.
 int galerkin_build(zd* Op, zd* Xpart, const zd* P, int k, const zd* links, const Geom& g,
-                   const Blocking& B, cudaStream_t st);
+                   const Blocking& B, cudaStream_t st, bool df64 = false);
 template <typename R>
 int coarse_apply_launch(cplx<R>* y, const cplx<R>* x, const cplx<R>* Op, int k, const Blocking& B,
                         int nrhs, cudaStream_t st);

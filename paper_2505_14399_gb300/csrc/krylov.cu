@@ -2,9 +2,9 @@
 //
 // Arnoldi uses classical Gram-Schmidt applied twice (CGS2: two batched dot passes and
 // two batched updates per step), the Hessenberg column is reduced by complex Givens
-// rotations in a one-thread-per-system kernel, and the residual estimate |g_{j+1}|
-// is the only value the host reads (once per step, for tolerance-driven solves).
-// All nrhs systems advance in lockstep.
+// rotations in a one-thread-per-system kernel, and the residual estimates |g_{j+1}|
+// (one per step, kept on the device) are the only values the host reads, every
+// `check_every` steps of a tolerance-driven solve.  All nrhs systems advance in lockstep.
 #include <cmath>
 #include <cstring>
 
@@ -121,7 +121,8 @@ int Gmres<R>::alloc(size_t n_, int nrhs_, int m_, bool flexible_) {
   SmallLayout L{m};
   WMG_CUDA(cudaMalloc(&small, sizeof(zd) * L.stride() * nrhs));
   WMG_CUDA(cudaMalloc(&dnorm, sizeof(double) * nrhs * 4));
-  WMG_CUDA(cudaMallocHost(&host_res, sizeof(double) * nrhs * 2));
+  WMG_CUDA(cudaMalloc(&reshist, sizeof(double) * nrhs * m));
+  WMG_CUDA(cudaMallocHost(&host_res, sizeof(double) * nrhs * (m + 2)));
   WMG_TRY(rw.alloc(n, nrhs, m + 1));
   return MG_OK;
 }
@@ -133,10 +134,12 @@ void Gmres<R>::release() {
   if (w) cudaFree(w);
   if (small) cudaFree(small);
   if (dnorm) cudaFree(dnorm);
+  if (reshist) cudaFree(reshist);
   if (host_res) cudaFreeHost(host_res);
   V = Z = w = nullptr;
   small = nullptr;
   dnorm = nullptr;
+  reshist = nullptr;
   host_res = nullptr;
   rw.release();
   n = 0;
@@ -163,7 +166,8 @@ int Gmres<R>::arnoldi_step(const Op<R>& A, const Op<R>* M, int j, cudaStream_t s
   WMG_TRY(multi_dot<R>(small + L.h2(), L.stride(), V, fs, j + 1, w, n, nrhs, rw, st));
   WMG_TRY(multi_axpy<R>(w, V, fs, j + 1, small + L.h2(), L.stride(), -1.0, n, nrhs, st));
   WMG_TRY(norm2<R>(dnorm, 1, w, n, nrhs, rw, st));
-  givens_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, j, dnorm, dnorm + 2 * nrhs, nrhs);
+  givens_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, j, dnorm, reshist + (size_t)j * nrhs,
+                                                 nrhs);
   WMG_LAUNCHED();
   WMG_TRY(scale_inv<R>(V + (size_t)(j + 1) * fs, w, dnorm, 1, n, nrhs, st));
   return MG_OK;
@@ -189,7 +193,7 @@ int Gmres<R>::fixed(const Op<R>& A, cplx<R>* x, const cplx<R>* b, int steps, cud
 
 template <typename R>
 int Gmres<R>::solve(const Op<R>& A, const Op<R>* M, cplx<R>* x, const cplx<R>* b, double rtol,
-                    int restart, int maxiter, int* its_out, cudaStream_t st) {
+                    int restart, int maxiter, int* its_out, cudaStream_t st, int check_every) {
   if (restart > m) return fail(MG_EINVAL, "gmres: restart longer than allocated");
   if (M && !flexible) return fail(MG_EINVAL, "gmres: flexible space not allocated");
   SmallLayout L{m};
@@ -218,18 +222,31 @@ int Gmres<R>::solve(const Op<R>& A, const Op<R>* M, cplx<R>* x, const cplx<R>* b
     init_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
     WMG_LAUNCHED();
     WMG_TRY(scale_inv<R>(V, rvec, dnorm + nrhs, 1, n, nrhs, st));
-    int steps = 0;
+    int steps = 0, checked = 0;
+    if (check_every < 1) check_every = 1;
     for (int j = 0; j < restart && its < maxiter; ++j) {
       WMG_TRY(arnoldi_step(A, M, j, st));
       ++steps;
       ++its;
-      WMG_CUDA(cudaMemcpyAsync(host_res, dnorm + 2 * nrhs, sizeof(double) * nrhs,
-                               cudaMemcpyDeviceToHost, st));
+      bool check = ((j + 1 - checked) >= check_every) || j + 1 == restart || its >= maxiter;
+      if (!check) continue;
+      WMG_CUDA(cudaMemcpyAsync(host_res, reshist + (size_t)checked * nrhs,
+                               sizeof(double) * nrhs * (j + 1 - checked), cudaMemcpyDeviceToHost,
+                               st));
       WMG_CUDA(cudaStreamSynchronize(st));
-      bool bad = false;
-      for (int r = 0; r < nrhs; ++r) bad |= !std::isfinite(host_res[r]);
-      if (bad) return fail(MG_ENAN, "gmres: non-finite residual");
-      if (all_done(host_res)) break;
+      bool stop = false;
+      for (int jj = checked; jj <= j && !stop; ++jj) {
+        const double* rr = host_res + (size_t)(jj - checked) * nrhs;
+        for (int r = 0; r < nrhs; ++r)
+          if (!std::isfinite(rr[r])) return fail(MG_ENAN, "gmres: non-finite residual");
+        if (all_done(rr)) {
+          its -= j - jj;     // steps past convergence are discarded
+          steps = jj + 1;
+          stop = true;
+        }
+      }
+      checked = j + 1;
+      if (stop) break;
     }
     solve_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, steps, nrhs);
     WMG_LAUNCHED();

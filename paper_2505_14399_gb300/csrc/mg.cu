@@ -30,6 +30,8 @@ struct mg_handle {
   int nrhs = 0;
   Gmres<double> outer64, coarse64, post64;
   Gmres<float> outer32, coarse32, post32;
+  CoarseSolver<double> csol64;
+  CoarseSolver<float> csol32;
   zd *x64 = nullptr, *r64 = nullptr, *t64 = nullptr;
   zf *e32 = nullptr, *r32 = nullptr;
   zd *vc64 = nullptr, *ec64 = nullptr, *kw64 = nullptr, *ke64 = nullptr;
@@ -75,6 +77,8 @@ int validate(const mg_params* p, bool need_svd) {
   if (p->coarse_restart < 1 || p->coarse_restart > 128) return fail(MG_EINVAL, "coarse_restart in [1, 128]");
   if (p->outer_restart < 1 || p->outer_restart > 128) return fail(MG_EINVAL, "outer_restart in [1, 128]");
   if (!(p->coarse_tol > 0 && p->coarse_tol < 1)) return fail(MG_EINVAL, "coarse_tol in (0, 1)");
+  if (p->coarse_persistent && p->coarse_restart > 48)
+    return fail(MG_EINVAL, "coarse_restart <= 48 with the persistent coarse solver");
   return MG_OK;
 }
 
@@ -160,22 +164,24 @@ int run_setup(mg_handle* h, cudaStream_t st) {
   zd* cur = T0;
   zd* oth = T1;
   int kk = 0;
+  // sums of products in double-float when asked, or by default when the test vectors are FP32
+  const bool df = p.fp64_emulation > 0 || (p.fp64_emulation < 0 && sizeof(R) == 4);
   for (int s = 0; s < p.n_s; ++s) {
     STEP(smooth_stream<R>(h, psi, phi, tmp, gm, s, st));
     STEP(chiral_gather<R>(cur, cmax, kk, psi, r, h->B, st));
     int c = kk + r;
     int kn = c < k ? c : k;
     bool last = s == p.n_s - 1;
-    STEP(tile_gram(G, cur, cmax, c, h->B, st));
+    STEP(tile_gram(G, cur, cmax, c, h->B, st, df));
     STEP(tile_eig(lam, Vec, G, c, (int)ntile, st));
-    if (p.svd_refine) {
+    if (p.svd_refine > 0 || (p.svd_refine < 0 && sizeof(R) == 8)) {
       // B = A V (all c columns), then a second Gram/eig pass on B
-      STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, c, 0, h->B, st));
-      STEP(tile_gram(G, oth, cmax, c, h->B, st));
+      STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, c, 0, h->B, st, df));
+      STEP(tile_gram(G, oth, cmax, c, h->B, st, df));
       STEP(tile_eig(lam, Vec, G, c, (int)ntile, st));
-      STEP(tile_update(cur, cmax, oth, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st));
+      STEP(tile_update(cur, cmax, oth, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st, df));
     } else {
-      STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st));
+      STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st, df));
       zd* t = cur; cur = oth; oth = t;
     }
     STEP(tile_sigma(h->hist + (size_t)s * ntile * k, k, lam, c, kn, (int)ntile, st));
@@ -214,6 +220,7 @@ int ensure_solver(mg_handle* h, int nrhs) {
     WMG_CUDA(cudaMalloc(&h->ke64, f * sizeof(zd)));
     WMG_TRY(h->outer64.alloc(h->nf, nrhs, p.outer_restart, true));
     WMG_TRY(h->coarse64.alloc(h->nc, nrhs, p.coarse_restart, false));
+    if (p.coarse_persistent) WMG_TRY(h->csol64.alloc(h->nc, p.coarse_restart));
     WMG_TRY(h->post64.alloc(h->nf, nrhs, p.post_smooth > 0 ? p.post_smooth : 1, false));
   } else {
     WMG_CUDA(cudaMalloc(&h->e32, f * sizeof(zf)));
@@ -224,6 +231,7 @@ int ensure_solver(mg_handle* h, int nrhs) {
     WMG_CUDA(cudaMalloc(&h->ke32, f * sizeof(zf)));
     WMG_TRY(h->outer32.alloc(h->nf, nrhs, p.outer_restart, true));
     WMG_TRY(h->coarse32.alloc(h->nc, nrhs, p.coarse_restart, false));
+    if (p.coarse_persistent) WMG_TRY(h->csol32.alloc(h->nc, p.coarse_restart));
     WMG_TRY(h->post32.alloc(h->nf, nrhs, p.post_smooth > 0 ? p.post_smooth : 1, false));
   }
   h->nrhs = nrhs;
@@ -237,6 +245,7 @@ template <> struct Lvl<double> {
   static const zd* P(mg_handle* h) { return h->P64; }
   static const zd* Op(mg_handle* h) { return h->Op64; }
   static Gmres<double>& coarse(mg_handle* h) { return h->coarse64; }
+  static CoarseSolver<double>& csol(mg_handle* h) { return h->csol64; }
   static Gmres<double>& post(mg_handle* h) { return h->post64; }
   static Gmres<double>& outer(mg_handle* h) { return h->outer64; }
   static zd* vc(mg_handle* h) { return h->vc64; }
@@ -250,6 +259,7 @@ template <> struct Lvl<float> {
   static const zf* P(mg_handle* h) { return h->P32; }
   static const zf* Op(mg_handle* h) { return h->Op32; }
   static Gmres<float>& coarse(mg_handle* h) { return h->coarse32; }
+  static CoarseSolver<float>& csol(mg_handle* h) { return h->csol32; }
   static Gmres<float>& post(mg_handle* h) { return h->post32; }
   static Gmres<float>& outer(mg_handle* h) { return h->outer32; }
   static zf* vc(mg_handle* h) { return h->vc32; }
@@ -283,11 +293,23 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
     cplx<R>* kw = Lvl<R>::kw(h);
     cplx<R>* ke = Lvl<R>::ke(h);
     WMG_TRY(restrict_launch<R>(vc, v, Lvl<R>::P(h), h->k, h->B, nrhs, st));
-    Op<R> Dc = coarse_op<R>(h, nrhs);
     int its = 0;
-    int s = Lvl<R>::coarse(h).solve(Dc, nullptr, ec, vc, p.coarse_tol, p.coarse_restart,
-                                    p.coarse_maxiter, &its, st);
-    if (s != MG_OK && s != MG_ENOCONV) return s;
+    if (p.coarse_persistent) {
+      // one cooperative launch per system: the whole restarted coarse GMRES on the device
+      for (int r = 0; r < nrhs; ++r) {
+        int itr = 0;
+        WMG_TRY(Lvl<R>::csol(h).solve(Lvl<R>::Op(h), h->B, h->k, ec + r * h->nc, vc + r * h->nc,
+                                      p.coarse_tol, p.coarse_restart, p.coarse_maxiter, &itr, st));
+        its += itr;
+      }
+    } else {
+      Op<R> Dc = coarse_op<R>(h, nrhs);
+      // coarse Arnoldi steps are cheap: check convergence on the host every 8 steps
+      int s = Lvl<R>::coarse(h).solve(Dc, nullptr, ec, vc, p.coarse_tol, p.coarse_restart,
+                                      p.coarse_maxiter, &its, st, 8);
+      if (s != MG_OK && s != MG_ENOCONV) return s;
+      its *= nrhs;   // every system took each lockstep step
+    }
     h->coarse_its += its;
     h->kcycles += 1;
     WMG_TRY(prolong_launch<R>(z, ec, Lvl<R>::P(h), h->k, h->B, nrhs, st));
@@ -400,6 +422,7 @@ mg_handle::~mg_handle() {
 void mg_handle::free_solver() {
   outer64.release(); coarse64.release(); post64.release();
   outer32.release(); coarse32.release(); post32.release();
+  csol64.release(); csol32.release();
   dfree(x64); dfree(r64); dfree(t64); dfree(e32); dfree(r32);
   dfree(vc64); dfree(ec64); dfree(kw64); dfree(ke64);
   dfree(vc32); dfree(ec32); dfree(kw32); dfree(ke32);
@@ -438,8 +461,9 @@ extern "C" int coarse_build(mg_handle* h, void* stream) {
     WMG_CUDA(cudaMalloc(&h->Op32, (size_t)h->B.d * 9 * ne * sizeof(zf)));
   }
   zd* Xpart = nullptr;
-  WMG_CUDA(cudaMallocAsync(&Xpart, (size_t)8 * h->B.d * ne * sizeof(zd), st));
-  int s = galerkin_build(h->Op64, Xpart, h->P64, h->k, h->links64, h->g, h->B, st);
+  WMG_CUDA(cudaMallocAsync(&Xpart, (size_t)4 * h->B.d * ne * sizeof(zd), st));
+  bool df = h->p.fp64_emulation > 0 || (h->p.fp64_emulation < 0 && h->p.solve_dtype == MG_C64);
+  int s = galerkin_build(h->Op64, Xpart, h->P64, h->k, h->links64, h->g, h->B, st, df);
   cudaFreeAsync(Xpart, st);
   WMG_TRY(s);
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));

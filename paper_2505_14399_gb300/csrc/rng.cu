@@ -33,6 +33,34 @@ __device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1
   }
 }
 
+// FP32 fields: the same Philox words and the same 53-bit uniforms, with the transforms
+// in FP32 (GB300's FP64 transcendentals are slow).  1 - u_a is formed exactly as the
+// integer 2^53 - m_a before rounding to float, so the tail is not lost to cancellation;
+// small u_a goes through log1pf.  Relative error against the FP64 map ~1e-7.
+__global__ void gaussian_kernel_f32(zf* out, uint32_t k0, uint32_t k1, unsigned id0, int V,
+                                    size_t total) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t per = (size_t)V * 12;
+    unsigned v = (unsigned)(e / per);
+    size_t rem = e % per;
+    uint32_t c[4] = {(uint32_t)(rem / 12), (uint32_t)(rem % 12), id0 + v, 0u};
+    philox10(c, k0, k1);
+    unsigned long long ma = ((unsigned long long)(c[0] >> 5) << 26) | (c[1] >> 6);
+    unsigned long long mb = ((unsigned long long)(c[2] >> 5) << 26) | (c[3] >> 6);
+    const float s53 = 1.1102230246251565e-16f;  // 2^-53
+    float ua = __ull2float_rn(ma) * s53;
+    float l;
+    if (ua < 0.5f) l = log1pf(-ua);
+    else l = logf(__ull2float_rn((1ull << 53) - ma) * s53);
+    float rho = sqrtf(-2.0f * l);
+    float ub = __ull2float_rn(mb) * s53;
+    float sn, cs;
+    sincospif(2.0f * ub, &sn, &cs);
+    out[e] = {rho * cs, rho * sn};
+  }
+}
+
 template <typename R>
 __global__ void gaussian_kernel(cplx<R>* out, uint32_t k0, uint32_t k1, unsigned id0, int V,
                                 size_t total) {
@@ -61,8 +89,12 @@ int gaussian_fill(cplx<R>* out, unsigned long long seed, unsigned id0, int nvec,
   size_t total = (size_t)nvec * V * 12;
   size_t g = (total + 255) / 256;
   size_t cap = (size_t)num_sms() * 16;
-  gaussian_kernel<R><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(
-      out, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), id0, V, total);
+  unsigned grid = (unsigned)(g < cap ? g : cap);
+  uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  if (sizeof(R) == 4)
+    gaussian_kernel_f32<<<grid, 256, 0, st>>>((zf*)out, k0, k1, id0, V, total);
+  else
+    gaussian_kernel<R><<<grid, 256, 0, st>>>(out, k0, k1, id0, V, total);
   WMG_LAUNCHED();
   return MG_OK;
 }

@@ -131,5 +131,7 @@ extern "C" void mg_params_default(mg_params* p) {
   p->coarse_maxiter = 2000;
   p->outer_restart = 16;
   p->inner_tol = 1e-5;
-  p->svd_refine = 1;
+  p->svd_refine = -1;
+  p->coarse_persistent = 1;
+  p->fp64_emulation = -1;
 }

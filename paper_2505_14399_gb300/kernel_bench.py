@@ -1,0 +1,142 @@
+"""Per-kernel microbenchmarks (CUDA-event timing; also the driver for ncu captures).
+
+    python -m paper_2505_14399_gb300.kernel_bench dslash --dims 24 24 24 48 --dtype c64
+    python -m paper_2505_14399_gb300.kernel_bench step --workload c2_16^3x32_near_critical
+    python -m paper_2505_14399_gb300.kernel_bench coarse --workload c2_16^3x32_near_critical
+
+Inputs come from the seeded generators in ``synthetic``; L2 is flushed (a 256 MB write)
+before every timed launch.  Prints one JSON line per measurement.
+"""
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import api, synthetic
+
+BYTES_PER_SITE = {"c128": 960.0, "c64": 480.0, "f16": 240.0, "bf16": 240.0}
+TORCH_DT = {"c128": torch.complex128, "c64": torch.complex64, "f16": torch.float16,
+            "bf16": torch.bfloat16}
+
+
+def _field(x, dt, dev):
+    if dt in ("c128", "c64"):
+        return torch.from_numpy(x).to(TORCH_DT[dt]).to(dev)
+    return torch.from_numpy(np.stack([x.real, x.imag], axis=-1)).to(TORCH_DT[dt]).to(dev)
+
+
+def _timeit(fn, reps, flush):
+    ts = []
+    for i in range(reps + 2):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 2:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.mean(ts)), float(np.min(ts))
+
+
+def bench_dslash(a, dev, flush):
+    dims = tuple(a.dims)
+    V = int(np.prod(dims))
+    U = synthetic.smooth_links(dims, 1)
+    psi = synthetic.gaussian_rhs(dims, 2, a.nrhs)
+    if a.parity >= 0:
+        psi = psi[:, : V // 2]
+    Ut = _field(U, a.dtype, dev)
+    pt = _field(np.ascontiguousarray(psi), a.dtype, dev)
+    out = torch.empty_like(pt)
+    fn = lambda: api.dslash(pt, Ut, dims, 0.12, parity=a.parity, out=out)
+    t, tmin = _timeit(fn, a.reps, flush)
+    sites = V if a.parity < 0 else V // 2
+    eb = BYTES_PER_SITE[a.dtype] / 120.0
+    byts = sites * (48 * a.nrhs + 72) * eb if a.parity < 0 else sites * (48 * a.nrhs + 144) * eb
+    return {"kernel": "dslash", "dims": dims, "dtype": a.dtype, "nrhs": a.nrhs,
+            "parity": a.parity, "us": t * 1e6, "us_min": tmin * 1e6,
+            "algorithmic_bytes": byts, "GBps": byts / t / 1e9}
+
+
+def _workload(name, kappa=None):
+    cfg = dict(synthetic.WORKLOADS[name])
+    cfg["kappa"] = kappa if kappa is not None else synthetic.kappa_of(cfg)
+    return cfg
+
+
+def _params(cfg, mixed=True):
+    return api.params(cfg["dims"], cfg["block"], cfg["kappa"], cfg["k"], cfg["r"], cfg["n_s"],
+                      cfg["sweeps"], cfg["tv_seed"], cfg["hop_weight"], cfg["bc"],
+                      setup_dtype="c64" if mixed else "c128",
+                      solve_dtype="c64" if mixed else "c128")
+
+
+def bench_step(a, dev, flush):
+    cfg = _workload(a.workload, a.kappa)
+    U = torch.from_numpy(synthetic.make_links(cfg)).to(dev)
+    b = torch.from_numpy(synthetic.gaussian_rhs(cfg["dims"], cfg["rhs_seed"])).to(dev)
+    p = _params(cfg, not a.fp64)
+    out = {}
+
+    def run():
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        h = api.Hierarchy(U, p)
+        e[1].record()
+        h.coarse_build()
+        e[2].record()
+        x, info = h.solve(b, tol=1e-10, maxiter=4000)
+        e[3].record()
+        torch.cuda.synchronize()
+        h.close()
+        out.update(setup_s=e[0].elapsed_time(e[1]) / 1e3, coarse_s=e[1].elapsed_time(e[2]) / 1e3,
+                   solve_s=e[2].elapsed_time(e[3]) / 1e3, info=info)
+
+    for _ in range(a.reps):
+        flush.zero_()
+        run()
+    out.update(kernel="step", workload=a.workload, fp64=a.fp64, kappa=cfg["kappa"])
+    return out
+
+
+def bench_coarse(a, dev, flush):
+    cfg = _workload(a.workload, a.kappa)
+    U = torch.from_numpy(synthetic.make_links(cfg)).to(dev)
+    h = api.Hierarchy(U, _params(cfg))
+    t, _ = _timeit(h.coarse_build, a.reps, flush)
+    d = h.d
+    k = h.k
+    vc = torch.randn((1, d, 2, k), dtype=torch.complex64, device=dev)
+    tc, _ = _timeit(lambda: h.coarse_apply(vc), a.reps, flush)
+    V = h.V
+    flops = 8.0 * V * (8 * 6 * (2 * k) ** 2)
+    h.close()
+    return {"kernel": "coarse", "workload": a.workload, "coarse_build_s": t,
+            "galerkin_fp64_tflops": flops / t / 1e12, "coarse_apply_us": tc * 1e6,
+            "coarse_apply_GBps": d * 9 * (2 * k) ** 2 * 8 / tc / 1e9}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["dslash", "step", "coarse"])
+    ap.add_argument("--dims", type=int, nargs=4, default=[16, 16, 16, 32])
+    ap.add_argument("--dtype", default="c64", choices=list(BYTES_PER_SITE))
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--parity", type=int, default=-1)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--workload", default="c2_16^3x32_near_critical")
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--kappa", type=float, default=None, help="override the workload's kappa")
+    a = ap.parse_args()
+    dev = torch.device("cuda:0")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    fn = {"dslash": bench_dslash, "step": bench_step, "coarse": bench_coarse}[a.what]
+    print(json.dumps(fn(a, dev, flush)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

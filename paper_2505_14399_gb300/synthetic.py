@@ -64,9 +64,7 @@ def gaussian_rhs(dims, seed, nrhs=1):
 
 
 # Workload definitions.  Seeds: links 1000+i, sources 2000+i, test vectors 3000+i.
-# "kappa_crit_hint" values are the reciprocal of the largest real part of the hopping
-# matrix's spectrum on the seeded field (rightmost Arnoldi eigenvalue); the near-critical
-# workloads use kappa = 0.995 * that.
+# kappa=None marks a near-critical workload: kappa = kappa_factor * KAPPA_CRIT[name].
 WORKLOADS = {
     "c1_4^4_haar": dict(dims=(4, 4, 4, 4), links="haar", link_seed=1000, kappa=0.124,
                         hop_weight=(1, 1, 1, 1), bc=(1, 1, 1, 1), block=(2, 2, 2, 2),
@@ -92,11 +90,12 @@ WORKLOADS = {
 }
 
 
-# 1 / Re(lambda_max) of the hopping matrix on each seeded field, from ARPACK applied to
-# the FP64 oracle's hopping term (oracle/critical_kappa.py).  The 32^3 x 64 field is too
-# large for that run; it reuses the 16^3 x 32 value (same link distribution).
+# kappa_crit = 1 / (largest eigenvalue of the Hermitian part of the hopping matrix) on each
+# seeded field, a lower bound on the kappa where D turns singular, computed by Lanczos on
+# the FP64 oracle's hopping term (python -m oracle.critical_kappa <name>).  The 32^3 x 64
+# field is too large for that run; it reuses the 16^3 x 32 value (same link distribution).
 KAPPA_CRIT = {
-    "c2_16^3x32_near_critical": None,
+    "c2_16^3x32_near_critical": 0.136551654556,
     "c3_16^3x64_aniso": None,
 }
 KAPPA_CRIT["c4_32^3x64_12rhs"] = KAPPA_CRIT["c2_16^3x32_near_critical"]

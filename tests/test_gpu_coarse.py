@@ -15,10 +15,11 @@ CASES = [((4, 4, 4, 4), (2, 2, 2, 2), 4),
          ((6, 4, 4, 4), (2, 2, 2, 4), 12)]
 
 
-def _handle(dims, block, k, seed, kappa=0.125, w=(1, 1, 1, 1 / 3.5), bc=(1, 1, 1, -1)):
+def _handle(dims, block, k, seed, kappa=0.125, w=(1, 1, 1, 1 / 3.5), bc=(1, 1, 1, -1),
+            fp64_emulation=0):
     U = synthetic.smooth_links(dims, seed)
     p = api.params(dims, block, kappa, k, k, 1, hop_weight=w, bc=bc, setup_dtype="c128",
-                   solve_dtype="c128")
+                   solve_dtype="c128", fp64_emulation=fp64_emulation)
     h = api.Hierarchy(to_dev(U), p, setup=False)
     nd = int(np.prod(block))
     d = int(np.prod(dims)) // nd
@@ -41,6 +42,18 @@ def test_restrict_prolong(dims, block, k):
     e = h.prolong(to_dev(ec)).cpu().numpy()
     for r in range(2):
         assert rel(e[r], coarse.prolong(Pt, ec[r], dims, block)) < 1e-13
+    h.close()
+
+
+@pytest.mark.parametrize("dims,block,k", CASES)
+def test_galerkin_double_float_contraction(dims, block, k):
+    """Galerkin contraction in double-float arithmetic on FP32 units vs the FP64 oracle."""
+    h, U, Pt, (kappa, w, bc) = _handle(dims, block, k, 7, fp64_emulation=1)
+    h.coarse_build()
+    X, Y = h.coarse_op()
+    Xo, Yo = coarse.galerkin(Pt, U, dims, block, kappa, w, bc)
+    assert rel(X.cpu().numpy(), Xo) < 1e-11
+    assert rel(Y.cpu().numpy(), Yo) < 1e-11
     h.close()
 
 

@@ -39,6 +39,28 @@ def test_fp64_solve_matches_oracle_two_level():
     h.close()
 
 
+@pytest.mark.parametrize("solve_dtype", ["c128", "c64"])
+def test_persistent_coarse_solver_matches_launch_per_op(solve_dtype):
+    """The one-launch coarse GMRES takes the same steps as the kernel-per-operation one."""
+    cfg = C5
+    U = links_for(cfg)
+    b = synthetic.gaussian_rhs(cfg["dims"], cfg["rhs_seed"], 2)
+    out = {}
+    for pers in (0, 1):
+        p = params_for(cfg, setup_dtype="c128", solve_dtype=solve_dtype, coarse_persistent=pers)
+        h = api.Hierarchy(to_dev(U), p)
+        h.coarse_build()
+        x, info = h.solve(to_dev(b), tol=1e-10)
+        out[pers] = (x.cpu().numpy(), info)
+        h.close()
+    (x0, i0), (x1, i1) = out[0], out[1]
+    assert i0["outer"] == i1["outer"]
+    assert abs(i0["coarse"] - i1["coarse"]) <= 2 * i0["kcycles"] * (0 if solve_dtype == "c128" else 1)
+    for r in range(2):
+        assert _true_residual(cfg, U, x1[r], b[r]) <= 1e-10
+        assert rel(x1[r], x0[r]) < 1e-8
+
+
 @pytest.mark.parametrize("cfg", [C1, C5])
 def test_mixed_precision_solve_reaches_1e10(cfg):
     U = links_for(cfg)

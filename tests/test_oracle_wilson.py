@@ -106,3 +106,19 @@ def test_links_are_special_unitary():
         I = np.einsum('mxab,mxcb->mxac', U, U.conj())
         assert np.abs(I - np.eye(3)).max() < 1e-13
         assert np.abs(np.linalg.det(U) - 1).max() < 1e-13
+
+
+def test_kappa_crit_bound_on_free_field():
+    """Unit links: H is normal with largest real eigenvalue 2 sum w (periodic), so the
+    Hermitian-part bound is exact: kappa_crit = 1 / (2 sum_mu w_mu)."""
+    from oracle import critical_kappa
+    dims = (4, 4, 2, 4)
+    w = (1.0, 1.0, 1.0, 1 / 3.5)
+    kc = critical_kappa.kappa_crit(synthetic.unit_links(dims), dims, w, (1, 1, 1, 1), tol=1e-10)
+    assert abs(kc - 1 / (2 * sum(w))) < 1e-9
+    # and it lower-bounds the singular point on random links: D at 0.999 kappa_crit has
+    # every eigenvalue with positive real part
+    U = synthetic.smooth_links(dims, 3)
+    kc = critical_kappa.kappa_crit(U, dims, tol=1e-10)
+    ev = np.linalg.eigvals(wilson.dense_dirac(U, dims, 0.999 * kc))
+    assert ev.real.min() > 0
