@@ -119,6 +119,14 @@ long long mg_kernel_launches(void);
  * valid until the next call). */
 const char* mg_autotune_report(void);
 
+/* Per-kernel timing: enable = 1 brackets every subsequent instrumented launch with CUDA
+ * events on its own stream (capacity max_launches, 0 = 100000) and clears earlier records;
+ * enable = 0 stops recording.  mg_profile_report() synchronises on the recorded events and
+ * returns a JSON object {kernel: {launches, ms, bytes, flops}} with the algorithmic bytes
+ * and flops of the recorded launches (library-owned string, valid until the next call). */
+int mg_profile_enable(int enable, int max_launches);
+const char* mg_profile_report(void);
+
 /* Failure-path self-test: runs the grid barrier used by the persistent coarse solver with
  * an arrival count that is never reached, so its bounded wait expires (a few ms).  Returns
  * MG_ETIMEOUT when the timeout is reported to the host as designed; the CUDA context stays
@@ -188,6 +196,11 @@ int mg_destroy(mg_handle* h);
  * written as complex double fields out[r][site][4][3].  links: complex double. */
 int mg_test_vectors(void* out, const void* links, const mg_params* p, int stream_index,
                     void* stream);
+
+/* out = D in (dagger: D^dag in) with the handle's operator and its lane-contiguous link
+ * copy (the stencil the solver runs); dtype MG_C128 or MG_C64 fields, nrhs of them. */
+int mg_apply_fine(mg_handle* h, void* out, const void* in, int nrhs, int dtype, int dagger,
+                  void* stream);
 
 /* P tiles: P[j][alpha][i][row], row = (local site * 2 + spin in chirality) * 3 + colour,
  * local site lexicographic inside the aggregate; complex double.  sigma[j][alpha][k]

@@ -62,6 +62,8 @@ SIGNATURES = {
     "mg_kernel_launches": (C.c_longlong, []),
     "mg_autotune_report": (C.c_char_p, []),
     "mg_selftest_barrier_timeout": (I, [P]),
+    "mg_profile_enable": (I, [I, I]),
+    "mg_profile_report": (C.c_char_p, []),
     "wilson_dslash": (I, [P, P, P, C.POINTER(C.c_int), D, C.POINTER(C.c_double),
                           C.POINTER(C.c_int), I, I, I, I, P]),
     "mg_setup_streaming_svd": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),
@@ -72,6 +74,7 @@ SIGNATURES = {
     "mg_destroy": (I, [P]),
     "mg_test_vectors": (I, [P, P, C.POINTER(MgParams), I, P]),
     "mg_get_prolongator": (I, [P, P, P, P]),
+    "mg_apply_fine": (I, [P, P, P, I, I, I, P]),
     "mg_get_sigma_history": (I, [P, P, P]),
     "mg_set_prolongator": (I, [P, P, P]),
     "mg_restrict": (I, [P, P, P, I, P]),

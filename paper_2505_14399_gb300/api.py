@@ -138,6 +138,16 @@ class Hierarchy:
                    "kcycles": info.kcycles, "coarse": info.coarse_iterations,
                    "residual": info.true_residual}
 
+    def apply_fine(self, v, dagger=False, out=None):
+        """D v with the hierarchy's operator (lane-contiguous link copy)."""
+        dt = _DT[v.dtype]
+        nrhs = v.numel() // (self.V * 12)
+        if out is None:
+            out = torch.empty_like(v)
+        L.check(L.lib().mg_apply_fine(self._h, _ptr(out), _ptr(v), nrhs, dt, int(dagger),
+                                      _stream(v)), "mg_apply_fine")
+        return out
+
     def prolongator(self):
         P = torch.empty((self.d, 2, self.k, 6 * self.nd), dtype=torch.complex128,
                         device=self.device)

@@ -6,61 +6,11 @@
 // does not change the arithmetic), so results are bitwise reproducible run to run.
 #include "common.cuh"
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace wmg {
 
 namespace {
-
-constexpr int RT = 256;  // threads per reduction CTA
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <typename R>
-__device__ __forceinline__ R warp_sum_r(R v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// CTA sum of (a, b); result valid in thread 0.
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { sh[2 * wid] = a; sh[2 * wid + 1] = b; }
-  __syncthreads();
-  if (wid == 0) {
-    int nw = blockDim.x >> 5;
-    a = lane < nw ? sh[2 * lane] : 0.0;
-    b = lane < nw ? sh[2 * lane + 1] : 0.0;
-    a = warp_sum(a);
-    b = warp_sum(b);
-  }
-  __syncthreads();
-}
-
-// Final reduction over the nblk partials of every (rhs, i), done by the last CTA.
-// mode 0: complex dot -> out[rhs*ldo + i]; mode 1: norm -> dout[rhs*ldo] = sqrt(re).
-__device__ void finish_partials(double* partial, int nv, int nblk, int maxvec, int rhs,
-                                zd* out, double* dout, int ldo, int mode, double* sh) {
-  for (int i = 0; i < nv; ++i) {
-    const double* p = partial + ((size_t)rhs * maxvec + i) * nblk * 2;
-    double a = 0, b = 0;
-    for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
-      a += __ldcg(p + 2 * k);
-      b += __ldcg(p + 2 * k + 1);
-    }
-    block_sum2(a, b, sh);
-    if (threadIdx.x == 0) {
-      if (mode == 0) out[(size_t)rhs * ldo + i] = {a, b};
-      else dout[(size_t)rhs * ldo] = sqrt(a);
-    }
-  }
-}
 
 template <typename R>
 __global__ void __launch_bounds__(RT)
@@ -68,9 +18,8 @@ multi_dot_kernel(zd* out, int ldo, const cplx<R>* __restrict__ V, size_t vstride
                  const cplx<R>* __restrict__ w, size_t n, double* partial, unsigned* counter,
                  int nblk, int maxvec) {
   __shared__ double sh[(RT / 32) * 8 * 2];
-  __shared__ bool last;
   int rhs = blockIdx.y;
-  size_t chunk = (n + nblk - 1) / nblk;
+  size_t chunk = reduce_chunk(n, nblk);   // even: 16-byte FP32 pairs
   size_t k0 = (size_t)blockIdx.x * chunk;
   size_t k1 = min(n, k0 + chunk);
   const cplx<R>* wr = w + (size_t)rhs * n;
@@ -82,45 +31,44 @@ multi_dot_kernel(zd* out, int ldo, const cplx<R>* __restrict__ V, size_t vstride
 #pragma unroll
     for (int q = 0; q < G; ++q) { ar[q] = 0; ai[q] = 0; }
     const cplx<R>* vb = V + (size_t)i0 * vstride + (size_t)rhs * n;
-    for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
-      cplx<R> b = wr[k];
+    if (sizeof(R) == 4 && ((k0 | k1 | vstride) & 1) == 0) {
+      // FP32: two complex numbers per 16-byte load
+      const float4* w4 = reinterpret_cast<const float4*>(wr);
+      const float4* v4 = reinterpret_cast<const float4*>(vb);
+      size_t vs4 = vstride / 2;
+      for (size_t k = k0 / 2 + threadIdx.x; k < k1 / 2; k += RT) {
+        float4 b = w4[k];
 #pragma unroll
-      for (int q = 0; q < G; ++q) {
-        if (q < ni) {
-          cplx<R> a = vb[(size_t)q * vstride + k];
-          ar[q] = fma(a.re, b.re, ar[q]); ar[q] = fma(a.im, b.im, ar[q]);
-          ai[q] = fma(a.re, b.im, ai[q]); ai[q] = fma(-a.im, b.re, ai[q]);
+        for (int q = 0; q < G; ++q) {
+          if (q < ni) {
+            float4 a = v4[(size_t)q * vs4 + k];
+            ar[q] = fma((R)a.x, (R)b.x, ar[q]); ar[q] = fma((R)a.y, (R)b.y, ar[q]);
+            ar[q] = fma((R)a.z, (R)b.z, ar[q]); ar[q] = fma((R)a.w, (R)b.w, ar[q]);
+            ai[q] = fma((R)a.x, (R)b.y, ai[q]); ai[q] = fma(-(R)a.y, (R)b.x, ai[q]);
+            ai[q] = fma((R)a.z, (R)b.w, ai[q]); ai[q] = fma(-(R)a.w, (R)b.z, ai[q]);
+          }
+        }
+      }
+    } else {
+      for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
+        cplx<R> b = wr[k];
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          if (q < ni) {
+            cplx<R> a = vb[(size_t)q * vstride + k];
+            ar[q] = fma(a.re, b.re, ar[q]); ar[q] = fma(a.im, b.im, ar[q]);
+            ai[q] = fma(a.re, b.im, ai[q]); ai[q] = fma(-a.im, b.re, ai[q]);
+          }
         }
       }
     }
-    // CTA reduction of the ni pairs in the vectors' own precision (FP64 arithmetic is
-    // scarce on this GPU): warp shuffles, then one shared-memory pass; only the CTA
-    // partial is widened to FP64 for the cross-CTA sum.
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    R* shg = reinterpret_cast<R*>(sh);  // [RT/32][G][2]
-#pragma unroll
-    for (int q = 0; q < G; ++q) {
-      if (q < ni) {
-        R dr = warp_sum_r(ar[q]);
-        R di = warp_sum_r(ai[q]);
-        if (lane == 0) { shg[(wid * G + q) * 2] = dr; shg[(wid * G + q) * 2 + 1] = di; }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < 2 * ni) {
-      int q = threadIdx.x >> 1, part = threadIdx.x & 1;
-      R s = 0;
-      for (int wv = 0; wv < RT / 32; ++wv) s += shg[(wv * G + q) * 2 + part];
-      partial[(((size_t)rhs * maxvec + i0 + q) * nblk + blockIdx.x) * 2 + part] = (double)s;
-    }
-    __syncthreads();
+    // CTA reduction in the vectors' own precision (FP64 arithmetic is scarce on this GPU);
+    // only the CTA partial is widened to FP64 for the cross-CTA sum.
+    cta_store_partials<R, G>(ar, ai, ni, i0, rhs, maxvec, nblk, partial,
+                             reinterpret_cast<R*>(sh));
   }
-  __threadfence();
-  if (threadIdx.x == 0) last = (atomicAdd(counter + rhs, 1u) == (unsigned)nblk - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  finish_partials(partial, nv, nblk, maxvec, rhs, out, nullptr, ldo, 0, sh);
+  if (!last_cta(counter, rhs, nblk)) return;
+  finish_partials(partial, nv, nblk, maxvec, rhs, out, nullptr, ldo, 0);
   if (threadIdx.x == 0) counter[rhs] = 0;
 }
 
@@ -129,9 +77,8 @@ __global__ void __launch_bounds__(RT)
 norm_kernel(double* nrm, int ldn, const cplx<R>* __restrict__ w, size_t n, double* partial,
             unsigned* counter, int nblk, int maxvec) {
   __shared__ double sh[64];
-  __shared__ bool last;
   int rhs = blockIdx.y;
-  size_t chunk = (n + nblk - 1) / nblk;
+  size_t chunk = reduce_chunk(n, nblk);   // even: 16-byte FP32 pairs
   size_t k0 = (size_t)blockIdx.x * chunk;
   size_t k1 = min(n, k0 + chunk);
   const cplx<R>* wr = w + (size_t)rhs * n;
@@ -152,13 +99,10 @@ norm_kernel(double* nrm, int ldn, const cplx<R>* __restrict__ w, size_t n, doubl
     double* p = partial + ((size_t)rhs * maxvec * nblk + blockIdx.x) * 2;
     p[0] = (double)s;
     p[1] = 0;
+    __threadfence();
   }
-  __threadfence();
-  if (threadIdx.x == 0) last = (atomicAdd(counter + rhs, 1u) == (unsigned)nblk - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  finish_partials(partial, 1, nblk, maxvec, rhs, nullptr, nrm, ldn, 1, sh);
+  if (!last_cta(counter, rhs, nblk)) return;
+  finish_partials(partial, 1, nblk, maxvec, rhs, nullptr, nrm, ldn, 1);
   if (threadIdx.x == 0) counter[rhs] = 0;
 }
 
@@ -173,12 +117,97 @@ __global__ void multi_axpy_kernel(cplx<R>* w, const cplx<R>* __restrict__ V, siz
   }
   __syncthreads();
   cplx<R>* wr = w + (size_t)rhs * n;
+  if (sizeof(R) == 4 && ((n | vstride) & 1) == 0) {
+    // FP32: two complex numbers per 16-byte access
+    float4* w4 = reinterpret_cast<float4*>(wr);
+    const float4* v4 = reinterpret_cast<const float4*>(V + (size_t)rhs * n);
+    size_t vs4 = vstride / 2;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n / 2;
+         k += (size_t)gridDim.x * blockDim.x) {
+      float4 acc = w4[k];
+      for (int i = 0; i < nv; ++i) {
+        float4 v = v4[(size_t)i * vs4 + k];
+        float cr = (float)cs[i].re, ci = (float)cs[i].im;
+        acc.x = fmaf(cr, v.x, acc.x); acc.x = fmaf(-ci, v.y, acc.x);
+        acc.y = fmaf(cr, v.y, acc.y); acc.y = fmaf(ci, v.x, acc.y);
+        acc.z = fmaf(cr, v.z, acc.z); acc.z = fmaf(-ci, v.w, acc.z);
+        acc.w = fmaf(cr, v.w, acc.w); acc.w = fmaf(ci, v.z, acc.w);
+      }
+      w4[k] = acc;
+    }
+    return;
+  }
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
     cplx<R> acc = wr[k];
     for (int i = 0; i < nv; ++i) cfma(acc, cs[i], V[(size_t)i * vstride + (size_t)rhs * n + k]);
     wr[k] = acc;
   }
+}
+
+// w[rhs] += sgn * sum_i c_i V_i[rhs] and nrm[rhs] = ||w[rhs]|| (after the update) in one pass,
+// with the same fixed partition and final tree as norm_kernel.
+template <typename R>
+__global__ void __launch_bounds__(RT)
+multi_axpy_norm_kernel(cplx<R>* w, const cplx<R>* __restrict__ V, size_t vstride, int nv,
+                       const zd* c, int ldc, double sgn, size_t n, double* nrm, int ldn,
+                       double* partial, unsigned* counter, int nblk, int maxvec) {
+  __shared__ cplx<R> cs[128];
+  __shared__ double sh[64];
+  int rhs = blockIdx.y;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    zd v = c[(size_t)rhs * ldc + i];
+    cs[i] = {(R)(sgn * v.re), (R)(sgn * v.im)};
+  }
+  __syncthreads();
+  size_t chunk = reduce_chunk(n, nblk);
+  size_t k0 = (size_t)blockIdx.x * chunk;
+  size_t k1 = min(n, k0 + chunk);
+  cplx<R>* wr = w + (size_t)rhs * n;
+  const cplx<R>* vb = V + (size_t)rhs * n;
+  R acc2 = 0;
+  if (sizeof(R) == 4 && ((k0 | k1 | vstride) & 1) == 0) {
+    float4* w4 = reinterpret_cast<float4*>(wr);
+    const float4* v4 = reinterpret_cast<const float4*>(vb);
+    size_t vs4 = vstride / 2;
+    for (size_t k = k0 / 2 + threadIdx.x; k < k1 / 2; k += RT) {
+      float4 a = w4[k];
+      for (int i = 0; i < nv; ++i) {
+        float4 v = v4[(size_t)i * vs4 + k];
+        float cr = (float)cs[i].re, ci = (float)cs[i].im;
+        a.x = fmaf(cr, v.x, a.x); a.x = fmaf(-ci, v.y, a.x);
+        a.y = fmaf(cr, v.y, a.y); a.y = fmaf(ci, v.x, a.y);
+        a.z = fmaf(cr, v.z, a.z); a.z = fmaf(-ci, v.w, a.z);
+        a.w = fmaf(cr, v.w, a.w); a.w = fmaf(ci, v.z, a.w);
+      }
+      w4[k] = a;
+      acc2 = fma((R)a.x, (R)a.x, acc2); acc2 = fma((R)a.y, (R)a.y, acc2);
+      acc2 = fma((R)a.z, (R)a.z, acc2); acc2 = fma((R)a.w, (R)a.w, acc2);
+    }
+  } else {
+    for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
+      cplx<R> a = wr[k];
+      for (int i = 0; i < nv; ++i) cfma(a, cs[i], vb[(size_t)i * vstride + k]);
+      wr[k] = a;
+      acc2 = fma(a.re, a.re, acc2);
+      acc2 = fma(a.im, a.im, acc2);
+    }
+  }
+  acc2 = warp_sum_r(acc2);
+  R* shr = reinterpret_cast<R*>(sh);
+  if ((threadIdx.x & 31) == 0) shr[threadIdx.x >> 5] = acc2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R s = 0;
+    for (int wv = 0; wv < RT / 32; ++wv) s += shr[wv];
+    double* p = partial + ((size_t)rhs * maxvec * nblk + blockIdx.x) * 2;
+    p[0] = (double)s;
+    p[1] = 0;
+    __threadfence();
+  }
+  if (!last_cta(counter, rhs, nblk)) return;
+  finish_partials(partial, 1, nblk, maxvec, rhs, nullptr, nrm, ldn, 1);
+  if (threadIdx.x == 0) counter[rhs] = 0;
 }
 
 template <typename R>
@@ -273,6 +302,7 @@ int multi_dot(zd* out, int ldo, const cplx<R>* V, size_t vstride, int nv, const 
               size_t n, int nrhs, ReduceWork& rw, cudaStream_t st) {
   if (nv > rw.maxvec || nrhs > rw.nrhs_cap) return fail(MG_EINVAL, "multi_dot: workspace too small");
   dim3 grid(rw.nblk, nrhs);
+  ProfScope ps("multi_dot", (double)(nv + 1) * nrhs * n * sizeof(cplx<R>), 8.0 * nv * n * nrhs, st);
   multi_dot_kernel<R><<<grid, RT, 0, st>>>(out, ldo, V, vstride, nv, w, n, rw.partial,
                                            rw.counter, rw.nblk, rw.maxvec);
   WMG_LAUNCHED();
@@ -285,6 +315,7 @@ int multi_axpy(cplx<R>* w, const cplx<R>* V, size_t vstride, int nv, const zd* c
   if (nv > 128) return fail(MG_EINVAL, "multi_axpy: too many vectors");
   if (nv == 0) return MG_OK;
   dim3 grid(grid_for(n), nrhs);
+  ProfScope ps("multi_axpy", (double)(nv + 2) * nrhs * n * sizeof(cplx<R>), 8.0 * nv * n * nrhs, st);
   multi_axpy_kernel<R><<<grid, 256, 0, st>>>(w, V, vstride, nv, c, ldc, sgn, n);
   WMG_LAUNCHED();
   return MG_OK;
@@ -295,7 +326,21 @@ int norm2(double* nrm, int ldn, const cplx<R>* w, size_t n, int nrhs, ReduceWork
           cudaStream_t st) {
   if (nrhs > rw.nrhs_cap) return fail(MG_EINVAL, "norm2: workspace too small");
   dim3 grid(rw.nblk, nrhs);
+  ProfScope ps("norm", (double)nrhs * n * sizeof(cplx<R>), 4.0 * n * nrhs, st);
   norm_kernel<R><<<grid, RT, 0, st>>>(nrm, ldn, w, n, rw.partial, rw.counter, rw.nblk, rw.maxvec);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+template <typename R>
+int multi_axpy_norm(cplx<R>* w, const cplx<R>* V, size_t vstride, int nv, const zd* c, int ldc,
+                    double sgn, size_t n, int nrhs, double* nrm, int ldn, ReduceWork& rw,
+                    cudaStream_t st) {
+  if (nv > 128) return fail(MG_EINVAL, "multi_axpy_norm: too many vectors");
+  if (nrhs > rw.nrhs_cap) return fail(MG_EINVAL, "multi_axpy_norm: workspace too small");
+  dim3 grid(rw.nblk, nrhs);
+  multi_axpy_norm_kernel<R><<<grid, RT, 0, st>>>(w, V, vstride, nv, c, ldc, sgn, n, nrm, ldn,
+                                                 rw.partial, rw.counter, rw.nblk, rw.maxvec);
   WMG_LAUNCHED();
   return MG_OK;
 }
@@ -304,6 +349,7 @@ template <typename R>
 int scale_inv(cplx<R>* y, const cplx<R>* x, const double* s, int lds, size_t n, int nrhs,
               cudaStream_t st) {
   dim3 grid(grid_for(n), nrhs);
+  ProfScope ps("scale", 2.0 * nrhs * n * sizeof(cplx<R>), 2.0 * n * nrhs, st);
   scale_inv_kernel<R><<<grid, 256, 0, st>>>(y, x, s, lds, n);
   WMG_LAUNCHED();
   return MG_OK;
@@ -354,6 +400,9 @@ int apply_gamma5(cplx<R>* y, const cplx<R>* x, size_t nsites_total, cudaStream_t
   template int multi_axpy<R>(cplx<R>*, const cplx<R>*, size_t, int, const zd*, int, double, \
                              size_t, int, cudaStream_t);                                   \
   template int norm2<R>(double*, int, const cplx<R>*, size_t, int, ReduceWork&, cudaStream_t); \
+  template int multi_axpy_norm<R>(cplx<R>*, const cplx<R>*, size_t, int, const zd*, int,   \
+                                  double, size_t, int, double*, int, ReduceWork&,          \
+                                  cudaStream_t);                                           \
   template int scale_inv<R>(cplx<R>*, const cplx<R>*, const double*, int, size_t, int,     \
                             cudaStream_t);                                                 \
   template int axpby<R>(cplx<R>*, double, const cplx<R>*, double, size_t, int, cudaStream_t); \

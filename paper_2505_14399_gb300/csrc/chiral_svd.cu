@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ 
 }
 
 // Parallel cyclic Jacobi on a Hermitian c x c matrix per CTA (Brent-Luk round robin).
-__global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const zd* G, int c) {
+__global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const zd* G, int c,
+                                                    double rtol) {
   extern __shared__ zd sm[];
   int ce = c + (c & 1);              // padded to even
   zd* A = sm;                         // ce x ce
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
           zd g = A[a * ce + b];
           double ag = sqrt(norm2(g));
           double da = A[a * ce + a].re, db = A[b * ce + b].re;
-          if (ag > 1e-15 * sqrt(fabs(da * db)) && ag > 1e-300) {
+          if (ag > rtol * sqrt(fabs(da * db)) && ag > 1e-300) {
             double zeta = (db - da) / (2.0 * ag);
             double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             c0 = 1.0 / sqrt(1.0 + tt * tt);
@@ -373,13 +374,15 @@ int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaSt
               bool df64) {
   if (c > MAXC) return fail(MG_EINVAL, "tile_gram: more than 64 columns");
   size_t sh = sizeof(zd) * GR * c;
+  ProfScope ps(df64 ? "svd_gram_df64" : "svd_gram_fp64", 16.0 * B.M * c * B.d * 2,
+               8.0 * B.M * c * (c + 1) / 2 * B.d * 2, st);
   if (df64) gram_kernel<true><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
   else gram_kernel<false><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
   WMG_LAUNCHED();
   return MG_OK;
 }
 
-int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st) {
+int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, double rtol) {
   if (c > MAXC) return fail(MG_EINVAL, "tile_eig: more than 64 columns");
   int ce = c + (c & 1);
   size_t sh = sizeof(zd) * 2 * ce * ce + sizeof(double) * (ce / 2 + 1) + sizeof(zd) * ce +
@@ -390,7 +393,8 @@ int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st) {
                                   200 * 1024));
     attr_set = true;
   }
-  jacobi_kernel<<<ntiles, GT, sh, st>>>(lam, Vec, G, c);
+  ProfScope ps("svd_jacobi_fp64", 32.0 * c * c * ntiles, 0.0, st);
+  jacobi_kernel<<<ntiles, GT, sh, st>>>(lam, Vec, G, c, rtol);
   WMG_LAUNCHED();
   return MG_OK;
 }
@@ -408,6 +412,8 @@ int tile_update(zd* out, int cmax_out, const zd* tiles, int cmax, int c, const z
                                   100 * 1024));
     attr_set = true;
   }
+  ProfScope ps(df64 ? "svd_update_df64" : "svd_update_fp64", 16.0 * B.M * (c + kout) * B.d * 2,
+               8.0 * B.M * c * kout * B.d * 2, st);
   if (df64)
     update_kernel<true><<<B.d * 2, GT, sh, st>>>(out, cmax_out, tiles, cmax, c, Vec, lam, kout,
                                                  scale_inv, B.M);

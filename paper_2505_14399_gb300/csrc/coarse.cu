@@ -336,6 +336,8 @@ int restrict_launch(cplx<R>* vc, const cplx<R>* v, const cplx<R>* P, int k, cons
                                   200 * 1024));
     set = true;
   }
+  ProfScope ps("restrict", (double)sizeof(cplx<R>) * (12.0 * B.nd * B.d * (k + nrhs) + 2.0 * B.d * k * nrhs),
+               8.0 * 12 * B.nd * B.d * k * nrhs, st);
   restrict_kernel<R><<<grid, 256, sh, st>>>(vc, v, P, k, B);
   WMG_LAUNCHED();
   return MG_OK;
@@ -347,6 +349,8 @@ int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const
   size_t total = (size_t)nrhs * B.nd * B.d * 12;
   size_t gsz = (total + 255) / 256;
   size_t cap = (size_t)num_sms() * 16;
+  ProfScope ps("prolong", (double)sizeof(cplx<R>) * (12.0 * B.nd * B.d * (k + nrhs) + 2.0 * B.d * k * nrhs),
+               8.0 * 12 * B.nd * B.d * k * nrhs, st);
   prolong_kernel<R><<<(unsigned)(gsz < cap ? gsz : cap), 256, 0, st>>>(v, vc, P, k, B, total);
   WMG_LAUNCHED();
   return MG_OK;
@@ -376,6 +380,8 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, int k, const zd* links, const
     set = true;
   }
   dim3 grid(B.d, 4);
+  ProfScope ps(df64 ? "galerkin_df64" : "galerkin_fp64", 16.0 * (12.0 * B.nd * B.d * k * 5 + 36.0 * B.nd * B.d),
+               768.0 * k * k * B.nd * B.d, st);
   if (df64) galerkin_hop_kernel<true><<<grid, GTH, sh, st>>>(Op, Xpart, P, k, links, hg, B);
   else galerkin_hop_kernel<false><<<grid, GTH, sh, st>>>(Op, Xpart, P, k, links, hg, B);
   WMG_LAUNCHED();
@@ -390,6 +396,8 @@ int coarse_apply_launch(cplx<R>* y, const cplx<R>* x, const cplx<R>* Op, int k, 
   if (2 * k > 64) return fail(MG_EINVAL, "coarse_apply: 2k > 64");
   dim3 grid(B.d, nrhs);
   size_t sh = sizeof(cplx<R>) * 18 * 2 * k;
+  ProfScope ps("coarse_apply", (double)sizeof(cplx<R>) * B.d * (9.0 * 4 * k * k + 4.0 * k * nrhs),
+               8.0 * 9 * 4 * k * k * B.d * nrhs, st);
   coarse_apply_kernel<R><<<grid, 9 * 2 * k, sh, st>>>(y, x, Op, 2 * k, B);
   WMG_LAUNCHED();
   return MG_OK;

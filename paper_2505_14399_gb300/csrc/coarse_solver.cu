@@ -168,7 +168,11 @@ __global__ void __launch_bounds__(CT) coarse_gmres_kernel(CArgs<R> a) {
   double* scratch = cs + m;                             // [CT/32][m+2][2]
   const int n2k = a.n2k;
   const int spc = a.spc;
-  cplx<R>* sx = reinterpret_cast<cplx<R>*>(scratch + (CT / 32) * (m + 2) * 2);  // [spc][9][n2k]
+  // staged vectors and operator start on a 16-byte boundary (16-byte copies below)
+  uintptr_t p_sx = reinterpret_cast<uintptr_t>(scratch + (CT / 32) * (m + 2) * 2);
+  p_sx = (p_sx + 15) & ~(uintptr_t)15;   // the host reserves 16 bytes for this
+  cplx<R>* sx = reinterpret_cast<cplx<R>*>(p_sx);   // [spc][9][n2k]
+  // spc * 9 * 2k complex numbers: a multiple of 16 bytes, so sOp stays aligned
   cplx<R>* sOp = sx + (size_t)spc * 9 * n2k;          // [spc][9][n2k][n2k] if op_in_smem
   __shared__ double s_res;
 
@@ -190,9 +194,22 @@ __global__ void __launch_bounds__(CT) coarse_gmres_kernel(CArgs<R> a) {
   const int nloc = j1 > j0 ? j1 - j0 : 0;
   const size_t blk_el = (size_t)n2k * n2k;
   if (a.op_in_smem) {
-    // this CTA's coarse sites are contiguous in Op: one coalesced copy per launch
-    const cplx<R>* src = a.Op + (size_t)j0 * 9 * blk_el;
-    for (size_t e = threadIdx.x; e < (size_t)nloc * 9 * blk_el; e += CT) sOp[e] = src[e];
+    // this CTA's coarse sites are contiguous in Op: one coalesced copy per launch, 16-byte
+    // accesses with four loads in flight per thread (both ends are 16-byte aligned: the
+    // slice is a multiple of 9 (2k)^2 complex numbers and the host aligns the layout)
+    const float4* src = reinterpret_cast<const float4*>(a.Op + (size_t)j0 * 9 * blk_el);
+    float4* dst = reinterpret_cast<float4*>(sOp);
+    size_t n16 = (size_t)nloc * 9 * blk_el * sizeof(cplx<R>) / 16;
+    size_t e = threadIdx.x;
+    for (; e + 3 * CT < n16; e += 4 * CT) {
+      float4 v0 = __ldg(src + e), v1 = __ldg(src + e + CT);
+      float4 v2 = __ldg(src + e + 2 * CT), v3 = __ldg(src + e + 3 * CT);
+      dst[e] = v0;
+      dst[e + CT] = v1;
+      dst[e + 2 * CT] = v2;
+      dst[e + 3 * CT] = v3;
+    }
+    for (; e < n16; e += CT) dst[e] = __ldg(src + e);
   }
   __syncthreads();
 
@@ -425,7 +442,7 @@ template <typename R>
 size_t CoarseSolver<R>::smem_bytes() const {
   // H, sn, g, y, hv (zd) + cs, scratch (double); staged vectors and operator added at launch
   size_t z = (size_t)(m + 1) * m + m + (m + 1) + m + (m + 2);
-  return z * sizeof(zd) + sizeof(double) * (m + (CT / 32) * (m + 2) * 2);
+  return z * sizeof(zd) + sizeof(double) * (m + (CT / 32) * (m + 2) * 2) + 16;  // + alignment pad
 }
 
 template <typename R>
@@ -485,6 +502,7 @@ int CoarseSolver<R>::solve(const cplx<R>* Op, const Blocking& B, int k, cplx<R>*
   args.spc = spc;
   args.op_in_smem = op_in_smem;
   void* kargs[] = {&args};
+  ProfScope ps("coarse_gmres", (double)sizeof(cplx<R>) * B.d * 9.0 * n2k * n2k, 0.0, st);
   WMG_CUDA(cudaLaunchCooperativeKernel((void*)coarse_gmres_kernel<R>, dim3(grid), dim3(CT), kargs,
                                        sh, st));
   count_launch();

@@ -40,6 +40,24 @@ void count_launch(long long n = 1);
     if (s_ != MG_OK) return s_;                                                     \
   } while (0)
 
+// ------------------------------------------------------------------ per-kernel timing
+// When enabled (mg_profile_enable), every instrumented launch is bracketed by CUDA events
+// on its own stream; mg_profile_report() aggregates durations with the launch's
+// algorithmic bytes and flops per kernel name.  Disabled: one branch per launch.
+bool prof_enabled();
+void prof_begin(const char* name, double bytes, double flops, cudaStream_t st);
+void prof_end(cudaStream_t st);
+struct ProfScope {
+  bool on;
+  cudaStream_t st;
+  ProfScope(const char* name, double bytes, double flops, cudaStream_t s) : on(prof_enabled()), st(s) {
+    if (on) prof_begin(name, bytes, flops, s);
+  }
+  ~ProfScope() {
+    if (on) prof_end(st);
+  }
+};
+
 // ------------------------------------------------------------------ complex numbers
 template <typename R>
 struct cplx {

@@ -70,12 +70,20 @@ template <typename H, typename S> struct SiteIOHalf {
 template <> struct SiteIO<StF16> : SiteIOHalf<__half2, StF16> {};
 template <> struct SiteIO<StBF16> : SiteIOHalf<__nv_bfloat162, StBF16> {};
 
-// Load a 3x3 link.
-template <typename S>
-__device__ __forceinline__ void load_link(const typename S::elem* L, size_t idx,
+// Load the 3x3 link U_mu(site).  LL = 0: ABI layout [mu][site][3][3] (one link contiguous);
+// LL = 1: lane-contiguous layout [mu][3x3 entry][site], so a warp reading one entry for 32
+// consecutive sites touches one contiguous 32 x element_size span (the solver's copy).
+template <typename S, int LL>
+__device__ __forceinline__ void load_link(const typename S::elem* L, int V, int mu, int site,
                                           cplx<typename S::real> u[9]) {
+  if (LL == 0) {
+    size_t idx = ((size_t)mu * V + site) * 9;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) u[i] = S::ld(L, idx * 9 + i);
+    for (int i = 0; i < 9; ++i) u[i] = S::ld(L, idx + i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) u[i] = S::ld(L, ((size_t)mu * 9 + i) * V + site);
+  }
 }
 
 // Project psi with (1 + s gamma_mu) to the upper spin pair h (2 spins x 3 colours),
@@ -159,7 +167,7 @@ template <typename R> __device__ __forceinline__ R wgt(const KGeom& g, int mu);
 template <> __device__ __forceinline__ double wgt<double>(const KGeom& g, int mu) { return g.wd[mu]; }
 template <> __device__ __forceinline__ float wgt<float>(const KGeom& g, int mu) { return g.wf[mu]; }
 
-template <int MU, int DAG, typename S>
+template <int MU, int DAG, typename S, int LL>
 __device__ __forceinline__ void hop_pair(const KGeom& g, int site, const int c[4],
                                          const typename S::elem* in, size_t in_off,
                                          bool half_in, const typename S::elem* links,
@@ -177,7 +185,7 @@ __device__ __forceinline__ void hop_pair(const KGeom& g, int site, const int c[4
     project<MU, SF, R>(p, h);
 #pragma unroll
     for (int i = 0; i < 6; ++i) h[i] = cf * h[i];
-    load_link<S>(links, (size_t)MU * g.V + site, u);
+    load_link<S, LL>(links, g.V, MU, site, u);
     mul_link<R>(u, h, gg);
     accumulate<MU, SF, R>(acc, gg);
   }
@@ -190,7 +198,7 @@ __device__ __forceinline__ void hop_pair(const KGeom& g, int site, const int c[4
     project<MU, SB, R>(p, h);
 #pragma unroll
     for (int i = 0; i < 6; ++i) h[i] = cf * h[i];
-    load_link<S>(links, (size_t)MU * g.V + nb, u);
+    load_link<S, LL>(links, g.V, MU, nb, u);
     mul_link_dag<R>(u, h, gg);
     accumulate<MU, SB, R>(acc, gg);
   }
@@ -198,7 +206,7 @@ __device__ __forceinline__ void hop_pair(const KGeom& g, int site, const int c[4
 
 // parity < 0: out = in - kappa H in (full lattice).  parity p >= 0: out_p = -kappa H in_{1-p}
 // on half-lattice (checkerboard-indexed) fields.
-template <typename S, int DAG, int TPB, int MINB>
+template <typename S, int DAG, int TPB, int MINB, int LL>
 __global__ void __launch_bounds__(TPB, MINB)
 dslash_kernel(typename S::elem* __restrict__ out, const typename S::elem* __restrict__ in,
               const typename S::elem* __restrict__ links, KGeom g, int parity, int nsites,
@@ -231,10 +239,10 @@ dslash_kernel(typename S::elem* __restrict__ out, const typename S::elem* __rest
   for (int k = 0; k < 12; ++k) acc[k] = {0, 0};
   bool half_in = parity >= 0;
   size_t in_off = rhs * in_stride;
-  hop_pair<0, DAG, S>(g, site, c, in, in_off, half_in, links, acc);
-  hop_pair<1, DAG, S>(g, site, c, in, in_off, half_in, links, acc);
-  hop_pair<2, DAG, S>(g, site, c, in, in_off, half_in, links, acc);
-  hop_pair<3, DAG, S>(g, site, c, in, in_off, half_in, links, acc);
+  hop_pair<0, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+  hop_pair<1, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+  hop_pair<2, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+  hop_pair<3, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
   R mk = (R)(-g.kappa);
   cplx<R> res[12];
   if (parity < 0) {
@@ -279,61 +287,101 @@ struct Shape {
 constexpr Shape kShapes[] = {{128, 1}, {128, 6}, {128, 8}, {256, 4}, {64, 16}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-template <typename S, int DAG, int TPB, int MINB>
+template <typename S, int DAG, int TPB, int MINB, int LL>
 void launch_shape(void* out, const void* in, const void* links, const KGeom& k, int parity,
                   int nsites, int nrhs, cudaStream_t st, size_t in_stride, size_t out_stride) {
   typedef typename S::elem E;
   dim3 grid((nsites + TPB - 1) / TPB, nrhs);
-  dslash_kernel<S, DAG, TPB, MINB><<<grid, TPB, 0, st>>>((E*)out, (const E*)in, (const E*)links, k,
-                                                         parity, nsites, in_stride, out_stride);
+  dslash_kernel<S, DAG, TPB, MINB, LL><<<grid, TPB, 0, st>>>((E*)out, (const E*)in,
+                                                             (const E*)links, k, parity, nsites,
+                                                             in_stride, out_stride);
 }
 
-template <typename S, int DAG>
+template <typename S, int DAG, int LL>
 void launch_variant(int v, void* out, const void* in, const void* links, const KGeom& k,
                     int parity, int nsites, int nrhs, cudaStream_t st, size_t is, size_t os) {
   switch (v) {
-    case 1: launch_shape<S, DAG, 128, 6>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
-    case 2: launch_shape<S, DAG, 128, 8>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
-    case 3: launch_shape<S, DAG, 256, 4>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
-    case 4: launch_shape<S, DAG, 64, 16>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
-    default: launch_shape<S, DAG, 128, 1>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    case 1: launch_shape<S, DAG, 128, 6, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    case 2: launch_shape<S, DAG, 128, 8, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    case 3: launch_shape<S, DAG, 256, 4, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    case 4: launch_shape<S, DAG, 64, 16, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    default: launch_shape<S, DAG, 128, 1, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
   }
 }
 
 template <typename S>
 int launch_typed(void* out, const void* in, const void* links, const Geom& g, int parity,
                  int dagger, int nrhs, cudaStream_t st, size_t in_stride, size_t out_stride,
-                 int dtype) {
+                 int dtype, int layout) {
   KGeom k = to_kgeom(g);
   int nsites = parity < 0 ? g.V : g.V / 2;
   auto run = [&](int v) {
-    if (dagger) launch_variant<S, 1>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
-    else launch_variant<S, 0>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+    if (layout == 0) {
+      if (dagger) launch_variant<S, 1, 0>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+      else launch_variant<S, 0, 0>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+    } else {
+      if (dagger) launch_variant<S, 1, 1>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+      else launch_variant<S, 0, 1>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+    }
   };
-  int v = tuned_variant(dtype, parity, dagger, g.V, nrhs, st, kNumShapes, run);
+  int v = tuned_variant(dtype + 16 * layout, parity, dagger, g.V, nrhs, st, kNumShapes, run);
   if (v < 0) return fail(MG_ECUDA, "dslash autotune failed");
+  // algorithmic bytes: in + out spinors per rhs and each link once (parity: all 4V links)
+  double real_bytes = (double)sizeof(typename S::real) * (sizeof(typename S::elem) == 4 ? 0.5 : 1.0);
+  double per_site = parity < 0 ? 48.0 * nrhs + 72.0 : 48.0 * nrhs + 144.0;
+  ProfScope ps(dtype == MG_C128 ? "dslash_c128" : dtype == MG_C64 ? "dslash_c64"
+               : dtype == MG_F16 ? "dslash_f16" : "dslash_bf16",
+               per_site * real_bytes * nsites, 1320.0 * nsites * nrhs, st);
   run(v);
   WMG_LAUNCHED();
   return MG_OK;
 }
 
+template <typename To>
+__global__ void link_to_lanes_kernel(cplx<To>* dst, const zd* __restrict__ src, int V) {
+  size_t total = (size_t)4 * V * 9;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    // e enumerates the destination [mu][entry][site]
+    size_t site = e % V, rest = e / V;
+    int entry = (int)(rest % 9), mu = (int)(rest / 9);
+    zd v = src[((size_t)mu * V + site) * 9 + entry];
+    dst[e] = {(To)v.re, (To)v.im};
+  }
+}
+
 }  // namespace
+
+template <typename To>
+int link_to_lanes(cplx<To>* dst, const zd* src, int V, cudaStream_t st) {
+  size_t total = (size_t)4 * V * 9;
+  size_t g = (total + 255) / 256, cap = (size_t)num_sms() * 16;
+  link_to_lanes_kernel<To><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(dst, src, V);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+template int link_to_lanes<double>(zd*, const zd*, int, cudaStream_t);
+template int link_to_lanes<float>(zf*, const zd*, int, cudaStream_t);
 
 int dslash_launch(int dtype, void* out, const void* in, const void* links, const Geom& g,
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,
-                  size_t out_stride) {
+                  size_t out_stride, int link_layout) {
   size_t half = (size_t)12 * (parity < 0 ? g.V : g.V / 2);
   if (in_stride == 0) in_stride = half;
   if (out_stride == 0) out_stride = half;
   switch (dtype) {
     case MG_C128:
-      return launch_typed<StC128>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype);
+      return launch_typed<StC128>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype,
+                                  link_layout);
     case MG_C64:
-      return launch_typed<StC64>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype);
+      return launch_typed<StC64>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype,
+                                  link_layout);
     case MG_F16:
-      return launch_typed<StF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype);
+      return launch_typed<StF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype,
+                                  link_layout);
     case MG_BF16:
-      return launch_typed<StBF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype);
+      return launch_typed<StBF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype,
+                                  link_layout);
   }
   return fail(MG_EINVAL, "dslash: unknown dtype");
 }

@@ -10,9 +10,13 @@ namespace wmg {
 
 // ------------------------------------------------------------------ Dslash
 // in/out strides are in complex elements between right-hand sides (0 = field size).
+// link_layout 0: ABI [mu][site][3][3]; 1: lane-contiguous [mu][9][site] (link_to_lanes).
 int dslash_launch(int dtype, void* out, const void* in, const void* links, const Geom& g,
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,
-                  size_t out_stride);
+                  size_t out_stride, int link_layout = 0);
+// dst[mu][e][site] = src[mu][site][e] (e < 9), converting complex double to To.
+template <typename To>
+int link_to_lanes(cplx<To>* dst, const zd* src, int V, cudaStream_t st);
 
 // Autotuned launch shape for a kernel with `nvar` candidate shapes; `run(v)` launches
 // shape v on the caller's arguments.  Returns the chosen shape or -1 on a CUDA error.
@@ -41,6 +45,11 @@ int multi_dot(zd* out, int ldo, const cplx<R>* V, size_t vstride, int nv, const 
 template <typename R>
 int multi_axpy(cplx<R>* w, const cplx<R>* V, size_t vstride, int nv, const zd* c, int ldc,
                double sgn, size_t n, int nrhs, cudaStream_t st);
+// multi_axpy followed by nrm[rhs*ldn] = ||w[rhs]||_2, in one pass over w
+template <typename R>
+int multi_axpy_norm(cplx<R>* w, const cplx<R>* V, size_t vstride, int nv, const zd* c, int ldc,
+                    double sgn, size_t n, int nrhs, double* nrm, int ldn, ReduceWork& rw,
+                    cudaStream_t st);
 // nrm[rhs*ldn] = ||w[rhs]||_2
 template <typename R>
 int norm2(double* nrm, int ldn, const cplx<R>* w, size_t n, int nrhs, ReduceWork& rw,
@@ -175,7 +184,9 @@ int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaSt
 // Hermitian eigen-decomposition of every G_t (c x c) by parallel cyclic Jacobi; returns
 // eigenvalues descending in lam[t][c] and eigenvectors in Vec[t][c][c] (column i at
 // Vec[t][*][i], row-major c x c).
-int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st);
+// rtol: a pair is rotated while |G_ab| > rtol sqrt(|G_aa G_bb|) (relative accuracy target).
+int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st,
+             double rtol = 1e-15);
 // out[t][i][row] = sum_c A[t][c][row] Vec[t][c][i] * (scale_inv ? 1/sqrt(lam[t][i]) : 1)
 // for i < kout; out tile stride cmax_out*M.
 // df64: sums of products in double-float arithmetic (df64.cuh) instead of FP64.

@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "reduce.cuh"
 
 namespace wmg {
 
@@ -37,16 +38,13 @@ __global__ void init_kernel(zd* small, SmallLayout L, const double* beta, double
   res[r] = beta[r];
 }
 
-// Finish column j: H[:, j] += h2, H[j+1, j] = ||w||, rotate, new rotation, residual.
-__global__ void givens_kernel(zd* small, SmallLayout L, int j, const double* wnorm, double* res,
-                              int nrhs) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
-  zd* s = small + (size_t)r * L.stride();
+// Finish column j of one system's Hessenberg matrix: H[:, j] += h2, H[j+1, j] = ||w||,
+// apply the previous rotations, form the new one, update g; returns |g_{j+1}|.
+__device__ double givens_update(zd* s, SmallLayout L, int j, double wnorm) {
   zd* col = s + L.H() + (size_t)j * (L.m + 1);
   const zd* h2 = s + L.h2();
   for (int i = 0; i <= j; ++i) col[i] = col[i] + h2[i];
-  col[j + 1] = {wnorm[r], 0};
+  col[j + 1] = {wnorm, 0};
   zd* cs = s + L.cs();
   zd* sn = s + L.sn();
   for (int i = 0; i < j; ++i) {
@@ -84,7 +82,170 @@ __global__ void givens_kernel(zd* small, SmallLayout L, int j, const double* wno
   zd gj = g[j];
   g[j] = c * gj;
   g[j + 1] = -cmulc(sv, gj);  // -conj(s) g_j
-  res[r] = sqrt(norm2(g[j + 1]));
+  return sqrt(norm2(g[j + 1]));
+}
+
+// CGS pass 1 update fused with the pass 2 projections:
+//   w -= sum_i c_i V_i   then   h2_i = V_i^dag w   (i < nv), one sweep over w.
+template <typename R>
+__global__ void __launch_bounds__(RT)
+cgs_update_dot_kernel(cplx<R>* w, const cplx<R>* __restrict__ V, size_t vstride, int nv,
+                      const zd* c, zd* h2, int ld, size_t n, double* partial, unsigned* counter,
+                      int nblk, int maxvec) {
+  constexpr int G = 8;
+  __shared__ cplx<R> cs[128];
+  __shared__ double sh[(RT / 32) * G * 2];
+  int rhs = blockIdx.y;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    zd v = c[(size_t)rhs * ld + i];
+    cs[i] = {(R)(-v.re), (R)(-v.im)};
+  }
+  __syncthreads();
+  size_t chunk = reduce_chunk(n, nblk);
+  size_t k0 = (size_t)blockIdx.x * chunk;
+  size_t k1 = min(n, k0 + chunk);
+  cplx<R>* wr = w + (size_t)rhs * n;
+  const cplx<R>* vb = V + (size_t)rhs * n;
+  if (nv <= G && sizeof(R) == 4 && ((k0 | k1 | vstride) & 1) == 0) {
+    // one sweep: the basis entries stay in registers between the update and the dots
+    R ar[G], ai[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) { ar[q] = 0; ai[q] = 0; }
+    float4* w4 = reinterpret_cast<float4*>(wr);
+    const float4* v4 = reinterpret_cast<const float4*>(vb);
+    size_t vs4 = vstride / 2;
+    for (size_t k = k0 / 2 + threadIdx.x; k < k1 / 2; k += RT) {
+      float4 a = w4[k];
+      float4 v[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        if (q < nv) {
+          v[q] = v4[(size_t)q * vs4 + k];
+          float cr = (float)cs[q].re, ci = (float)cs[q].im;
+          a.x = fmaf(cr, v[q].x, a.x); a.x = fmaf(-ci, v[q].y, a.x);
+          a.y = fmaf(cr, v[q].y, a.y); a.y = fmaf(ci, v[q].x, a.y);
+          a.z = fmaf(cr, v[q].z, a.z); a.z = fmaf(-ci, v[q].w, a.z);
+          a.w = fmaf(cr, v[q].w, a.w); a.w = fmaf(ci, v[q].z, a.w);
+        }
+      }
+      w4[k] = a;
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        if (q < nv) {
+          ar[q] = fma((R)v[q].x, (R)a.x, ar[q]); ar[q] = fma((R)v[q].y, (R)a.y, ar[q]);
+          ar[q] = fma((R)v[q].z, (R)a.z, ar[q]); ar[q] = fma((R)v[q].w, (R)a.w, ar[q]);
+          ai[q] = fma((R)v[q].x, (R)a.y, ai[q]); ai[q] = fma(-(R)v[q].y, (R)a.x, ai[q]);
+          ai[q] = fma((R)v[q].z, (R)a.w, ai[q]); ai[q] = fma(-(R)v[q].w, (R)a.z, ai[q]);
+        }
+      }
+    }
+    cta_store_partials<R, G>(ar, ai, nv, 0, rhs, maxvec, nblk, partial, reinterpret_cast<R*>(sh));
+    if (!last_cta(counter, rhs, nblk)) return;
+    finish_partials(partial, nv, nblk, maxvec, rhs, h2, nullptr, ld, 0);
+    if (threadIdx.x == 0) counter[rhs] = 0;
+    return;
+  }
+  // general case: update sweep, then projection sweeps over groups of G vectors
+  for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
+    cplx<R> a = wr[k];
+    for (int i = 0; i < nv; ++i) cfma(a, cs[i], vb[(size_t)i * vstride + k]);
+    wr[k] = a;
+  }
+  // projections on the updated w (each thread rereads its own elements: L1/L2 hits)
+  for (int i0 = 0; i0 < nv; i0 += G) {
+    int ni = min(G, nv - i0);
+    R ar[G], ai[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) { ar[q] = 0; ai[q] = 0; }
+    for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
+      cplx<R> b = wr[k];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        if (q < ni) {
+          cplx<R> a = vb[(size_t)(i0 + q) * vstride + k];
+          ar[q] = fma(a.re, b.re, ar[q]); ar[q] = fma(a.im, b.im, ar[q]);
+          ai[q] = fma(a.re, b.im, ai[q]); ai[q] = fma(-a.im, b.re, ai[q]);
+        }
+      }
+    }
+    cta_store_partials<R, G>(ar, ai, ni, i0, rhs, maxvec, nblk, partial,
+                             reinterpret_cast<R*>(sh));
+  }
+  if (!last_cta(counter, rhs, nblk)) return;
+  finish_partials(partial, nv, nblk, maxvec, rhs, h2, nullptr, ld, 0);
+  if (threadIdx.x == 0) counter[rhs] = 0;
+}
+
+// CGS pass 2 update fused with the norm and the Givens step:
+//   w -= sum_i c_i V_i ; ||w|| ; column j of the Hessenberg matrix reduced (last CTA).
+template <typename R>
+__global__ void __launch_bounds__(RT)
+cgs_update_norm_givens_kernel(cplx<R>* w, const cplx<R>* __restrict__ V, size_t vstride,
+                              int nv, zd* small, SmallLayout L, int j, size_t n, double* wnorm,
+                              double* res, double* partial, unsigned* counter, int nblk,
+                              int maxvec) {
+  __shared__ cplx<R> cs[128];
+  __shared__ double sh[64];
+  int rhs = blockIdx.y;
+  int nrhs = gridDim.y;
+  zd* sm = small + (size_t)rhs * L.stride();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    zd v = sm[L.h2() + i];
+    cs[i] = {(R)(-v.re), (R)(-v.im)};
+  }
+  __syncthreads();
+  size_t chunk = reduce_chunk(n, nblk);
+  size_t k0 = (size_t)blockIdx.x * chunk;
+  size_t k1 = min(n, k0 + chunk);
+  cplx<R>* wr = w + (size_t)rhs * n;
+  const cplx<R>* vb = V + (size_t)rhs * n;
+  R acc2 = 0;
+  if (sizeof(R) == 4 && ((k0 | k1 | vstride) & 1) == 0) {
+    float4* w4 = reinterpret_cast<float4*>(wr);
+    const float4* v4 = reinterpret_cast<const float4*>(vb);
+    size_t vs4 = vstride / 2;
+    for (size_t k = k0 / 2 + threadIdx.x; k < k1 / 2; k += RT) {
+      float4 a = w4[k];
+      for (int i = 0; i < nv; ++i) {
+        float4 v = v4[(size_t)i * vs4 + k];
+        float cr = (float)cs[i].re, ci = (float)cs[i].im;
+        a.x = fmaf(cr, v.x, a.x); a.x = fmaf(-ci, v.y, a.x);
+        a.y = fmaf(cr, v.y, a.y); a.y = fmaf(ci, v.x, a.y);
+        a.z = fmaf(cr, v.z, a.z); a.z = fmaf(-ci, v.w, a.z);
+        a.w = fmaf(cr, v.w, a.w); a.w = fmaf(ci, v.z, a.w);
+      }
+      w4[k] = a;
+      acc2 = fma((R)a.x, (R)a.x, acc2); acc2 = fma((R)a.y, (R)a.y, acc2);
+      acc2 = fma((R)a.z, (R)a.z, acc2); acc2 = fma((R)a.w, (R)a.w, acc2);
+    }
+  } else {
+    for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
+      cplx<R> a = wr[k];
+      for (int i = 0; i < nv; ++i) cfma(a, cs[i], vb[(size_t)i * vstride + k]);
+      wr[k] = a;
+      acc2 = fma(a.re, a.re, acc2);
+      acc2 = fma(a.im, a.im, acc2);
+    }
+  }
+  acc2 = warp_sum_r(acc2);
+  R* shr = reinterpret_cast<R*>(sh);
+  if ((threadIdx.x & 31) == 0) shr[threadIdx.x >> 5] = acc2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R t = 0;
+    for (int wv = 0; wv < RT / 32; ++wv) t += shr[wv];
+    double* p = partial + ((size_t)rhs * maxvec * nblk + blockIdx.x) * 2;
+    p[0] = (double)t;
+    p[1] = 0;
+    __threadfence();
+  }
+  if (!last_cta(counter, rhs, nblk)) return;
+  finish_partials(partial, 1, nblk, maxvec, rhs, nullptr, wnorm, 1, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    counter[rhs] = 0;
+    res[(size_t)j * nrhs + rhs] = givens_update(sm, L, j, wnorm[rhs]);
+  }
 }
 
 // Back substitution R y = g over the first `steps` columns.
@@ -161,14 +322,24 @@ int Gmres<R>::arnoldi_step(const Op<R>& A, const Op<R>* M, int j, cudaStream_t s
     WMG_TRY(A(w, vj, st));
   }
   zd* Hcol = small + L.H() + (size_t)j * (m + 1);
+  // CGS2 in three sweeps: projections; update + re-projections; update + norm + Givens
   WMG_TRY(multi_dot<R>(Hcol, L.stride(), V, fs, j + 1, w, n, nrhs, rw, st));
-  WMG_TRY(multi_axpy<R>(w, V, fs, j + 1, Hcol, L.stride(), -1.0, n, nrhs, st));
-  WMG_TRY(multi_dot<R>(small + L.h2(), L.stride(), V, fs, j + 1, w, n, nrhs, rw, st));
-  WMG_TRY(multi_axpy<R>(w, V, fs, j + 1, small + L.h2(), L.stride(), -1.0, n, nrhs, st));
-  WMG_TRY(norm2<R>(dnorm, 1, w, n, nrhs, rw, st));
-  givens_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, j, dnorm, reshist + (size_t)j * nrhs,
-                                                 nrhs);
+  dim3 grid(rw.nblk, nrhs);
+  double fb = (double)nrhs * n * sizeof(cplx<R>);
+  {
+  ProfScope ps("cgs_update_dot", (j + 3) * fb, 16.0 * (j + 1) * n * nrhs, st);
+  cgs_update_dot_kernel<R><<<grid, RT, 0, st>>>(w, V, fs, j + 1, Hcol, small + L.h2(),
+                                               L.stride(), n, rw.partial, rw.counter, rw.nblk,
+                                               rw.maxvec);
   WMG_LAUNCHED();
+  }
+  {
+  ProfScope ps("cgs_update_norm", (j + 3) * fb, 8.0 * (j + 2) * n * nrhs, st);
+  cgs_update_norm_givens_kernel<R><<<grid, RT, 0, st>>>(w, V, fs, j + 1, small, L, j, n, dnorm,
+                                                       reshist, rw.partial, rw.counter,
+                                                       rw.nblk, rw.maxvec);
+  WMG_LAUNCHED();
+  }
   WMG_TRY(scale_inv<R>(V + (size_t)(j + 1) * fs, w, dnorm, 1, n, nrhs, st));
   return MG_OK;
 }

@@ -17,8 +17,9 @@ struct mg_handle {
   int k = 0;
   size_t nf = 0;   // complex entries per fine field
   size_t nc = 0;   // complex entries per coarse field
-  zd* links64 = nullptr;
-  zf* links32 = nullptr;
+  zd* links64 = nullptr;       // ABI layout (Galerkin, gradient)
+  zd* links64L = nullptr;      // lane-contiguous [mu][9][site] copies for the stencil
+  zf* links32L = nullptr;
   zd* P64 = nullptr;
   zf* P32 = nullptr;
   double* sigma = nullptr;   // [tile][k]
@@ -97,11 +98,13 @@ int create_handle(mg_handle** out, const void* links, const mg_params* p, bool n
   h->nc = (size_t)h->B.d * 2 * h->k;
   size_t lb = (size_t)4 * h->g.V * 9;
   WMG_CUDA(cudaMalloc(&h->links64, lb * sizeof(zd)));
-  WMG_CUDA(cudaMalloc(&h->links32, lb * sizeof(zf)));
+  WMG_CUDA(cudaMalloc(&h->links64L, lb * sizeof(zd)));
+  WMG_CUDA(cudaMalloc(&h->links32L, lb * sizeof(zf)));
   Staged sl;
   WMG_TRY(stage_in(sl, links, lb * sizeof(zd), st));
   WMG_CUDA(cudaMemcpyAsync(h->links64, sl.dev, lb * sizeof(zd), cudaMemcpyDeviceToDevice, st));
-  WMG_TRY((convert<float, double>(h->links32, h->links64, nullptr, 0, lb, 1, st)));
+  WMG_TRY(link_to_lanes<double>(h->links64L, h->links64, h->g.V, st));
+  WMG_TRY(link_to_lanes<float>(h->links32L, h->links64, h->g.V, st));
   size_t ntile = (size_t)h->B.d * 2;
   WMG_CUDA(cudaMalloc(&h->P64, ntile * h->k * h->B.M * sizeof(zd)));
   WMG_CUDA(cudaMalloc(&h->P32, ntile * h->k * h->B.M * sizeof(zf)));
@@ -123,9 +126,9 @@ int smooth_stream(mg_handle* h, cplx<R>* psi, cplx<R>* phi, cplx<R>* tmp, Gmres<
   int r = p.r;
   WMG_TRY(gaussian_fill<R>(phi, p.seed, (unsigned)(s * r), r, h->g.V, st));
   int dt = sizeof(R) == 8 ? MG_C128 : MG_C64;
-  const void* L = sizeof(R) == 8 ? (const void*)h->links64 : (const void*)h->links32;
+  const void* L = sizeof(R) == 8 ? (const void*)h->links64L : (const void*)h->links32L;
   Op<R> D = [h, dt, L, r](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
-    return dslash_launch(dt, out, in, L, h->g, -1, 0, r, s2, h->nf, h->nf);
+    return dslash_launch(dt, out, in, L, h->g, -1, 0, r, s2, h->nf, h->nf, 1);
   };
   WMG_TRY(D(tmp, phi, st));
   WMG_TRY(axpby<R>(tmp, 0.0, tmp, -1.0, h->nf * r, 1, st));   // tmp = -D phi
@@ -166,6 +169,8 @@ int run_setup(mg_handle* h, cudaStream_t st) {
   int kk = 0;
   // sums of products in double-float when asked, or by default when the test vectors are FP32
   const bool df = p.fp64_emulation > 0 || (p.fp64_emulation < 0 && sizeof(R) == 4);
+  // rotate only above the accuracy of the Gram sums (FP64 ~1e-16, double-float ~1e-14)
+  const double eig_tol = df ? 1e-13 : 1e-15;
   for (int s = 0; s < p.n_s; ++s) {
     STEP(smooth_stream<R>(h, psi, phi, tmp, gm, s, st));
     STEP(chiral_gather<R>(cur, cmax, kk, psi, r, h->B, st));
@@ -173,12 +178,12 @@ int run_setup(mg_handle* h, cudaStream_t st) {
     int kn = c < k ? c : k;
     bool last = s == p.n_s - 1;
     STEP(tile_gram(G, cur, cmax, c, h->B, st, df));
-    STEP(tile_eig(lam, Vec, G, c, (int)ntile, st));
+    STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, eig_tol));
     if (p.svd_refine > 0 || (p.svd_refine < 0 && sizeof(R) == 8)) {
       // B = A V (all c columns), then a second Gram/eig pass on B
       STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, c, 0, h->B, st, df));
       STEP(tile_gram(G, oth, cmax, c, h->B, st, df));
-      STEP(tile_eig(lam, Vec, G, c, (int)ntile, st));
+      STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, eig_tol));
       STEP(tile_update(cur, cmax, oth, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st, df));
     } else {
       STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st, df));
@@ -241,7 +246,7 @@ int ensure_solver(mg_handle* h, int nrhs) {
 // Typed views of the handle's precision-dependent members.
 template <typename R> struct Lvl;
 template <> struct Lvl<double> {
-  static const void* links(mg_handle* h) { return h->links64; }
+  static const void* links(mg_handle* h) { return h->links64L; }
   static const zd* P(mg_handle* h) { return h->P64; }
   static const zd* Op(mg_handle* h) { return h->Op64; }
   static Gmres<double>& coarse(mg_handle* h) { return h->coarse64; }
@@ -255,7 +260,7 @@ template <> struct Lvl<double> {
   static constexpr int dtype = MG_C128;
 };
 template <> struct Lvl<float> {
-  static const void* links(mg_handle* h) { return h->links32; }
+  static const void* links(mg_handle* h) { return h->links32L; }
   static const zf* P(mg_handle* h) { return h->P32; }
   static const zf* Op(mg_handle* h) { return h->Op32; }
   static Gmres<float>& coarse(mg_handle* h) { return h->coarse32; }
@@ -272,7 +277,8 @@ template <> struct Lvl<float> {
 template <typename R>
 Op<R> fine_op(mg_handle* h, int nrhs) {
   return [h, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t st) -> int {
-    return dslash_launch(Lvl<R>::dtype, out, in, Lvl<R>::links(h), h->g, -1, 0, nrhs, st, h->nf, h->nf);
+    return dslash_launch(Lvl<R>::dtype, out, in, Lvl<R>::links(h), h->g, -1, 0, nrhs, st, h->nf,
+                         h->nf, 1);
   };
 }
 
@@ -415,7 +421,7 @@ int check_ready(mg_handle* h, bool need_coarse) {
 
 mg_handle::~mg_handle() {
   free_solver();
-  dfree(links64); dfree(links32); dfree(P64); dfree(P32); dfree(sigma); dfree(hist);
+  dfree(links64); dfree(links64L); dfree(links32L); dfree(P64); dfree(P32); dfree(sigma); dfree(hist);
   dfree(Op64); dfree(Op32);
 }
 
@@ -562,6 +568,22 @@ extern "C" int mg_test_vectors(void* out, const void* links, const mg_params* p,
   }
   WMG_TRY(stage_out_finish(so, out, fr * sizeof(zd), st));
   WMG_CUDA(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+extern "C" int mg_apply_fine(mg_handle* h, void* out, const void* in, int nrhs, int dtype,
+                             int dagger, void* stream) {
+  if (!h || !out || !in || nrhs < 1) return fail(MG_EINVAL, "mg_apply_fine: bad arguments");
+  if (out == in) return fail(MG_EINVAL, "mg_apply_fine: out must not alias in");
+  if (dtype != MG_C128 && dtype != MG_C64) return fail(MG_EINVAL, "mg_apply_fine: dtype");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bytes = h->nf * nrhs * (dtype == MG_C128 ? sizeof(zd) : sizeof(zf));
+  Staged si, so;
+  WMG_TRY(stage_in(si, in, bytes, st));
+  WMG_TRY(stage_out_alloc(so, out, bytes, st));
+  const void* L = dtype == MG_C128 ? (const void*)h->links64L : (const void*)h->links32L;
+  WMG_TRY(dslash_launch(dtype, so.dev, si.dev, L, h->g, -1, dagger, nrhs, st, h->nf, h->nf, 1));
+  WMG_TRY(stage_out_finish(so, out, bytes, st));
   return MG_OK;
 }
 

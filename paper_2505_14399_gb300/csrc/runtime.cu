@@ -1,7 +1,11 @@
 // Error reporting, geometry validation and host/device staging of ABI arguments.
 #include <atomic>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -102,7 +106,98 @@ int stage_out_finish(Staged& s, void* p, size_t bytes, cudaStream_t st) {
   return MG_OK;
 }
 
+// ------------------------------------------------------------------ per-kernel timing
+namespace {
+struct ProfRec {
+  const char* name;
+  double bytes, flops;
+  int ev0, ev1;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<cudaEvent_t> g_prof_events;
+std::vector<ProfRec> g_prof_recs;
+size_t g_prof_next = 0;
+std::vector<int> g_prof_open;   // stack of open records (launches do not nest across threads)
+std::string g_prof_json;
+}  // namespace
+
+bool prof_enabled() { return g_prof_on; }
+
+void prof_begin(const char* name, double bytes, double flops, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof_next + 2 > g_prof_events.size()) {
+    g_prof_open.push_back(-1);
+    return;
+  }
+  int e0 = (int)g_prof_next++, e1 = (int)g_prof_next++;
+  cudaEventRecord(g_prof_events[e0], st);
+  g_prof_recs.push_back({name, bytes, flops, e0, e1});
+  g_prof_open.push_back((int)g_prof_recs.size() - 1);
+}
+
+void prof_end(cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof_open.empty()) return;
+  int r = g_prof_open.back();
+  g_prof_open.pop_back();
+  if (r >= 0) cudaEventRecord(g_prof_events[g_prof_recs[r].ev1], st);
+}
+
 }  // namespace wmg
+
+extern "C" int mg_profile_enable(int enable, int max_launches) {
+  using namespace wmg;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_recs.clear();
+  g_prof_open.clear();
+  g_prof_next = 0;
+  if (enable) {
+    size_t need = (size_t)(max_launches > 0 ? max_launches : 100000) * 2;
+    while (g_prof_events.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return fail(MG_ECUDA, "mg_profile_enable: event");
+      g_prof_events.push_back(e);
+    }
+  }
+  g_prof_on = enable != 0;
+  return MG_OK;
+}
+
+extern "C" const char* mg_profile_report(void) {
+  using namespace wmg;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  struct Agg {
+    long long n = 0;
+    double ms = 0, bytes = 0, flops = 0;
+  };
+  std::map<std::string, Agg> agg;
+  for (auto& r : g_prof_recs) {
+    float ms = 0;
+    if (cudaEventSynchronize(g_prof_events[r.ev1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, g_prof_events[r.ev0], g_prof_events[r.ev1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    Agg& a = agg[r.name];
+    a.n += 1;
+    a.ms += ms;
+    a.bytes += r.bytes;
+    a.flops += r.flops;
+  }
+  std::ostringstream os;
+  os << "{";
+  bool first = true;
+  for (auto& kv : agg) {
+    if (!first) os << ",";
+    first = false;
+    os << "\"" << kv.first << "\":{\"launches\":" << kv.second.n << ",\"ms\":" << kv.second.ms
+       << ",\"bytes\":" << kv.second.bytes << ",\"flops\":" << kv.second.flops << "}";
+  }
+  os << "}";
+  g_prof_json = os.str();
+  return g_prof_json.c_str();
+}
 
 extern "C" const char* mg_last_error(void) { return wmg::g_last_error.c_str(); }
 

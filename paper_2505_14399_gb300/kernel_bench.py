@@ -48,15 +48,23 @@ def bench_dslash(a, dev, flush):
     psi = synthetic.gaussian_rhs(dims, 2, a.nrhs)
     if a.parity >= 0:
         psi = psi[:, : V // 2]
-    Ut = _field(U, a.dtype, dev)
     pt = _field(np.ascontiguousarray(psi), a.dtype, dev)
     out = torch.empty_like(pt)
-    fn = lambda: api.dslash(pt, Ut, dims, 0.12, parity=a.parity, out=out)
+    if a.layout == "lanes":
+        # the solver's stencil: the hierarchy's lane-contiguous link copy
+        if a.parity >= 0 or a.dtype not in ("c128", "c64"):
+            raise SystemExit("lane-contiguous links: full operator, c128/c64 only")
+        p = api.params(dims, (2, 2, 2, 2), 0.12, 4, 4, 1)
+        h = api.Hierarchy(torch.from_numpy(U).to(dev), p, setup=False)
+        fn = lambda: h.apply_fine(pt, out=out)
+    else:
+        Ut = _field(U, a.dtype, dev)
+        fn = lambda: api.dslash(pt, Ut, dims, 0.12, parity=a.parity, out=out)
     t, tmin = _timeit(fn, a.reps, flush)
     sites = V if a.parity < 0 else V // 2
     eb = BYTES_PER_SITE[a.dtype] / 120.0
     byts = sites * (48 * a.nrhs + 72) * eb if a.parity < 0 else sites * (48 * a.nrhs + 144) * eb
-    return {"kernel": "dslash", "dims": dims, "dtype": a.dtype, "nrhs": a.nrhs,
+    return {"kernel": "dslash", "layout": a.layout, "dims": dims, "dtype": a.dtype, "nrhs": a.nrhs,
             "parity": a.parity, "us": t * 1e6, "us_min": tmin * 1e6,
             "algorithmic_bytes": byts, "GBps": byts / t / 1e9}
 
@@ -127,6 +135,8 @@ def main():
     ap.add_argument("--dtype", default="c64", choices=list(BYTES_PER_SITE))
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--parity", type=int, default=-1)
+    ap.add_argument("--layout", default="abi", choices=["abi", "lanes"],
+                    help="links in the ABI layout or the solver's lane-contiguous copy")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--workload", default="c2_16^3x32_near_critical")
     ap.add_argument("--fp64", action="store_true")
