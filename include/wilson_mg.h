@@ -172,6 +172,34 @@ int mg_create(mg_handle** h, const void* links, const mg_params* p, void* stream
 int coarse_build(mg_handle* h, void* stream);
 
 /* ---------------------------------------------------------------------------------
+ * coarse_build_noalloc -- coarse_build without any device memory allocation.  The
+ * paper has no counterpart: this is a library service for callers that cannot let the
+ * library allocate device memory while they run -- e.g. an application that has handed
+ * nearly all of HBM to its own pool allocator (a library cudaMalloc would then fail or
+ * fragment that pool), or one that must keep a fixed device-memory footprint after
+ * start-up.  It recomputes D_c = P^dag D P (Eq. 5) into the handle's existing
+ * coarse-operator storage, e.g. after mg_set_prolongator.
+ *   Scratch: the Galerkin forward-hop partials, 4 * d * (2k)^2 complex doubles
+ *     (d = coarse sites), live in one fixed 24 MiB device array inside the library, so
+ *     d * k^2 must not exceed 98304 (the 16^3x32 lattice with 4^4 aggregates fits up to
+ *     k = 13); larger hierarchies return MG_EINVAL -- use coarse_build for those.
+ *     Nothing in the scratch has to start at zero: every partial is written before it
+ *     is read, so consecutive calls need no reset.
+ *   Preconditions: the handle has a prolongator and coarse_build has run on it once
+ *     (that call allocates the storage of D_c, which this call overwrites); otherwise
+ *     MG_EINVAL.
+ *   Set-up: the first call on each device looks up the device address of the scratch
+ *     array (once, with that device current) and caches it; make that first call before
+ *     any stream capture begins.
+ *   Concurrency: the scratch is shared by every handle of the process on a device, so
+ *     calls on the same device must not overlap (e.g. from two host threads): two
+ *     overlapping calls race on the scratch and both results are undefined.
+ *   Result: the same kernels in the same order as coarse_build, so the same D_c.
+ *   Synchronises `stream` before returning.
+ * ------------------------------------------------------------------------------- */
+int coarse_build_noalloc(mg_handle* h, void* stream);
+
+/* ---------------------------------------------------------------------------------
  * mg_solve -- x = D^{-1} b to ||b - D x|| <= tol ||b|| (checked in FP64) with FGMRES
  * preconditioned by the two-level K-cycle (restrict, coarse GMRES to coarse_tol,
  * prolong, post_smooth GMRES steps).  solve_dtype MG_C128: one FP64 FGMRES;

@@ -69,6 +69,7 @@ SIGNATURES = {
     "mg_setup_streaming_svd": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),
     "mg_create": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),
     "coarse_build": (I, [P, P]),
+    "coarse_build_noalloc": (I, [P, P]),
     "mg_solve": (I, [P, P, P, I, D, I, C.POINTER(MgSolveInfo), P]),
     "mg_solve_adjoint": (I, [P, P, P, I, D, I, C.POINTER(MgSolveInfo), P]),
     "mg_destroy": (I, [P]),

@@ -126,6 +126,9 @@ class Hierarchy:
     def coarse_build(self):
         L.check(L.lib().coarse_build(self._h, _stream()), "coarse_build")
 
+    def coarse_build_noalloc(self):
+        L.check(L.lib().coarse_build_noalloc(self._h, _stream()), "coarse_build_noalloc")
+
     def solve(self, b, tol=1e-10, maxiter=1000, adjoint=False, x=None):
         nrhs = b.numel() // (self.V * 12)
         if x is None:

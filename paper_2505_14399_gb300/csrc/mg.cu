@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -472,6 +474,65 @@ extern "C" int coarse_build(mg_handle* h, void* stream) {
   int s = galerkin_build(h->Op64, Xpart, h->P64, h->k, h->links64, h->g, h->B, st, df);
   cudaFreeAsync(Xpart, st);
   WMG_TRY(s);
+  WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  h->have_coarse = true;
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// coarse_build_noalloc: the same Galerkin rebuild with the forward-hop partials kept in a
+// fixed device array instead of a per-call allocation.  Nothing in the array has to start
+// at zero: galerkin_hop_kernel writes every partial before galerkin_finish_kernel reads it.
+static __device__ __align__(256) unsigned char g_galerkin_scratch[(size_t)24 << 20];
+
+namespace {
+
+constexpr size_t kGalerkinScratchBytes = sizeof(g_galerkin_scratch);
+constexpr int kScratchMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kScratchMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up on the first call
+// per device (with that device current) and cached.
+int galerkin_scratch(void** out) {
+  int dev = 0;
+  WMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kScratchMaxDevices)
+    return fail(MG_EINVAL, "coarse_build_noalloc: device ordinal above 63");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_galerkin_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(MG_ECUDA, std::string("coarse_build_noalloc: cudaGetSymbolAddress failed: ") +
+                                cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" int coarse_build_noalloc(mg_handle* h, void* stream) {
+  WMG_TRY(check_ready(h, false));
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t ne = (size_t)4 * h->k * h->k;
+  size_t need = (size_t)4 * h->B.d * ne * sizeof(zd);
+  if (need > kGalerkinScratchBytes)
+    return fail(MG_EINVAL, "coarse_build_noalloc: the Galerkin partials need " +
+                               std::to_string(need) + " bytes but the fixed scratch holds " +
+                               std::to_string(kGalerkinScratchBytes) +
+                               " (coarse sites * k^2 must be <= 98304); use coarse_build");
+  if (!h->Op64 || !h->Op32)
+    return fail(MG_EINVAL, "coarse_build_noalloc: the handle has no coarse-operator storage "
+                           "yet; call coarse_build once first (it allocates that storage)");
+  void* scratch = nullptr;
+  WMG_TRY(galerkin_scratch(&scratch));
+  bool df = h->p.fp64_emulation > 0 || (h->p.fp64_emulation < 0 && h->p.solve_dtype == MG_C64);
+  WMG_TRY(galerkin_build(h->Op64, static_cast<zd*>(scratch), h->P64, h->k, h->links64, h->g,
+                         h->B, st, df));
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
   WMG_CUDA(cudaStreamSynchronize(st));
   h->have_coarse = true;
