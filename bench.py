@@ -18,6 +18,10 @@ import sys
 import threading
 import time
 
+# the oracle leg runs single-threaded (its BLAS calls too), so `cores` = 1 is what it used
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -100,6 +104,49 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def kernel_bound(name, alu, peaks, peak_kind):
+    """(bound, peak, unit, source) of a library kernel, by the arithmetic it runs on."""
+    if name.endswith("_df64"):
+        # double-float: one real multiply-add (2 FP64-equivalent flops) costs 12 FP32
+        # instructions (1 mul, 3 fma, 8 add/sub), so the peak is the FP32 FMA rate / 12
+        return "alu", alu["fp32"] / 12.0, "TFLOP/s", "measured FP32 FMA rate / 12"
+    if name.endswith("_fp64") or name.startswith("galerkin"):
+        return "alu", alu["fp64"], "TFLOP/s", "measured FP64 FMA rate"
+    return "hbm", peaks["hbm_gbs"], "GB/s", peak_kind
+
+
+def dslash_32(api, synthetic, dev, flush, peaks, peak_kind, reps=20):
+    """The solver's FP32 stencil (lane-contiguous links) on a 32^3 x 64 lattice, one launch
+    per timing with the L2 flushed before it: 1.007 GB of algorithmic traffic per apply."""
+    import torch
+    dims = (32, 32, 32, 64)
+    V = int(np.prod(dims))
+    U = torch.from_numpy(synthetic.smooth_links(dims, 1003)).to(dev)
+    p = api.params(dims, (4, 4, 4, 4), 0.13, 24, 24, 2)
+    h = api.Hierarchy(U, p, setup=False)
+    del U
+    psi = torch.from_numpy(synthetic.gaussian_rhs(dims, 9)).to(torch.complex64).to(dev)
+    out = torch.empty_like(psi)
+    ev = []
+    for i in range(reps + 3):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.apply_fine(psi, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            ev.append(e0.elapsed_time(e1) / 1e3)
+    h.close()
+    t = float(np.mean(ev))
+    gbs = V * 480.0 / t / 1e9
+    return {"kernel": "dslash_c64, lane-contiguous links (32^3x64, L2 flushed)", "bound": "hbm",
+            "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_kind, "avg_launch_us": t * 1e6,
+            "algorithmic_bytes": V * 480.0}
+
+
 def workload():
     from paper_2505_14399_gb300 import synthetic
     cfg = dict(synthetic.WORKLOADS[WORKLOAD])
@@ -179,6 +226,13 @@ def gpu_arm(args):
         t = max_over_ranks(float(np.mean(times)), dev if world > 1 else None)
         return t, infos[-1], launches // max(K, 1), x, kern
 
+    # measured arithmetic peaks (FMA chains on every SM) for the ALU-bound kernels
+    alu = {}
+    for key, dt in (("fp64", _lib.MG_C128), ("fp32", _lib.MG_C64)):
+        tf = ctypes.c_double(0)
+        _lib.check(_lib.lib().mg_probe_fma_peak(dt, ctypes.byref(tf), None), "mg_probe_fma_peak")
+        alu[key] = tf.value
+
     pm, p64 = make_params(True), make_params(False)
     sampler = ClockSampler(local)
     sampler.start()
@@ -234,22 +288,23 @@ def gpu_arm(args):
             if v["ms"] > 0:
                 ent["GBps"] = v["bytes"] / (v["ms"] * 1e-3) / 1e9
                 ent["TFLOPs"] = v["flops"] / (v["ms"] * 1e-3) / 1e12
+                bound, pk, unit, src = kernel_bound(name, alu, peaks, peak_kind)
+                ach = ent["TFLOPs"] if unit == "TFLOP/s" else ent["GBps"]
+                ent.update({"bound": bound, "frac": ach / pk})
             kernels[name] = ent
-        top = max(kern.items(), key=lambda kv: kv[1]["ms"])
-        name, v = top
-        fp64_bound = name.startswith(("svd_", "galerkin"))
+        name, v = max(kern.items(), key=lambda kv: kv[1]["ms"])
         per_launch_s = v["ms"] * 1e-3 / max(v["launches"], 1e-9)
-        if fp64_bound:
-            # FP64 / double-float arithmetic: peak = nominal FP64 rate (no measured figure)
+        bound, pk, unit, src = kernel_bound(name, alu, peaks, peak_kind)
+        if unit == "TFLOP/s":
             ach = v["flops"] / max(v["launches"], 1e-9) / per_launch_s / 1e12
-            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": 1.25,
-                    "unit": "TFLOP/s", "frac": ach / 1.25,
-                    "peak_source": "nominal FP64 (not in the measured peaks file)",
-                    "traffic": None, "avg_launch_us": per_launch_s * 1e6}
+            roof = {"kernel": name, "bound": bound, "achieved": ach, "peak": pk,
+                    "unit": unit, "frac": ach / pk, "peak_source": src,
+                    "traffic": None, "avg_launch_us": per_launch_s * 1e6,
+                    "algorithmic_flops_per_launch": v["flops"] / max(v["launches"], 1e-9)}
         else:
             ach = v["bytes"] / max(v["launches"], 1e-9) / per_launch_s / 1e9
-            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_source": peak_kind,
+            roof = {"kernel": name, "bound": bound, "achieved": ach, "peak": pk,
+                    "unit": unit, "frac": ach / pk, "peak_source": src,
                     "traffic": None, "avg_launch_us": per_launch_s * 1e6,
                     "algorithmic_bytes_per_launch": v["bytes"] / max(v["launches"], 1e-9)}
     if roof is None:
@@ -258,7 +313,22 @@ def gpu_arm(args):
                 "peak_source": peak_kind, "traffic": None, "avg_launch_us": t_d * 1e6,
                 "algorithmic_bytes_per_launch": bytes_d}
 
-    # residual check of the timed result (FP64 on device via the library)
+    # fine-level outer iterations, Regular (one SVD of k test vectors) vs iCSVD streams, FP64
+    # solve on the same field and source (Table 2's comparison, synthetic near-critical lattice)
+    fine = {}
+    for tag, r, ns in (("regular_r12_ns1", cfg["k"], 1), ("icsvd_r8_ns4", cfg["r"], cfg["n_s"]),
+                       ("icsvd_r8_ns8", cfg["r"], 8)):
+        pf = api.params(dims, cfg["block"], cfg["kappa"], cfg["k"], r, ns, cfg["sweeps"],
+                        cfg["tv_seed"], cfg["hop_weight"], cfg["bc"], setup_dtype="c128",
+                        solve_dtype="c128")
+        _, inf = step(pf, Ud, bd)
+        fine[tag] = {"outer": inf["outer"], "coarse": inf["coarse"],
+                     "test_vectors": r * ns}
+    fine["reduction_regular_over_icsvd_ns4"] = (fine["regular_r12_ns1"]["outer"]
+                                                / max(fine["icsvd_r8_ns4"]["outer"], 1))
+
+    d32 = dslash_32(api, synthetic, dev, flush, peaks, peak_kind)
+
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -291,6 +361,9 @@ def gpu_arm(args):
             "clocks": clocks,
             "roofline": roof,
             "kernels": kernels,
+            "alu_peaks_tflops": alu,
+            "fine_iterations": fine,
+            "dslash_roofline_32^3x64": d32,
             "dslash_roofline": {"kernel": "dslash_c64 (16^3x32, L2 flushed, standalone)",
                                 "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
                                 "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
@@ -302,6 +375,23 @@ def gpu_arm(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def host_info():
+    """CPU model and the cores this process may run on (the oracle itself uses one)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    import platform
+    return {"cpu": model or platform.processor() or platform.machine(),
+            "arch": platform.machine(), "available_cores": len(os.sched_getaffinity(0))}
 
 
 def cpu_baseline(cfg, U, b, info, budget_s=20.0):
@@ -362,7 +452,7 @@ def cpu_baseline(cfg, U, b, info, budget_s=20.0):
     t_solve = kcycles * (t_rp + (cfg.get("post", 8) + 2) * t_dslash) + coarse_its * t_capply \
         + info.get("outer", 1) * t_dslash
     est = t_setup + t_gal + t_solve
-    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": ("full-volume smoothing of 1 of %d test vectors, iCSVD of %d of %d "
                        "aggregates, Galerkin over 1 of %d time slabs, one Dslash/restrict/"
                        "prolong/coarse apply; scaled by the GPU solve's counts (%d K-cycles, "

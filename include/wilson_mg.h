@@ -27,7 +27,10 @@
  * or pinned); host buffers are staged through device memory on the given stream.
  * `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  * asynchronous on that stream unless stated otherwise.  The caller owns every
- * buffer it passes; the library owns mg_handle and everything inside it.
+ * buffer it passes; the library owns mg_handle and everything inside it.  Device and
+ * pinned host memory the library releases (mg_destroy, a solver resized for another
+ * nrhs) stays in a process-wide cache and is reused by later handles; the cache is handed
+ * back to the driver when an allocation fails.
  *
  * Errors: every call returns an mg_status; no exception or device trap crosses
  * the ABI.  mg_last_error() gives a thread-local message for the last failure.
@@ -73,9 +76,11 @@ typedef struct mg_params {
   int sweeps;                /* smoother GMRES steps per test vector (Eq. 2)             */
   unsigned long long seed;   /* Philox key of the random initial guesses                 */
   int setup_dtype;           /* MG_C128 or MG_C64: arithmetic of the setup smoother      */
-  int solve_dtype;           /* MG_C128: plain FP64 solve; MG_C64 / MG_F16 / MG_BF16:
-                                inner FGMRES + K-cycle in that storage inside FP64
-                                iterative refinement                                     */
+  int solve_dtype;           /* MG_C128: plain FP64 solve; MG_C64: inner FGMRES +
+                                K-cycle in FP32 inside FP64 iterative refinement;
+                                MG_F16 / MG_BF16: the same with the K-cycle's
+                                post-smoother (its residual, Krylov basis and stencil,
+                                links included) in that half storage, FP32 arithmetic   */
   int post_smooth;           /* post-smoother GMRES steps in the K-cycle (8, Sec. 4)     */
   double coarse_tol;         /* coarse solve relative tolerance (0.03, Sec. 4)           */
   int coarse_restart;        /* coarse GMRES restart length                              */
@@ -87,11 +92,14 @@ typedef struct mg_params {
                                 -1: second pass only when setup_dtype is MG_C128 (FP32
                                 test vectors carry 1e-7 of their own error)              */
   int coarse_persistent;     /* 1: coarse GMRES as one persistent cooperative kernel
-                                (bounded grid barriers); 0: one launch per operation     */
-  int fp64_emulation;        /* sums of products of the SVD Gram/update and the Galerkin
-                                contraction: 1 double-float on FP32 units (~2^-48
-                                relative), 0 native FP64; -1 double-float only in the
-                                mixed form (setup / solve dtype MG_C64)                  */
+                                (bounded grid barriers) when the coarse system fits one
+                                grid (<= 2048 coarse rows per SM), else one launch per
+                                operation; 0: always one launch per operation            */
+  int fp64_emulation;        /* arithmetic of the SVD Gram, eigen-rotations and update
+                                and of the Galerkin contraction: 1 double-float on FP32
+                                units (~2^-48 relative), 0 native FP64; -1 double-float
+                                only in the mixed forms (SVD: setup_dtype MG_C64;
+                                Galerkin: solve_dtype other than MG_C128)                */
 } mg_params;
 
 typedef struct mg_solve_info {
@@ -132,6 +140,12 @@ const char* mg_profile_report(void);
  * MG_ETIMEOUT when the timeout is reported to the host as designed; the CUDA context stays
  * usable.  No fault, trap or unbounded wait is involved. */
 int mg_selftest_barrier_timeout(void* stream);
+
+/* Arithmetic-rate probe (diagnostic; synchronises `stream`): runs independent FMA chains on
+ * every SM (dtype MG_C128: FP64, MG_C64: FP32) for about 15 ms per launch and writes the
+ * best of three timed launches as TFLOP/s (2 flops per FMA) to *tflops.  These are the
+ * measured denominators of the ALU-bound kernels' rooflines. */
+int mg_probe_fma_peak(int dtype, double* tflops, void* stream);
 
 /* ---------------------------------------------------------------------------------
  * wilson_dslash -- the Wilson-Dirac stencil (the operator of Eq. 1).
@@ -226,7 +240,8 @@ int mg_test_vectors(void* out, const void* links, const mg_params* p, int stream
                     void* stream);
 
 /* out = D in (dagger: D^dag in) with the handle's operator and its lane-contiguous link
- * copy (the stencil the solver runs); dtype MG_C128 or MG_C64 fields, nrhs of them. */
+ * copy (the stencil the solver runs); dtype MG_C128 or MG_C64 fields, nrhs of them, or
+ * MG_F16 / MG_BF16 fields (half links) on a handle whose solve_dtype is that type. */
 int mg_apply_fine(mg_handle* h, void* out, const void* in, int nrhs, int dtype, int dagger,
                   void* stream);
 

@@ -62,6 +62,7 @@ SIGNATURES = {
     "mg_kernel_launches": (C.c_longlong, []),
     "mg_autotune_report": (C.c_char_p, []),
     "mg_selftest_barrier_timeout": (I, [P]),
+    "mg_probe_fma_peak": (I, [I, P, P]),
     "mg_profile_enable": (I, [I, I]),
     "mg_profile_report": (C.c_char_p, []),
     "wilson_dslash": (I, [P, P, P, C.POINTER(C.c_int), D, C.POINTER(C.c_double),

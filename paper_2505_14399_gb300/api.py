@@ -37,7 +37,7 @@ def params(dims, block, kappa, k, r, n_s, sweeps=5, seed=3000, hop_weight=(1, 1,
     """Build an mg_params structure (paper symbols k, r, n_s; aggregates of extent `block`)."""
     p = L.MgParams()
     L.lib().mg_params_default(C.byref(p))
-    dmap = {"c128": L.MG_C128, "c64": L.MG_C64}
+    dmap = {"c128": L.MG_C128, "c64": L.MG_C64, "f16": L.MG_F16, "bf16": L.MG_BF16}
     p.dims = L.ivec(dims)
     p.block = L.ivec(block)
     p.kappa = float(kappa)
@@ -144,7 +144,7 @@ class Hierarchy:
     def apply_fine(self, v, dagger=False, out=None):
         """D v with the hierarchy's operator (lane-contiguous link copy)."""
         dt = _DT[v.dtype]
-        nrhs = v.numel() // (self.V * 12)
+        nrhs = v.numel() // (self.V * 12 * (2 if dt >= L.MG_F16 else 1))
         if out is None:
             out = torch.empty_like(v)
         L.check(L.lib().mg_apply_fine(self._h, _ptr(out), _ptr(v), nrhs, dt, int(dagger),

@@ -109,95 +109,138 @@ __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ 
 }
 
 // Parallel cyclic Jacobi on a Hermitian c x c matrix per CTA (Brent-Luk round robin).
+// Rotation angles are computed in FP64 from the current entries; DF applies the rotations
+// to the matrix and the eigenvector basis in double-float arithmetic on the FP32 units
+// (this GPU's FP64 rate is ~1/64 of its FP32 rate), otherwise in FP64.
+template <typename T> struct JacOps;
+template <> struct JacOps<zd> {
+  static __device__ __forceinline__ zd from(zd v) { return v; }
+  static __device__ __forceinline__ zd val(zd v) { return v; }
+  static __device__ __forceinline__ zd zero() { return {0, 0}; }
+  static __device__ __forceinline__ zd one() { return {1, 0}; }
+};
+template <> struct JacOps<zdf> {
+  static __device__ __forceinline__ zdf from(zd v) { return zdf_from(v); }
+  static __device__ __forceinline__ zd val(zdf v) { return {df_val(v.re), df_val(v.im)}; }
+  static __device__ __forceinline__ zdf zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+  static __device__ __forceinline__ zdf one() { return {{1.f, 0.f}, {0.f, 0.f}}; }
+};
+
+// (xa, xb) <- (c xa - s ph xb, s xa + c ph xb), c and s real, ph a unit phase
+__device__ __forceinline__ void rot_pair(zd& xa, zd& xb, double c, double s, zd ph) {
+  zd e = ph * xb;
+  zd na = c * xa - s * e;
+  xb = s * xa + c * e;
+  xa = na;
+}
+__device__ __forceinline__ void rot_pair(zdf& xa, zdf& xb, df c, df s, zdf ph) {
+  zdf e = {df_dot2(ph.re, xb.re, df_neg(ph.im), xb.im), df_dot2(ph.re, xb.im, ph.im, xb.re)};
+  df ms = df_neg(s);
+  zdf na = {df_dot2(c, xa.re, ms, e.re), df_dot2(c, xa.im, ms, e.im)};
+  xb = {df_dot2(s, xa.re, c, e.re), df_dot2(s, xa.im, c, e.im)};
+  xa = na;
+}
+
+template <bool DF>
 __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const zd* G, int c,
                                                     double rtol) {
+  typedef typename std::conditional<DF, zdf, zd>::type T;
+  typedef typename std::conditional<DF, df, double>::type TR;
+  typedef JacOps<T> J;
   extern __shared__ zd sm[];
   int ce = c + (c & 1);              // padded to even
-  zd* A = sm;                         // ce x ce
-  zd* Vv = A + ce * ce;               // ce x ce
-  double* rc = reinterpret_cast<double*>(Vv + ce * ce);   // [ce/2] cos
-  zd* rs = reinterpret_cast<zd*>(rc + ce / 2 + 1);        // [ce/2] s e^{-i phi}... see below
-  zd* rph = rs + ce / 2;                                   // [ce/2] e^{-i phi}
-  int* top = reinterpret_cast<int*>(rph + ce / 2);        // [ce/2]
-  int* bot = top + ce / 2;                                 // [ce/2]
-  __shared__ int rotated;
+  int np = ce / 2;
+  T* A = reinterpret_cast<T*>(sm);    // ce x ce
+  T* Vv = A + ce * ce;                // ce x ce
+  double* rc = reinterpret_cast<double*>(Vv + ce * ce);   // [np] cos (FP64, skip test)
+  double* rsn = rc + np;                                   // [np] sin
+  TR* rcT = reinterpret_cast<TR*>(rsn + np);               // [np] cos, sin in T's arithmetic
+  TR* rsT = rcT + np;
+  T* rph = reinterpret_cast<T*>(rsT + np);                 // [np] e^{-i phi}
+  int* top = reinterpret_cast<int*>(rph + np);             // [np]
+  int* bot = top + np;                                     // [np]
+  __shared__ double dg[MAXC];
   int t = blockIdx.x;
   const zd* Gt = G + (size_t)t * c * c;
   for (int e = threadIdx.x; e < ce * ce; e += blockDim.x) {
     int i = e / ce, j = e % ce;
-    A[e] = (i < c && j < c) ? Gt[i * c + j] : zd{0, 0};
-    Vv[e] = (i == j) ? zd{1, 0} : zd{0, 0};
+    A[e] = (i < c && j < c) ? J::from(Gt[i * c + j]) : J::zero();
+    Vv[e] = (i == j) ? J::one() : J::zero();
   }
-  int np = ce / 2;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
     top[p] = 2 * p;
     bot[p] = 2 * p + 1;
   }
   __syncthreads();
   for (int sweep = 0; sweep < 30; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
-    __syncthreads();
+    int rotated = 0;   // this thread computed a rotation in this sweep
     for (int round = 0; round < ce - 1; ++round) {
       // rotation parameters
       for (int p = threadIdx.x; p < np; p += blockDim.x) {
         int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
-        double c0 = 1.0;
-        zd s0 = {0, 0}, ph = {1, 0};
+        double c0 = 1.0, s = 0.0;
+        zd ph = {1, 0};
         if (b < c) {
-          zd g = A[a * ce + b];
+          zd g = J::val(A[a * ce + b]);
           double ag = sqrt(norm2(g));
-          double da = A[a * ce + a].re, db = A[b * ce + b].re;
+          double da = J::val(A[a * ce + a]).re, db = J::val(A[b * ce + b]).re;
           if (ag > rtol * sqrt(fabs(da * db)) && ag > 1e-300) {
             double zeta = (db - da) / (2.0 * ag);
             double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             c0 = 1.0 / sqrt(1.0 + tt * tt);
-            double s = tt * c0;
+            s = tt * c0;
             ph = {g.re / ag, -g.im / ag};  // e^{-i phi}
-            s0 = {s, 0};
             rotated = 1;
           }
         }
         rc[p] = c0;
-        rs[p] = s0;
-        rph[p] = ph;
+        rsn[p] = s;
+        if constexpr (DF) {
+          rcT[p] = df_from(c0);
+          rsT[p] = df_from(s);
+        } else {
+          rcT[p] = c0;
+          rsT[p] = s;
+        }
+        rph[p] = J::from(ph);
       }
       __syncthreads();
       // rows: new_a = c A_a - s e^{i phi} A_b ; new_b = s A_a + c e^{i phi} A_b
       for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
         int p = e / ce, k = e % ce;
+        if (rsn[p] == 0.0 && rc[p] == 1.0) continue;
         int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
-        double cc = rc[p], s = rs[p].re;
-        if (s == 0.0 && cc == 1.0) continue;
-        zd eph = conj(rph[p]);  // e^{i phi}
-        zd xa = A[a * ce + k], xb = A[b * ce + k];
-        zd ebx = eph * xb;
-        A[a * ce + k] = cc * xa - s * ebx;
-        A[b * ce + k] = s * xa + cc * ebx;
+        T eph = rph[p];
+        if constexpr (DF) eph.im = df_neg(eph.im);
+        else eph.im = -eph.im;
+        T xa = A[a * ce + k], xb = A[b * ce + k];
+        rot_pair(xa, xb, rcT[p], rsT[p], eph);
+        A[a * ce + k] = xa;
+        A[b * ce + k] = xb;
       }
       __syncthreads();
       // columns: new_a = c M_a - s e^{-i phi} M_b ; new_b = s M_a + c e^{-i phi} M_b
       for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
         int p = e / ce, k = e % ce;
+        if (rsn[p] == 0.0 && rc[p] == 1.0) continue;
         int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
-        double cc = rc[p], s = rs[p].re;
-        if (s == 0.0 && cc == 1.0) continue;
-        zd mph = rph[p];
-        zd xa = A[k * ce + a], xb = A[k * ce + b];
-        zd ebx = mph * xb;
-        A[k * ce + a] = cc * xa - s * ebx;
-        A[k * ce + b] = s * xa + cc * ebx;
-        zd va = Vv[k * ce + a], vb = Vv[k * ce + b];
-        zd evb = mph * vb;
-        Vv[k * ce + a] = cc * va - s * evb;
-        Vv[k * ce + b] = s * va + cc * evb;
+        T mph = rph[p];
+        T xa = A[k * ce + a], xb = A[k * ce + b];
+        rot_pair(xa, xb, rcT[p], rsT[p], mph);
+        A[k * ce + a] = xa;
+        A[k * ce + b] = xb;
+        T va = Vv[k * ce + a], vb = Vv[k * ce + b];
+        rot_pair(va, vb, rcT[p], rsT[p], mph);
+        Vv[k * ce + a] = va;
+        Vv[k * ce + b] = vb;
       }
       __syncthreads();
       // the rotated pair's off-diagonal entries are zero by construction
       for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        if (!(rs[p].re == 0.0 && rc[p] == 1.0)) {
+        if (!(rsn[p] == 0.0 && rc[p] == 1.0)) {
           int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
-          A[a * ce + b] = {0, 0};
-          A[b * ce + a] = {0, 0};
+          A[a * ce + b] = J::zero();
+          A[b * ce + a] = J::zero();
         }
       }
       __syncthreads();
@@ -212,9 +255,11 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
       }
       __syncthreads();
     }
-    __syncthreads();
-    if (!rotated) break;
+    // a barrier that also ORs the flags: every thread takes the same exit decision
+    if (!__syncthreads_or(rotated)) break;
   }
+  for (int i = threadIdx.x; i < c; i += blockDim.x) dg[i] = J::val(A[i * ce + i]).re;
+  __syncthreads();
   // sort eigenvalues descending (stable by index), thread 0
   __shared__ int order[MAXC];
   if (threadIdx.x == 0) {
@@ -222,9 +267,9 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
     for (int i = 0; i < c; ++i) order[i] = i;
     for (int i = 1; i < c; ++i) {
       int key = order[i];
-      double kv = A[key * ce + key].re;
+      double kv = dg[key];
       int j = i - 1;
-      while (j >= 0 && A[order[j] * ce + order[j]].re < kv) {
+      while (j >= 0 && dg[order[j]] < kv) {
         order[j + 1] = order[j];
         --j;
       }
@@ -232,12 +277,11 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < c; i += blockDim.x)
-    lam[(size_t)t * c + i] = A[order[i] * ce + order[i]].re;
+  for (int i = threadIdx.x; i < c; i += blockDim.x) lam[(size_t)t * c + i] = dg[order[i]];
   zd* Vt = Vec + (size_t)t * c * c;
   for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
     int row = e / c, i = e % c;
-    Vt[row * c + i] = Vv[row * ce + order[i]];
+    Vt[row * c + i] = J::val(Vv[row * ce + order[i]]);
   }
 }
 
@@ -382,19 +426,23 @@ int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaSt
   return MG_OK;
 }
 
-int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, double rtol) {
+int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, double rtol,
+             bool df64) {
   if (c > MAXC) return fail(MG_EINVAL, "tile_eig: more than 64 columns");
-  int ce = c + (c & 1);
-  size_t sh = sizeof(zd) * 2 * ce * ce + sizeof(double) * (ce / 2 + 1) + sizeof(zd) * ce +
-              sizeof(int) * ce + 64;
+  int ce = c + (c & 1), np = ce / 2;
+  size_t sh = sizeof(zd) * 2 * ce * ce + sizeof(double) * 2 * np + sizeof(zd) * np +
+              sizeof(zd) * np + sizeof(int) * 2 * np + 64;
   static bool attr_set = false;
   if (!attr_set) {
-    WMG_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    WMG_CUDA(cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    WMG_CUDA(cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   200 * 1024));
     attr_set = true;
   }
-  ProfScope ps("svd_jacobi_fp64", 32.0 * c * c * ntiles, 0.0, st);
-  jacobi_kernel<<<ntiles, GT, sh, st>>>(lam, Vec, G, c, rtol);
+  ProfScope ps(df64 ? "svd_jacobi_df64" : "svd_jacobi_fp64", 32.0 * c * c * ntiles, 0.0, st);
+  if (df64) jacobi_kernel<true><<<ntiles, GT, sh, st>>>(lam, Vec, G, c, rtol);
+  else jacobi_kernel<false><<<ntiles, GT, sh, st>>>(lam, Vec, G, c, rtol);
   WMG_LAUNCHED();
   return MG_OK;
 }

@@ -95,10 +95,28 @@ constexpr int GNB = 8;       // fine sites staged per batch
 constexpr int GTH = 256;     // threads
 constexpr int GMAXE = 16;    // accumulator entries per thread ((2k)^2 <= 4096)
 
-template <bool DF>
+// (i sigma_mu psi)[s] in df64 (sign changes and swaps only: exact)
+__device__ __forceinline__ zdf isigma_df(int mu, int s, zdf p0, zdf p1) {
+  if (mu == 0) return s == 0 ? zdf_ti(p1) : zdf_ti(p0);
+  if (mu == 1) return s == 0 ? p1 : zdf_neg(p0);
+  return s == 0 ? zdf_ti(p0) : zdf_tmi(p1);
+}
+
+// Forward hops x -> y = x + mu of D = 1 - kappa sum_mu w_mu [(1 - gamma_mu) U_mu(x) delta_{x+mu}
+// + ...]: the spin projector (1 - gamma_mu) reduces the 2k columns of P at y to a half
+// spinor (2 spins x 3 colours), U_mu(x) transports its colour, and the reconstruction folds
+// into P(x).  Staged per fine site h and half-spinor row r (6 rows):
+//   sCh[h][r][b] = +-(U P_b(y))_r   (sign -1 for an antiperiodic wrapping hop)
+//   sPt[h][r][a] = (L P_a(x))_r     (L = reconstruction adjoint)
+// and every block accumulates sum_{h,r} conj(sPt[h][r][a]) sCh[h][r][b]; the factor
+// -kappa w_mu multiplies the finished block.  DF: P, links, staging and accumulation in
+// double-float on the FP32 units (P and links pre-split into (hi, lo) pairs); otherwise FP64.
+// NE: accumulator entries per thread (ceil((2k)^2 / GTH), rounded up to a launched size).
+template <bool DF, int NE>
 __global__ void __launch_bounds__(GTH)
-galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
-                    const zd* __restrict__ links, HopGeom g, Blocking B) {
+galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, const zdf* __restrict__ Pdf,
+                    int k, const zd* __restrict__ links, const zdf* __restrict__ Ldf, HopGeom g,
+                    Blocking B) {
   typedef typename std::conditional<DF, zdf, zd>::type T;
   typedef typename std::conditional<DF, zdfacc, zd>::type TA;
   extern __shared__ zd gsm_raw[];
@@ -106,20 +124,17 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
   int n2k = 2 * k;
   T* sPt = gsm;                        // [GNB][6][n2k]
   T* sCh = gsm + GNB * 6 * n2k;        // [GNB][6][n2k]
-  __shared__ int ssite[GNB], snb[GNB];
-  __shared__ double sph[GNB];
+  __shared__ int ssite[GNB], snb[GNB], sneg[GNB];
   int j = blockIdx.x, mu = blockIdx.y, dir = 2 * mu;
-  const bool fwd = true;
-  // projector sign of this hop in D: forward (1 - gamma), backward (1 + gamma)
-  int S = fwd ? -1 : +1;
   double coef = -g.kappa * g.w[mu];
   int ne = n2k * n2k;
   int bmu = B.b[mu];
   const int* bb = B.b;
+  size_t V = (size_t)B.nd * B.d;
   for (int pass = 0; pass < 2; ++pass) {  // 0: hops inside the aggregate, 1: crossing hops
-    TA acc[GMAXE];
+    TA acc[NE];
 #pragma unroll
-    for (int q = 0; q < GMAXE; ++q) acc[q] = TA{};
+    for (int q = 0; q < NE; ++q) acc[q] = TA{};
     int l = 0;
     while (true) {
       // collect the next batch of local sites of this pass (same scan in every thread)
@@ -135,7 +150,7 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
           lc[2] = q % bb[2]; lc[3] = q / bb[2];
           lm = lc[mu];
         }
-        bool cross = fwd ? (lm == bmu - 1) : (lm == 0);
+        bool cross = lm == bmu - 1;
         if ((pass == 1) == cross) lsel[nb++] = l;
         ++l;
       }
@@ -148,18 +163,10 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
         int r = x / g.L[0];
         c[1] = r % g.L[1]; r /= g.L[1];
         c[2] = r % g.L[2]; c[3] = r / g.L[2];
-        int y;
-        bool wrap;
-        if (fwd) {
-          wrap = c[mu] == g.L[mu] - 1;
-          y = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
-        } else {
-          wrap = c[mu] == 0;
-          y = wrap ? x + (g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu];
-        }
+        bool wrap = c[mu] == g.L[mu] - 1;
         ssite[threadIdx.x] = x;
-        snb[threadIdx.x] = y;
-        sph[threadIdx.x] = (wrap && g.bc[mu] < 0) ? -coef : coef;
+        snb[threadIdx.x] = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
+        sneg[threadIdx.x] = (wrap && g.bc[mu] < 0) ? 1 : 0;
       }
       __syncthreads();
       // stage chi and Ptil
@@ -170,62 +177,71 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
         int s = r / 3, cc = r % 3;
         int beta = bcol / k, ip = bcol % k;
         int x = ssite[h], y = snb[h];
-        // half spinor of column bcol of P at y, colour c' = 0..2, spin s
-        int jy, ly;
+        int jy, ly, jx, lx;
         B.block_of(y, &jy, &ly);
-        const zd* Py = P + ((size_t)(2 * jy + beta) * k + ip) * B.M;
-        zd hv[3];
+        B.block_of(x, &jx, &lx);
+        size_t oy = ((size_t)(2 * jy + beta) * k + ip) * B.M;
+        size_t ox = ((size_t)(2 * jx + beta) * k + ip) * B.M;
+        if constexpr (DF) {
+          // half spinor of column bcol at y: chirality 0 keeps spin s of the upper pair;
+          // chirality 1 gives i sigma_mu psi_dn (mu < 3) or -psi_dn (mu = 3)
+          zdf hv[3];
 #pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2) {
-          if (beta == 0) {
-            hv[c2] = Py[(ly * 2 + s) * 3 + c2];
-          } else {
-            zd p0 = Py[(ly * 2 + 0) * 3 + c2], p1 = Py[(ly * 2 + 1) * 3 + c2];
-            if (mu < 3) {
-              zd is = isigma(mu, s, p0, p1);
-              hv[c2] = (S > 0) ? -is : is;      // -S i sigma psi_dn
+          for (int c2 = 0; c2 < 3; ++c2) {
+            if (beta == 0) {
+              hv[c2] = zdf_ld(Pdf + oy + (ly * 2 + s) * 3 + c2);
             } else {
-              zd ps = s == 0 ? p0 : p1;
-              hv[c2] = (S > 0) ? ps : -ps;      // S psi_dn
+              zdf p0 = zdf_ld(Pdf + oy + (ly * 2 + 0) * 3 + c2);
+              zdf p1 = zdf_ld(Pdf + oy + (ly * 2 + 1) * 3 + c2);
+              hv[c2] = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
             }
           }
-        }
-        // colour transport
-        zd ch = {0, 0};
-        if (fwd) {
-          const zd* U = links + ((size_t)mu * B.nd * B.d + x) * 9;
+          const zdf* U = Ldf + ((size_t)mu * V + x) * 9 + cc * 3;
+          zdfacc t{};
+#pragma unroll
+          for (int c2 = 0; c2 < 3; ++c2) zdf_fma(t, zdf_ld(U + c2), hv[c2]);
+          zdf ch = zdf_norm(t);
+          sCh[(h * 6 + r) * n2k + bcol] = sneg[h] ? zdf_neg(ch) : ch;
+          zdf pt;
+          if (beta == 0) {
+            pt = zdf_ld(Pdf + ox + (lx * 2 + s) * 3 + cc);
+          } else {
+            zdf p0 = zdf_ld(Pdf + ox + (lx * 2 + 0) * 3 + cc);
+            zdf p1 = zdf_ld(Pdf + ox + (lx * 2 + 1) * 3 + cc);
+            pt = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
+          }
+          sPt[(h * 6 + r) * n2k + bcol] = pt;
+        } else {
+          const zd* Py = P + oy;
+          zd hv[3];
+#pragma unroll
+          for (int c2 = 0; c2 < 3; ++c2) {
+            if (beta == 0) {
+              hv[c2] = Py[(ly * 2 + s) * 3 + c2];
+            } else {
+              zd p0 = Py[(ly * 2 + 0) * 3 + c2], p1 = Py[(ly * 2 + 1) * 3 + c2];
+              hv[c2] = mu < 3 ? isigma(mu, s, p0, p1) : -(s == 0 ? p0 : p1);
+            }
+          }
+          const zd* U = links + ((size_t)mu * V + x) * 9;
+          zd ch = {0, 0};
 #pragma unroll
           for (int c2 = 0; c2 < 3; ++c2) cfma(ch, U[cc * 3 + c2], hv[c2]);
-        } else {
-          const zd* U = links + ((size_t)mu * B.nd * B.d + y) * 9;
-#pragma unroll
-          for (int c2 = 0; c2 < 3; ++c2) cfmac(ch, U[c2 * 3 + cc], hv[c2]);
-        }
-        if constexpr (DF) sCh[(h * 6 + r) * n2k + bcol] = zdf_from(sph[h] * ch);
-        else sCh[(h * 6 + r) * n2k + bcol] = sph[h] * ch;
-        // Ptil: column a = bcol of P(x) folded with the reconstruction
-        int jx, lx;
-        B.block_of(x, &jx, &lx);
-        const zd* Px = P + ((size_t)(2 * jx + beta) * k + ip) * B.M;
-        zd pt;
-        if (beta == 0) {
-          pt = Px[(lx * 2 + s) * 3 + cc];
-        } else {
-          zd p0 = Px[(lx * 2 + 0) * 3 + cc], p1 = Px[(lx * 2 + 1) * 3 + cc];
-          if (mu < 3) {
-            zd is = isigma(mu, s, p0, p1);
-            pt = (S > 0) ? -is : is;            // L^dag = -S i sigma
+          sCh[(h * 6 + r) * n2k + bcol] = sneg[h] ? -ch : ch;
+          const zd* Px = P + ox;
+          zd pt;
+          if (beta == 0) {
+            pt = Px[(lx * 2 + s) * 3 + cc];
           } else {
-            zd ps = s == 0 ? p0 : p1;
-            pt = (S > 0) ? ps : -ps;            // L^dag = S
+            zd p0 = Px[(lx * 2 + 0) * 3 + cc], p1 = Px[(lx * 2 + 1) * 3 + cc];
+            pt = mu < 3 ? isigma(mu, s, p0, p1) : -(s == 0 ? p0 : p1);
           }
+          sPt[(h * 6 + r) * n2k + bcol] = pt;
         }
-        if constexpr (DF) sPt[(h * 6 + r) * n2k + bcol] = zdf_from(pt);
-        else sPt[(h * 6 + r) * n2k + bcol] = pt;
       }
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < GMAXE; ++q) {
+      for (int q = 0; q < NE; ++q) {
         int e = threadIdx.x + q * GTH;
         if (e < ne) {
           int a = e / n2k, b = e % n2k;
@@ -244,15 +260,26 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
     zd* out = pass == 1 ? Op + ((size_t)j * 9 + 1 + dir) * ne
                         : Xpart + ((size_t)mu * B.d + j) * ne;
 #pragma unroll
-    for (int q = 0; q < GMAXE; ++q) {
+    for (int q = 0; q < NE; ++q) {
       int e = threadIdx.x + q * GTH;
       if (e < ne) {
         int a = e / n2k, b = e % n2k;
-        if constexpr (DF) out[(size_t)b * n2k + a] = zdf_result(acc[q]);   // column-major
-        else out[(size_t)b * n2k + a] = acc[q];
+        zd v;
+        if constexpr (DF) v = zdf_result(acc[q]);
+        else v = acc[q];
+        out[(size_t)b * n2k + a] = coef * v;   // column-major
       }
     }
     __syncthreads();
+  }
+}
+
+// complex double -> (hi, lo) float pairs
+__global__ void to_df_kernel(zdf* out, const zd* __restrict__ in, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    zdf v = zdf_from(in[i]);
+    reinterpret_cast<float4*>(out)[i] = make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo);
   }
 }
 
@@ -263,7 +290,7 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, int k,
 // with F_mu(j) the forward hops that stay inside aggregate j.  Element (a, b) of
 // sigma_3 M^dag sigma_3 is s_a s_b conj(M(b, a)), s = +1 / -1 for chirality 0 / 1.
 __global__ void __launch_bounds__(GTH)
-galerkin_finish_kernel(zd* Op, const zd* __restrict__ Xpart, const zd* __restrict__ P, int k,
+galerkin_finish_kernel(zd* Op, const zd* __restrict__ Xpart, const zd* __restrict__ PtP, int k,
                        Blocking B) {
   int j = blockIdx.x;
   int n2k = 2 * k, ne = n2k * n2k;
@@ -273,11 +300,7 @@ galerkin_finish_kernel(zd* Op, const zd* __restrict__ Xpart, const zd* __restric
     int aa = a / k, bb = b / k;
     double sab = (aa == bb) ? 1.0 : -1.0;
     zd acc = {0, 0};
-    if (aa == bb) {
-      const zd* Pa = P + ((size_t)(2 * j + aa) * k + a % k) * B.M;
-      const zd* Pb = P + ((size_t)(2 * j + bb) * k + b % k) * B.M;
-      for (int r = 0; r < B.M; ++r) cfmac(acc, Pa[r], Pb[r]);
-    }
+    if (aa == bb) acc = PtP[((size_t)(2 * j + aa) * k + a % k) * k + b % k];   // P_a^dag P_b
     for (int mu = 0; mu < 4; ++mu) {
       const zd* F = Xpart + ((size_t)mu * B.d + j) * ne;
       acc += F[e];
@@ -356,9 +379,46 @@ int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const
   return MG_OK;
 }
 
-int galerkin_build(zd* Op, zd* Xpart, const zd* P, int k, const zd* links, const Geom& g,
-                   const Blocking& B, cudaStream_t st, bool df64) {
+int to_df(zdf* out, const zd* in, size_t n, cudaStream_t st) {
+  size_t g = (n + 255) / 256, cap = (size_t)num_sms() * 16;
+  to_df_kernel<<<(unsigned)(g < cap ? (g < 1 ? 1 : g) : cap), 256, 0, st>>>(out, in, n);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+namespace {
+template <bool DF, int NE>
+int launch_hop(dim3 grid, size_t sh, cudaStream_t st, zd* Op, zd* Xpart, const zd* P,
+               const zdf* Pdf, int k, const zd* links, const zdf* Ldf, const HopGeom& hg,
+               const Blocking& B) {
+  static bool set = false;
+  if (!set) {
+    WMG_CUDA(cudaFuncSetAttribute(galerkin_hop_kernel<DF, NE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    set = true;
+  }
+  galerkin_hop_kernel<DF, NE><<<grid, GTH, sh, st>>>(Op, Xpart, P, Pdf, k, links, Ldf, hg, B);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+template <bool DF>
+int launch_hop_ne(dim3 grid, size_t sh, cudaStream_t st, zd* Op, zd* Xpart, const zd* P,
+                  const zdf* Pdf, int k, const zd* links, const zdf* Ldf, const HopGeom& hg,
+                  const Blocking& B) {
+  int ne = (4 * k * k + GTH - 1) / GTH;
+  if (ne <= 2) return launch_hop<DF, 2>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B);
+  if (ne <= 4) return launch_hop<DF, 4>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B);
+  if (ne <= 8) return launch_hop<DF, 8>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B);
+  if (ne <= 12) return launch_hop<DF, 12>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B);
+  return launch_hop<DF, 16>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B);
+}
+}  // namespace
+
+int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, const zd* links,
+                   const zdf* Ldf, const Geom& g, const Blocking& B, cudaStream_t st, bool df64) {
   if (4 * k * k > GTH * GMAXE) return fail(MG_EINVAL, "galerkin: k > 32");
+  if (df64 && (!Pdf || !Ldf)) return fail(MG_EINVAL, "galerkin: double-float copies missing");
   HopGeom hg;
   for (int m = 0; m < 4; ++m) {
     hg.L[m] = g.L[m];
@@ -371,21 +431,18 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, int k, const zd* links, const
   hg.stride[3] = g.L[0] * g.L[1] * g.L[2];
   hg.kappa = g.kappa;
   size_t sh = sizeof(zd) * 2 * GNB * 6 * 2 * k;
-  static bool set = false;
-  if (!set) {
-    WMG_CUDA(cudaFuncSetAttribute(galerkin_hop_kernel<false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    WMG_CUDA(cudaFuncSetAttribute(galerkin_hop_kernel<true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    set = true;
-  }
   dim3 grid(B.d, 4);
+  // diagonal term P_j^dag P_j: the Gram matrix of every P tile (profiled as a Gram launch)
+  WMG_TRY(tile_gram(PtP, P, k, k, B, st, df64));
+  if (df64) WMG_TRY(to_df(Pdf, P, (size_t)B.d * 2 * k * B.M, st));
   ProfScope ps(df64 ? "galerkin_df64" : "galerkin_fp64", 16.0 * (12.0 * B.nd * B.d * k * 5 + 36.0 * B.nd * B.d),
                768.0 * k * k * B.nd * B.d, st);
-  if (df64) galerkin_hop_kernel<true><<<grid, GTH, sh, st>>>(Op, Xpart, P, k, links, hg, B);
-  else galerkin_hop_kernel<false><<<grid, GTH, sh, st>>>(Op, Xpart, P, k, links, hg, B);
-  WMG_LAUNCHED();
-  galerkin_finish_kernel<<<B.d, GTH, 0, st>>>(Op, Xpart, P, k, B);
+  if (df64) {
+    WMG_TRY(launch_hop_ne<true>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B));
+  } else {
+    WMG_TRY(launch_hop_ne<false>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B));
+  }
+  galerkin_finish_kernel<<<B.d, GTH, 0, st>>>(Op, Xpart, PtP, k, B);
   WMG_LAUNCHED();
   return MG_OK;
 }

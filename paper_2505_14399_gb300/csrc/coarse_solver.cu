@@ -429,12 +429,12 @@ int CoarseSolver<R>::alloc(size_t nc_, int m_) {
   WMG_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return fail(MG_ECUDA, "cooperative launch unsupported");
   max_grid = num_sms();   // one CTA per SM
-  WMG_CUDA(cudaMalloc(&V, sizeof(cplx<R>) * nc * (m + 1)));
-  WMG_CUDA(cudaMalloc(&W, sizeof(cplx<R>) * nc));
-  WMG_CUDA(cudaMalloc(&partial, sizeof(double) * 2 * 2 * (m + 2) * max_grid));
-  WMG_CUDA(cudaMalloc(&state, sizeof(BarrierState) + 2 * sizeof(int)));
+  WMG_TRY(dev_alloc(&V, sizeof(cplx<R>) * nc * (m + 1)));
+  WMG_TRY(dev_alloc(&W, sizeof(cplx<R>) * nc));
+  WMG_TRY(dev_alloc(&partial, sizeof(double) * 2 * 2 * (m + 2) * max_grid));
+  WMG_TRY(dev_alloc(&state, sizeof(BarrierState) + 2 * sizeof(int)));
   WMG_CUDA(cudaMemset(state, 0, sizeof(BarrierState) + 2 * sizeof(int)));
-  WMG_CUDA(cudaMallocHost(&host_state, sizeof(BarrierState) + 2 * sizeof(int)));
+  WMG_TRY(host_alloc(&host_state, sizeof(BarrierState) + 2 * sizeof(int)));
   return MG_OK;
 }
 
@@ -447,17 +447,25 @@ size_t CoarseSolver<R>::smem_bytes() const {
 
 template <typename R>
 void CoarseSolver<R>::release() {
-  if (V) cudaFree(V);
-  if (W) cudaFree(W);
-  if (partial) cudaFree(partial);
-  if (state) cudaFree(state);
-  if (host_state) cudaFreeHost(host_state);
+  dev_free(V);
+  dev_free(W);
+  dev_free(partial);
+  dev_free(state);
+  host_free(host_state);
   V = W = nullptr;
   partial = nullptr;
   state = nullptr;
   host_state = nullptr;
   nc = 0;
   m = 0;
+}
+
+template <typename R>
+bool CoarseSolver<R>::fits(const Blocking& B, int k) const {
+  int grid = max_grid < B.d ? max_grid : B.d;
+  if (grid < 1) return false;
+  int spc = (B.d + grid - 1) / grid;
+  return (long long)spc * 2 * k <= (long long)CT * RPT;
 }
 
 template <typename R>

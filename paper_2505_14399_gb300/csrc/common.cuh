@@ -15,6 +15,15 @@ namespace wmg {
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
 void count_launch(long long n = 1);
+// Library-wide caching allocator (device memory and pinned host memory); see runtime.cu.
+int dev_alloc_bytes(void** p, size_t bytes);
+void dev_free(void* p);
+int host_alloc_bytes(void** p, size_t bytes);
+void host_free(void* p);
+template <typename T>
+inline int dev_alloc(T** p, size_t bytes) { return dev_alloc_bytes(reinterpret_cast<void**>(p), bytes); }
+template <typename T>
+inline int host_alloc(T** p, size_t bytes) { return host_alloc_bytes(reinterpret_cast<void**>(p), bytes); }
 
 #define WMG_CUDA(call)                                                              \
   do {                                                                              \

@@ -75,4 +75,34 @@ __device__ __forceinline__ zd zdf_result(const zdfacc& acc) {
   return {df_to_double(acc.re.s, acc.re.e), df_to_double(acc.im.s, acc.im.e)};
 }
 
+__device__ __forceinline__ double df_val(df a) { return (double)a.hi + (double)a.lo; }
+
+// a * b + c * d as a normalised df64 value (two Dot2 steps and a Fast-TwoSum)
+__device__ __forceinline__ df df_dot2(df a, df b, df c, df d) {
+  dfacc t{0.0f, 0.0f};
+  df_fma(t, a, b);
+  df_fma(t, c, d);
+  float h = __fadd_rn(t.s, t.e);
+  return {h, __fsub_rn(t.e, __fsub_rn(h, t.s))};
+}
+
+// An accumulator as a normalised df64 value (Fast-TwoSum: |s| >= |e| holds for the
+// accumulated sum and its collected rounding errors).
+__device__ __forceinline__ df df_norm(dfacc a) {
+  float h = __fadd_rn(a.s, a.e);
+  return {h, __fsub_rn(a.e, __fsub_rn(h, a.s))};
+}
+__device__ __forceinline__ zdf zdf_norm(const zdfacc& a) { return {df_norm(a.re), df_norm(a.im)}; }
+
+// complex df64 sign and i-multiples (exact)
+__device__ __forceinline__ zdf zdf_neg(zdf a) { return {df_neg(a.re), df_neg(a.im)}; }
+__device__ __forceinline__ zdf zdf_ti(zdf a) { return {df_neg(a.im), a.re}; }    // i a
+__device__ __forceinline__ zdf zdf_tmi(zdf a) { return {a.im, df_neg(a.re)}; }   // -i a
+
+// 16-byte load / store of a complex df64 value stored as (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ zdf zdf_ld(const zdf* p) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+
 }  // namespace wmg

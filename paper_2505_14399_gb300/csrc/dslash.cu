@@ -7,6 +7,7 @@
 // [site][spin][colour] layout; links are read through the read-only path.
 #include "common.cuh"
 #include "internal.h"
+#include "vec.cuh"
 
 namespace wmg {
 
@@ -337,8 +338,9 @@ int launch_typed(void* out, const void* in, const void* links, const Geom& g, in
   return MG_OK;
 }
 
-template <typename To>
-__global__ void link_to_lanes_kernel(cplx<To>* dst, const zd* __restrict__ src, int V) {
+template <typename E>
+__global__ void link_to_lanes_kernel(E* dst, const zd* __restrict__ src, int V) {
+  typedef typename VecT<E>::R R;
   size_t total = (size_t)4 * V * 9;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -346,22 +348,24 @@ __global__ void link_to_lanes_kernel(cplx<To>* dst, const zd* __restrict__ src, 
     size_t site = e % V, rest = e / V;
     int entry = (int)(rest % 9), mu = (int)(rest / 9);
     zd v = src[((size_t)mu * V + site) * 9 + entry];
-    dst[e] = {(To)v.re, (To)v.im};
+    VecT<E>::st(dst, e, cplx<R>{(R)v.re, (R)v.im});
   }
 }
 
 }  // namespace
 
-template <typename To>
-int link_to_lanes(cplx<To>* dst, const zd* src, int V, cudaStream_t st) {
+template <typename E>
+int link_to_lanes_v(E* dst, const zd* src, int V, cudaStream_t st) {
   size_t total = (size_t)4 * V * 9;
   size_t g = (total + 255) / 256, cap = (size_t)num_sms() * 16;
-  link_to_lanes_kernel<To><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(dst, src, V);
+  link_to_lanes_kernel<E><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(dst, src, V);
   WMG_LAUNCHED();
   return MG_OK;
 }
-template int link_to_lanes<double>(zd*, const zd*, int, cudaStream_t);
-template int link_to_lanes<float>(zf*, const zd*, int, cudaStream_t);
+template int link_to_lanes_v<zd>(zd*, const zd*, int, cudaStream_t);
+template int link_to_lanes_v<zf>(zf*, const zd*, int, cudaStream_t);
+template int link_to_lanes_v<zh>(zh*, const zd*, int, cudaStream_t);
+template int link_to_lanes_v<zbf>(zbf*, const zd*, int, cudaStream_t);
 
 int dslash_launch(int dtype, void* out, const void* in, const void* links, const Geom& g,
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,

@@ -5,6 +5,8 @@
 #include <vector>
 
 #include "common.cuh"
+#include "vec.cuh"
+#include "df64.cuh"
 
 namespace wmg {
 
@@ -14,9 +16,13 @@ namespace wmg {
 int dslash_launch(int dtype, void* out, const void* in, const void* links, const Geom& g,
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,
                   size_t out_stride, int link_layout = 0);
-// dst[mu][e][site] = src[mu][site][e] (e < 9), converting complex double to To.
+// dst[mu][e][site] = src[mu][site][e] (e < 9), converting complex double to E (vec.cuh).
+template <typename E>
+int link_to_lanes_v(E* dst, const zd* src, int V, cudaStream_t st);
 template <typename To>
-int link_to_lanes(cplx<To>* dst, const zd* src, int V, cudaStream_t st);
+inline int link_to_lanes(cplx<To>* dst, const zd* src, int V, cudaStream_t st) {
+  return link_to_lanes_v<cplx<To>>(dst, src, V, st);
+}
 
 // Autotuned launch shape for a kernel with `nvar` candidate shapes; `run(v)` launches
 // shape v on the caller's arguments.  Returns the chosen shape or -1 on a CUDA error.
@@ -37,80 +43,131 @@ struct ReduceWork {
   void release();
 };
 
-// out[rhs*ldo + i] = sum_k conj(V_i[rhs][k]) w[rhs][k], i < nv; V_i = V + i*vstride.
-template <typename R>
-int multi_dot(zd* out, int ldo, const cplx<R>* V, size_t vstride, int nv, const cplx<R>* w,
-              size_t n, int nrhs, ReduceWork& rw, cudaStream_t st);
+// Routines on vectors of element type E (vec.cuh: zd, zf, zh, zbf); the wrappers without
+// the _v suffix take cplx<R> vectors.
+// out[rhs*ldo + i] = scale * sum_k conj(V_i[rhs][k]) w[rhs][k], i < nv; V_i = V + i*vstride.
+template <typename E>
+int multi_dot_v(zd* out, int ldo, const E* V, size_t vstride, int nv, const E* w, size_t n,
+                int nrhs, ReduceWork& rw, cudaStream_t st, double scale = 1.0);
 // w[rhs] += sgn * sum_i c[rhs*ldc + i] V_i[rhs]   (coefficients read on the device)
-template <typename R>
-int multi_axpy(cplx<R>* w, const cplx<R>* V, size_t vstride, int nv, const zd* c, int ldc,
-               double sgn, size_t n, int nrhs, cudaStream_t st);
-// multi_axpy followed by nrm[rhs*ldn] = ||w[rhs]||_2, in one pass over w
-template <typename R>
-int multi_axpy_norm(cplx<R>* w, const cplx<R>* V, size_t vstride, int nv, const zd* c, int ldc,
-                    double sgn, size_t n, int nrhs, double* nrm, int ldn, ReduceWork& rw,
-                    cudaStream_t st);
-// nrm[rhs*ldn] = ||w[rhs]||_2
-template <typename R>
-int norm2(double* nrm, int ldn, const cplx<R>* w, size_t n, int nrhs, ReduceWork& rw,
-          cudaStream_t st);
+template <typename E>
+int multi_axpy_v(E* w, const E* V, size_t vstride, int nv, const zd* c, int ldc, double sgn,
+                 size_t n, int nrhs, cudaStream_t st);
+// nrm[rhs*ldn] = sqrt(scale) ||w[rhs]||_2
+template <typename E>
+int norm2_v(double* nrm, int ldn, const E* w, size_t n, int nrhs, ReduceWork& rw,
+            cudaStream_t st, double scale = 1.0);
 // y[rhs] = x[rhs] / s[rhs*lds]   (s = 0 gives y = 0)
-template <typename R>
-int scale_inv(cplx<R>* y, const cplx<R>* x, const double* s, int lds, size_t n, int nrhs,
-              cudaStream_t st);
+template <typename E>
+int scale_inv_v(E* y, const E* x, const double* s, int lds, size_t n, int nrhs, cudaStream_t st);
 // y = a*x + b*y with real scalars
-template <typename R>
-int axpby(cplx<R>* y, double a, const cplx<R>* x, double b, size_t n, int nrhs,
-          cudaStream_t st);
-// y = x * s[rhs] (device scale) where mode 0: s, mode 1: 1/s
-template <typename Ro, typename Ri>
-int convert(cplx<Ro>* y, const cplx<Ri>* x, const double* s, int inv, size_t n, int nrhs,
-            cudaStream_t st);
-// y += a * s[rhs] * x (x in lower precision, y FP64)
-template <typename Ri>
-int accumulate_scaled(zd* y, const cplx<Ri>* x, const double* s, size_t n, int nrhs,
-                      cudaStream_t st);
-template <typename R>
-int fill_zero(cplx<R>* y, size_t n, cudaStream_t st);
+template <typename E>
+int axpby_v(E* y, double a, const E* x, double b, size_t n, int nrhs, cudaStream_t st);
+// y += a*x, x in another storage (arithmetic of y)
+template <typename Ey, typename Ex>
+int axpy_mixed(Ey* y, double a, const Ex* x, size_t n, cudaStream_t st);
+// y = a*x1 + b*x2, y in another storage than x1, x2 (arithmetic of x)
+template <typename Eo, typename Ei>
+int lincomb_v(Eo* y, double a, const Ei* x1, double b, const Ei* x2, size_t n, cudaStream_t st);
+// y = x * s[rhs] (device scale) where inv 0: s, inv 1: 1/s; s = nullptr: plain copy
+template <typename Eo, typename Ei>
+int convert_v(Eo* y, const Ei* x, const double* s, int inv, size_t n, int nrhs, cudaStream_t st);
+// y += s[rhs] * x (x in lower precision, y FP64)
+template <typename Ei>
+int accumulate_scaled_v(zd* y, const Ei* x, const double* s, size_t n, int nrhs, cudaStream_t st);
+template <typename E>
+int fill_zero_v(E* y, size_t n, cudaStream_t st);
 // multiply spins 2,3 by -1 (gamma_5 in the chiral basis) on fields of V sites
+template <typename E>
+int apply_gamma5_v(E* y, const E* x, size_t nsites_total, cudaStream_t st);
+
 template <typename R>
-int apply_gamma5(cplx<R>* y, const cplx<R>* x, size_t nsites_total, cudaStream_t st);
+inline int multi_dot(zd* out, int ldo, const cplx<R>* V, size_t vstride, int nv,
+                     const cplx<R>* w, size_t n, int nrhs, ReduceWork& rw, cudaStream_t st) {
+  return multi_dot_v<cplx<R>>(out, ldo, V, vstride, nv, w, n, nrhs, rw, st);
+}
+template <typename R>
+inline int multi_axpy(cplx<R>* w, const cplx<R>* V, size_t vstride, int nv, const zd* c,
+                      int ldc, double sgn, size_t n, int nrhs, cudaStream_t st) {
+  return multi_axpy_v<cplx<R>>(w, V, vstride, nv, c, ldc, sgn, n, nrhs, st);
+}
+template <typename R>
+inline int norm2(double* nrm, int ldn, const cplx<R>* w, size_t n, int nrhs, ReduceWork& rw,
+                 cudaStream_t st) {
+  return norm2_v<cplx<R>>(nrm, ldn, w, n, nrhs, rw, st);
+}
+template <typename R>
+inline int scale_inv(cplx<R>* y, const cplx<R>* x, const double* s, int lds, size_t n, int nrhs,
+                     cudaStream_t st) {
+  return scale_inv_v<cplx<R>>(y, x, s, lds, n, nrhs, st);
+}
+template <typename R>
+inline int axpby(cplx<R>* y, double a, const cplx<R>* x, double b, size_t n, int nrhs,
+                 cudaStream_t st) {
+  return axpby_v<cplx<R>>(y, a, x, b, n, nrhs, st);
+}
+template <typename Ro, typename Ri>
+inline int convert(cplx<Ro>* y, const cplx<Ri>* x, const double* s, int inv, size_t n, int nrhs,
+                   cudaStream_t st) {
+  return convert_v<cplx<Ro>, cplx<Ri>>(y, x, s, inv, n, nrhs, st);
+}
+template <typename Ri>
+inline int accumulate_scaled(zd* y, const cplx<Ri>* x, const double* s, size_t n, int nrhs,
+                             cudaStream_t st) {
+  return accumulate_scaled_v<cplx<Ri>>(y, x, s, n, nrhs, st);
+}
+template <typename R>
+inline int fill_zero(cplx<R>* y, size_t n, cudaStream_t st) {
+  return fill_zero_v<cplx<R>>(y, n, st);
+}
+template <typename R>
+inline int apply_gamma5(cplx<R>* y, const cplx<R>* x, size_t nsites_total, cudaStream_t st) {
+  return apply_gamma5_v<cplx<R>>(y, x, nsites_total, st);
+}
 
 // ------------------------------------------------------------------ Krylov engine
+// Vectors of element type E (vec.cuh).  Bases in half storage use the (1/n) inner product
+// (unit root-mean-square columns); norms and tolerances are relative, so callers see no
+// difference.
+template <typename E>
+using OpV = std::function<int(E* out, const E* in, cudaStream_t st)>;
 template <typename R>
-using Op = std::function<int(cplx<R>* out, const cplx<R>* in, cudaStream_t st)>;
+using Op = OpV<cplx<R>>;
 
-template <typename R>
-class Gmres {
+template <typename E>
+class GmresV {
  public:
-  ~Gmres() { release(); }
+  ~GmresV() { release(); }
   int alloc(size_t n, int nrhs, int m, bool flexible);
   void release();
-  // x = argmin ||b - A x|| over K_m(A, b), x0 = 0 (fixed number of steps, no host sync)
-  int fixed(const Op<R>& A, cplx<R>* x, const cplx<R>* b, int m, cudaStream_t st);
+  // x = argmin ||b - A x|| over K_m(A, b), x0 = 0 (fixed number of steps, no host sync);
+  // accumulate: x += that minimiser instead (x holds the caller's vector on entry)
+  int fixed(const OpV<E>& A, E* x, const E* b, int m, cudaStream_t st, bool accumulate = false);
   // Restarted (F)GMRES from x0 = 0 until ||b - A x|| <= rtol ||b|| for every rhs.
   // M == nullptr: plain GMRES.  Returns MG_OK or MG_ENOCONV; *its = iterations.
   // check_every: host convergence check interval in Arnoldi steps; steps taken past
   // convergence are discarded from the least-squares update, so the iterate and the
   // iteration count equal those of a per-step check.
-  int solve(const Op<R>& A, const Op<R>* M, cplx<R>* x, const cplx<R>* b, double rtol,
-            int restart, int maxiter, int* its, cudaStream_t st, int check_every = 1);
+  int solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double rtol, int restart,
+            int maxiter, int* its, cudaStream_t st, int check_every = 1);
   size_t n = 0;
   int nrhs = 0, m = 0;
   bool flexible = false;
 
  private:
-  int arnoldi_step(const Op<R>& A, const Op<R>* M, int j, cudaStream_t st);
-  cplx<R>* V = nullptr;   // (m+1) x nrhs x n
-  cplx<R>* Z = nullptr;   // m x nrhs x n
-  cplx<R>* w = nullptr;   // nrhs x n
+  int arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st);
+  double ip_scale() const { return VecT<E>::rms ? 1.0 / (double)n : 1.0; }
+  E* V = nullptr;         // (m+1) x nrhs x n
+  E* Z = nullptr;         // m x nrhs x n
+  E* w = nullptr;         // nrhs x n
   zd* small = nullptr;    // device scalars (Hessenberg, rotations, rhs)
   double* dnorm = nullptr;
   double* reshist = nullptr;   // [m][nrhs] residual estimate after each Arnoldi step
   double* host_res = nullptr;  // pinned, (m + 2) * nrhs
   ReduceWork rw;
-  size_t off_H = 0, off_h2 = 0, off_cs = 0, off_g = 0, off_y = 0;
 };
+template <typename R>
+using Gmres = GmresV<cplx<R>>;
 
 // ------------------------------------------------------------------ persistent coarse GMRES
 struct Blocking;
@@ -123,6 +180,9 @@ class CoarseSolver {
   void release();
   int solve(const cplx<R>* Op, const Blocking& B, int k, cplx<R>* x, const cplx<R>* b,
             double rtol, int restart, int maxiter, int* its, cudaStream_t st);
+  // whether one cooperative grid holds the coarse system (each CTA keeps its rows in
+  // registers: at most 2048 rows per CTA, one CTA per SM)
+  bool fits(const Blocking& B, int k) const;
   size_t nc = 0;
   int m = 0;
 
@@ -185,8 +245,8 @@ int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaSt
 // eigenvalues descending in lam[t][c] and eigenvectors in Vec[t][c][c] (column i at
 // Vec[t][*][i], row-major c x c).
 // rtol: a pair is rotated while |G_ab| > rtol sqrt(|G_aa G_bb|) (relative accuracy target).
-int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st,
-             double rtol = 1e-15);
+int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, double rtol,
+             bool df64 = false);
 // out[t][i][row] = sum_c A[t][c][row] Vec[t][c][i] * (scale_inv ? 1/sqrt(lam[t][i]) : 1)
 // for i < kout; out tile stride cmax_out*M.
 // df64: sums of products in double-float arithmetic (df64.cuh) instead of FP64.
@@ -208,8 +268,12 @@ template <typename R>
 int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const Blocking& B,
                    int nrhs, cudaStream_t st);
 // Galerkin: Op[j][blk][b][a] (column-major blocks; blk 0 = X, 1 + dir = Y_dir), FP64.
-int galerkin_build(zd* Op, zd* Xpart, const zd* P, int k, const zd* links, const Geom& g,
-                   const Blocking& B, cudaStream_t st, bool df64 = false);
+// Scratch: Xpart (4 d (2k)^2), PtP (2 d k^2), and with df64 Pdf (P as (hi, lo) pairs, filled
+// here) and Ldf (the links as (hi, lo) pairs, filled by the caller).
+int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, const zd* links,
+                   const zdf* Ldf, const Geom& g, const Blocking& B, cudaStream_t st, bool df64);
+// complex double -> (hi, lo) float pairs
+int to_df(zdf* out, const zd* in, size_t n, cudaStream_t st);
 template <typename R>
 int coarse_apply_launch(cplx<R>* y, const cplx<R>* x, const cplx<R>* Op, int k, const Blocking& B,
                         int nrhs, cudaStream_t st);

@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "reduce.cuh"
+#include "vec.cuh"
 
 namespace wmg {
 
@@ -85,42 +86,53 @@ __device__ double givens_update(zd* s, SmallLayout L, int j, double wnorm) {
   return sqrt(norm2(g[j + 1]));
 }
 
-// CGS pass 1 update fused with the pass 2 projections:
-//   w -= sum_i c_i V_i   then   h2_i = V_i^dag w   (i < nv), one sweep over w.
-template <typename R>
-__global__ void __launch_bounds__(RT)
-cgs_update_dot_kernel(cplx<R>* w, const cplx<R>* __restrict__ V, size_t vstride, int nv,
-                      const zd* c, zd* h2, int ld, size_t n, double* partial, unsigned* counter,
-                      int nblk, int maxvec) {
+// CGS pass 1 update fused with the pass 2 projections and the norm:
+//   w -= sum_i h1_i V_i,  then  h2_i = V_i^dag w (i < nv)  and  s = ||w||^2, one sweep over w.
+// The last CTA completes column j of the Hessenberg matrix: with V orthonormal, the vector
+// left after the pass 2 update, w - V h2, has squared norm s - ||h2||^2 (Pythagoras), which
+// is H[j+1, j]; the Givens step runs on that value, so the pass 2 update needs no reduction
+// of its own.  h2 is O(eps ||A v_j||) after pass 1, so the subtraction loses nothing unless
+// the Krylov space is (numerically) invariant, where H[j+1, j] ~ 0 ends the solve anyway.
+template <typename E>
+__global__ void __launch_bounds__(RT, 3)
+cgs_update_dot_kernel(E* w, const E* __restrict__ V, size_t vstride, int nv,
+                      zd* small, SmallLayout L, int j, size_t n, double* wnorm, double* res,
+                      double* partial, unsigned* counter, int nblk, int maxvec, double scale) {
+  typedef VecT<E> T;
+  typedef typename T::R R;
   constexpr int G = 8;
   __shared__ cplx<R> cs[128];
   __shared__ double sh[(RT / 32) * G * 2];
   int rhs = blockIdx.y;
+  int nrhs = gridDim.y;
+  zd* sm = small + (size_t)rhs * L.stride();
+  const zd* c = sm + L.H() + (size_t)j * (L.m + 1);
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    zd v = c[(size_t)rhs * ld + i];
+    zd v = c[i];
     cs[i] = {(R)(-v.re), (R)(-v.im)};
   }
   __syncthreads();
   size_t chunk = reduce_chunk(n, nblk);
   size_t k0 = (size_t)blockIdx.x * chunk;
   size_t k1 = min(n, k0 + chunk);
-  cplx<R>* wr = w + (size_t)rhs * n;
-  const cplx<R>* vb = V + (size_t)rhs * n;
-  if (nv <= G && sizeof(R) == 4 && ((k0 | k1 | vstride) & 1) == 0) {
+  E* wr = w + (size_t)rhs * n;
+  const E* vb = V + (size_t)rhs * n;
+  R ss = 0;
+  bool packed = false;
+  if constexpr (T::packed) packed = nv <= G && ((k0 | k1 | vstride) & 1) == 0;
+  if (packed) {
     // one sweep: the basis entries stay in registers between the update and the dots
     R ar[G], ai[G];
 #pragma unroll
     for (int q = 0; q < G; ++q) { ar[q] = 0; ai[q] = 0; }
-    float4* w4 = reinterpret_cast<float4*>(wr);
-    const float4* v4 = reinterpret_cast<const float4*>(vb);
-    size_t vs4 = vstride / 2;
+    size_t vs2 = vstride / 2;
     for (size_t k = k0 / 2 + threadIdx.x; k < k1 / 2; k += RT) {
-      float4 a = w4[k];
+      float4 a = T::ld2(wr, k);
       float4 v[G];
 #pragma unroll
       for (int q = 0; q < G; ++q) {
         if (q < nv) {
-          v[q] = v4[(size_t)q * vs4 + k];
+          v[q] = T::ld2(vb + (size_t)q * 2 * vs2, k);
           float cr = (float)cs[q].re, ci = (float)cs[q].im;
           a.x = fmaf(cr, v[q].x, a.x); a.x = fmaf(-ci, v[q].y, a.x);
           a.y = fmaf(cr, v[q].y, a.y); a.y = fmaf(ci, v[q].x, a.y);
@@ -128,7 +140,10 @@ cgs_update_dot_kernel(cplx<R>* w, const cplx<R>* __restrict__ V, size_t vstride,
           a.w = fmaf(cr, v[q].w, a.w); a.w = fmaf(ci, v[q].z, a.w);
         }
       }
-      w4[k] = a;
+      a = T::rnd2(a);   // continue with the values as stored
+      T::st2(wr, k, a);
+      ss = fma((R)a.x, (R)a.x, ss); ss = fma((R)a.y, (R)a.y, ss);
+      ss = fma((R)a.z, (R)a.z, ss); ss = fma((R)a.w, (R)a.w, ss);
 #pragma unroll
       for (int q = 0; q < G; ++q) {
         if (q < nv) {
@@ -140,112 +155,113 @@ cgs_update_dot_kernel(cplx<R>* w, const cplx<R>* __restrict__ V, size_t vstride,
       }
     }
     cta_store_partials<R, G>(ar, ai, nv, 0, rhs, maxvec, nblk, partial, reinterpret_cast<R*>(sh));
-    if (!last_cta(counter, rhs, nblk)) return;
-    finish_partials(partial, nv, nblk, maxvec, rhs, h2, nullptr, ld, 0);
-    if (threadIdx.x == 0) counter[rhs] = 0;
-    return;
-  }
-  // general case: update sweep, then projection sweeps over groups of G vectors
-  for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
-    cplx<R> a = wr[k];
-    for (int i = 0; i < nv; ++i) cfma(a, cs[i], vb[(size_t)i * vstride + k]);
-    wr[k] = a;
-  }
-  // projections on the updated w (each thread rereads its own elements: L1/L2 hits)
-  for (int i0 = 0; i0 < nv; i0 += G) {
-    int ni = min(G, nv - i0);
-    R ar[G], ai[G];
-#pragma unroll
-    for (int q = 0; q < G; ++q) { ar[q] = 0; ai[q] = 0; }
+  } else {
+    // general case: update sweep (with the norm), then projection sweeps over groups of G
     for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
-      cplx<R> b = wr[k];
+      cplx<R> a = T::ld(wr, k);
+      for (int i = 0; i < nv; ++i) cfma(a, cs[i], T::ld(vb, (size_t)i * vstride + k));
+      a = T::rnd(a);
+      T::st(wr, k, a);
+      ss = fma(a.re, a.re, ss);
+      ss = fma(a.im, a.im, ss);
+    }
+    // projections on the updated w (each thread rereads its own elements: L1/L2 hits)
+    for (int i0 = 0; i0 < nv; i0 += G) {
+      int ni = min(G, nv - i0);
+      R ar[G], ai[G];
 #pragma unroll
-      for (int q = 0; q < G; ++q) {
-        if (q < ni) {
-          cplx<R> a = vb[(size_t)(i0 + q) * vstride + k];
-          ar[q] = fma(a.re, b.re, ar[q]); ar[q] = fma(a.im, b.im, ar[q]);
-          ai[q] = fma(a.re, b.im, ai[q]); ai[q] = fma(-a.im, b.re, ai[q]);
+      for (int q = 0; q < G; ++q) { ar[q] = 0; ai[q] = 0; }
+      for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
+        cplx<R> b = T::ld(wr, k);
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          if (q < ni) {
+            cplx<R> a = T::ld(vb, (size_t)(i0 + q) * vstride + k);
+            ar[q] = fma(a.re, b.re, ar[q]); ar[q] = fma(a.im, b.im, ar[q]);
+            ai[q] = fma(a.re, b.im, ai[q]); ai[q] = fma(-a.im, b.re, ai[q]);
+          }
         }
       }
+      cta_store_partials<R, G>(ar, ai, ni, i0, rhs, maxvec, nblk, partial,
+                               reinterpret_cast<R*>(sh));
     }
-    cta_store_partials<R, G>(ar, ai, ni, i0, rhs, maxvec, nblk, partial,
-                             reinterpret_cast<R*>(sh));
   }
+  // ||w||^2 goes to slot nv (< maxvec: nv <= m)
+  R zero = 0;
+  cta_store_partials<R, 1>(&ss, &zero, 1, nv, rhs, maxvec, nblk, partial,
+                           reinterpret_cast<R*>(sh));
   if (!last_cta(counter, rhs, nblk)) return;
-  finish_partials(partial, nv, nblk, maxvec, rhs, h2, nullptr, ld, 0);
-  if (threadIdx.x == 0) counter[rhs] = 0;
+  finish_partials(partial, nv + 1, nblk, maxvec, rhs, small + L.h2(), nullptr, L.stride(), 0,
+                  scale);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    counter[rhs] = 0;
+    const zd* h2 = sm + L.h2();
+    double hh = 0;
+    for (int i = 0; i < nv; ++i) hh += norm2(h2[i]);
+    double b2 = h2[nv].re - hh;
+    double beta = b2 > 0 ? sqrt(b2) : 0.0;
+    wnorm[rhs] = beta;
+    res[(size_t)j * nrhs + rhs] = givens_update(sm, L, j, beta);
+  }
 }
 
-// CGS pass 2 update fused with the norm and the Givens step:
-//   w -= sum_i c_i V_i ; ||w|| ; column j of the Hessenberg matrix reduced (last CTA).
-template <typename R>
-__global__ void __launch_bounds__(RT)
-cgs_update_norm_givens_kernel(cplx<R>* w, const cplx<R>* __restrict__ V, size_t vstride,
-                              int nv, zd* small, SmallLayout L, int j, size_t n, double* wnorm,
-                              double* res, double* partial, unsigned* counter, int nblk,
-                              int maxvec) {
+// CGS pass 2 update written straight into the next basis column:
+//   v_{j+1} = (w - sum_i h2_i V_i) / H[j+1, j]   (0 if H[j+1, j] = 0).
+template <typename E>
+__global__ void __launch_bounds__(256)
+cgs_update_scale_kernel(E* vout, const E* __restrict__ w, const E* __restrict__ V,
+                        size_t vstride, int nv, const zd* small, SmallLayout L,
+                        const double* wnorm, size_t n) {
+  typedef VecT<E> T;
+  typedef typename T::R R;
   __shared__ cplx<R> cs[128];
-  __shared__ double sh[64];
   int rhs = blockIdx.y;
-  int nrhs = gridDim.y;
-  zd* sm = small + (size_t)rhs * L.stride();
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    zd v = sm[L.h2() + i];
-    cs[i] = {(R)(-v.re), (R)(-v.im)};
-  }
+  const zd* h2 = small + (size_t)rhs * L.stride() + L.h2();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = {(R)(-h2[i].re), (R)(-h2[i].im)};
   __syncthreads();
-  size_t chunk = reduce_chunk(n, nblk);
-  size_t k0 = (size_t)blockIdx.x * chunk;
-  size_t k1 = min(n, k0 + chunk);
-  cplx<R>* wr = w + (size_t)rhs * n;
-  const cplx<R>* vb = V + (size_t)rhs * n;
-  R acc2 = 0;
-  if (sizeof(R) == 4 && ((k0 | k1 | vstride) & 1) == 0) {
-    float4* w4 = reinterpret_cast<float4*>(wr);
-    const float4* v4 = reinterpret_cast<const float4*>(vb);
-    size_t vs4 = vstride / 2;
-    for (size_t k = k0 / 2 + threadIdx.x; k < k1 / 2; k += RT) {
-      float4 a = w4[k];
+  double beta = wnorm[rhs];
+  R f = beta > 0 ? (R)(1.0 / beta) : (R)0;
+  const E* wr = w + (size_t)rhs * n;
+  const E* vb = V + (size_t)rhs * n;
+  E* outr = vout + (size_t)rhs * n;
+  bool packed = false;
+  if constexpr (T::packed) packed = ((n | vstride) & 1) == 0;
+  if (packed) {
+    size_t vs2 = vstride / 2;
+    float ff = (float)f;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n / 2;
+         k += (size_t)gridDim.x * blockDim.x) {
+      float4 a = T::ld2(wr, k);
       for (int i = 0; i < nv; ++i) {
-        float4 v = v4[(size_t)i * vs4 + k];
+        float4 v = T::ld2(vb + (size_t)i * 2 * vs2, k);
         float cr = (float)cs[i].re, ci = (float)cs[i].im;
         a.x = fmaf(cr, v.x, a.x); a.x = fmaf(-ci, v.y, a.x);
         a.y = fmaf(cr, v.y, a.y); a.y = fmaf(ci, v.x, a.y);
         a.z = fmaf(cr, v.z, a.z); a.z = fmaf(-ci, v.w, a.z);
         a.w = fmaf(cr, v.w, a.w); a.w = fmaf(ci, v.z, a.w);
       }
-      w4[k] = a;
-      acc2 = fma((R)a.x, (R)a.x, acc2); acc2 = fma((R)a.y, (R)a.y, acc2);
-      acc2 = fma((R)a.z, (R)a.z, acc2); acc2 = fma((R)a.w, (R)a.w, acc2);
+      T::st2(outr, k, make_float4(ff * a.x, ff * a.y, ff * a.z, ff * a.w));
     }
-  } else {
-    for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
-      cplx<R> a = wr[k];
-      for (int i = 0; i < nv; ++i) cfma(a, cs[i], vb[(size_t)i * vstride + k]);
-      wr[k] = a;
-      acc2 = fma(a.re, a.re, acc2);
-      acc2 = fma(a.im, a.im, acc2);
-    }
+    return;
   }
-  acc2 = warp_sum_r(acc2);
-  R* shr = reinterpret_cast<R*>(sh);
-  if ((threadIdx.x & 31) == 0) shr[threadIdx.x >> 5] = acc2;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    R t = 0;
-    for (int wv = 0; wv < RT / 32; ++wv) t += shr[wv];
-    double* p = partial + ((size_t)rhs * maxvec * nblk + blockIdx.x) * 2;
-    p[0] = (double)t;
-    p[1] = 0;
-    __threadfence();
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    cplx<R> a = T::ld(wr, k);
+    for (int i = 0; i < nv; ++i) cfma(a, cs[i], T::ld(vb, (size_t)i * vstride + k));
+    T::st(outr, k, {f * a.re, f * a.im});
   }
-  if (!last_cta(counter, rhs, nblk)) return;
-  finish_partials(partial, 1, nblk, maxvec, rhs, nullptr, wnorm, 1, 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    counter[rhs] = 0;
-    res[(size_t)j * nrhs + rhs] = givens_update(sm, L, j, wnorm[rhs]);
-  }
+}
+
+// CTAs per (rhs) row of a reduction launch: one wave of `kernel` at its occupancy, capped by
+// the partial buffer's chunk count.
+template <typename K>
+int reduction_blocks(K kernel, int cap) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, RT, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  int b = occ * num_sms();
+  return b < cap ? b : cap;
 }
 
 // Back substitution R y = g over the first `steps` columns.
@@ -267,36 +283,36 @@ __global__ void solve_kernel(zd* small, SmallLayout L, int steps, int nrhs) {
 
 }  // namespace
 
-template <typename R>
-int Gmres<R>::alloc(size_t n_, int nrhs_, int m_, bool flexible_) {
+template <typename E>
+int GmresV<E>::alloc(size_t n_, int nrhs_, int m_, bool flexible_) {
   if (n == n_ && nrhs >= nrhs_ && m >= m_ && (flexible || !flexible_)) return MG_OK;
   release();
   n = n_;
   nrhs = nrhs_;
   m = m_;
   flexible = flexible_;
-  size_t fb = sizeof(cplx<R>) * n * nrhs;
-  WMG_CUDA(cudaMalloc(&V, fb * (m + 1)));
-  if (flexible) WMG_CUDA(cudaMalloc(&Z, fb * m));
-  WMG_CUDA(cudaMalloc(&w, fb));
+  size_t fb = sizeof(E) * n * nrhs;
+  WMG_TRY(dev_alloc(&V, fb * (m + 1)));
+  if (flexible) WMG_TRY(dev_alloc(&Z, fb * m));
+  WMG_TRY(dev_alloc(&w, fb));
   SmallLayout L{m};
-  WMG_CUDA(cudaMalloc(&small, sizeof(zd) * L.stride() * nrhs));
-  WMG_CUDA(cudaMalloc(&dnorm, sizeof(double) * nrhs * 4));
-  WMG_CUDA(cudaMalloc(&reshist, sizeof(double) * nrhs * m));
-  WMG_CUDA(cudaMallocHost(&host_res, sizeof(double) * nrhs * (m + 2)));
+  WMG_TRY(dev_alloc(&small, sizeof(zd) * L.stride() * nrhs));
+  WMG_TRY(dev_alloc(&dnorm, sizeof(double) * nrhs * 4));
+  WMG_TRY(dev_alloc(&reshist, sizeof(double) * nrhs * m));
+  WMG_TRY(host_alloc(&host_res, sizeof(double) * nrhs * (m + 2)));
   WMG_TRY(rw.alloc(n, nrhs, m + 1));
   return MG_OK;
 }
 
-template <typename R>
-void Gmres<R>::release() {
-  if (V) cudaFree(V);
-  if (Z) cudaFree(Z);
-  if (w) cudaFree(w);
-  if (small) cudaFree(small);
-  if (dnorm) cudaFree(dnorm);
-  if (reshist) cudaFree(reshist);
-  if (host_res) cudaFreeHost(host_res);
+template <typename E>
+void GmresV<E>::release() {
+  dev_free(V);
+  dev_free(Z);
+  dev_free(w);
+  dev_free(small);
+  dev_free(dnorm);
+  dev_free(reshist);
+  host_free(host_res);
   V = Z = w = nullptr;
   small = nullptr;
   dnorm = nullptr;
@@ -309,76 +325,80 @@ void Gmres<R>::release() {
 }
 
 // dnorm layout: [0..nrhs) current ||w||, [nrhs..2nrhs) beta, [2nrhs..3nrhs) residual estimate
-template <typename R>
-int Gmres<R>::arnoldi_step(const Op<R>& A, const Op<R>* M, int j, cudaStream_t st) {
+template <typename E>
+int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st) {
   SmallLayout L{m};
   size_t fs = n * nrhs;
-  cplx<R>* vj = V + (size_t)j * fs;
+  E* vj = V + (size_t)j * fs;
   if (M) {
-    cplx<R>* zj = Z + (size_t)j * fs;
+    E* zj = Z + (size_t)j * fs;
     WMG_TRY((*M)(zj, vj, st));
     WMG_TRY(A(w, zj, st));
   } else {
     WMG_TRY(A(w, vj, st));
   }
   zd* Hcol = small + L.H() + (size_t)j * (m + 1);
-  // CGS2 in three sweeps: projections; update + re-projections; update + norm + Givens
-  WMG_TRY(multi_dot<R>(Hcol, L.stride(), V, fs, j + 1, w, n, nrhs, rw, st));
-  dim3 grid(rw.nblk, nrhs);
-  double fb = (double)nrhs * n * sizeof(cplx<R>);
+  // CGS2 in three sweeps: projections; update + re-projections + norm + Givens;
+  // update + normalisation into column j + 1
+  WMG_TRY(multi_dot_v<E>(Hcol, L.stride(), V, fs, j + 1, w, n, nrhs, rw, st, ip_scale()));
+  static const int ud_blocks = reduction_blocks(cgs_update_dot_kernel<E>, 1 << 30);
+  int nb = ud_blocks < rw.nblk ? ud_blocks : rw.nblk;
+  double fb = (double)nrhs * n * sizeof(E);
   {
-  ProfScope ps("cgs_update_dot", (j + 3) * fb, 16.0 * (j + 1) * n * nrhs, st);
-  cgs_update_dot_kernel<R><<<grid, RT, 0, st>>>(w, V, fs, j + 1, Hcol, small + L.h2(),
-                                               L.stride(), n, rw.partial, rw.counter, rw.nblk,
-                                               rw.maxvec);
+  ProfScope ps("cgs_update_dot", (j + 3) * fb, (16.0 * (j + 1) + 4.0) * n * nrhs, st);
+  cgs_update_dot_kernel<E><<<dim3(nb, nrhs), RT, 0, st>>>(w, V, fs, j + 1, small, L, j, n, dnorm,
+                                                         reshist, rw.partial, rw.counter, nb,
+                                                         rw.maxvec, ip_scale());
   WMG_LAUNCHED();
   }
   {
-  ProfScope ps("cgs_update_norm", (j + 3) * fb, 8.0 * (j + 2) * n * nrhs, st);
-  cgs_update_norm_givens_kernel<R><<<grid, RT, 0, st>>>(w, V, fs, j + 1, small, L, j, n, dnorm,
-                                                       reshist, rw.partial, rw.counter,
-                                                       rw.nblk, rw.maxvec);
+  ProfScope ps("cgs_update_scale", (j + 3) * fb, (8.0 * (j + 1) + 2.0) * n * nrhs, st);
+  size_t g = (n / 2 + 255) / 256;
+  size_t cap = (size_t)num_sms() * 8;
+  dim3 grid((unsigned)(g < cap ? (g < 1 ? 1 : g) : cap), nrhs);
+  cgs_update_scale_kernel<E><<<grid, 256, 0, st>>>(V + (size_t)(j + 1) * fs, w, V, fs, j + 1,
+                                                   small, L, dnorm, n);
   WMG_LAUNCHED();
   }
-  WMG_TRY(scale_inv<R>(V + (size_t)(j + 1) * fs, w, dnorm, 1, n, nrhs, st));
   return MG_OK;
 }
 
-template <typename R>
-int Gmres<R>::fixed(const Op<R>& A, cplx<R>* x, const cplx<R>* b, int steps, cudaStream_t st) {
+template <typename E>
+int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t st,
+                     bool accumulate) {
   if (steps > m) return fail(MG_EINVAL, "gmres: more steps than allocated");
   SmallLayout L{m};
   size_t fs = n * nrhs;
-  WMG_TRY(fill_zero<R>(x, fs, st));
+  if (!accumulate) WMG_TRY(fill_zero_v<E>(x, fs, st));
   if (steps == 0) return MG_OK;
-  WMG_TRY(norm2<R>(dnorm + nrhs, 1, b, n, nrhs, rw, st));
+  WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, b, n, nrhs, rw, st, ip_scale()));
   init_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
   WMG_LAUNCHED();
-  WMG_TRY(scale_inv<R>(V, b, dnorm + nrhs, 1, n, nrhs, st));
+  WMG_TRY(scale_inv_v<E>(V, b, dnorm + nrhs, 1, n, nrhs, st));
   for (int j = 0; j < steps; ++j) WMG_TRY(arnoldi_step(A, nullptr, j, st));
   solve_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, steps, nrhs);
   WMG_LAUNCHED();
-  WMG_TRY(multi_axpy<R>(x, V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
+  WMG_TRY(multi_axpy_v<E>(x, V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
   return MG_OK;
 }
 
-template <typename R>
-int Gmres<R>::solve(const Op<R>& A, const Op<R>* M, cplx<R>* x, const cplx<R>* b, double rtol,
-                    int restart, int maxiter, int* its_out, cudaStream_t st, int check_every) {
+template <typename E>
+int GmresV<E>::solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double rtol,
+                     int restart, int maxiter, int* its_out, cudaStream_t st, int check_every) {
   if (restart > m) return fail(MG_EINVAL, "gmres: restart longer than allocated");
   if (M && !flexible) return fail(MG_EINVAL, "gmres: flexible space not allocated");
   SmallLayout L{m};
   size_t fs = n * nrhs;
-  WMG_TRY(fill_zero<R>(x, fs, st));
+  WMG_TRY(fill_zero_v<E>(x, fs, st));
   // bnorm on host
   std::vector<double> bn(nrhs), res(nrhs);
-  WMG_TRY(norm2<R>(dnorm + nrhs, 1, b, n, nrhs, rw, st));
+  WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, b, n, nrhs, rw, st, ip_scale()));
   WMG_CUDA(cudaMemcpyAsync(host_res, dnorm + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
   WMG_CUDA(cudaStreamSynchronize(st));
   for (int r = 0; r < nrhs; ++r) bn[r] = host_res[r];
   // r = b (x0 = 0); the residual lives in w between cycles
-  cplx<R>* rvec = w;
-  WMG_CUDA(cudaMemcpyAsync(rvec, b, sizeof(cplx<R>) * fs, cudaMemcpyDeviceToDevice, st));
+  E* rvec = w;
+  WMG_CUDA(cudaMemcpyAsync(rvec, b, sizeof(E) * fs, cudaMemcpyDeviceToDevice, st));
   int its = 0;
   bool converged = false;
   for (int r = 0; r < nrhs; ++r) res[r] = bn[r];
@@ -389,10 +409,10 @@ int Gmres<R>::solve(const Op<R>& A, const Op<R>* M, cplx<R>* x, const cplx<R>* b
   };
   if (all_done(res.data())) converged = true;
   while (!converged && its < maxiter) {
-    WMG_TRY(norm2<R>(dnorm + nrhs, 1, rvec, n, nrhs, rw, st));
+    WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, rvec, n, nrhs, rw, st, ip_scale()));
     init_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
     WMG_LAUNCHED();
-    WMG_TRY(scale_inv<R>(V, rvec, dnorm + nrhs, 1, n, nrhs, st));
+    WMG_TRY(scale_inv_v<E>(V, rvec, dnorm + nrhs, 1, n, nrhs, st));
     int steps = 0, checked = 0;
     if (check_every < 1) check_every = 1;
     for (int j = 0; j < restart && its < maxiter; ++j) {
@@ -421,11 +441,11 @@ int Gmres<R>::solve(const Op<R>& A, const Op<R>* M, cplx<R>* x, const cplx<R>* b
     }
     solve_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, steps, nrhs);
     WMG_LAUNCHED();
-    WMG_TRY(multi_axpy<R>(x, M ? Z : V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
+    WMG_TRY(multi_axpy_v<E>(x, M ? Z : V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
     // true residual r = b - A x
     WMG_TRY(A(rvec, x, st));
-    WMG_TRY(axpby<R>(rvec, 1.0, b, -1.0, fs, 1, st));
-    WMG_TRY(norm2<R>(dnorm + 3 * nrhs, 1, rvec, n, nrhs, rw, st));
+    WMG_TRY(axpby_v<E>(rvec, 1.0, b, -1.0, fs, 1, st));
+    WMG_TRY(norm2_v<E>(dnorm + 3 * nrhs, 1, rvec, n, nrhs, rw, st, ip_scale()));
     WMG_CUDA(cudaMemcpyAsync(host_res + nrhs, dnorm + 3 * nrhs, sizeof(double) * nrhs,
                              cudaMemcpyDeviceToHost, st));
     WMG_CUDA(cudaStreamSynchronize(st));
@@ -436,7 +456,9 @@ int Gmres<R>::solve(const Op<R>& A, const Op<R>* M, cplx<R>* x, const cplx<R>* b
   return MG_OK;
 }
 
-template class Gmres<float>;
-template class Gmres<double>;
+template class GmresV<zf>;
+template class GmresV<zd>;
+template class GmresV<zh>;
+template class GmresV<zbf>;
 
 }  // namespace wmg

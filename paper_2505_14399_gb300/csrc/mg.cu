@@ -5,6 +5,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -22,12 +23,16 @@ struct mg_handle {
   zd* links64 = nullptr;       // ABI layout (Galerkin, gradient)
   zd* links64L = nullptr;      // lane-contiguous [mu][9][site] copies for the stencil
   zf* links32L = nullptr;
+  void* links16L = nullptr;    // half-storage solve: zh or zbf lane-contiguous links
   zd* P64 = nullptr;
   zf* P32 = nullptr;
   double* sigma = nullptr;   // [tile][k]
   double* hist = nullptr;    // [n_s][tile][k]
   zd* Op64 = nullptr;
   zf* Op32 = nullptr;
+  zd* PtP = nullptr;           // [tile][k][k] Gram matrices of the P tiles (Galerkin diagonal)
+  zdf* Pdf = nullptr;          // double-float Galerkin: P and the links as (hi, lo) pairs
+  zdf* Ldf = nullptr;
   bool have_P = false, have_coarse = false;
   // solver state, sized for `nrhs`
   int nrhs = 0;
@@ -35,6 +40,9 @@ struct mg_handle {
   Gmres<float> outer32, coarse32, post32;
   CoarseSolver<double> csol64;
   CoarseSolver<float> csol32;
+  GmresV<zh> posth;            // half-storage post-smoother (solve_dtype MG_F16)
+  GmresV<zbf> postb;           // (solve_dtype MG_BF16)
+  void *kwh = nullptr, *keh = nullptr;
   zd *x64 = nullptr, *r64 = nullptr, *t64 = nullptr;
   zf *e32 = nullptr, *r32 = nullptr;
   zd *vc64 = nullptr, *ec64 = nullptr, *kw64 = nullptr, *ke64 = nullptr;
@@ -53,8 +61,13 @@ namespace {
 
 template <typename T>
 void dfree(T*& p) {
-  if (p) cudaFree(p);
+  dev_free(p);
   p = nullptr;
+}
+
+// Galerkin sums of products in double-float (explicit, or by default in the mixed forms)
+bool galerkin_df(const mg_params& p) {
+  return p.fp64_emulation > 0 || (p.fp64_emulation < 0 && p.solve_dtype != MG_C128);
 }
 
 int validate(const mg_params* p, bool need_svd) {
@@ -74,8 +87,9 @@ int validate(const mg_params* p, bool need_svd) {
     if (p->setup_dtype != MG_C128 && p->setup_dtype != MG_C64)
       return fail(MG_EINVAL, "setup_dtype must be MG_C128 or MG_C64");
   }
-  if (p->solve_dtype != MG_C128 && p->solve_dtype != MG_C64)
-    return fail(MG_EINVAL, "solve_dtype must be MG_C128 or MG_C64");
+  if (p->solve_dtype != MG_C128 && p->solve_dtype != MG_C64 && p->solve_dtype != MG_F16 &&
+      p->solve_dtype != MG_BF16)
+    return fail(MG_EINVAL, "solve_dtype must be MG_C128, MG_C64, MG_F16 or MG_BF16");
   if (p->post_smooth < 0 || p->post_smooth > 64) return fail(MG_EINVAL, "post_smooth in [0, 64]");
   if (p->coarse_restart < 1 || p->coarse_restart > 128) return fail(MG_EINVAL, "coarse_restart in [1, 128]");
   if (p->outer_restart < 1 || p->outer_restart > 128) return fail(MG_EINVAL, "outer_restart in [1, 128]");
@@ -99,21 +113,32 @@ int create_handle(mg_handle** out, const void* links, const mg_params* p, bool n
   h->nf = (size_t)h->g.V * 12;
   h->nc = (size_t)h->B.d * 2 * h->k;
   size_t lb = (size_t)4 * h->g.V * 9;
-  WMG_CUDA(cudaMalloc(&h->links64, lb * sizeof(zd)));
-  WMG_CUDA(cudaMalloc(&h->links64L, lb * sizeof(zd)));
-  WMG_CUDA(cudaMalloc(&h->links32L, lb * sizeof(zf)));
+  WMG_TRY(dev_alloc(&h->links64, lb * sizeof(zd)));
+  WMG_TRY(dev_alloc(&h->links64L, lb * sizeof(zd)));
+  WMG_TRY(dev_alloc(&h->links32L, lb * sizeof(zf)));
   Staged sl;
   WMG_TRY(stage_in(sl, links, lb * sizeof(zd), st));
   WMG_CUDA(cudaMemcpyAsync(h->links64, sl.dev, lb * sizeof(zd), cudaMemcpyDeviceToDevice, st));
   WMG_TRY(link_to_lanes<double>(h->links64L, h->links64, h->g.V, st));
   WMG_TRY(link_to_lanes<float>(h->links32L, h->links64, h->g.V, st));
+  if (p->solve_dtype == MG_F16 || p->solve_dtype == MG_BF16) {
+    WMG_TRY(dev_alloc(&h->links16L, lb * 4));
+    if (p->solve_dtype == MG_F16) WMG_TRY(link_to_lanes_v<zh>((zh*)h->links16L, h->links64, h->g.V, st));
+    else WMG_TRY(link_to_lanes_v<zbf>((zbf*)h->links16L, h->links64, h->g.V, st));
+  }
   size_t ntile = (size_t)h->B.d * 2;
-  WMG_CUDA(cudaMalloc(&h->P64, ntile * h->k * h->B.M * sizeof(zd)));
-  WMG_CUDA(cudaMalloc(&h->P32, ntile * h->k * h->B.M * sizeof(zf)));
-  WMG_CUDA(cudaMalloc(&h->sigma, ntile * h->k * sizeof(double)));
+  WMG_TRY(dev_alloc(&h->P64, ntile * h->k * h->B.M * sizeof(zd)));
+  WMG_TRY(dev_alloc(&h->P32, ntile * h->k * h->B.M * sizeof(zf)));
+  WMG_TRY(dev_alloc(&h->sigma, ntile * h->k * sizeof(double)));
+  WMG_TRY(dev_alloc(&h->PtP, ntile * h->k * h->k * sizeof(zd)));
+  if (galerkin_df(*p)) {
+    WMG_TRY(dev_alloc(&h->Pdf, ntile * h->k * h->B.M * sizeof(zdf)));
+    WMG_TRY(dev_alloc(&h->Ldf, lb * sizeof(zdf)));
+    WMG_TRY(to_df(h->Ldf, h->links64, lb, st));
+  }
   WMG_CUDA(cudaMemsetAsync(h->sigma, 0, ntile * h->k * sizeof(double), st));
   int ns = p->n_s > 0 ? p->n_s : 1;
-  WMG_CUDA(cudaMalloc(&h->hist, (size_t)ns * ntile * h->k * sizeof(double)));
+  WMG_TRY(dev_alloc(&h->hist, (size_t)ns * ntile * h->k * sizeof(double)));
   WMG_CUDA(cudaMemsetAsync(h->hist, 0, (size_t)ns * ntile * h->k * sizeof(double), st));
   WMG_CUDA(cudaStreamSynchronize(st));
   *out = h.release();
@@ -154,18 +179,19 @@ int run_setup(mg_handle* h, cudaStream_t st) {
   Gmres<R> gm;
   int status = MG_OK;
   auto cleanup = [&]() {
+    cudaStreamSynchronize(st);   // the cached blocks are reused only after their work ends
     dfree(phi); dfree(psi); dfree(tmp); dfree(T0); dfree(T1); dfree(G); dfree(Vec); dfree(lam);
   };
 #define STEP(x) do { status = (x); if (status != MG_OK) { cleanup(); return status; } } while (0)
 #define CSTEP(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { cleanup(); return fail(e_ == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); } } while (0)
-  CSTEP(cudaMalloc(&phi, fr * sizeof(cplx<R>)));
-  CSTEP(cudaMalloc(&psi, fr * sizeof(cplx<R>)));
-  CSTEP(cudaMalloc(&tmp, fr * sizeof(cplx<R>)));
-  CSTEP(cudaMalloc(&T0, ntile * cmax * M * sizeof(zd)));
-  CSTEP(cudaMalloc(&T1, ntile * cmax * M * sizeof(zd)));
-  CSTEP(cudaMalloc(&G, ntile * cmax * cmax * sizeof(zd)));
-  CSTEP(cudaMalloc(&Vec, ntile * cmax * cmax * sizeof(zd)));
-  CSTEP(cudaMalloc(&lam, ntile * cmax * sizeof(double)));
+  STEP(dev_alloc(&phi, fr * sizeof(cplx<R>)));
+  STEP(dev_alloc(&psi, fr * sizeof(cplx<R>)));
+  STEP(dev_alloc(&tmp, fr * sizeof(cplx<R>)));
+  STEP(dev_alloc(&T0, ntile * cmax * M * sizeof(zd)));
+  STEP(dev_alloc(&T1, ntile * cmax * M * sizeof(zd)));
+  STEP(dev_alloc(&G, ntile * cmax * cmax * sizeof(zd)));
+  STEP(dev_alloc(&Vec, ntile * cmax * cmax * sizeof(zd)));
+  STEP(dev_alloc(&lam, ntile * cmax * sizeof(double)));
   zd* cur = T0;
   zd* oth = T1;
   int kk = 0;
@@ -180,12 +206,12 @@ int run_setup(mg_handle* h, cudaStream_t st) {
     int kn = c < k ? c : k;
     bool last = s == p.n_s - 1;
     STEP(tile_gram(G, cur, cmax, c, h->B, st, df));
-    STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, eig_tol));
+    STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, eig_tol, df));
     if (p.svd_refine > 0 || (p.svd_refine < 0 && sizeof(R) == 8)) {
       // B = A V (all c columns), then a second Gram/eig pass on B
       STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, c, 0, h->B, st, df));
       STEP(tile_gram(G, oth, cmax, c, h->B, st, df));
-      STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, eig_tol));
+      STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, eig_tol, df));
       STEP(tile_update(cur, cmax, oth, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st, df));
     } else {
       STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, kn, last ? 1 : 0, h->B, st, df));
@@ -211,35 +237,44 @@ int run_setup(mg_handle* h, cudaStream_t st) {
 
 int ensure_solver(mg_handle* h, int nrhs) {
   if (h->nrhs == nrhs) return MG_OK;
+  if (h->nrhs) cudaDeviceSynchronize();   // no queued work may still use the old buffers
   h->free_solver();
   size_t f = h->nf * nrhs, c = h->nc * nrhs;
   const mg_params& p = h->p;
-  WMG_CUDA(cudaMalloc(&h->x64, f * sizeof(zd)));
-  WMG_CUDA(cudaMalloc(&h->r64, f * sizeof(zd)));
-  WMG_CUDA(cudaMalloc(&h->t64, f * sizeof(zd)));
-  WMG_CUDA(cudaMalloc(&h->dscal, 8 * nrhs * sizeof(double)));
-  WMG_CUDA(cudaMallocHost(&h->hscal, 8 * nrhs * sizeof(double)));
+  WMG_TRY(dev_alloc(&h->x64, f * sizeof(zd)));
+  WMG_TRY(dev_alloc(&h->r64, f * sizeof(zd)));
+  WMG_TRY(dev_alloc(&h->t64, f * sizeof(zd)));
+  WMG_TRY(dev_alloc(&h->dscal, 8 * nrhs * sizeof(double)));
+  WMG_TRY(host_alloc(&h->hscal, 8 * nrhs * sizeof(double)));
   WMG_TRY(h->rw.alloc(h->nf, nrhs, 2));
   if (p.solve_dtype == MG_C128) {
-    WMG_CUDA(cudaMalloc(&h->vc64, c * sizeof(zd)));
-    WMG_CUDA(cudaMalloc(&h->ec64, c * sizeof(zd)));
-    WMG_CUDA(cudaMalloc(&h->kw64, f * sizeof(zd)));
-    WMG_CUDA(cudaMalloc(&h->ke64, f * sizeof(zd)));
+    WMG_TRY(dev_alloc(&h->vc64, c * sizeof(zd)));
+    WMG_TRY(dev_alloc(&h->ec64, c * sizeof(zd)));
+    WMG_TRY(dev_alloc(&h->kw64, f * sizeof(zd)));
+    WMG_TRY(dev_alloc(&h->ke64, f * sizeof(zd)));
     WMG_TRY(h->outer64.alloc(h->nf, nrhs, p.outer_restart, true));
     WMG_TRY(h->coarse64.alloc(h->nc, nrhs, p.coarse_restart, false));
     if (p.coarse_persistent) WMG_TRY(h->csol64.alloc(h->nc, p.coarse_restart));
     WMG_TRY(h->post64.alloc(h->nf, nrhs, p.post_smooth > 0 ? p.post_smooth : 1, false));
   } else {
-    WMG_CUDA(cudaMalloc(&h->e32, f * sizeof(zf)));
-    WMG_CUDA(cudaMalloc(&h->r32, f * sizeof(zf)));
-    WMG_CUDA(cudaMalloc(&h->vc32, c * sizeof(zf)));
-    WMG_CUDA(cudaMalloc(&h->ec32, c * sizeof(zf)));
-    WMG_CUDA(cudaMalloc(&h->kw32, f * sizeof(zf)));
-    WMG_CUDA(cudaMalloc(&h->ke32, f * sizeof(zf)));
+    WMG_TRY(dev_alloc(&h->e32, f * sizeof(zf)));
+    WMG_TRY(dev_alloc(&h->r32, f * sizeof(zf)));
+    WMG_TRY(dev_alloc(&h->vc32, c * sizeof(zf)));
+    WMG_TRY(dev_alloc(&h->ec32, c * sizeof(zf)));
+    WMG_TRY(dev_alloc(&h->kw32, f * sizeof(zf)));
+    WMG_TRY(dev_alloc(&h->ke32, f * sizeof(zf)));
     WMG_TRY(h->outer32.alloc(h->nf, nrhs, p.outer_restart, true));
     WMG_TRY(h->coarse32.alloc(h->nc, nrhs, p.coarse_restart, false));
     if (p.coarse_persistent) WMG_TRY(h->csol32.alloc(h->nc, p.coarse_restart));
-    WMG_TRY(h->post32.alloc(h->nf, nrhs, p.post_smooth > 0 ? p.post_smooth : 1, false));
+    int ps = p.post_smooth > 0 ? p.post_smooth : 1;
+    if (p.solve_dtype == MG_F16 || p.solve_dtype == MG_BF16) {
+      WMG_TRY(dev_alloc(&h->kwh, f * 4));
+      WMG_TRY(dev_alloc(&h->keh, f * 4));
+      if (p.solve_dtype == MG_F16) WMG_TRY(h->posth.alloc(h->nf, nrhs, ps, false));
+      else WMG_TRY(h->postb.alloc(h->nf, nrhs, ps, false));
+    } else {
+      WMG_TRY(h->post32.alloc(h->nf, nrhs, ps, false));
+    }
   }
   h->nrhs = nrhs;
   return MG_OK;
@@ -284,6 +319,30 @@ Op<R> fine_op(mg_handle* h, int nrhs) {
   };
 }
 
+// the fine operator on half-storage fields (lane-contiguous half links, FP32 arithmetic)
+template <typename H>
+OpV<H> fine_op_half(mg_handle* h, int nrhs) {
+  int dt = std::is_same<H, zh>::value ? MG_F16 : MG_BF16;
+  return [h, nrhs, dt](H* out, const H* in, cudaStream_t st) -> int {
+    return dslash_launch(dt, out, in, h->links16L, h->g, -1, 0, nrhs, st, h->nf, h->nf, 1);
+  };
+}
+
+// Post-smoother in half storage: e = GMRES_steps(D, v - D z) with the residual, the Krylov
+// basis and the stencil in H, then z += e.  v is a unit-norm FGMRES column, so its entries
+// are ~ n^-1/2; the residual is scaled by n^1/2 before it is stored in H and the correction
+// scaled back, which keeps FP16 entries O(1).
+template <typename H>
+int post_smooth_half(mg_handle* h, GmresV<H>& gm, zf* z, const zf* v, zf* kw, int nrhs,
+                     cudaStream_t st) {
+  size_t f = h->nf * nrhs;
+  double s = std::sqrt((double)h->nf);
+  WMG_TRY((lincomb_v<H, zf>((H*)h->kwh, s, v, -s, kw, f, st)));   // kw holds D z
+  WMG_TRY(gm.fixed(fine_op_half<H>(h, nrhs), (H*)h->keh, (const H*)h->kwh, h->p.post_smooth, st));
+  WMG_TRY((axpy_mixed<zf, H>(z, 1.0 / s, (const H*)h->keh, f, st)));
+  return MG_OK;
+}
+
 template <typename R>
 Op<R> coarse_op(mg_handle* h, int nrhs) {
   return [h, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t st) -> int {
@@ -302,7 +361,7 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
     cplx<R>* ke = Lvl<R>::ke(h);
     WMG_TRY(restrict_launch<R>(vc, v, Lvl<R>::P(h), h->k, h->B, nrhs, st));
     int its = 0;
-    if (p.coarse_persistent) {
+    if (p.coarse_persistent && Lvl<R>::csol(h).fits(h->B, h->k)) {
       // one cooperative launch per system: the whole restarted coarse GMRES on the device
       for (int r = 0; r < nrhs; ++r) {
         int itr = 0;
@@ -324,6 +383,10 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
     if (p.post_smooth > 0) {
       Op<R> D = fine_op<R>(h, nrhs);
       WMG_TRY(D(kw, z, st));
+      if constexpr (std::is_same<R, float>::value) {
+        if (p.solve_dtype == MG_F16) return post_smooth_half<zh>(h, h->posth, z, v, kw, nrhs, st);
+        if (p.solve_dtype == MG_BF16) return post_smooth_half<zbf>(h, h->postb, z, v, kw, nrhs, st);
+      }
       WMG_TRY(axpby<R>(kw, 1.0, v, -1.0, h->nf * nrhs, 1, st));   // kw = v - D z
       WMG_TRY(Lvl<R>::post(h).fixed(D, ke, kw, p.post_smooth, st));
       WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, h->nf * nrhs, 1, st));    // z += e
@@ -423,19 +486,21 @@ int check_ready(mg_handle* h, bool need_coarse) {
 
 mg_handle::~mg_handle() {
   free_solver();
-  dfree(links64); dfree(links64L); dfree(links32L); dfree(P64); dfree(P32); dfree(sigma); dfree(hist);
-  dfree(Op64); dfree(Op32);
+  dfree(links64); dfree(links64L); dfree(links32L); dfree(links16L); dfree(P64); dfree(P32); dfree(sigma); dfree(hist);
+  dfree(Op64); dfree(Op32); dfree(PtP); dfree(Pdf); dfree(Ldf);
 }
 
 void mg_handle::free_solver() {
   outer64.release(); coarse64.release(); post64.release();
   outer32.release(); coarse32.release(); post32.release();
   csol64.release(); csol32.release();
+  posth.release(); postb.release();
+  dfree(kwh); dfree(keh);
   dfree(x64); dfree(r64); dfree(t64); dfree(e32); dfree(r32);
   dfree(vc64); dfree(ec64); dfree(kw64); dfree(ke64);
   dfree(vc32); dfree(ec32); dfree(kw32); dfree(ke32);
   dfree(dscal);
-  if (hscal) cudaFreeHost(hscal);
+  host_free(hscal);
   hscal = nullptr;
   rw.release();
   nrhs = 0;
@@ -465,13 +530,14 @@ extern "C" int coarse_build(mg_handle* h, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   size_t ne = (size_t)4 * h->k * h->k;
   if (!h->Op64) {
-    WMG_CUDA(cudaMalloc(&h->Op64, (size_t)h->B.d * 9 * ne * sizeof(zd)));
-    WMG_CUDA(cudaMalloc(&h->Op32, (size_t)h->B.d * 9 * ne * sizeof(zf)));
+    WMG_TRY(dev_alloc(&h->Op64, (size_t)h->B.d * 9 * ne * sizeof(zd)));
+    WMG_TRY(dev_alloc(&h->Op32, (size_t)h->B.d * 9 * ne * sizeof(zf)));
   }
   zd* Xpart = nullptr;
   WMG_CUDA(cudaMallocAsync(&Xpart, (size_t)4 * h->B.d * ne * sizeof(zd), st));
-  bool df = h->p.fp64_emulation > 0 || (h->p.fp64_emulation < 0 && h->p.solve_dtype == MG_C64);
-  int s = galerkin_build(h->Op64, Xpart, h->P64, h->k, h->links64, h->g, h->B, st, df);
+  bool df = galerkin_df(h->p);
+  int s = galerkin_build(h->Op64, Xpart, h->P64, h->Pdf, h->PtP, h->k, h->links64, h->Ldf, h->g,
+                         h->B, st, df);
   cudaFreeAsync(Xpart, st);
   WMG_TRY(s);
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
@@ -530,9 +596,9 @@ extern "C" int coarse_build_noalloc(mg_handle* h, void* stream) {
                            "yet; call coarse_build once first (it allocates that storage)");
   void* scratch = nullptr;
   WMG_TRY(galerkin_scratch(&scratch));
-  bool df = h->p.fp64_emulation > 0 || (h->p.fp64_emulation < 0 && h->p.solve_dtype == MG_C64);
-  WMG_TRY(galerkin_build(h->Op64, static_cast<zd*>(scratch), h->P64, h->k, h->links64, h->g,
-                         h->B, st, df));
+  bool df = galerkin_df(h->p);
+  WMG_TRY(galerkin_build(h->Op64, static_cast<zd*>(scratch), h->P64, h->Pdf, h->PtP, h->k,
+                         h->links64, h->Ldf, h->g, h->B, st, df));
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
   WMG_CUDA(cudaStreamSynchronize(st));
   h->have_coarse = true;
@@ -636,13 +702,17 @@ extern "C" int mg_apply_fine(mg_handle* h, void* out, const void* in, int nrhs, 
                              int dagger, void* stream) {
   if (!h || !out || !in || nrhs < 1) return fail(MG_EINVAL, "mg_apply_fine: bad arguments");
   if (out == in) return fail(MG_EINVAL, "mg_apply_fine: out must not alias in");
-  if (dtype != MG_C128 && dtype != MG_C64) return fail(MG_EINVAL, "mg_apply_fine: dtype");
+  bool half = dtype == MG_F16 || dtype == MG_BF16;
+  if (dtype != MG_C128 && dtype != MG_C64 && !half) return fail(MG_EINVAL, "mg_apply_fine: dtype");
+  if (half && dtype != h->p.solve_dtype)
+    return fail(MG_EINVAL, "mg_apply_fine: half storage needs a handle with that solve_dtype");
   cudaStream_t st = (cudaStream_t)stream;
-  size_t bytes = h->nf * nrhs * (dtype == MG_C128 ? sizeof(zd) : sizeof(zf));
+  size_t bytes = h->nf * nrhs * dtype_bytes(dtype);
   Staged si, so;
   WMG_TRY(stage_in(si, in, bytes, st));
   WMG_TRY(stage_out_alloc(so, out, bytes, st));
-  const void* L = dtype == MG_C128 ? (const void*)h->links64L : (const void*)h->links32L;
+  const void* L = dtype == MG_C128 ? (const void*)h->links64L
+                  : dtype == MG_C64 ? (const void*)h->links32L : (const void*)h->links16L;
   WMG_TRY(dslash_launch(dtype, so.dev, si.dev, L, h->g, -1, dagger, nrhs, st, h->nf, h->nf, 1));
   WMG_TRY(stage_out_finish(so, out, bytes, st));
   return MG_OK;

@@ -32,24 +32,34 @@ __host__ __device__ __forceinline__ size_t reduce_chunk(size_t n, int nblk) {
 }
 
 // Final reduction over the nblk partials of every (rhs, i), done by the last CTA.
-// mode 0: complex dot -> out[rhs*ldo + i]; mode 1: norm -> dout[rhs*ldo] = sqrt(re).
+// mode 0: complex dot -> out[rhs*ldo + i] = scale * sum; mode 1: norm -> dout[rhs*ldo] =
+// sqrt(scale * re).  scale = 1 except for the (1/n) inner product of half-storage bases.
 // One warp per vector: lanes sum strided partials, then a shuffle tree (fixed order).
 __device__ __forceinline__ void finish_partials(const double* partial, int nv, int nblk,
                                                 int maxvec, int rhs, zd* out, double* dout,
-                                                int ldo, int mode) {
+                                                int ldo, int mode, double scale = 1.0) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = wid; i < nv; i += nw) {
-    const double* p = partial + ((size_t)rhs * maxvec + i) * nblk * 2;
-    double a = 0, b = 0;
-    for (int k = lane; k < nblk; k += 32) {
-      a += __ldcg(p + 2 * k);
-      b += __ldcg(p + 2 * k + 1);
+    const double2* p = reinterpret_cast<const double2*>(partial) + ((size_t)rhs * maxvec + i) * nblk;
+    // four independent accumulators keep four 16-byte loads in flight per lane
+    double2 s0 = {0, 0}, s1 = {0, 0}, s2 = {0, 0}, s3 = {0, 0};
+    int k = lane;
+    for (; k + 96 < nblk; k += 128) {
+      double2 v0 = __ldcg(p + k), v1 = __ldcg(p + k + 32);
+      double2 v2 = __ldcg(p + k + 64), v3 = __ldcg(p + k + 96);
+      s0.x += v0.x; s0.y += v0.y; s1.x += v1.x; s1.y += v1.y;
+      s2.x += v2.x; s2.y += v2.y; s3.x += v3.x; s3.y += v3.y;
     }
+    for (; k < nblk; k += 32) {
+      double2 v0 = __ldcg(p + k);
+      s0.x += v0.x; s0.y += v0.y;
+    }
+    double a = (s0.x + s1.x) + (s2.x + s3.x), b = (s0.y + s1.y) + (s2.y + s3.y);
     a = warp_sum(a);
     b = warp_sum(b);
     if (lane == 0) {
-      if (mode == 0) out[(size_t)rhs * ldo + i] = {a, b};
-      else dout[(size_t)rhs * ldo] = sqrt(a);
+      if (mode == 0) out[(size_t)rhs * ldo + i] = {a * scale, b * scale};
+      else dout[(size_t)rhs * ldo] = sqrt(a * scale);
     }
   }
 }

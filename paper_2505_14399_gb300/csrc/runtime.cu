@@ -2,6 +2,8 @@
 #include <atomic>
 #include <cstring>
 #include <map>
+#include <unordered_map>
+#include <utility>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -41,6 +43,86 @@ int make_geom(Geom& g, const int dims[4], double kappa, const double w[4], const
   g.kappa = kappa;
   return MG_OK;
 }
+
+// ------------------------------------------------------------------ memory cache
+// Device and pinned-host blocks released by the library are kept, per device and rounded
+// size, and handed out again: building and destroying hierarchies of the same shape in a
+// loop then costs no cudaMalloc / cudaFree (both of which synchronise the device).  On an
+// allocation failure the cache is returned to the driver and the allocation retried.
+// Callers release blocks only when no queued work still uses them.
+namespace {
+
+struct MemCache {
+  std::mutex mu;
+  std::multimap<std::pair<int, size_t>, void*> free_dev, free_host;
+  std::unordered_map<void*, std::pair<int, size_t>> live_dev, live_host;
+};
+
+MemCache& mem_cache() {
+  static MemCache* c = new MemCache();   // never destroyed: blocks may be freed at exit
+  return *c;
+}
+
+size_t round_block(size_t b) {
+  size_t g = b < ((size_t)1 << 20) ? 512 : ((size_t)2 << 20);
+  if (b == 0) b = 1;
+  return (b + g - 1) / g * g;
+}
+
+int cached_alloc(void** p, size_t bytes, bool host) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::pair<int, size_t> key(dev, round_block(bytes));
+  MemCache& c = mem_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  auto& fl = host ? c.free_host : c.free_dev;
+  auto& live = host ? c.live_host : c.live_dev;
+  auto it = fl.find(key);
+  if (it != fl.end()) {
+    *p = it->second;
+    fl.erase(it);
+    live[*p] = key;
+    return MG_OK;
+  }
+  cudaError_t e = host ? cudaMallocHost(p, key.second) : cudaMalloc(p, key.second);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+    for (auto& kv : fl) {
+      if (host) cudaFreeHost(kv.second);
+      else cudaFree(kv.second);
+    }
+    fl.clear();
+    e = host ? cudaMallocHost(p, key.second) : cudaMalloc(p, key.second);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA,
+                std::string(host ? "pinned" : "device") + " allocation of " +
+                    std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  }
+  live[*p] = key;
+  return MG_OK;
+}
+
+void cached_free(void* p, bool host) {
+  if (!p) return;
+  MemCache& c = mem_cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  auto& live = host ? c.live_host : c.live_dev;
+  auto it = live.find(p);
+  if (it == live.end()) return;
+  (host ? c.free_host : c.free_dev).emplace(it->second, p);
+  live.erase(it);
+}
+
+}  // namespace
+
+int dev_alloc_bytes(void** p, size_t bytes) { return cached_alloc(p, bytes, false); }
+void dev_free(void* p) { cached_free(p, false); }
+int host_alloc_bytes(void** p, size_t bytes) { return cached_alloc(p, bytes, true); }
+void host_free(void* p) { cached_free(p, true); }
 
 int num_sms() {
   static int n = 0;

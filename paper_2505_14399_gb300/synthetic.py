@@ -96,7 +96,7 @@ WORKLOADS = {
 # field is too large for that run; it reuses the 16^3 x 32 value (same link distribution).
 KAPPA_CRIT = {
     "c2_16^3x32_near_critical": 0.136551654556,
-    "c3_16^3x64_aniso": None,
+    "c3_16^3x64_aniso": 0.165482664759,
 }
 KAPPA_CRIT["c4_32^3x64_12rhs"] = KAPPA_CRIT["c2_16^3x32_near_critical"]
 

@@ -102,3 +102,16 @@ def test_handle_operator_lane_contiguous_links(dtype, dagger):
         ref = wilson.dslash(psi[r], U, dims, 0.127, w, bc, dagger)
         assert rel(out[r], ref) < TOL[dtype]
     h.close()
+
+
+@pytest.mark.parametrize("dt,tdt,tol", [("f16", torch.float16, 2e-3), ("bf16", torch.bfloat16, 1.5e-2)])
+def test_handle_operator_half_links(dt, tdt, tol):
+    """The half-storage smoother's stencil (lane-contiguous half links) against the oracle."""
+    U, psi = _fields(DIMS, 2, 60)
+    w, bc = ANISO, (1, 1, 1, -1)
+    p = api.params(DIMS, (2, 2, 2, 2), 0.127, 4, 4, 1, hop_weight=w, bc=bc, solve_dtype=dt)
+    h = api.Hierarchy(to_dev(U), p, setup=False)
+    out = from_half_pair(h.apply_fine(half_pair(psi, tdt)))
+    for r in range(2):
+        assert rel(out[r], wilson.dslash(psi[r], U, DIMS, 0.127, w, bc)) < tol
+    h.close()

@@ -108,3 +108,42 @@ def test_full_size_near_critical_solve():
         x, info = h.solve(to_dev(b), tol=1e-10, maxiter=2000)
         assert _true_residual(c, U, x.cpu().numpy()[0], b[0]) <= 1e-10
         h.close()
+
+
+@pytest.mark.parametrize("solve_dtype", ["f16", "bf16"])
+@pytest.mark.parametrize("cfg", [C1, C5])
+def test_half_storage_smoother_solve_reaches_1e10(cfg, solve_dtype):
+    """K-cycle post-smoother in FP16/BF16 storage (FP32 arithmetic) inside FP64 refinement."""
+    U = links_for(cfg)
+    b = synthetic.gaussian_rhs(cfg["dims"], cfg["rhs_seed"], 2)
+    p = params_for(cfg, setup_dtype="c64", solve_dtype=solve_dtype)
+    h = api.Hierarchy(to_dev(U), p)
+    h.coarse_build()
+    x, info = h.solve(to_dev(b), tol=1e-10)
+    x = x.cpu().numpy()
+    for r in range(2):
+        assert _true_residual(cfg, U, x[r], b[r]) <= 1e-10
+    # the half smoother may cost iterations, not correctness: stay within 2x of FP32's
+    p32 = params_for(cfg, setup_dtype="c64", solve_dtype="c64")
+    h32 = api.Hierarchy(to_dev(U), p32)
+    h32.coarse_build()
+    _, info32 = h32.solve(to_dev(b), tol=1e-10)
+    assert info["outer"] <= 2 * info32["outer"] + 2
+    h.close()
+    h32.close()
+
+
+def test_full_size_anisotropic_half_storage_solve():
+    """16^3 x 64, w_t = 1/3.5, 2x2x2x4 aggregates, k = 24, 64 test vectors streamed in 4:
+    FP16 and BF16 smoother storage inside FP64 refinement reach 1e-10 (FP64 oracle check)."""
+    cfg = synthetic.WORKLOADS["c3_16^3x64_aniso"]
+    c = dict(cfg, kappa=synthetic.kappa_of(cfg))
+    U = links_for(cfg)
+    b = synthetic.gaussian_rhs(cfg["dims"], cfg["rhs_seed"])
+    for solve_dtype in ("f16", "bf16"):
+        p = params_for(c, setup_dtype="c64", solve_dtype=solve_dtype)
+        h = api.Hierarchy(to_dev(U), p)
+        h.coarse_build()
+        x, info = h.solve(to_dev(b), tol=1e-10, maxiter=3000)
+        assert _true_residual(c, U, x.cpu().numpy()[0], b[0]) <= 1e-10
+        h.close()
