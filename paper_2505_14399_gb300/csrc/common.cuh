@@ -15,6 +15,11 @@ namespace wmg {
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
 void count_launch(long long n = 1);
+// Pinned, device-visible error word: a kernel whose bounded wait gives up stores a non-zero
+// code there; take_device_error() returns it (0 if none) and clears it.  Read only after the
+// stream that ran the kernel has been synchronised.
+int* device_error_word();
+int take_device_error();
 // Library-wide caching allocator (device memory and pinned host memory); see runtime.cu.
 int dev_alloc_bytes(void** p, size_t bytes);
 void dev_free(void* p);

@@ -7,10 +7,12 @@
 // `check_every` steps of a tolerance-driven solve.  All nrhs systems advance in lockstep.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
 #include "reduce.cuh"
+#include "tma.cuh"
 #include "vec.cuh"
 
 namespace wmg {
@@ -253,6 +255,214 @@ cgs_update_scale_kernel(E* vout, const E* __restrict__ w, const E* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------- bulk-copy fed CGS sweeps
+// Complex-float bases of at most ST_NV columns.  Each CTA owns one contiguous chunk of every
+// vector (the fixed partition of the reductions) and streams it through shared memory in
+// tiles (1024 or 512 elements): thread 0 issues one bulk copy per vector and tile into a ring of
+// `stages` buffers, completion arrives as transaction bytes on the stage's mbarrier, and
+// the CTA computes from shared memory while the following tiles are in flight.  The bytes
+// in flight per SM no longer depend on registers (the register-fed sweeps above reached a
+// third of the HBM bandwidth at their occupancy).
+//   MODE 0: h_i = V_i^dag w                      (CGS pass 1 projections)
+//   MODE 1: w -= V c; h2_i = V_i^dag w; ||w||^2; Givens step as in cgs_update_dot_kernel
+// A bounded wait that gives up sets *err, waits (bounded) for the CTA's copies in flight
+// and returns; the caller reports MG_ETIMEOUT.
+constexpr int ST_NV = 16;      // columns handled (NVM = 8 or 16 accumulator sets)
+constexpr int ST_MAXS = 6;
+constexpr int ST_WAIT = 1 << 20;
+
+// Tile length (complex elements per vector, a multiple of 2 RT) and ring depth: about
+// 100 KB of copies in flight per CTA, two CTAs per SM.
+__host__ __device__ inline int st_te(int nv) { return nv <= 3 ? 4 * RT : 2 * RT; }
+__host__ __device__ inline int st_stages(int nv) {
+  return nv <= 1 ? 6 : nv <= 3 ? 3 : nv <= 5 ? 4 : nv <= 8 ? 3 : 2;
+}
+__host__ __device__ inline size_t st_smem(int nv) {
+  return (size_t)st_stages(nv) * (nv + 1) * st_te(nv) * sizeof(zf);
+}
+
+template <int MODE, int NVM>
+__global__ void __launch_bounds__(RT)
+stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_t n, zd* out,
+                  int ldo, zd* small, SmallLayout L, int j, double* wnorm, double* res,
+                  double* partial, unsigned* counter, int nblk, int maxvec, double scale,
+                  int* err) {
+  extern __shared__ __align__(16) unsigned char st_raw[];
+  __shared__ uint64_t bars[ST_MAXS];
+  __shared__ float sh[(RT / 32) * NVM * 2];
+  __shared__ zf cs[NVM];
+  float4* buf = reinterpret_cast<float4*>(st_raw);
+  const int stages = st_stages(nv);
+  const int te = st_te(nv);
+  const int tp = te / 2;   // float4 packs per vector and tile
+  const int nvec = nv + 1;
+  int rhs = blockIdx.y;
+  int nrhs = gridDim.y;
+  zd* sm = small ? small + (size_t)rhs * L.stride() : nullptr;
+  if (MODE == 1 && threadIdx.x < nv) {
+    zd c = sm[L.H() + (size_t)j * (L.m + 1) + threadIdx.x];
+    cs[threadIdx.x] = {(float)(-c.re), (float)(-c.im)};
+  }
+  size_t chunk = reduce_chunk(n, nblk);
+  size_t k0 = (size_t)blockIdx.x * chunk;
+  size_t k1 = min(n, k0 + chunk);
+  size_t len = k1 > k0 ? k1 - k0 : 0;
+  int ntiles = (int)((len + te - 1) / te);
+  zf* wr = w + (size_t)rhs * n;
+  const zf* vb = V + (size_t)rhs * n;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < stages; ++st) mbar_init(&bars[st], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int it) {   // thread 0: tile `it` of every vector into stage it % stages
+    int st = it % stages;
+    size_t e0 = k0 + (size_t)it * te;
+    uint32_t cnt = (uint32_t)min((size_t)te, k1 - e0);
+    uint32_t bytes = cnt * (uint32_t)sizeof(zf);
+    mbar_arrive_expect_tx(&bars[st], bytes * nvec);
+    bulk_g2s(buf + (size_t)(st * nvec) * tp, wr + e0, bytes, &bars[st]);
+    for (int q = 0; q < nv; ++q)
+      bulk_g2s(buf + (size_t)(st * nvec + 1 + q) * tp, vb + (size_t)q * vstride + e0, bytes,
+               &bars[st]);
+  };
+  if (threadIdx.x == 0)
+    for (int it = 0; it < stages && it < ntiles; ++it) issue(it);
+  float ar[NVM], ai[NVM];
+#pragma unroll
+  for (int q = 0; q < NVM; ++q) { ar[q] = 0.f; ai[q] = 0.f; }
+  float ss = 0.f;
+  int failed_at = -1;
+  for (int it = 0; it < ntiles; ++it) {
+    int st = it % stages;
+    bool ok = mbar_wait(&bars[st], (uint32_t)((it / stages) & 1), ST_WAIT);
+    if (ok) {
+      size_t e0 = (size_t)it * te;
+      int cnt = (int)min((size_t)te, len - e0);
+      const float4* sb = buf + (size_t)(st * nvec) * tp;
+      for (int p = threadIdx.x; 2 * p < cnt; p += RT) {
+        float4 a = sb[p];
+        if (MODE == 1) {
+#pragma unroll
+          for (int q = 0; q < NVM; ++q) {
+            if (q < nv) {
+              float4 v = sb[(size_t)(1 + q) * tp + p];
+              float cr = cs[q].re, ci = cs[q].im;
+              a.x = fmaf(cr, v.x, a.x); a.x = fmaf(-ci, v.y, a.x);
+              a.y = fmaf(cr, v.y, a.y); a.y = fmaf(ci, v.x, a.y);
+              a.z = fmaf(cr, v.z, a.z); a.z = fmaf(-ci, v.w, a.z);
+              a.w = fmaf(cr, v.w, a.w); a.w = fmaf(ci, v.z, a.w);
+            }
+          }
+          reinterpret_cast<float4*>(wr + k0 + e0)[p] = a;
+          ss = fmaf(a.x, a.x, ss); ss = fmaf(a.y, a.y, ss);
+          ss = fmaf(a.z, a.z, ss); ss = fmaf(a.w, a.w, ss);
+        }
+#pragma unroll
+        for (int q = 0; q < NVM; ++q) {
+          if (q < nv) {
+            float4 v = sb[(size_t)(1 + q) * tp + p];
+            ar[q] = fmaf(v.x, a.x, ar[q]); ar[q] = fmaf(v.y, a.y, ar[q]);
+            ar[q] = fmaf(v.z, a.z, ar[q]); ar[q] = fmaf(v.w, a.w, ar[q]);
+            ai[q] = fmaf(v.x, a.y, ai[q]); ai[q] = fmaf(-v.y, a.x, ai[q]);
+            ai[q] = fmaf(v.z, a.w, ai[q]); ai[q] = fmaf(-v.w, a.z, ai[q]);
+          }
+        }
+      }
+    }
+    // every thread is done with stage st (and agrees whether its copies arrived)
+    if (!__syncthreads_and(ok)) {
+      failed_at = it;
+      break;
+    }
+    if (threadIdx.x == 0 && it + stages < ntiles) {
+      fence_proxy_async();
+      issue(it + stages);
+    }
+  }
+  if (failed_at >= 0) {
+    if (threadIdx.x == 0) {
+      *(volatile int*)err = 1;
+      // let the copies still in flight land before the CTA's shared memory is released
+      for (int it = failed_at; it < ntiles && it < failed_at + stages; ++it)
+        mbar_wait(&bars[it % stages], (uint32_t)((it / stages) & 1), ST_WAIT);
+    }
+    return;
+  }
+  cta_store_partials<float, NVM>(ar, ai, nv, 0, rhs, maxvec, nblk, partial, sh);
+  if (MODE == 1) {
+    float zero = 0.f;
+    cta_store_partials<float, 1>(&ss, &zero, 1, nv, rhs, maxvec, nblk, partial, sh);
+  }
+  if (!last_cta(counter, rhs, nblk)) return;
+  if (MODE == 0) {
+    finish_partials(partial, nv, nblk, maxvec, rhs, out, nullptr, ldo, 0, scale);
+    if (threadIdx.x == 0) counter[rhs] = 0;
+    return;
+  }
+  finish_partials(partial, nv + 1, nblk, maxvec, rhs, small + L.h2(), nullptr, L.stride(), 0,
+                  scale);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    counter[rhs] = 0;
+    const zd* h2 = sm + L.h2();
+    double hh = 0;
+    for (int i = 0; i < nv; ++i) hh += norm2(h2[i]);
+    double b2 = h2[nv].re - hh;
+    double beta = b2 > 0 ? sqrt(b2) : 0.0;
+    wnorm[rhs] = beta;
+    res[(size_t)j * nrhs + rhs] = givens_update(sm, L, j, beta);
+  }
+}
+
+template <int NVM>
+int stream_cgs_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* small,
+                      SmallLayout L, int j, double* dnorm, double* reshist, ReduceWork& rw,
+                      double scale, int* err, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    int mx = (int)st_smem(NVM);
+    WMG_CUDA(cudaFuncSetAttribute(stream_cgs_kernel<0, NVM>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    WMG_CUDA(cudaFuncSetAttribute(stream_cgs_kernel<1, NVM>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    attr = true;
+  }
+  int nv = j + 1;
+  int per_sm = NVM <= 8 ? 2 : 1;
+  int nb = rw.nblk < per_sm * num_sms() ? rw.nblk : per_sm * num_sms();
+  size_t sh = st_smem(nv);
+  double fb = (double)nrhs * n * sizeof(zf);
+  zd* Hcol = small + L.H() + (size_t)j * (L.m + 1);
+  {
+    ProfScope ps("multi_dot", (nv + 1) * fb, 8.0 * nv * n * nrhs, st);
+    stream_cgs_kernel<0, NVM><<<dim3(nb, nrhs), RT, sh, st>>>(
+        w, V, fs, nv, n, Hcol, L.stride(), small, L, j, dnorm, reshist, rw.partial, rw.counter,
+        nb, rw.maxvec, scale, err);
+    WMG_LAUNCHED();
+  }
+  {
+    ProfScope ps("cgs_update_dot", (nv + 2) * fb, (16.0 * nv + 4.0) * n * nrhs, st);
+    stream_cgs_kernel<1, NVM><<<dim3(nb, nrhs), RT, sh, st>>>(
+        w, V, fs, nv, n, nullptr, 0, small, L, j, dnorm, reshist, rw.partial, rw.counter, nb,
+        rw.maxvec, scale, err);
+    WMG_LAUNCHED();
+  }
+  return MG_OK;
+}
+
+// Both CGS reduction sweeps of Arnoldi step j through the bulk-copy kernels (complex float,
+// j + 1 <= ST_NV basis columns).
+int stream_cgs(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* small, SmallLayout L,
+               int j, double* dnorm, double* reshist, ReduceWork& rw, double scale,
+               cudaStream_t st) {
+  int* err = device_error_word();
+  if (!err) return fail(MG_ECUDA, "stream_cgs: no error word");
+  if (j + 1 <= 8)
+    return stream_cgs_launch<8>(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, scale, err, st);
+  return stream_cgs_launch<16>(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, scale, err, st);
+}
+
 // CTAs per (rhs) row of a reduction launch: one wave of `kernel` at its occupancy, capped by
 // the partial buffer's chunk count.
 template <typename K>
@@ -340,16 +550,24 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
   zd* Hcol = small + L.H() + (size_t)j * (m + 1);
   // CGS2 in three sweeps: projections; update + re-projections + norm + Givens;
   // update + normalisation into column j + 1
-  WMG_TRY(multi_dot_v<E>(Hcol, L.stride(), V, fs, j + 1, w, n, nrhs, rw, st, ip_scale()));
-  static const int ud_blocks = reduction_blocks(cgs_update_dot_kernel<E>, 1 << 30);
-  int nb = ud_blocks < rw.nblk ? ud_blocks : rw.nblk;
   double fb = (double)nrhs * n * sizeof(E);
-  {
-  ProfScope ps("cgs_update_dot", (j + 3) * fb, (16.0 * (j + 1) + 4.0) * n * nrhs, st);
-  cgs_update_dot_kernel<E><<<dim3(nb, nrhs), RT, 0, st>>>(w, V, fs, j + 1, small, L, j, n, dnorm,
-                                                         reshist, rw.partial, rw.counter, nb,
-                                                         rw.maxvec, ip_scale());
-  WMG_LAUNCHED();
+  bool streamed = false;
+  if constexpr (std::is_same<E, zf>::value) {
+    if (j + 1 <= ST_NV && (n & 1) == 0) {
+      WMG_TRY(stream_cgs(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, ip_scale(), st));
+      streamed = true;
+    }
+  }
+  if (!streamed) {
+    WMG_TRY(multi_dot_v<E>(Hcol, L.stride(), V, fs, j + 1, w, n, nrhs, rw, st, ip_scale()));
+    static const int ud_blocks = reduction_blocks(cgs_update_dot_kernel<E>, 1 << 30);
+    int nb = ud_blocks < rw.nblk ? ud_blocks : rw.nblk;
+    ProfScope ps("cgs_update_dot", (j + 3) * fb, (16.0 * (j + 1) + 4.0) * n * nrhs, st);
+    cgs_update_dot_kernel<E><<<dim3(nb, nrhs), RT, 0, st>>>(w, V, fs, j + 1, small, L, j, n,
+                                                           dnorm, reshist, rw.partial,
+                                                           rw.counter, nb, rw.maxvec,
+                                                           ip_scale());
+    WMG_LAUNCHED();
   }
   {
   ProfScope ps("cgs_update_scale", (j + 3) * fb, (8.0 * (j + 1) + 2.0) * n * nrhs, st);
@@ -425,6 +643,7 @@ int GmresV<E>::solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double 
                                sizeof(double) * nrhs * (j + 1 - checked), cudaMemcpyDeviceToHost,
                                st));
       WMG_CUDA(cudaStreamSynchronize(st));
+      if (take_device_error()) return fail(MG_ETIMEOUT, "gmres: a bounded copy wait gave up");
       bool stop = false;
       for (int jj = checked; jj <= j && !stop; ++jj) {
         const double* rr = host_res + (size_t)(jj - checked) * nrhs;
@@ -449,6 +668,7 @@ int GmresV<E>::solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double 
     WMG_CUDA(cudaMemcpyAsync(host_res + nrhs, dnorm + 3 * nrhs, sizeof(double) * nrhs,
                              cudaMemcpyDeviceToHost, st));
     WMG_CUDA(cudaStreamSynchronize(st));
+    if (take_device_error()) return fail(MG_ETIMEOUT, "gmres: a bounded copy wait gave up");
     if (all_done(host_res + nrhs)) converged = true;
   }
   if (its_out) *its_out = its;

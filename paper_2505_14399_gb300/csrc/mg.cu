@@ -227,6 +227,10 @@ int run_setup(mg_handle* h, cudaStream_t st) {
   CSTEP(cudaMemcpyAsync(h->sigma, h->hist + (size_t)(p.n_s - 1) * ntile * k,
                         ntile * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CSTEP(cudaStreamSynchronize(st));
+  if (take_device_error()) {
+    cleanup();
+    return fail(MG_ETIMEOUT, "setup: a bounded copy wait gave up");
+  }
   cleanup();
   h->have_P = true;
   h->have_coarse = false;
@@ -462,6 +466,7 @@ int solve_impl(mg_handle* h, zd* x, const zd* b, int nrhs, double tol, int maxit
   WMG_CUDA(cudaMemcpyAsync(h->r64, b, h->nf * nrhs * sizeof(zd), cudaMemcpyDeviceToDevice, st));
   WMG_TRY(axpby<double>(h->r64, -1.0, h->t64, 1.0, h->nf * nrhs, 1, st));
   WMG_TRY(host_norms(h, h->r64, nrhs, rn.data(), st));
+  if (take_device_error()) return fail(MG_ETIMEOUT, "mg_solve: a bounded copy wait gave up");
   double worst = 0;
   for (int r = 0; r < nrhs; ++r) worst = std::fmax(worst, rn[r] / (bn[r] > 0 ? bn[r] : 1));
   if (info) {

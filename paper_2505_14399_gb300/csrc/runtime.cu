@@ -119,6 +119,29 @@ void cached_free(void* p, bool host) {
 
 }  // namespace
 
+int* device_error_word() {
+  static std::mutex mu;
+  static int* word = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!word) {
+    if (cudaMallocHost(&word, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      word = nullptr;
+      return nullptr;
+    }
+    *word = 0;
+  }
+  return word;
+}
+
+int take_device_error() {
+  int* w = device_error_word();
+  if (!w) return 0;
+  int v = *(volatile int*)w;
+  *(volatile int*)w = 0;
+  return v;
+}
+
 int dev_alloc_bytes(void** p, size_t bytes) { return cached_alloc(p, bytes, false); }
 void dev_free(void* p) { cached_free(p, false); }
 int host_alloc_bytes(void** p, size_t bytes) { return cached_alloc(p, bytes, true); }
