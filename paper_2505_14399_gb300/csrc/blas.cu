@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(RT)
 multi_dot_kernel(zd* out, int ldo, const E* __restrict__ V, size_t vstride, int nv,
                  const E* __restrict__ w, size_t n, double* partial, unsigned* counter,
                  int nblk, int maxvec, double scale) {
+  dep_entry();
   typedef VecT<E> T;
   typedef typename T::R R;
   __shared__ double sh[(RT / 32) * 8 * 2];
@@ -87,6 +88,7 @@ template <typename E>
 __global__ void __launch_bounds__(RT)
 norm_kernel(double* nrm, int ldn, const E* __restrict__ w, size_t n, double* partial,
             unsigned* counter, int nblk, int maxvec, double scale) {
+  dep_entry();
   typedef VecT<E> T;
   typedef typename T::R R;
   __shared__ double sh[64];
@@ -133,6 +135,7 @@ norm_kernel(double* nrm, int ldn, const E* __restrict__ w, size_t n, double* par
 template <typename E>
 __global__ void multi_axpy_kernel(E* w, const E* __restrict__ V, size_t vstride, int nv,
                                   const zd* c, int ldc, double sgn, size_t n) {
+  dep_entry();
   typedef VecT<E> T;
   typedef typename T::R R;
   __shared__ cplx<R> cs[128];
@@ -173,6 +176,7 @@ __global__ void multi_axpy_kernel(E* w, const E* __restrict__ V, size_t vstride,
 
 template <typename E>
 __global__ void scale_inv_kernel(E* y, const E* x, const double* s, int lds, size_t n) {
+  dep_entry();
   typedef VecT<E> T;
   typedef typename T::R R;
   int rhs = blockIdx.y;
@@ -189,6 +193,7 @@ __global__ void scale_inv_kernel(E* y, const E* x, const double* s, int lds, siz
 
 template <typename E>
 __global__ void axpby_kernel(E* y, double a, const E* x, double b, size_t n) {
+  dep_entry();
   typedef VecT<E> T;
   typedef typename T::R R;
   R ar = (R)a, br = (R)b;
@@ -202,6 +207,7 @@ __global__ void axpby_kernel(E* y, double a, const E* x, double b, size_t n) {
 // y += a * x with x and y of possibly different storage (arithmetic of y)
 template <typename Ey, typename Ex>
 __global__ void axpy_mixed_kernel(Ey* y, double a, const Ex* x, size_t n) {
+  dep_entry();
   typedef typename VecT<Ey>::R R;
   R ar = (R)a;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -215,6 +221,7 @@ __global__ void axpy_mixed_kernel(Ey* y, double a, const Ex* x, size_t n) {
 // y = a * x1 + b * x2 (x1, x2 in one storage, y in another; arithmetic of x)
 template <typename Eo, typename Ei>
 __global__ void lincomb_kernel(Eo* y, double a, const Ei* x1, double b, const Ei* x2, size_t n) {
+  dep_entry();
   typedef typename VecT<Ei>::R R;
   typedef typename VecT<Eo>::R Ro;
   R ar = (R)a, br = (R)b;
@@ -227,6 +234,7 @@ __global__ void lincomb_kernel(Eo* y, double a, const Ei* x1, double b, const Ei
 
 template <typename Eo, typename Ei>
 __global__ void convert_kernel(Eo* y, const Ei* x, const double* s, int inv, size_t n) {
+  dep_entry();
   typedef typename VecT<Eo>::R Ro;
   int rhs = blockIdx.y;
   double f = 1.0;
@@ -243,6 +251,7 @@ __global__ void convert_kernel(Eo* y, const Ei* x, const double* s, int inv, siz
 
 template <typename Ei>
 __global__ void accumulate_scaled_kernel(zd* y, const Ei* x, const double* s, size_t n) {
+  dep_entry();
   int rhs = blockIdx.y;
   double f = s[rhs];
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
@@ -300,9 +309,7 @@ int multi_dot_v(zd* out, int ldo, const E* V, size_t vstride, int nv, const E* w
   if (nv > rw.maxvec || nrhs > rw.nrhs_cap) return fail(MG_EINVAL, "multi_dot: workspace too small");
   dim3 grid(rw.nblk, nrhs);
   ProfScope ps("multi_dot", (double)(nv + 1) * nrhs * n * sizeof(E), 8.0 * nv * n * nrhs, st);
-  multi_dot_kernel<E><<<grid, RT, 0, st>>>(out, ldo, V, vstride, nv, w, n, rw.partial,
-                                           rw.counter, rw.nblk, rw.maxvec, scale);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(multi_dot_kernel<E>, grid, RT, 0, st, out, ldo, V, vstride, nv, w, n, rw.partial, rw.counter, rw.nblk, rw.maxvec, scale);
   return MG_OK;
 }
 
@@ -313,8 +320,7 @@ int multi_axpy_v(E* w, const E* V, size_t vstride, int nv, const zd* c, int ldc,
   if (nv == 0) return MG_OK;
   dim3 grid(grid_for(VecT<E>::packed ? n / 2 : n), nrhs);
   ProfScope ps("multi_axpy", (double)(nv + 2) * nrhs * n * sizeof(E), 8.0 * nv * n * nrhs, st);
-  multi_axpy_kernel<E><<<grid, 256, 0, st>>>(w, V, vstride, nv, c, ldc, sgn, n);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(multi_axpy_kernel<E>, grid, 256, 0, st, w, V, vstride, nv, c, ldc, sgn, n);
   return MG_OK;
 }
 
@@ -324,9 +330,7 @@ int norm2_v(double* nrm, int ldn, const E* w, size_t n, int nrhs, ReduceWork& rw
   if (nrhs > rw.nrhs_cap) return fail(MG_EINVAL, "norm2: workspace too small");
   dim3 grid(rw.nblk, nrhs);
   ProfScope ps("norm", (double)nrhs * n * sizeof(E), 4.0 * n * nrhs, st);
-  norm_kernel<E><<<grid, RT, 0, st>>>(nrm, ldn, w, n, rw.partial, rw.counter, rw.nblk,
-                                      rw.maxvec, scale);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(norm_kernel<E>, grid, RT, 0, st, nrm, ldn, w, n, rw.partial, rw.counter, rw.nblk, rw.maxvec, scale);
   return MG_OK;
 }
 
@@ -334,38 +338,33 @@ template <typename E>
 int scale_inv_v(E* y, const E* x, const double* s, int lds, size_t n, int nrhs, cudaStream_t st) {
   dim3 grid(grid_for(n), nrhs);
   ProfScope ps("scale", 2.0 * nrhs * n * sizeof(E), 2.0 * n * nrhs, st);
-  scale_inv_kernel<E><<<grid, 256, 0, st>>>(y, x, s, lds, n);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(scale_inv_kernel<E>, grid, 256, 0, st, y, x, s, lds, n);
   return MG_OK;
 }
 
 template <typename E>
 int axpby_v(E* y, double a, const E* x, double b, size_t n, int nrhs, cudaStream_t st) {
   size_t tot = n * nrhs;
-  axpby_kernel<E><<<grid_for(tot), 256, 0, st>>>(y, a, x, b, tot);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(axpby_kernel<E>, grid_for(tot), 256, 0, st, y, a, x, b, tot);
   return MG_OK;
 }
 
 template <typename Ey, typename Ex>
 int axpy_mixed(Ey* y, double a, const Ex* x, size_t n, cudaStream_t st) {
-  axpy_mixed_kernel<Ey, Ex><<<grid_for(n), 256, 0, st>>>(y, a, x, n);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(axpy_mixed_kernel<Ey, Ex>, grid_for(n), 256, 0, st, y, a, x, n);
   return MG_OK;
 }
 
 template <typename Eo, typename Ei>
 int lincomb_v(Eo* y, double a, const Ei* x1, double b, const Ei* x2, size_t n, cudaStream_t st) {
-  lincomb_kernel<Eo, Ei><<<grid_for(n), 256, 0, st>>>(y, a, x1, b, x2, n);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(lincomb_kernel<Eo, Ei>, grid_for(n), 256, 0, st, y, a, x1, b, x2, n);
   return MG_OK;
 }
 
 template <typename Eo, typename Ei>
 int convert_v(Eo* y, const Ei* x, const double* s, int inv, size_t n, int nrhs, cudaStream_t st) {
   dim3 grid(grid_for(n), nrhs);
-  convert_kernel<Eo, Ei><<<grid, 256, 0, st>>>(y, x, s, inv, n);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(convert_kernel<Eo, Ei>, grid, 256, 0, st, y, x, s, inv, n);
   return MG_OK;
 }
 
@@ -373,8 +372,7 @@ template <typename Ei>
 int accumulate_scaled_v(zd* y, const Ei* x, const double* s, size_t n, int nrhs,
                         cudaStream_t st) {
   dim3 grid(grid_for(n), nrhs);
-  accumulate_scaled_kernel<Ei><<<grid, 256, 0, st>>>(y, x, s, n);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(accumulate_scaled_kernel<Ei>, grid, 256, 0, st, y, x, s, n);
   return MG_OK;
 }
 

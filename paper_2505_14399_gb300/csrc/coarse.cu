@@ -29,6 +29,7 @@ template <typename R>
 __global__ void __launch_bounds__(256)
 restrict_kernel(cplx<R>* vc, const cplx<R>* __restrict__ v, const cplx<R>* __restrict__ P,
                 int k, Blocking B) {
+  dep_entry();
   extern __shared__ unsigned char smraw[];
   cplx<R>* sv = reinterpret_cast<cplx<R>*>(smraw);
   int t = blockIdx.x, rhs = blockIdx.y;
@@ -59,6 +60,7 @@ restrict_kernel(cplx<R>* vc, const cplx<R>* __restrict__ v, const cplx<R>* __res
 template <typename R>
 __global__ void prolong_kernel(cplx<R>* v, const cplx<R>* __restrict__ vc,
                                const cplx<R>* __restrict__ P, int k, Blocking B, size_t total) {
+  dep_entry();
   size_t V12 = (size_t)B.nd * B.d * 12;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -321,6 +323,7 @@ template <typename R>
 __global__ void __launch_bounds__(576)
 coarse_apply_kernel(cplx<R>* y, const cplx<R>* __restrict__ x, const cplx<R>* __restrict__ Op,
                     int n2k, Blocking B) {
+  dep_entry();
   extern __shared__ unsigned char csm[];
   cplx<R>* sx = reinterpret_cast<cplx<R>*>(csm);     // [9][n2k]
   cplx<R>* sp = sx + 9 * n2k;                         // [9][n2k] partial rows
@@ -361,8 +364,7 @@ int restrict_launch(cplx<R>* vc, const cplx<R>* v, const cplx<R>* P, int k, cons
   }
   ProfScope ps("restrict", (double)sizeof(cplx<R>) * (12.0 * B.nd * B.d * (k + nrhs) + 2.0 * B.d * k * nrhs),
                8.0 * 12 * B.nd * B.d * k * nrhs, st);
-  restrict_kernel<R><<<grid, 256, sh, st>>>(vc, v, P, k, B);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(restrict_kernel<R>, grid, 256, sh, st, vc, v, P, k, B);
   return MG_OK;
 }
 
@@ -374,8 +376,7 @@ int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const
   size_t cap = (size_t)num_sms() * 16;
   ProfScope ps("prolong", (double)sizeof(cplx<R>) * (12.0 * B.nd * B.d * (k + nrhs) + 2.0 * B.d * k * nrhs),
                8.0 * 12 * B.nd * B.d * k * nrhs, st);
-  prolong_kernel<R><<<(unsigned)(gsz < cap ? gsz : cap), 256, 0, st>>>(v, vc, P, k, B, total);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(prolong_kernel<R>, (unsigned)(gsz < cap ? gsz : cap), 256, 0, st, v, vc, P, k, B, total);
   return MG_OK;
 }
 
@@ -455,8 +456,7 @@ int coarse_apply_launch(cplx<R>* y, const cplx<R>* x, const cplx<R>* Op, int k, 
   size_t sh = sizeof(cplx<R>) * 18 * 2 * k;
   ProfScope ps("coarse_apply", (double)sizeof(cplx<R>) * B.d * (9.0 * 4 * k * k + 4.0 * k * nrhs),
                8.0 * 9 * 4 * k * k * B.d * nrhs, st);
-  coarse_apply_kernel<R><<<grid, 9 * 2 * k, sh, st>>>(y, x, Op, 2 * k, B);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(coarse_apply_kernel<R>, grid, 9 * 2 * k, sh, st, y, x, Op, 2 * k, B);
   return MG_OK;
 }
 

@@ -1,6 +1,8 @@
 // Shared device/host helpers of the GB300 Wilson multigrid library.
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -52,6 +54,48 @@ inline int host_alloc(T** p, size_t bytes) { return host_alloc_bytes(reinterpret
   do {                                                                              \
     int s_ = (expr);                                                                \
     if (s_ != MG_OK) return s_;                                                     \
+  } while (0)
+
+// ------------------------------------------------------------------ dependent launches
+// Programmatic dependent launch: a kernel started with launch_dep() may be scheduled while
+// the previous kernel on its stream is still finishing (its launch latency and prologue
+// overlap that tail).  Every such kernel calls dep_entry() before touching global memory:
+// griddepcontrol.wait returns once the previous grid has completed and its writes are
+// visible (immediately for a kernel launched the ordinary way), and
+// griddepcontrol.launch_dependents lets the next kernel be scheduled in turn.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void dep_entry() {
+  dep_wait();
+  dep_trigger();
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+#define WMG_LAUNCH_DEP(...)                                                         \
+  do {                                                                              \
+    cudaError_t e_ = ::wmg::launch_dep(__VA_ARGS__);                                \
+    ::wmg::count_launch();                                                          \
+    if (e_ != cudaSuccess)                                                          \
+      return ::wmg::fail(MG_ECUDA, std::string("kernel launch at ") + __FILE__ +    \
+                         ":" + std::to_string(__LINE__) + ": " +                    \
+                         cudaGetErrorString(e_));                                   \
   } while (0)
 
 // ------------------------------------------------------------------ per-kernel timing

@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(TPB, MINB)
 dslash_kernel(typename S::elem* __restrict__ out, const typename S::elem* __restrict__ in,
               const typename S::elem* __restrict__ links, KGeom g, int parity, int nsites,
               size_t in_stride, size_t out_stride) {
+  dep_entry();
   typedef typename S::real R;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsites) return;
@@ -293,9 +294,7 @@ void launch_shape(void* out, const void* in, const void* links, const KGeom& k, 
                   int nsites, int nrhs, cudaStream_t st, size_t in_stride, size_t out_stride) {
   typedef typename S::elem E;
   dim3 grid((nsites + TPB - 1) / TPB, nrhs);
-  dslash_kernel<S, DAG, TPB, MINB, LL><<<grid, TPB, 0, st>>>((E*)out, (const E*)in,
-                                                             (const E*)links, k, parity, nsites,
-                                                             in_stride, out_stride);
+  launch_dep(dslash_kernel<S, DAG, TPB, MINB, LL>, grid, TPB, 0, st, (E*)out, (const E*)in, (const E*)links, k, parity, nsites, in_stride, out_stride);
 }
 
 template <typename S, int DAG, int LL>

@@ -33,6 +33,7 @@ struct SmallLayout {
 };
 
 __global__ void init_kernel(zd* small, SmallLayout L, const double* beta, double* res, int nrhs) {
+  dep_entry();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   zd* s = small + (size_t)r * L.stride();
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(RT, 3)
 cgs_update_dot_kernel(E* w, const E* __restrict__ V, size_t vstride, int nv,
                       zd* small, SmallLayout L, int j, size_t n, double* wnorm, double* res,
                       double* partial, unsigned* counter, int nblk, int maxvec, double scale) {
+  dep_entry();
   typedef VecT<E> T;
   typedef typename T::R R;
   constexpr int G = 8;
@@ -215,6 +217,7 @@ __global__ void __launch_bounds__(256)
 cgs_update_scale_kernel(E* vout, const E* __restrict__ w, const E* __restrict__ V,
                         size_t vstride, int nv, const zd* small, SmallLayout L,
                         const double* wnorm, size_t n) {
+  dep_entry();
   typedef VecT<E> T;
   typedef typename T::R R;
   __shared__ cplx<R> cs[128];
@@ -299,10 +302,6 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
   int rhs = blockIdx.y;
   int nrhs = gridDim.y;
   zd* sm = small ? small + (size_t)rhs * L.stride() : nullptr;
-  if (MODE == 1 && threadIdx.x < nv) {
-    zd c = sm[L.H() + (size_t)j * (L.m + 1) + threadIdx.x];
-    cs[threadIdx.x] = {(float)(-c.re), (float)(-c.im)};
-  }
   size_t chunk = reduce_chunk(n, nblk);
   size_t k0 = (size_t)blockIdx.x * chunk;
   size_t k1 = min(n, k0 + chunk);
@@ -326,8 +325,19 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
       bulk_g2s(buf + (size_t)(st * nvec + 1 + q) * tp, vb + (size_t)q * vstride + e0, bytes,
                &bars[st]);
   };
+  // dependent launch: w comes from the previous kernel in projection mode; in update mode w
+  // and V are unchanged by it (only the coefficients are new), so the first tiles are in
+  // flight before the wait
+  if (MODE == 0) dep_wait();
   if (threadIdx.x == 0)
     for (int it = 0; it < stages && it < ntiles; ++it) issue(it);
+  if (MODE == 1) dep_wait();
+  dep_trigger();
+  if (MODE == 1 && threadIdx.x < nv) {
+    zd c = sm[L.H() + (size_t)j * (L.m + 1) + threadIdx.x];
+    cs[threadIdx.x] = {(float)(-c.re), (float)(-c.im)};
+  }
+  __syncthreads();
   float ar[NVM], ai[NVM];
 #pragma unroll
   for (int q = 0; q < NVM; ++q) { ar[q] = 0.f; ai[q] = 0.f; }
@@ -436,17 +446,11 @@ int stream_cgs_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* sma
   zd* Hcol = small + L.H() + (size_t)j * (L.m + 1);
   {
     ProfScope ps("multi_dot", (nv + 1) * fb, 8.0 * nv * n * nrhs, st);
-    stream_cgs_kernel<0, NVM><<<dim3(nb, nrhs), RT, sh, st>>>(
-        w, V, fs, nv, n, Hcol, L.stride(), small, L, j, dnorm, reshist, rw.partial, rw.counter,
-        nb, rw.maxvec, scale, err);
-    WMG_LAUNCHED();
+    WMG_LAUNCH_DEP(stream_cgs_kernel<0, NVM>, dim3(nb, nrhs), RT, sh, st, w, V, fs, nv, n, Hcol, L.stride(), small, L, j, dnorm, reshist, rw.partial, rw.counter, nb, rw.maxvec, scale, err);
   }
   {
     ProfScope ps("cgs_update_dot", (nv + 2) * fb, (16.0 * nv + 4.0) * n * nrhs, st);
-    stream_cgs_kernel<1, NVM><<<dim3(nb, nrhs), RT, sh, st>>>(
-        w, V, fs, nv, n, nullptr, 0, small, L, j, dnorm, reshist, rw.partial, rw.counter, nb,
-        rw.maxvec, scale, err);
-    WMG_LAUNCHED();
+    WMG_LAUNCH_DEP(stream_cgs_kernel<1, NVM>, dim3(nb, nrhs), RT, sh, st, w, V, fs, nv, n, nullptr, 0, small, L, j, dnorm, reshist, rw.partial, rw.counter, nb, rw.maxvec, scale, err);
   }
   return MG_OK;
 }
@@ -476,6 +480,7 @@ int reduction_blocks(K kernel, int cap) {
 
 // Back substitution R y = g over the first `steps` columns.
 __global__ void solve_kernel(zd* small, SmallLayout L, int steps, int nrhs) {
+  dep_entry();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   zd* s = small + (size_t)r * L.stride();
@@ -563,20 +568,14 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
     static const int ud_blocks = reduction_blocks(cgs_update_dot_kernel<E>, 1 << 30);
     int nb = ud_blocks < rw.nblk ? ud_blocks : rw.nblk;
     ProfScope ps("cgs_update_dot", (j + 3) * fb, (16.0 * (j + 1) + 4.0) * n * nrhs, st);
-    cgs_update_dot_kernel<E><<<dim3(nb, nrhs), RT, 0, st>>>(w, V, fs, j + 1, small, L, j, n,
-                                                           dnorm, reshist, rw.partial,
-                                                           rw.counter, nb, rw.maxvec,
-                                                           ip_scale());
-    WMG_LAUNCHED();
+    WMG_LAUNCH_DEP(cgs_update_dot_kernel<E>, dim3(nb, nrhs), RT, 0, st, w, V, fs, j + 1, small, L, j, n, dnorm, reshist, rw.partial, rw.counter, nb, rw.maxvec, ip_scale());
   }
   {
   ProfScope ps("cgs_update_scale", (j + 3) * fb, (8.0 * (j + 1) + 2.0) * n * nrhs, st);
   size_t g = (n / 2 + 255) / 256;
   size_t cap = (size_t)num_sms() * 8;
   dim3 grid((unsigned)(g < cap ? (g < 1 ? 1 : g) : cap), nrhs);
-  cgs_update_scale_kernel<E><<<grid, 256, 0, st>>>(V + (size_t)(j + 1) * fs, w, V, fs, j + 1,
-                                                   small, L, dnorm, n);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(cgs_update_scale_kernel<E>, grid, 256, 0, st, V + (size_t)(j + 1) * fs, w, V, fs, j + 1, small, L, dnorm, n);
   }
   return MG_OK;
 }
@@ -590,12 +589,10 @@ int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t 
   if (!accumulate) WMG_TRY(fill_zero_v<E>(x, fs, st));
   if (steps == 0) return MG_OK;
   WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, b, n, nrhs, rw, st, ip_scale()));
-  init_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(init_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
   WMG_TRY(scale_inv_v<E>(V, b, dnorm + nrhs, 1, n, nrhs, st));
   for (int j = 0; j < steps; ++j) WMG_TRY(arnoldi_step(A, nullptr, j, st));
-  solve_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, steps, nrhs);
-  WMG_LAUNCHED();
+  WMG_LAUNCH_DEP(solve_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, steps, nrhs);
   WMG_TRY(multi_axpy_v<E>(x, V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
   return MG_OK;
 }
@@ -628,8 +625,7 @@ int GmresV<E>::solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double 
   if (all_done(res.data())) converged = true;
   while (!converged && its < maxiter) {
     WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, rvec, n, nrhs, rw, st, ip_scale()));
-    init_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
-    WMG_LAUNCHED();
+    WMG_LAUNCH_DEP(init_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
     WMG_TRY(scale_inv_v<E>(V, rvec, dnorm + nrhs, 1, n, nrhs, st));
     int steps = 0, checked = 0;
     if (check_every < 1) check_every = 1;
@@ -658,8 +654,7 @@ int GmresV<E>::solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double 
       checked = j + 1;
       if (stop) break;
     }
-    solve_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(small, L, steps, nrhs);
-    WMG_LAUNCHED();
+    WMG_LAUNCH_DEP(solve_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, steps, nrhs);
     WMG_TRY(multi_axpy_v<E>(x, M ? Z : V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
     // true residual r = b - A x
     WMG_TRY(A(rvec, x, st));
