@@ -16,6 +16,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "grid.cuh"
 #include "internal.h"
 
 namespace wmg {
@@ -25,45 +26,6 @@ namespace {
 constexpr int CT = 256;       // threads per CTA
 constexpr int RPT = 8;        // rows per thread (registers)
 constexpr int MAXM = 48;      // restart length supported in shared memory
-
-struct BarrierState {
-  unsigned count;
-  unsigned gen;
-  int err;
-  int pad;
-};
-
-// Bounded sense-reversing grid barrier.  Returns false if the wait gave up or another
-// CTA raised the error word.
-__device__ bool grid_barrier(BarrierState* bs, unsigned nblocks, long long limit = (1ll << 22)) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &bs->gen;
-    volatile int* verr = &bs->err;
-    unsigned g = *vgen;
-    __threadfence();
-    unsigned arrived = atomicAdd(&bs->count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(&bs->count, 0u);
-      __threadfence();
-      atomicAdd((unsigned*)&bs->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g && *verr == 0) {
-        if (++spins > limit) {   // 2^22 polls: about a second
-          atomicExch((int*)&bs->err, 1);
-          break;
-        }
-        __nanosleep(20);
-      }
-    }
-    __threadfence();
-    ok = (*verr == 0);
-  }
-  __syncthreads();
-  return ok != 0;
-}
 
 // L1-bypassing load of a complex value written by another CTA.
 __device__ __forceinline__ zf ldcg_c(const zf* p) {
