@@ -44,13 +44,12 @@ __global__ void init_kernel(zd* small, SmallLayout L, const double* beta, double
 
 // Finish column j of one system's Hessenberg matrix: H[:, j] += h2, H[j+1, j] = ||w||,
 // apply the previous rotations, form the new one, update g; returns |g_{j+1}|.
-__device__ double givens_update(zd* s, SmallLayout L, int j, double wnorm) {
-  zd* col = s + L.H() + (size_t)j * (L.m + 1);
-  const zd* h2 = s + L.h2();
+// col = H[:, j] (j + 2 entries), h2 (j + 1), cs / sn (rotations 0..j; entry j is written),
+// gp = {g_j, g_{j+1}}.  The arrays may live in global or shared memory.
+__device__ double givens_core(zd* col, const zd* h2, zd* cs, zd* sn, zd* gp, int j,
+                              double wnorm) {
   for (int i = 0; i <= j; ++i) col[i] = col[i] + h2[i];
   col[j + 1] = {wnorm, 0};
-  zd* cs = s + L.cs();
-  zd* sn = s + L.sn();
   for (int i = 0; i < j; ++i) {
     double c = cs[i].re;
     zd sv = sn[i];
@@ -82,11 +81,15 @@ __device__ double givens_update(zd* s, SmallLayout L, int j, double wnorm) {
   col[j + 1] = {0, 0};
   cs[j] = {c, 0};
   sn[j] = sv;
-  zd* g = s + L.g();
-  zd gj = g[j];
-  g[j] = c * gj;
-  g[j + 1] = -cmulc(sv, gj);  // -conj(s) g_j
-  return sqrt(norm2(g[j + 1]));
+  zd gj = gp[0];
+  gp[0] = c * gj;
+  gp[1] = -cmulc(sv, gj);  // -conj(s) g_j
+  return sqrt(norm2(gp[1]));
+}
+
+__device__ double givens_update(zd* s, SmallLayout L, int j, double wnorm) {
+  return givens_core(s + L.H() + (size_t)j * (L.m + 1), s + L.h2(), s + L.cs(), s + L.sn(),
+                     s + L.g() + j, j, wnorm);
 }
 
 // CGS pass 1 update fused with the pass 2 projections and the norm:
@@ -410,19 +413,36 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
     if (threadIdx.x == 0) counter[rhs] = 0;
     return;
   }
-  finish_partials(partial, nv + 1, nblk, maxvec, rhs, small + L.h2(), nullptr, L.stride(), 0,
-                  scale);
+  // the Givens step on shared-memory copies: one thread's chain of dependent updates then
+  // touches shared memory instead of L2
+  __shared__ zd g_col[NVM + 2], g_h2[NVM + 1], g_cs[NVM], g_sn[NVM], g_g[2];
+  finish_partials(partial, nv + 1, nblk, maxvec, rhs, g_h2, nullptr, 0, 0, scale);
+  const zd* colg = sm + L.H() + (size_t)j * (L.m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += RT) g_col[i] = colg[i];
+  for (int i = threadIdx.x; i < j; i += RT) {
+    g_cs[i] = sm[L.cs() + i];
+    g_sn[i] = sm[L.sn() + i];
+  }
+  if (threadIdx.x < 2) g_g[threadIdx.x] = sm[L.g() + j + threadIdx.x];
   __syncthreads();
   if (threadIdx.x == 0) {
     counter[rhs] = 0;
-    const zd* h2 = sm + L.h2();
     double hh = 0;
-    for (int i = 0; i < nv; ++i) hh += norm2(h2[i]);
-    double b2 = h2[nv].re - hh;
+    for (int i = 0; i < nv; ++i) hh += norm2(g_h2[i]);
+    double b2 = g_h2[nv].re - hh;
     double beta = b2 > 0 ? sqrt(b2) : 0.0;
     wnorm[rhs] = beta;
-    res[(size_t)j * nrhs + rhs] = givens_update(sm, L, j, beta);
+    res[(size_t)j * nrhs + rhs] = givens_core(g_col, g_h2, g_cs, g_sn, g_g, j, beta);
   }
+  __syncthreads();
+  zd* colw = sm + L.H() + (size_t)j * (L.m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += RT) colw[i] = g_col[i];
+  for (int i = threadIdx.x; i <= nv; i += RT) sm[L.h2() + i] = g_h2[i];
+  if (threadIdx.x == 0) {
+    sm[L.cs() + j] = g_cs[j];
+    sm[L.sn() + j] = g_sn[j];
+  }
+  if (threadIdx.x < 2) sm[L.g() + j + threadIdx.x] = g_g[threadIdx.x];
 }
 
 template <int NVM>
