@@ -155,7 +155,8 @@ class GmresV {
   bool flexible = false;
 
  private:
-  int arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st);
+  int arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st,
+                   bool single_pass = false);
   double ip_scale() const { return VecT<E>::rms ? 1.0 / (double)n : 1.0; }
   E* V = nullptr;         // (m+1) x nrhs x n
   E* Z = nullptr;         // m x nrhs x n

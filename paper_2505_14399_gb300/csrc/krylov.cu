@@ -271,6 +271,8 @@ cgs_update_scale_kernel(E* vout, const E* __restrict__ w, const E* __restrict__ 
 // third of the HBM bandwidth at their occupancy).
 //   MODE 0: h_i = V_i^dag w                      (CGS pass 1 projections)
 //   MODE 1: w -= V c; h2_i = V_i^dag w; ||w||^2; Givens step as in cgs_update_dot_kernel
+//   MODE 2: h_i = V_i^dag w and ||w||^2; H[:, j] = h, H[j+1, j]^2 = ||w||^2 - ||h||^2 and
+//           the Givens step (single-pass classical Gram-Schmidt; see GmresV::fixed)
 // A bounded wait that gives up sets *err, waits (bounded) for the CTA's copies in flight
 // and returns; the caller reports MG_ETIMEOUT.
 constexpr int ST_NV = 16;      // columns handled (NVM = 8 or 16 accumulator sets)
@@ -331,7 +333,7 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
   // dependent launch: w comes from the previous kernel in projection mode; in update mode w
   // and V are unchanged by it (only the coefficients are new), so the first tiles are in
   // flight before the wait
-  if (MODE == 0) dep_wait();
+  if (MODE != 1) dep_wait();
   if (threadIdx.x == 0)
     for (int it = 0; it < stages && it < ntiles; ++it) issue(it);
   if (MODE == 1) dep_wait();
@@ -368,6 +370,8 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
             }
           }
           reinterpret_cast<float4*>(wr + k0 + e0)[p] = a;
+        }
+        if (MODE != 0) {
           ss = fmaf(a.x, a.x, ss); ss = fmaf(a.y, a.y, ss);
           ss = fmaf(a.z, a.z, ss); ss = fmaf(a.w, a.w, ss);
         }
@@ -403,7 +407,7 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
     return;
   }
   cta_store_partials<float, NVM>(ar, ai, nv, 0, rhs, maxvec, nblk, partial, sh);
-  if (MODE == 1) {
+  if (MODE != 0) {
     float zero = 0.f;
     cta_store_partials<float, 1>(&ss, &zero, 1, nv, rhs, maxvec, nblk, partial, sh);
   }
@@ -424,6 +428,9 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
     g_sn[i] = sm[L.sn() + i];
   }
   if (threadIdx.x < 2) g_g[threadIdx.x] = sm[L.g() + j + threadIdx.x];
+  // single pass: the column is the projections alone (givens_core adds them to zero)
+  if (MODE == 2)
+    for (int i = threadIdx.x; i <= j + 1; i += RT) g_col[i] = {0, 0};
   __syncthreads();
   if (threadIdx.x == 0) {
     counter[rhs] = 0;
@@ -448,13 +455,15 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
 template <int NVM>
 int stream_cgs_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* small,
                       SmallLayout L, int j, double* dnorm, double* reshist, ReduceWork& rw,
-                      double scale, int* err, cudaStream_t st) {
+                      double scale, int* err, bool cgs1, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     int mx = (int)st_smem(NVM);
     WMG_CUDA(cudaFuncSetAttribute(stream_cgs_kernel<0, NVM>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     WMG_CUDA(cudaFuncSetAttribute(stream_cgs_kernel<1, NVM>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    WMG_CUDA(cudaFuncSetAttribute(stream_cgs_kernel<2, NVM>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     attr = true;
   }
@@ -464,6 +473,11 @@ int stream_cgs_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* sma
   size_t sh = st_smem(nv);
   double fb = (double)nrhs * n * sizeof(zf);
   zd* Hcol = small + L.H() + (size_t)j * (L.m + 1);
+  if (cgs1) {
+    ProfScope ps("cgs1_dot_norm", (nv + 1) * fb, (8.0 * nv + 4.0) * n * nrhs, st);
+    WMG_LAUNCH_DEP(stream_cgs_kernel<2, NVM>, dim3(nb, nrhs), RT, sh, st, w, V, fs, nv, n, nullptr, 0, small, L, j, dnorm, reshist, rw.partial, rw.counter, nb, rw.maxvec, scale, err);
+    return MG_OK;
+  }
   {
     ProfScope ps("multi_dot", (nv + 1) * fb, 8.0 * nv * n * nrhs, st);
     WMG_LAUNCH_DEP(stream_cgs_kernel<0, NVM>, dim3(nb, nrhs), RT, sh, st, w, V, fs, nv, n, Hcol, L.stride(), small, L, j, dnorm, reshist, rw.partial, rw.counter, nb, rw.maxvec, scale, err);
@@ -478,13 +492,15 @@ int stream_cgs_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* sma
 // Both CGS reduction sweeps of Arnoldi step j through the bulk-copy kernels (complex float,
 // j + 1 <= ST_NV basis columns).
 int stream_cgs(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* small, SmallLayout L,
-               int j, double* dnorm, double* reshist, ReduceWork& rw, double scale,
+               int j, double* dnorm, double* reshist, ReduceWork& rw, double scale, bool cgs1,
                cudaStream_t st) {
   int* err = device_error_word();
   if (!err) return fail(MG_ECUDA, "stream_cgs: no error word");
   if (j + 1 <= 8)
-    return stream_cgs_launch<8>(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, scale, err, st);
-  return stream_cgs_launch<16>(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, scale, err, st);
+    return stream_cgs_launch<8>(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, scale, err,
+                                cgs1, st);
+  return stream_cgs_launch<16>(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, scale, err,
+                               cgs1, st);
 }
 
 // CTAs per (rhs) row of a reduction launch: one wave of `kernel` at its occupancy, capped by
@@ -561,7 +577,8 @@ void GmresV<E>::release() {
 
 // dnorm layout: [0..nrhs) current ||w||, [nrhs..2nrhs) beta, [2nrhs..3nrhs) residual estimate
 template <typename E>
-int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st) {
+int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st,
+                            bool single_pass) {
   SmallLayout L{m};
   size_t fs = n * nrhs;
   E* vj = V + (size_t)j * fs;
@@ -579,7 +596,8 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
   bool streamed = false;
   if constexpr (std::is_same<E, zf>::value) {
     if (j + 1 <= ST_NV && (n & 1) == 0) {
-      WMG_TRY(stream_cgs(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, ip_scale(), st));
+      WMG_TRY(stream_cgs(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, ip_scale(),
+                         single_pass, st));
       streamed = true;
     }
   }
@@ -611,7 +629,12 @@ int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t 
   WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, b, n, nrhs, rw, st, ip_scale()));
   WMG_LAUNCH_DEP(init_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
   WMG_TRY(scale_inv_v<E>(V, b, dnorm + nrhs, 1, n, nrhs, st));
-  for (int j = 0; j < steps; ++j) WMG_TRY(arnoldi_step(A, nullptr, j, st));
+  // A fixed number of steps from zero (the smoothers): complex-float bases of up to 16
+  // columns orthogonalise with a single classical Gram-Schmidt pass, H[j+1, j] from
+  // Pythagoras.  Over these few steps the basis stays orthogonal to ~eps_32 times the
+  // conditioning of the small Krylov basis, which leaves the smoother's approximate
+  // minimisation unchanged to FP32 rounding; the tolerance-driven solves keep CGS2.
+  for (int j = 0; j < steps; ++j) WMG_TRY(arnoldi_step(A, nullptr, j, st, true));
   WMG_LAUNCH_DEP(solve_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, steps, nrhs);
   WMG_TRY(multi_axpy_v<E>(x, V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
   return MG_OK;
