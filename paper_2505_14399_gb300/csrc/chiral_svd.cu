@@ -47,8 +47,9 @@ constexpr int GR = 32;    // rows staged per chunk
 constexpr int MAXC = 64;  // max columns per tile
 
 // G = A^dag A, upper triangle computed, mirrored.  DF: df64 arithmetic (FP32 units,
-// error-free transformations) instead of FP64.
-template <bool DF>
+// error-free transformations) instead of FP64.  MAXP: column pairs per thread
+// (>= c (c + 1) / 2 / GT), which sets the accumulator registers.
+template <bool DF, int MAXP>
 __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ tiles, int cmax,
                                                   int c, int M) {
   typedef typename std::conditional<DF, zdf, zd>::type T;
@@ -58,7 +59,6 @@ __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ 
   int t = blockIdx.x;
   const zd* A = tiles + (size_t)t * cmax * M;
   int npairs = c * (c + 1) / 2;
-  constexpr int MAXP = (MAXC * (MAXC + 1) / 2 + GT - 1) / GT;
   TA acc[MAXP];
   int pi[MAXP], pj[MAXP];
 #pragma unroll
@@ -420,8 +420,18 @@ int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaSt
   size_t sh = sizeof(zd) * GR * c;
   ProfScope ps(df64 ? "svd_gram_df64" : "svd_gram_fp64", 16.0 * B.M * c * B.d * 2,
                8.0 * B.M * c * (c + 1) / 2 * B.d * 2, st);
-  if (df64) gram_kernel<true><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
-  else gram_kernel<false><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+  int np = (c * (c + 1) / 2 + GT - 1) / GT;
+  if (df64) {
+    if (np <= 1) gram_kernel<true, 1><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+    else if (np <= 2) gram_kernel<true, 2><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+    else if (np <= 4) gram_kernel<true, 4><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+    else gram_kernel<true, 9><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+  } else {
+    if (np <= 1) gram_kernel<false, 1><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+    else if (np <= 2) gram_kernel<false, 2><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+    else if (np <= 4) gram_kernel<false, 4><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+    else gram_kernel<false, 9><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+  }
   WMG_LAUNCHED();
   return MG_OK;
 }

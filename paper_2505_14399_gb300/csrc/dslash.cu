@@ -168,41 +168,79 @@ template <typename R> __device__ __forceinline__ R wgt(const KGeom& g, int mu);
 template <> __device__ __forceinline__ double wgt<double>(const KGeom& g, int mu) { return g.wd[mu]; }
 template <> __device__ __forceinline__ float wgt<float>(const KGeom& g, int mu) { return g.wf[mu]; }
 
+// forward hop of direction MU: (1 + SF gamma) U_mu(x) psi(x + mu)
+template <int MU, int DAG, typename S, int LL>
+__device__ __forceinline__ void hop_fwd(const KGeom& g, int site, const int c[4],
+                                        const typename S::elem* in, size_t in_off,
+                                        bool half_in, const typename S::elem* links,
+                                        cplx<typename S::real> acc[12]) {
+  typedef typename S::real R;
+  constexpr int SF = DAG ? +1 : -1;  // forward projector sign
+  R w = wgt<R>(g, MU);
+  int nb = (c[MU] == g.L[MU] - 1) ? site - (g.L[MU] - 1) * g.stride[MU] : site + g.stride[MU];
+  R cf = (c[MU] == g.L[MU] - 1 && g.bc[MU] < 0) ? -w : w;
+  cplx<R> p[12], h[6], gg[6], u[9];
+  SiteIO<S>::load(in + in_off, half_in ? (size_t)(nb >> 1) : (size_t)nb, p);
+  project<MU, SF, R>(p, h);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) h[i] = cf * h[i];
+  load_link<S, LL>(links, g.V, MU, site, u);
+  mul_link<R>(u, h, gg);
+  accumulate<MU, SF, R>(acc, gg);
+}
+
+// backward hop of direction MU: (1 + SB gamma) U_mu(x - mu)^dag psi(x - mu)
+template <int MU, int DAG, typename S, int LL>
+__device__ __forceinline__ void hop_bwd(const KGeom& g, int site, const int c[4],
+                                        const typename S::elem* in, size_t in_off,
+                                        bool half_in, const typename S::elem* links,
+                                        cplx<typename S::real> acc[12]) {
+  typedef typename S::real R;
+  constexpr int SB = DAG ? -1 : +1;  // backward projector sign
+  R w = wgt<R>(g, MU);
+  int nb = (c[MU] == 0) ? site + (g.L[MU] - 1) * g.stride[MU] : site - g.stride[MU];
+  R cf = (c[MU] == 0 && g.bc[MU] < 0) ? -w : w;
+  cplx<R> p[12], h[6], gg[6], u[9];
+  SiteIO<S>::load(in + in_off, half_in ? (size_t)(nb >> 1) : (size_t)nb, p);
+  project<MU, SB, R>(p, h);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) h[i] = cf * h[i];
+  load_link<S, LL>(links, g.V, MU, nb, u);
+  mul_link_dag<R>(u, h, gg);
+  accumulate<MU, SB, R>(acc, gg);
+}
+
 template <int MU, int DAG, typename S, int LL>
 __device__ __forceinline__ void hop_pair(const KGeom& g, int site, const int c[4],
                                          const typename S::elem* in, size_t in_off,
                                          bool half_in, const typename S::elem* links,
                                          cplx<typename S::real> acc[12]) {
-  typedef typename S::real R;
-  constexpr int SF = DAG ? +1 : -1;  // forward projector sign
-  constexpr int SB = -SF;
-  R w = wgt<R>(g, MU);
-  // forward: (1 + SF gamma) U_mu(x) psi(x + mu)
-  {
-    int nb = (c[MU] == g.L[MU] - 1) ? site - (g.L[MU] - 1) * g.stride[MU] : site + g.stride[MU];
-    R cf = (c[MU] == g.L[MU] - 1 && g.bc[MU] < 0) ? -w : w;
-    cplx<R> p[12], h[6], gg[6], u[9];
-    SiteIO<S>::load(in + in_off, half_in ? (size_t)(nb >> 1) : (size_t)nb, p);
-    project<MU, SF, R>(p, h);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) h[i] = cf * h[i];
-    load_link<S, LL>(links, g.V, MU, site, u);
-    mul_link<R>(u, h, gg);
-    accumulate<MU, SF, R>(acc, gg);
+  hop_fwd<MU, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+  hop_bwd<MU, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+}
+
+// Site index of thread i (parity < 0: lexicographic; else the i-th site of that parity)
+// and its coordinates.
+__device__ __forceinline__ int stencil_site(const KGeom& g, int parity, int i, int c[4]) {
+  int site;
+  if (parity < 0) {
+    site = i;
+  } else {
+    int s0 = 2 * i;
+    int x0 = s0 % g.L[0];
+    int rest = s0 / g.L[0];
+    int y = rest % g.L[1];
+    int z = (rest / g.L[1]) % g.L[2];
+    int t = rest / (g.L[1] * g.L[2]);
+    site = s0 + (((x0 + y + z + t) & 1) != parity ? 1 : 0);
   }
-  // backward: (1 + SB gamma) U_mu(x - mu)^dag psi(x - mu)
-  {
-    int nb = (c[MU] == 0) ? site + (g.L[MU] - 1) * g.stride[MU] : site - g.stride[MU];
-    R cf = (c[MU] == 0 && g.bc[MU] < 0) ? -w : w;
-    cplx<R> p[12], h[6], gg[6], u[9];
-    SiteIO<S>::load(in + in_off, half_in ? (size_t)(nb >> 1) : (size_t)nb, p);
-    project<MU, SB, R>(p, h);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) h[i] = cf * h[i];
-    load_link<S, LL>(links, g.V, MU, nb, u);
-    mul_link_dag<R>(u, h, gg);
-    accumulate<MU, SB, R>(acc, gg);
-  }
+  c[0] = site % g.L[0];
+  int rest = site / g.L[0];
+  c[1] = rest % g.L[1];
+  rest /= g.L[1];
+  c[2] = rest % g.L[2];
+  c[3] = rest / g.L[2];
+  return site;
 }
 
 // parity < 0: out = in - kappa H in (full lattice).  parity p >= 0: out_p = -kappa H in_{1-p}
@@ -263,6 +301,69 @@ dslash_kernel(typename S::elem* __restrict__ out, const typename S::elem* __rest
   }
 }
 
+// Two threads per site, warp-uniform: the first 64 threads of a CTA take the forward hops
+// of 64 sites, the other 64 the backward hops of the same sites; the halves meet in shared
+// memory.  Twice the threads with half the dependent work each, for lattices too small to
+// fill the GPU with one thread per site.
+template <typename S, int DAG, int LL>
+__global__ void __launch_bounds__(128)
+dslash_split_kernel(typename S::elem* __restrict__ out, const typename S::elem* __restrict__ in,
+                    const typename S::elem* __restrict__ links, KGeom g, int parity, int nsites,
+                    size_t in_stride, size_t out_stride) {
+  dep_entry();
+  typedef typename S::real R;
+  __shared__ cplx<R> sacc[12][64];
+  const int half = threadIdx.x >> 6, ls = threadIdx.x & 63;
+  const int i = blockIdx.x * 64 + ls;
+  const bool active = i < nsites;
+  const size_t rhs = blockIdx.y;
+  const bool half_in = parity >= 0;
+  const size_t in_off = rhs * in_stride;
+  cplx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {0, 0};
+  int site = 0;
+  int c[4] = {0, 0, 0, 0};
+  if (active) {
+    site = stencil_site(g, parity, i, c);
+    if (half == 0) {
+      hop_fwd<0, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+      hop_fwd<1, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+      hop_fwd<2, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+      hop_fwd<3, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+    } else {
+      hop_bwd<0, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+      hop_bwd<1, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+      hop_bwd<2, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+      hop_bwd<3, DAG, S, LL>(g, site, c, in, in_off, half_in, links, acc);
+    }
+  }
+  if (half == 1) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sacc[k][ls] = acc[k];
+  }
+  __syncthreads();
+  if (half != 0 || !active) return;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] += sacc[k][ls];
+  R mk = (R)(-g.kappa);
+  cplx<R> res[12];
+  if (parity < 0) {
+    cplx<R> p[12];
+    SiteIO<S>::load(in + in_off, (size_t)site, p);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      res[k].re = fma(mk, acc[k].re, p[k].re);
+      res[k].im = fma(mk, acc[k].im, p[k].im);
+    }
+    SiteIO<S>::store(out + rhs * out_stride, (size_t)site, res);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) res[k] = mk * acc[k];
+    SiteIO<S>::store(out + rhs * out_stride, (size_t)i, res);
+  }
+}
+
 KGeom to_kgeom(const Geom& g) {
   KGeom k;
   for (int m = 0; m < 4; ++m) {
@@ -286,7 +387,8 @@ KGeom to_kgeom(const Geom& g) {
 struct Shape {
   int tpb, minb;
 };
-constexpr Shape kShapes[] = {{128, 1}, {128, 6}, {128, 8}, {256, 4}, {64, 16}};
+constexpr Shape kShapes[] = {{128, 1}, {128, 6}, {128, 8}, {256, 4}, {64, 16}, {128, 0}};
+// the last entry is the two-threads-per-site kernel (dslash_split_kernel)
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 template <typename S, int DAG, int TPB, int MINB, int LL>
@@ -305,6 +407,13 @@ void launch_variant(int v, void* out, const void* in, const void* links, const K
     case 2: launch_shape<S, DAG, 128, 8, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
     case 3: launch_shape<S, DAG, 256, 4, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
     case 4: launch_shape<S, DAG, 64, 16, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
+    case 5: {
+      typedef typename S::elem E;
+      dim3 grid((nsites + 63) / 64, nrhs);
+      launch_dep(dslash_split_kernel<S, DAG, LL>, grid, 128, 0, st, (E*)out, (const E*)in,
+                 (const E*)links, k, parity, nsites, is, os);
+      break;
+    }
     default: launch_shape<S, DAG, 128, 1, LL>(out, in, links, k, parity, nsites, nrhs, st, is, os); break;
   }
 }
