@@ -3,6 +3,7 @@
     python -m paper_2505_14399_gb300.kernel_bench dslash --dims 24 24 24 48 --dtype c64
     python -m paper_2505_14399_gb300.kernel_bench step --workload c2_16^3x32_near_critical
     python -m paper_2505_14399_gb300.kernel_bench coarse --workload c2_16^3x32_near_critical
+    python -m paper_2505_14399_gb300.kernel_bench scan --sweeps 20
 
 Inputs come from the seeded generators in ``synthetic``; L2 is flushed (a 256 MB write)
 before every timed launch.  Prints one JSON line per measurement.
@@ -128,9 +129,55 @@ def bench_coarse(a, dev, flush):
             "coarse_apply_GBps": d * 9 * (2 * k) ** 2 * 8 / tc / 1e9}
 
 
+def bench_scan(a, dev, flush):
+    """The paper's parameter studies on the synthetic near-critical lattice (one JSON line
+    per point): fine-level FGMRES iterations of the FP64 solve and seconds of the mixed
+    setup + solve, against the number of sampled test vectors m = n_s r (streams of r = 8,
+    k = 12; Fig. 1 / Table 2), the truncation rank k at m = 64 (Fig. 3), and the smoother
+    iterations that make each test vector (Figs. 4-5), each with the Regular setup (k test
+    vectors, no truncation) beside it."""
+    cfg = _workload(a.workload, a.kappa)
+    U = torch.from_numpy(synthetic.make_links(cfg)).to(dev)
+    b = torch.from_numpy(synthetic.gaussian_rhs(cfg["dims"], cfg["rhs_seed"])).to(dev)
+
+    def point(study, k, r, n_s, sweeps):
+        res = {"study": study, "k": k, "r": r, "n_s": n_s, "m": r * n_s, "sweeps": sweeps}
+        for tag, mixed in (("fp64", False), ("mixed", True)):
+            p = api.params(cfg["dims"], cfg["block"], cfg["kappa"], k, r, n_s, sweeps,
+                           cfg["tv_seed"], cfg["hop_weight"], cfg["bc"],
+                           setup_dtype="c64" if mixed else "c128",
+                           solve_dtype="c64" if mixed else "c128")
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h = api.Hierarchy(U, p)
+            h.coarse_build()
+            _, info = h.solve(b, tol=1e-10, maxiter=4000)
+            e1.record()
+            torch.cuda.synchronize()
+            h.close()
+            res[tag] = {"outer": info["outer"], "coarse": info["coarse"],
+                        "seconds": e0.elapsed_time(e1) / 1e3}
+        print(json.dumps(res), flush=True)
+
+    sw = a.sweeps
+    for n_s in (2, 4, 8, 12, 16):                         # m = 16 ... 128
+        point("m", 12, 8, n_s, sw)
+    point("m", 12, 12, 1, sw)                              # Regular
+    for k in (8, 12, 16, 24):                              # truncation at m = 64
+        point("k", k, 16, 4, sw)
+        point("k", k, k, 1, sw)                            # Regular with k vectors
+    for s in (2, 5, 10, 20, 30):                           # smoother iterations
+        point("sweeps", 12, 8, 4, s)
+        point("sweeps", 12, 12, 1, s)
+    return {"kernel": "scan", "workload": a.workload, "kappa": cfg["kappa"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["dslash", "step", "coarse"])
+    ap.add_argument("what", choices=["dslash", "step", "coarse", "scan"])
     ap.add_argument("--dims", type=int, nargs=4, default=[16, 16, 16, 32])
     ap.add_argument("--dtype", default="c64", choices=list(BYTES_PER_SITE))
     ap.add_argument("--nrhs", type=int, default=1)
@@ -141,10 +188,13 @@ def main():
     ap.add_argument("--workload", default="c2_16^3x32_near_critical")
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--kappa", type=float, default=None, help="override the workload's kappa")
+    ap.add_argument("--sweeps", type=int, default=20,
+                    help="scan: smoother iterations per test vector for the m and k studies")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    fn = {"dslash": bench_dslash, "step": bench_step, "coarse": bench_coarse}[a.what]
+    fn = {"dslash": bench_dslash, "step": bench_step, "coarse": bench_coarse,
+          "scan": bench_scan}[a.what]
     print(json.dumps(fn(a, dev, flush)), flush=True)
 
 
