@@ -179,8 +179,12 @@ class CoarseSolver {
   ~CoarseSolver() { release(); }
   int alloc(size_t nc, int m);
   void release();
+  // Enqueues the solve on `st` without waiting for it: a barrier wait that gives up raises
+  // the device error word, and the iteration count accumulates on the device.
   int solve(const cplx<R>* Op, const Blocking& B, int k, cplx<R>* x, const cplx<R>* b,
-            double rtol, int restart, int maxiter, int* its, cudaStream_t st);
+            double rtol, int restart, int maxiter, cudaStream_t st);
+  // iterations of the solves since the last call (synchronises `st`), then resets the count
+  int take_iterations(long long* its, cudaStream_t st);
   // whether one cooperative grid holds the coarse system (each CTA keeps its rows in
   // registers: at most 2048 rows per CTA, one CTA per SM)
   bool fits(const Blocking& B, int k) const;
@@ -188,10 +192,9 @@ class CoarseSolver {
   int m = 0;
 
  private:
-  size_t smem_bytes() const;
   cplx<R>* V = nullptr;
   cplx<R>* W = nullptr;
-  double* partial = nullptr;
+  R* partial = nullptr;
   void* state = nullptr;
   void* host_state = nullptr;
   int max_grid = 0;

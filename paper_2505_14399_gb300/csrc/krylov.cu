@@ -682,7 +682,7 @@ int GmresV<E>::solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double 
                                sizeof(double) * nrhs * (j + 1 - checked), cudaMemcpyDeviceToHost,
                                st));
       WMG_CUDA(cudaStreamSynchronize(st));
-      if (take_device_error()) return fail(MG_ETIMEOUT, "gmres: a bounded copy wait gave up");
+      if (take_device_error()) return fail(MG_ETIMEOUT, "gmres: a bounded wait gave up");
       bool stop = false;
       for (int jj = checked; jj <= j && !stop; ++jj) {
         const double* rr = host_res + (size_t)(jj - checked) * nrhs;
@@ -706,7 +706,7 @@ int GmresV<E>::solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double 
     WMG_CUDA(cudaMemcpyAsync(host_res + nrhs, dnorm + 3 * nrhs, sizeof(double) * nrhs,
                              cudaMemcpyDeviceToHost, st));
     WMG_CUDA(cudaStreamSynchronize(st));
-    if (take_device_error()) return fail(MG_ETIMEOUT, "gmres: a bounded copy wait gave up");
+    if (take_device_error()) return fail(MG_ETIMEOUT, "gmres: a bounded wait gave up");
     if (all_done(host_res + nrhs)) converged = true;
   }
   if (its_out) *its_out = its;

@@ -229,7 +229,7 @@ int run_setup(mg_handle* h, cudaStream_t st) {
   CSTEP(cudaStreamSynchronize(st));
   if (take_device_error()) {
     cleanup();
-    return fail(MG_ETIMEOUT, "setup: a bounded copy wait gave up");
+    return fail(MG_ETIMEOUT, "setup: a bounded wait gave up");
   }
   cleanup();
   h->have_P = true;
@@ -367,12 +367,10 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
     int its = 0;
     if (p.coarse_persistent && Lvl<R>::csol(h).fits(h->B, h->k)) {
       // one cooperative launch per system: the whole restarted coarse GMRES on the device
-      for (int r = 0; r < nrhs; ++r) {
-        int itr = 0;
+      // (its iteration count accumulates there and is read once per solve)
+      for (int r = 0; r < nrhs; ++r)
         WMG_TRY(Lvl<R>::csol(h).solve(Lvl<R>::Op(h), h->B, h->k, ec + r * h->nc, vc + r * h->nc,
-                                      p.coarse_tol, p.coarse_restart, p.coarse_maxiter, &itr, st));
-        its += itr;
-      }
+                                      p.coarse_tol, p.coarse_restart, p.coarse_maxiter, st));
     } else {
       Op<R> Dc = coarse_op<R>(h, nrhs);
       // coarse Arnoldi steps are cheap: check convergence on the host every 8 steps
@@ -413,6 +411,8 @@ int solve_impl(mg_handle* h, zd* x, const zd* b, int nrhs, double tol, int maxit
   WMG_TRY(ensure_solver(h, nrhs));
   h->coarse_its = 0;
   h->kcycles = 0;
+  WMG_TRY(h->csol64.take_iterations(nullptr, st));   // drop counts of an unfinished solve
+  WMG_TRY(h->csol32.take_iterations(nullptr, st));
   std::vector<double> bn(nrhs), rn(nrhs);
   WMG_TRY(host_norms(h, b, nrhs, bn.data(), st));
   int outer = 0, refinements = 0;
@@ -466,7 +466,11 @@ int solve_impl(mg_handle* h, zd* x, const zd* b, int nrhs, double tol, int maxit
   WMG_CUDA(cudaMemcpyAsync(h->r64, b, h->nf * nrhs * sizeof(zd), cudaMemcpyDeviceToDevice, st));
   WMG_TRY(axpby<double>(h->r64, -1.0, h->t64, 1.0, h->nf * nrhs, 1, st));
   WMG_TRY(host_norms(h, h->r64, nrhs, rn.data(), st));
-  if (take_device_error()) return fail(MG_ETIMEOUT, "mg_solve: a bounded copy wait gave up");
+  if (take_device_error()) return fail(MG_ETIMEOUT, "mg_solve: a bounded wait gave up");
+  long long c64 = 0, c32 = 0;
+  WMG_TRY(h->csol64.take_iterations(&c64, st));
+  WMG_TRY(h->csol32.take_iterations(&c32, st));
+  h->coarse_its += c64 + c32;
   double worst = 0;
   for (int r = 0; r < nrhs; ++r) worst = std::fmax(worst, rn[r] / (bn[r] > 0 ? bn[r] : 1));
   if (info) {
