@@ -74,13 +74,13 @@ multi_dot_kernel(zd* out, int ldo, const E* __restrict__ V, size_t vstride, int 
         }
       }
     }
-    // CTA reduction in the vectors' own arithmetic (FP64 arithmetic is scarce on this GPU);
-    // only the CTA partial is widened to FP64 for the cross-CTA sum.
-    cta_store_partials<R, G>(ar, ai, ni, i0, rhs, maxvec, nblk, partial,
+    // CTA and cross-CTA reductions in the vectors' own arithmetic (FP64 arithmetic is scarce
+    // on this GPU)
+    cta_store_partials<R, G>(ar, ai, ni, i0, rhs, maxvec, nblk, partials_as<R>(partial),
                              reinterpret_cast<R*>(sh));
   }
   if (!last_cta(counter, rhs, nblk)) return;
-  finish_partials(partial, nv, nblk, maxvec, rhs, out, nullptr, ldo, 0, scale);
+  finish_partials(partials_as<R>(partial), nv, nblk, maxvec, rhs, out, nullptr, ldo, 0, scale);
   if (threadIdx.x == 0) counter[rhs] = 0;
 }
 
@@ -113,7 +113,7 @@ norm_kernel(double* nrm, int ldn, const E* __restrict__ w, size_t n, double* par
       acc = fma(a.im, a.im, acc);
     }
   }
-  // CTA tree in the vectors' arithmetic, FP64 only across CTAs
+  // CTA tree and cross-CTA sum in the vectors' arithmetic
   acc = warp_sum_r(acc);
   R* shr = reinterpret_cast<R*>(sh);
   if ((threadIdx.x & 31) == 0) shr[threadIdx.x >> 5] = acc;
@@ -121,13 +121,13 @@ norm_kernel(double* nrm, int ldn, const E* __restrict__ w, size_t n, double* par
   if (threadIdx.x == 0) {
     R s = 0;
     for (int wv = 0; wv < RT / 32; ++wv) s += shr[wv];
-    double* p = partial + ((size_t)rhs * maxvec * nblk + blockIdx.x) * 2;
-    p[0] = (double)s;
+    R* p = partials_as<R>(partial) + ((size_t)rhs * maxvec * nblk + blockIdx.x) * 2;
+    p[0] = s;
     p[1] = 0;
     __threadfence();
   }
   if (!last_cta(counter, rhs, nblk)) return;
-  finish_partials(partial, 1, nblk, maxvec, rhs, nullptr, nrm, ldn, 1, scale);
+  finish_partials(partials_as<R>(partial), 1, nblk, maxvec, rhs, nullptr, nrm, ldn, 1, scale);
   if (threadIdx.x == 0) counter[rhs] = 0;
 }
 

@@ -59,22 +59,23 @@ __device__ double givens_core(zd* col, const zd* h2, zd* cs, zd* sn, zd* gp, int
     col[i] = na;
     col[i + 1] = nb;
   }
+  // c = |a| / rho, s = (a / |a|) conj(b) / rho with rho^2 = |a|^2 + |b|^2, from two
+  // reciprocal square roots (one thread's serial FP64 chain: no hypot, sqrt or divide)
   zd a = col[j], b = col[j + 1];
-  double na = sqrt(norm2(a)), nbv = sqrt(norm2(b));
-  double rho = hypot(na, nbv);
+  double na2 = norm2(a), rho2 = na2 + norm2(b);
   double c;
   zd sv;
-  if (rho == 0.0) {
+  if (!(rho2 > 0.0)) {
     c = 1.0;
     sv = {0, 0};
-  } else if (na == 0.0) {
+  } else if (!(na2 > 0.0)) {
+    double ir = rsqrt(rho2);
     c = 0.0;
-    sv = {b.re / rho, -b.im / rho};  // s b = |b|^2/rho: choose s = conj(b)/rho
+    sv = {b.re * ir, -b.im * ir};  // s b = |b|^2/rho: choose s = conj(b)/rho
   } else {
-    c = na / rho;
-    // s = (a/|a|) conj(b) / rho
-    zd ua = {a.re / na, a.im / na};
-    sv = (1.0 / rho) * (ua * conj(b));
+    double ir = rsqrt(rho2), ina = rsqrt(na2);
+    c = na2 * ina * ir;
+    sv = (ina * ir) * (a * conj(b));
   }
   zd top = c * a + sv * b;
   col[j] = top;
@@ -87,17 +88,41 @@ __device__ double givens_core(zd* col, const zd* h2, zd* cs, zd* sn, zd* gp, int
   return sqrt(norm2(gp[1]));
 }
 
-__device__ double givens_update(zd* s, SmallLayout L, int j, double wnorm) {
-  return givens_core(s + L.H() + (size_t)j * (L.m + 1), s + L.h2(), s + L.cs(), s + L.sn(),
-                     s + L.g() + j, j, wnorm);
+// Column j of the Hessenberg matrix and its Givens step, run by one whole CTA on shared-memory
+// copies (one thread's chain of dependent updates then touches shared memory, not L2): the
+// column gets the projections h2 (added to the pass-1 values, or alone when `single`) and
+// H[j+1, j] = beta; the rotation updates cs, sn, g and the residual estimate res.  Called by
+// the extra CTA of the normalising update, so this serial FP64 chain runs beside the
+// memory-bound update instead of ending the reduction sweep.
+constexpr int GV_MAX = 130;   // m <= 128
+__device__ void givens_deferred(zd* sm, SmallLayout L, int j, double beta, bool single,
+                                double* res) {
+  __shared__ zd g_col[GV_MAX], g_h2[GV_MAX], g_cs[GV_MAX], g_sn[GV_MAX], g_g[2];
+  const zd* colg = sm + L.H() + (size_t)j * (L.m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) g_col[i] = single ? zd{0, 0} : colg[i];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) g_h2[i] = sm[L.h2() + i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    g_cs[i] = sm[L.cs() + i];
+    g_sn[i] = sm[L.sn() + i];
+  }
+  if (threadIdx.x < 2) g_g[threadIdx.x] = sm[L.g() + j + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) *res = givens_core(g_col, g_h2, g_cs, g_sn, g_g, j, beta);
+  __syncthreads();
+  zd* colw = sm + L.H() + (size_t)j * (L.m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) colw[i] = g_col[i];
+  if (threadIdx.x == 0) {
+    sm[L.cs() + j] = g_cs[j];
+    sm[L.sn() + j] = g_sn[j];
+  }
+  if (threadIdx.x < 2) sm[L.g() + j + threadIdx.x] = g_g[threadIdx.x];
 }
 
 // CGS pass 1 update fused with the pass 2 projections and the norm:
 //   w -= sum_i h1_i V_i,  then  h2_i = V_i^dag w (i < nv)  and  s = ||w||^2, one sweep over w.
-// The last CTA completes column j of the Hessenberg matrix: with V orthonormal, the vector
-// left after the pass 2 update, w - V h2, has squared norm s - ||h2||^2 (Pythagoras), which
-// is H[j+1, j]; the Givens step runs on that value, so the pass 2 update needs no reduction
-// of its own.  h2 is O(eps ||A v_j||) after pass 1, so the subtraction loses nothing unless
+// The last CTA stores h2 and H[j+1, j]: with V orthonormal, the vector left after the pass 2
+// update, w - V h2, has squared norm s - ||h2||^2 (Pythagoras), so the pass 2 update needs no
+// reduction of its own (it also completes the Hessenberg column and the Givens step).  h2 is O(eps ||A v_j||) after pass 1, so the subtraction loses nothing unless
 // the Krylov space is (numerically) invariant, where H[j+1, j] ~ 0 ends the solve anyway.
 template <typename E>
 __global__ void __launch_bounds__(RT, 3)
@@ -111,7 +136,6 @@ cgs_update_dot_kernel(E* w, const E* __restrict__ V, size_t vstride, int nv,
   __shared__ cplx<R> cs[128];
   __shared__ double sh[(RT / 32) * G * 2];
   int rhs = blockIdx.y;
-  int nrhs = gridDim.y;
   zd* sm = small + (size_t)rhs * L.stride();
   const zd* c = sm + L.H() + (size_t)j * (L.m + 1);
   for (int i = threadIdx.x; i < nv; i += blockDim.x) {
@@ -161,7 +185,8 @@ cgs_update_dot_kernel(E* w, const E* __restrict__ V, size_t vstride, int nv,
         }
       }
     }
-    cta_store_partials<R, G>(ar, ai, nv, 0, rhs, maxvec, nblk, partial, reinterpret_cast<R*>(sh));
+    cta_store_partials<R, G>(ar, ai, nv, 0, rhs, maxvec, nblk, partials_as<R>(partial),
+                             reinterpret_cast<R*>(sh));
   } else {
     // general case: update sweep (with the norm), then projection sweeps over groups of G
     for (size_t k = k0 + threadIdx.x; k < k1; k += RT) {
@@ -189,16 +214,17 @@ cgs_update_dot_kernel(E* w, const E* __restrict__ V, size_t vstride, int nv,
           }
         }
       }
-      cta_store_partials<R, G>(ar, ai, ni, i0, rhs, maxvec, nblk, partial,
+      cta_store_partials<R, G>(ar, ai, ni, i0, rhs, maxvec, nblk, partials_as<R>(partial),
                                reinterpret_cast<R*>(sh));
     }
   }
   // ||w||^2 goes to slot nv (< maxvec: nv <= m)
   R zero = 0;
-  cta_store_partials<R, 1>(&ss, &zero, 1, nv, rhs, maxvec, nblk, partial,
+  cta_store_partials<R, 1>(&ss, &zero, 1, nv, rhs, maxvec, nblk, partials_as<R>(partial),
                            reinterpret_cast<R*>(sh));
   if (!last_cta(counter, rhs, nblk)) return;
-  finish_partials(partial, nv + 1, nblk, maxvec, rhs, small + L.h2(), nullptr, L.stride(), 0,
+  finish_partials(partials_as<R>(partial), nv + 1, nblk, maxvec, rhs, small + L.h2(), nullptr,
+                  L.stride(), 0,
                   scale);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -207,24 +233,30 @@ cgs_update_dot_kernel(E* w, const E* __restrict__ V, size_t vstride, int nv,
     double hh = 0;
     for (int i = 0; i < nv; ++i) hh += norm2(h2[i]);
     double b2 = h2[nv].re - hh;
-    double beta = b2 > 0 ? sqrt(b2) : 0.0;
-    wnorm[rhs] = beta;
-    res[(size_t)j * nrhs + rhs] = givens_update(sm, L, j, beta);
+    wnorm[rhs] = b2 > 0 ? sqrt(b2) : 0.0;   // the Givens step follows in the update
   }
 }
 
 // CGS pass 2 update written straight into the next basis column:
 //   v_{j+1} = (w - sum_i h2_i V_i) / H[j+1, j]   (0 if H[j+1, j] = 0).
+// The last CTA of every rhs row does not update: it completes Hessenberg column j = nv - 1
+// and its Givens step (givens_deferred) while the others stream the vectors.
 template <typename E>
 __global__ void __launch_bounds__(256)
 cgs_update_scale_kernel(E* vout, const E* __restrict__ w, const E* __restrict__ V,
-                        size_t vstride, int nv, const zd* small, SmallLayout L,
-                        const double* wnorm, size_t n) {
+                        size_t vstride, int nv, zd* small, SmallLayout L,
+                        const double* wnorm, size_t n, double* res, int single) {
   dep_entry();
   typedef VecT<E> T;
   typedef typename T::R R;
   __shared__ cplx<R> cs[128];
   int rhs = blockIdx.y;
+  if (blockIdx.x == gridDim.x - 1) {
+    givens_deferred(small + (size_t)rhs * L.stride(), L, nv - 1, wnorm[rhs], single != 0,
+                    res + (size_t)(nv - 1) * gridDim.y + rhs);
+    return;
+  }
+  const size_t nthreads = (size_t)(gridDim.x - 1) * blockDim.x;
   const zd* h2 = small + (size_t)rhs * L.stride() + L.h2();
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = {(R)(-h2[i].re), (R)(-h2[i].im)};
   __syncthreads();
@@ -238,8 +270,7 @@ cgs_update_scale_kernel(E* vout, const E* __restrict__ w, const E* __restrict__ 
   if (packed) {
     size_t vs2 = vstride / 2;
     float ff = (float)f;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n / 2;
-         k += (size_t)gridDim.x * blockDim.x) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n / 2; k += nthreads) {
       float4 a = T::ld2(wr, k);
       for (int i = 0; i < nv; ++i) {
         float4 v = T::ld2(vb + (size_t)i * 2 * vs2, k);
@@ -253,8 +284,7 @@ cgs_update_scale_kernel(E* vout, const E* __restrict__ w, const E* __restrict__ 
     }
     return;
   }
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (size_t)gridDim.x * blockDim.x) {
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += nthreads) {
     cplx<R> a = T::ld(wr, k);
     for (int i = 0; i < nv; ++i) cfma(a, cs[i], T::ld(vb, (size_t)i * vstride + k));
     T::st(outr, k, {f * a.re, f * a.im});
@@ -270,9 +300,11 @@ cgs_update_scale_kernel(E* vout, const E* __restrict__ w, const E* __restrict__ 
 // in flight per SM no longer depend on registers (the register-fed sweeps above reached a
 // third of the HBM bandwidth at their occupancy).
 //   MODE 0: h_i = V_i^dag w                      (CGS pass 1 projections)
-//   MODE 1: w -= V c; h2_i = V_i^dag w; ||w||^2; Givens step as in cgs_update_dot_kernel
-//   MODE 2: h_i = V_i^dag w and ||w||^2; H[:, j] = h, H[j+1, j]^2 = ||w||^2 - ||h||^2 and
-//           the Givens step (single-pass classical Gram-Schmidt; see GmresV::fixed)
+//   MODE 1: w -= V c; h2_i = V_i^dag w; ||w||^2; H[j+1, j] as in cgs_update_dot_kernel
+//   MODE 2: h_i = V_i^dag w and ||w||^2; H[j+1, j]^2 = ||w||^2 - ||h||^2 (single-pass
+//           classical Gram-Schmidt; see GmresV::fixed)
+// In modes 1 and 2 the Hessenberg column and its Givens step are completed by the
+// normalising update that follows (givens_deferred).
 // A bounded wait that gives up sets *err, waits (bounded) for the CTA's copies in flight
 // and returns; the caller reports MG_ETIMEOUT.
 constexpr int ST_NV = 16;      // columns handled (NVM = 8 or 16 accumulator sets)
@@ -305,7 +337,6 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
   const int tp = te / 2;   // float4 packs per vector and tile
   const int nvec = nv + 1;
   int rhs = blockIdx.y;
-  int nrhs = gridDim.y;
   zd* sm = small ? small + (size_t)rhs * L.stride() : nullptr;
   size_t chunk = reduce_chunk(n, nblk);
   size_t k0 = (size_t)blockIdx.x * chunk;
@@ -406,50 +437,33 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
     }
     return;
   }
-  cta_store_partials<float, NVM>(ar, ai, nv, 0, rhs, maxvec, nblk, partial, sh);
+  cta_store_partials<float, NVM>(ar, ai, nv, 0, rhs, maxvec, nblk, partials_as<float>(partial),
+                                 sh);
   if (MODE != 0) {
     float zero = 0.f;
-    cta_store_partials<float, 1>(&ss, &zero, 1, nv, rhs, maxvec, nblk, partial, sh);
+    cta_store_partials<float, 1>(&ss, &zero, 1, nv, rhs, maxvec, nblk,
+                                 partials_as<float>(partial), sh);
   }
   if (!last_cta(counter, rhs, nblk)) return;
   if (MODE == 0) {
-    finish_partials(partial, nv, nblk, maxvec, rhs, out, nullptr, ldo, 0, scale);
+    finish_partials(partials_as<float>(partial), nv, nblk, maxvec, rhs, out, nullptr, ldo, 0,
+                    scale);
     if (threadIdx.x == 0) counter[rhs] = 0;
     return;
   }
-  // the Givens step on shared-memory copies: one thread's chain of dependent updates then
-  // touches shared memory instead of L2
-  __shared__ zd g_col[NVM + 2], g_h2[NVM + 1], g_cs[NVM], g_sn[NVM], g_g[2];
-  finish_partials(partial, nv + 1, nblk, maxvec, rhs, g_h2, nullptr, 0, 0, scale);
-  const zd* colg = sm + L.H() + (size_t)j * (L.m + 1);
-  for (int i = threadIdx.x; i <= j + 1; i += RT) g_col[i] = colg[i];
-  for (int i = threadIdx.x; i < j; i += RT) {
-    g_cs[i] = sm[L.cs() + i];
-    g_sn[i] = sm[L.sn() + i];
-  }
-  if (threadIdx.x < 2) g_g[threadIdx.x] = sm[L.g() + j + threadIdx.x];
-  // single pass: the column is the projections alone (givens_core adds them to zero)
-  if (MODE == 2)
-    for (int i = threadIdx.x; i <= j + 1; i += RT) g_col[i] = {0, 0};
+  // projections and H[j+1, j]; the Givens step follows in the normalising update
+  __shared__ zd g_h2[NVM + 1];
+  finish_partials(partials_as<float>(partial), nv + 1, nblk, maxvec, rhs, g_h2, nullptr, 0, 0,
+                  scale);
   __syncthreads();
+  for (int i = threadIdx.x; i <= nv; i += RT) sm[L.h2() + i] = g_h2[i];
   if (threadIdx.x == 0) {
     counter[rhs] = 0;
     double hh = 0;
     for (int i = 0; i < nv; ++i) hh += norm2(g_h2[i]);
     double b2 = g_h2[nv].re - hh;
-    double beta = b2 > 0 ? sqrt(b2) : 0.0;
-    wnorm[rhs] = beta;
-    res[(size_t)j * nrhs + rhs] = givens_core(g_col, g_h2, g_cs, g_sn, g_g, j, beta);
+    wnorm[rhs] = b2 > 0 ? sqrt(b2) : 0.0;
   }
-  __syncthreads();
-  zd* colw = sm + L.H() + (size_t)j * (L.m + 1);
-  for (int i = threadIdx.x; i <= j + 1; i += RT) colw[i] = g_col[i];
-  for (int i = threadIdx.x; i <= nv; i += RT) sm[L.h2() + i] = g_h2[i];
-  if (threadIdx.x == 0) {
-    sm[L.cs() + j] = g_cs[j];
-    sm[L.sn() + j] = g_sn[j];
-  }
-  if (threadIdx.x < 2) sm[L.g() + j + threadIdx.x] = g_g[threadIdx.x];
 }
 
 template <int NVM>
@@ -612,8 +626,9 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
   ProfScope ps("cgs_update_scale", (j + 3) * fb, (8.0 * (j + 1) + 2.0) * n * nrhs, st);
   size_t g = (n / 2 + 255) / 256;
   size_t cap = (size_t)num_sms() * 8;
-  dim3 grid((unsigned)(g < cap ? (g < 1 ? 1 : g) : cap), nrhs);
-  WMG_LAUNCH_DEP(cgs_update_scale_kernel<E>, grid, 256, 0, st, V + (size_t)(j + 1) * fs, w, V, fs, j + 1, small, L, dnorm, n);
+  // + 1 CTA per rhs row for the deferred Givens step
+  dim3 grid((unsigned)(g < cap ? (g < 1 ? 1 : g) : cap) + 1, nrhs);
+  WMG_LAUNCH_DEP(cgs_update_scale_kernel<E>, grid, 256, 0, st, V + (size_t)(j + 1) * fs, w, V, fs, j + 1, small, L, dnorm, n, reshist, single_pass && streamed ? 1 : 0);
   }
   return MG_OK;
 }

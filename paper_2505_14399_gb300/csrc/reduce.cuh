@@ -2,11 +2,13 @@
 //
 // A vector of length n is cut into `nblk` fixed chunks (one CTA each, an even number of
 // elements so FP32 pairs can move as 16-byte accesses).  Each CTA reduces its chunk in the
-// vectors' own precision with a fixed shuffle/shared-memory tree and stores one FP64
-// partial; the last CTA to finish (detected with an atomic counter) sums the partials in
-// index order.  The partition and the order do not depend on timing, so results are
+// vectors' own precision with a fixed shuffle/shared-memory tree and stores one partial in
+// that precision; the last CTA to finish (detected with an atomic counter) sums the partials
+// in index order.  The partition and the order do not depend on timing, so results are
 // bitwise reproducible.
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -35,41 +37,50 @@ __host__ __device__ __forceinline__ size_t reduce_chunk(size_t n, int nblk) {
 // mode 0: complex dot -> out[rhs*ldo + i] = scale * sum; mode 1: norm -> dout[rhs*ldo] =
 // sqrt(scale * re).  scale = 1 except for the (1/n) inner product of half-storage bases.
 // One warp per vector: lanes sum strided partials, then a shuffle tree (fixed order).
-__device__ __forceinline__ void finish_partials(const double* partial, int nv, int nblk,
+// Partials are P = double for FP64 vectors and P = float for the FP32-arithmetic ones, so the
+// reduction of the last CTA, which every following kernel waits for, does not run on the
+// FP64 units (1/74 of the FP32 rate on this part).
+template <typename P>
+__device__ __forceinline__ void finish_partials(const P* partial, int nv, int nblk,
                                                 int maxvec, int rhs, zd* out, double* dout,
                                                 int ldo, int mode, double scale = 1.0) {
+  typedef typename std::conditional<sizeof(P) == 8, double2, float2>::type P2;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = wid; i < nv; i += nw) {
-    const double2* p = reinterpret_cast<const double2*>(partial) + ((size_t)rhs * maxvec + i) * nblk;
-    // four independent accumulators keep four 16-byte loads in flight per lane
-    double2 s0 = {0, 0}, s1 = {0, 0}, s2 = {0, 0}, s3 = {0, 0};
+    const P2* p = reinterpret_cast<const P2*>(partial) + ((size_t)rhs * maxvec + i) * nblk;
+    // four independent accumulators keep four loads in flight per lane
+    P2 s0 = {0, 0}, s1 = {0, 0}, s2 = {0, 0}, s3 = {0, 0};
     int k = lane;
     for (; k + 96 < nblk; k += 128) {
-      double2 v0 = __ldcg(p + k), v1 = __ldcg(p + k + 32);
-      double2 v2 = __ldcg(p + k + 64), v3 = __ldcg(p + k + 96);
+      P2 v0 = __ldcg(p + k), v1 = __ldcg(p + k + 32);
+      P2 v2 = __ldcg(p + k + 64), v3 = __ldcg(p + k + 96);
       s0.x += v0.x; s0.y += v0.y; s1.x += v1.x; s1.y += v1.y;
       s2.x += v2.x; s2.y += v2.y; s3.x += v3.x; s3.y += v3.y;
     }
     for (; k < nblk; k += 32) {
-      double2 v0 = __ldcg(p + k);
+      P2 v0 = __ldcg(p + k);
       s0.x += v0.x; s0.y += v0.y;
     }
-    double a = (s0.x + s1.x) + (s2.x + s3.x), b = (s0.y + s1.y) + (s2.y + s3.y);
-    a = warp_sum(a);
-    b = warp_sum(b);
+    P a = (s0.x + s1.x) + (s2.x + s3.x), b = (s0.y + s1.y) + (s2.y + s3.y);
+    a = warp_sum_r(a);
+    b = warp_sum_r(b);
     if (lane == 0) {
-      if (mode == 0) out[(size_t)rhs * ldo + i] = {a * scale, b * scale};
-      else dout[(size_t)rhs * ldo] = sqrt(a * scale);
+      if (mode == 0) out[(size_t)rhs * ldo + i] = {(double)a * scale, (double)b * scale};
+      else dout[(size_t)rhs * ldo] = sqrt((double)a * scale);
     }
   }
 }
 
-// CTA reduction of ni complex values held per thread (R precision) into the FP64 partial
-// slots partial[((rhs*maxvec + i0 + q) * nblk + blockIdx.x) * 2 + {0,1}], q < ni <= G.
+// The partial buffer (FP64 slots) viewed as partials of type P.
+template <typename P>
+__device__ __forceinline__ P* partials_as(double* partial) { return reinterpret_cast<P*>(partial); }
+
+// CTA reduction of ni complex values held per thread (R precision) into the partial slots
+// partial[((rhs*maxvec + i0 + q) * nblk + blockIdx.x) * 2 + {0,1}] (type R), q < ni <= G.
 template <typename R, int G>
 __device__ __forceinline__ void cta_store_partials(const R* ar, const R* ai, int ni, int i0,
                                                    int rhs, int maxvec, int nblk,
-                                                   double* partial, R* shg) {
+                                                   R* partial, R* shg) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < G; ++q) {
@@ -84,7 +95,7 @@ __device__ __forceinline__ void cta_store_partials(const R* ar, const R* ai, int
     int q = threadIdx.x >> 1, part = threadIdx.x & 1;
     R s = 0;
     for (int wv = 0; wv < RT / 32; ++wv) s += shg[(wv * G + q) * 2 + part];
-    partial[(((size_t)rhs * maxvec + i0 + q) * nblk + blockIdx.x) * 2 + part] = (double)s;
+    partial[(((size_t)rhs * maxvec + i0 + q) * nblk + blockIdx.x) * 2 + part] = s;
     __threadfence();   // the writer publishes its partial before the CTA signals completion
   }
   __syncthreads();

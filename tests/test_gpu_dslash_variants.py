@@ -1,5 +1,7 @@
 """Every launch shape of the stencil (the autotuner's candidates, forced one at a time through
-WMG_DSLASH_VARIANT in a child process) against the FP64 oracle."""
+WMG_DSLASH_VARIANT in a child process) against the FP64 oracle: both link layouts, both
+directions of the operator, full and single-parity, 2 and 5 right-hand sides (variants 6 and
+7 take 2 and 4 per thread, so both leave a ragged last group)."""
 import os
 import subprocess
 import sys
@@ -35,11 +37,23 @@ for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
         ref = wilson.dslash_parity(half[r], U, dims, 0.13, 1, w, bc)
         e = np.linalg.norm(out[r] - ref) / np.linalg.norm(ref)
         assert e < tol, ("parity", dt, e)
+# the solver's lane-contiguous link copy, five right-hand sides (ragged groups of 2 and 4)
+psi5 = synthetic.gaussian_rhs(dims, 72, 5)
+p = api.params(dims, (2, 2, 2, 2), 0.13, 4, 4, 1, 1, 1, w, bc)
+h = api.Hierarchy(torch.from_numpy(U).cuda(), p, setup=False)
+for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):
+    for dag in (False, True):
+        out = h.apply_fine(torch.from_numpy(psi5).to(dt).cuda(), dagger=dag).cpu().numpy()
+        for r in range(5):
+            ref = wilson.dslash(psi5[r], U, dims, 0.13, w, bc, dag)
+            e = np.linalg.norm(out[r] - ref) / np.linalg.norm(ref)
+            assert e < tol, ("lanes", dt, dag, r, e)
+h.close()
 print("ok")
 """
 
 
-@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("variant", range(8))
 def test_forced_launch_shape_matches_oracle(variant):
     env = dict(os.environ, WMG_DSLASH_VARIANT=str(variant), PYTHONPATH=ROOT)
     r = subprocess.run([sys.executable, "-c", CHILD], cwd=ROOT, env=env, capture_output=True,
