@@ -152,16 +152,16 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
   int np = ce / 2;
   T* A = reinterpret_cast<T*>(sm);    // ce x ce
   T* Vv = A + ce * ce;                // ce x ce
-  double* rc = reinterpret_cast<double*>(Vv + ce * ce);   // [np] cos (FP64, skip test)
-  double* rsn = rc + np;                                   // [np] sin
-  TR* rcT = reinterpret_cast<TR*>(rsn + np);               // [np] cos, sin in T's arithmetic
-  TR* rsT = rcT + np;
-  T* rph = reinterpret_cast<T*>(rsT + np);                 // [np] e^{-i phi}
-  int* top = reinterpret_cast<int*>(rph + np);             // [np]
-  int* bot = top + np;                                     // [np]
+  T* rph = Vv + ce * ce;              // [np] e^{-i phi}
+  TR* rcT = reinterpret_cast<TR*>(rph + np);   // [np] cos
+  TR* rsT = rcT + np;                          // [np] sin
+  int* top = reinterpret_cast<int*>(rsT + np);   // [np]
+  int* bot = top + np;                           // [np]
+  int* rflag = bot + np;                         // [np] pair rotated in this round
   __shared__ double dg[MAXC];
   int t = blockIdx.x;
   const zd* Gt = G + (size_t)t * c * c;
+  const float rtol2 = (float)(rtol * rtol);
   for (int e = threadIdx.x; e < ce * ce; e += blockDim.x) {
     int i = e / ce, j = e % ce;
     A[e] = (i < c && j < c) ? J::from(Gt[i * c + j]) : J::zero();
@@ -178,37 +178,66 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
       // rotation parameters
       for (int p = threadIdx.x; p < np; p += blockDim.x) {
         int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
-        double c0 = 1.0, s = 0.0;
-        zd ph = {1, 0};
-        if (b < c) {
-          zd g = J::val(A[a * ce + b]);
-          double ag = sqrt(norm2(g));
-          double da = J::val(A[a * ce + a]).re, db = J::val(A[b * ce + b]).re;
-          if (ag > rtol * sqrt(fabs(da * db)) && ag > 1e-300) {
-            double zeta = (db - da) / (2.0 * ag);
-            double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c0 = 1.0 / sqrt(1.0 + tt * tt);
-            s = tt * c0;
-            ph = {g.re / ag, -g.im / ag};  // e^{-i phi}
-            rotated = 1;
-          }
-        }
-        rc[p] = c0;
-        rsn[p] = s;
+        int f = 0;
         if constexpr (DF) {
-          rcT[p] = df_from(c0);
-          rsT[p] = df_from(s);
+          // The angle comes from FP32 copies (the diagonal difference formed in df64 first,
+          // so close eigenvalues keep their separation); cos, sin and the phase are then
+          // made an exact rotation in df64 (c = (1 + t^2)^-1/2, s = t c, |phase| = 1) by
+          // Newton reciprocal square roots on the FP32 units.  An angle good to FP32 leaves
+          // ~1e-7 of the pair's coupling, removed when the pair comes round again; the
+          // rotation applied is unitary to df64 accuracy either way.
+          df cT = {1.f, 0.f}, sT = {0.f, 0.f};
+          zdf phT = {{1.f, 0.f}, {0.f, 0.f}};
+          if (b < c) {
+            zdf g = A[a * ce + b];
+            df da = A[a * ce + a].re, db = A[b * ce + b].re;
+            float gr = df_to_float(g.re), gi = df_to_float(g.im);
+            float ag2 = fmaf(gr, gr, gi * gi);
+            if (ag2 > rtol2 * fabsf(da.hi * db.hi) && ag2 > 0.f) {
+              float ia = rsqrtf(ag2);            // 1 / |g|
+              float zeta = 0.5f * df_to_float(df_add(db, df_neg(da))) * ia;
+              float tt = fabsf(zeta) > 1e18f
+                             ? 0.5f / zeta
+                             : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+              cT = df_rsqrt(df_add({1.f, 0.f}, df_two_prod(tt, tt)));
+              sT = df_mul_f(cT, tt);
+              float pr = gr * ia, pi = -gi * ia;   // e^{-i phi} to FP32, then normalised
+              df q = df_rsqrt(df_add(df_two_prod(pr, pr), df_two_prod(pi, pi)));
+              phT = {df_mul_f(q, pr), df_mul_f(q, pi)};
+              f = 1;
+            }
+          }
+          rcT[p] = cT;
+          rsT[p] = sT;
+          rph[p] = phT;
         } else {
+          double c0 = 1.0, s = 0.0;
+          zd ph = {1, 0};
+          if (b < c) {
+            zd g = J::val(A[a * ce + b]);
+            double ag = sqrt(norm2(g));
+            double da = J::val(A[a * ce + a]).re, db = J::val(A[b * ce + b]).re;
+            if (ag > rtol * sqrt(fabs(da * db)) && ag > 1e-300) {
+              double zeta = (db - da) / (2.0 * ag);
+              double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+              c0 = 1.0 / sqrt(1.0 + tt * tt);
+              s = tt * c0;
+              ph = {g.re / ag, -g.im / ag};  // e^{-i phi}
+              f = 1;
+            }
+          }
           rcT[p] = c0;
           rsT[p] = s;
+          rph[p] = J::from(ph);
         }
-        rph[p] = J::from(ph);
+        rflag[p] = f;
+        rotated |= f;
       }
       __syncthreads();
       // rows: new_a = c A_a - s e^{i phi} A_b ; new_b = s A_a + c e^{i phi} A_b
       for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
         int p = e / ce, k = e % ce;
-        if (rsn[p] == 0.0 && rc[p] == 1.0) continue;
+        if (!rflag[p]) continue;
         int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
         T eph = rph[p];
         if constexpr (DF) eph.im = df_neg(eph.im);
@@ -222,7 +251,7 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
       // columns: new_a = c M_a - s e^{-i phi} M_b ; new_b = s M_a + c e^{-i phi} M_b
       for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
         int p = e / ce, k = e % ce;
-        if (rsn[p] == 0.0 && rc[p] == 1.0) continue;
+        if (!rflag[p]) continue;
         int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
         T mph = rph[p];
         T xa = A[k * ce + a], xb = A[k * ce + b];
@@ -235,15 +264,17 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
         Vv[k * ce + b] = vb;
       }
       __syncthreads();
-      // the rotated pair's off-diagonal entries are zero by construction
-      for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        if (!(rsn[p] == 0.0 && rc[p] == 1.0)) {
-          int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
-          A[a * ce + b] = J::zero();
-          A[b * ce + a] = J::zero();
+      if constexpr (!DF) {
+        // with the exact FP64 angle the rotated pair's off-diagonal entries are zero
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+          if (rflag[p]) {
+            int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+            A[a * ce + b] = J::zero();
+            A[b * ce + a] = J::zero();
+          }
         }
+        __syncthreads();
       }
-      __syncthreads();
       // round-robin: keep top[0], rotate the others
       if (threadIdx.x == 0 && np > 1) {
         int tlast = top[np - 1];
@@ -260,18 +291,27 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
   }
   for (int i = threadIdx.x; i < c; i += blockDim.x) dg[i] = J::val(A[i * ce + i]).re;
   __syncthreads();
-  // sort eigenvalues descending (stable by index), thread 0
+  // sort eigenvalues descending (stable by index), thread 0; the df64 path compares the
+  // normalised (hi, lo) pairs on the FP32 units
   __shared__ int order[MAXC];
   if (threadIdx.x == 0) {
     // stable insertion sort by value descending (ties keep index order)
     for (int i = 0; i < c; ++i) order[i] = i;
     for (int i = 1; i < c; ++i) {
       int key = order[i];
-      double kv = dg[key];
       int j = i - 1;
-      while (j >= 0 && dg[order[j]] < kv) {
-        order[j + 1] = order[j];
-        --j;
+      if constexpr (DF) {
+        df kv = A[key * ce + key].re;
+        while (j >= 0 && df_less(A[order[j] * ce + order[j]].re, kv)) {
+          order[j + 1] = order[j];
+          --j;
+        }
+      } else {
+        double kv = dg[key];
+        while (j >= 0 && dg[order[j]] < kv) {
+          order[j + 1] = order[j];
+          --j;
+        }
       }
       order[j + 1] = key;
     }
@@ -440,8 +480,8 @@ int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, do
              bool df64) {
   if (c > MAXC) return fail(MG_EINVAL, "tile_eig: more than 64 columns");
   int ce = c + (c & 1), np = ce / 2;
-  size_t sh = sizeof(zd) * 2 * ce * ce + sizeof(double) * 2 * np + sizeof(zd) * np +
-              sizeof(zd) * np + sizeof(int) * 2 * np + 64;
+  // A, V, phases (16-byte complex in both arithmetics), cos, sin (8 bytes), three int arrays
+  size_t sh = sizeof(zd) * (2 * ce * ce + np) + sizeof(double) * 2 * np + sizeof(int) * 3 * np + 64;
   static bool attr_set = false;
   if (!attr_set) {
     WMG_CUDA(cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -94,6 +94,52 @@ __device__ __forceinline__ df df_norm(dfacc a) {
 }
 __device__ __forceinline__ zdf zdf_norm(const zdfacc& a) { return {df_norm(a.re), df_norm(a.im)}; }
 
+// Normalised df64 arithmetic for the few scalar steps that need it (Jacobi rotations).
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {   // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_fast_two_sum(s, e);
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float df_to_float(df a) { return __fadd_rn(a.hi, a.lo); }
+// Exact comparison of normalised values.
+__device__ __forceinline__ bool df_less(df a, df b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+// 1 / sqrt(x), x > 0: the FP32 estimate refined by two Newton steps y <- y + y (1 - x y^2) / 2
+// in df64 (each step squares the relative error: ~1e-7 -> ~1e-14 -> rounding).
+__device__ __forceinline__ df df_rsqrt(df x) {
+  df y = {rsqrtf(x.hi), 0.0f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    df r = df_add({1.0f, 0.0f}, df_neg(df_mul(x, df_mul(y, y))));
+    y = df_add(y, df_mul(y, df_mul_f(r, 0.5f)));
+  }
+  return y;
+}
+
 // complex df64 sign and i-multiples (exact)
 __device__ __forceinline__ zdf zdf_neg(zdf a) { return {df_neg(a.re), df_neg(a.im)}; }
 __device__ __forceinline__ zdf zdf_ti(zdf a) { return {df_neg(a.im), a.re}; }    // i a
