@@ -2,7 +2,9 @@
 // chiralities at once.
 //
 // Every (aggregate j, chirality alpha) owns a tile A = [Phi_{s-1} | Psi_s] of M = 6 n_d
-// rows (Eq. 3 split) stored column-major in FP64.  One stream is:
+// rows (Eq. 3 split) stored column-major in FP64, or in double-float (zdf, the same 16 bytes)
+// when the sums run in double-float: those tiles then stay double-float from the gather to
+// the final prolongator, so no kernel converts them on the FP64 units.  One stream is:
 //   gather   : chiral split of the r new smoothed vectors into columns kk.. of all tiles
 //   gram     : G = A^dag A (c x c Hermitian, c = kk + r), one CTA per tile
 //   eig      : parallel cyclic Jacobi (Brent-Luk ordering) on G in shared memory,
@@ -21,8 +23,8 @@ namespace wmg {
 
 namespace {
 
-template <typename R>
-__global__ void gather_kernel(zd* tiles, int cmax, int col0, const cplx<R>* __restrict__ f,
+template <typename R, typename TO>
+__global__ void gather_kernel(TO* tiles, int cmax, int col0, const cplx<R>* __restrict__ f,
                               int nvec, Blocking B) {
   size_t total = (size_t)nvec * B.L[0] * B.L[1] * B.L[2] * B.L[3] * 12;
   size_t V12 = total / nvec;
@@ -38,7 +40,8 @@ __global__ void gather_kernel(zd* tiles, int cmax, int col0, const cplx<R>* __re
     int row = (l * 2 + (spin & 1)) * 3 + col;
     size_t t = (size_t)j * 2 + alpha;
     cplx<R> x = f[e];
-    tiles[(t * cmax + col0 + v) * B.M + row] = {(double)x.re, (double)x.im};
+    if constexpr (std::is_same<TO, zdf>::value) tiles[(t * cmax + col0 + v) * B.M + row] = zdf_from(x);
+    else tiles[(t * cmax + col0 + v) * B.M + row] = {(double)x.re, (double)x.im};
   }
 }
 
@@ -50,14 +53,14 @@ constexpr int MAXC = 64;  // max columns per tile
 // error-free transformations) instead of FP64.  MAXP: column pairs per thread
 // (>= c (c + 1) / 2 / GT), which sets the accumulator registers.
 template <bool DF, int MAXP>
-__global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ tiles, int cmax,
+__global__ void __launch_bounds__(GT) gram_kernel(zd* G, const void* __restrict__ tiles, int cmax,
                                                   int c, int M) {
   typedef typename std::conditional<DF, zdf, zd>::type T;
   typedef typename std::conditional<DF, zdfacc, zd>::type TA;
   extern __shared__ zd smraw_g[];
   T* sA = reinterpret_cast<T*>(smraw_g);  // [GR][c]
   int t = blockIdx.x;
-  const zd* A = tiles + (size_t)t * cmax * M;
+  const T* A = reinterpret_cast<const T*>(tiles) + (size_t)t * cmax * M;
   int npairs = c * (c + 1) / 2;
   TA acc[MAXP];
   int pi[MAXP], pj[MAXP];
@@ -76,9 +79,8 @@ __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const zd* __restrict__ 
     __syncthreads();
     for (int e = threadIdx.x; e < nr * c; e += GT) {
       int col = e / nr, rr = e % nr;
-      zd v = A[(size_t)col * M + r0 + rr];
-      if constexpr (DF) sA[rr * c + col] = zdf_from(v);
-      else sA[rr * c + col] = v;
+      if constexpr (DF) sA[rr * c + col] = zdf_ld(A + (size_t)col * M + r0 + rr);
+      else sA[rr * c + col] = A[(size_t)col * M + r0 + rr];
     }
     __syncthreads();
 #pragma unroll
@@ -328,10 +330,10 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
 constexpr int UK = 64;  // max output columns per update
 
 template <bool DF>
-__global__ void __launch_bounds__(GT) update_kernel(zd* out, int cmax_out, const zd* __restrict__ tiles,
-                                                    int cmax, int c, const zd* __restrict__ Vec,
-                                                    const double* lam, int kout, int scale_inv,
-                                                    int M) {
+__global__ void __launch_bounds__(GT) update_kernel(void* out, int cmax_out,
+                                                    const void* __restrict__ tiles, int cmax, int c,
+                                                    const zd* __restrict__ Vec, const double* lam,
+                                                    int kout, int scale_inv, int M) {
   typedef typename std::conditional<DF, zdf, zd>::type T;
   typedef typename std::conditional<DF, zdfacc, zd>::type TA;
   extern __shared__ zd smraw_u[];
@@ -350,21 +352,21 @@ __global__ void __launch_bounds__(GT) update_kernel(zd* out, int cmax_out, const
     else sV[e] = v;
   }
   __syncthreads();
-  const zd* A = tiles + (size_t)t * cmax * M;
-  zd* O = out + (size_t)t * cmax_out * M;
+  const T* A = reinterpret_cast<const T*>(tiles) + (size_t)t * cmax * M;
+  T* O = reinterpret_cast<T*>(out) + (size_t)t * cmax_out * M;
   for (int r = threadIdx.x; r < M; r += blockDim.x) {
     for (int i0 = 0; i0 < kout; i0 += 16) {
       TA acc[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) acc[q] = TA{};
       for (int col = 0; col < c; ++col) {
-        zd a0 = A[(size_t)col * M + r];
         if constexpr (DF) {
-          zdf a = zdf_from(a0);
+          zdf a = zdf_ld(A + (size_t)col * M + r);
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             if (i0 + q < kout) zdf_fma(acc[q], a, sV[col * kout + i0 + q]);
         } else {
+          zd a0 = A[(size_t)col * M + r];
 #pragma unroll
           for (int q = 0; q < 16; ++q)
             if (i0 + q < kout) cfma(acc[q], a0, sV[col * kout + i0 + q]);
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(GT) update_kernel(zd* out, int cmax_out, const
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         if (i0 + q < kout) {
-          if constexpr (DF) O[(size_t)(i0 + q) * M + r] = zdf_result(acc[q]);
+          if constexpr (DF) O[(size_t)(i0 + q) * M + r] = zdf_norm(acc[q]);
           else O[(size_t)(i0 + q) * M + r] = acc[q];
         }
       }
@@ -415,6 +417,73 @@ __global__ void __launch_bounds__(GT) phase_kernel(zd* tiles, int cmax, int k, i
   }
 }
 
+// The same canonical phase on double-float tiles, in double-float arithmetic: the column sum
+// accumulated error-free on the FP32 units, q = conj(s) / |s| normalised by a Newton
+// reciprocal square root, each entry multiplied by q.
+__global__ void __launch_bounds__(GT) phase_df_kernel(zdf* tiles, int cmax, int k, int M) {
+  __shared__ df sh[2][GT / 32];
+  __shared__ zdf q;
+  int t = blockIdx.x;
+  zdf* A = tiles + (size_t)t * cmax * M;
+  const df one = {1.0f, 0.0f};
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = 0; i < k; ++i) {
+    zdf* col = A + (size_t)i * M;
+    dfacc a{0.f, 0.f}, b{0.f, 0.f};
+    for (int r = threadIdx.x; r < M; r += blockDim.x) {
+      zdf v = col[r];
+      df_fma(a, v.re, one);
+      df_fma(b, v.im, one);
+    }
+    df ar = df_norm(a), br = df_norm(b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df x = {__shfl_down_sync(0xffffffffu, ar.hi, o), __shfl_down_sync(0xffffffffu, ar.lo, o)};
+      df y = {__shfl_down_sync(0xffffffffu, br.hi, o), __shfl_down_sync(0xffffffffu, br.lo, o)};
+      ar = df_add(ar, x);
+      br = df_add(br, y);
+    }
+    if (lane == 0) { sh[0][wid] = ar; sh[1][wid] = br; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      df sa = {0.f, 0.f}, sb = {0.f, 0.f};
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        sa = df_add(sa, sh[0][w]);
+        sb = df_add(sb, sh[1][w]);
+      }
+      df n2 = df_add(df_mul(sa, sa), df_mul(sb, sb));
+      if (n2.hi > 0.f) {
+        df inv = df_rsqrt(n2);
+        q = {df_mul(sa, inv), df_neg(df_mul(sb, inv))};
+      } else {
+        q = {one, {0.f, 0.f}};
+      }
+    }
+    __syncthreads();
+    zdf f = q;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) {
+      zdf v = col[r];
+      col[r] = {df_dot2(v.re, f.re, df_neg(v.im), f.im), df_dot2(v.re, f.im, v.im, f.re)};
+    }
+    __syncthreads();
+  }
+}
+
+// First k columns of double-float tiles -> P (complex double), P32 (complex float, the
+// rounded value) and, when Pdf is given, the double-float copy; outputs [tile][k][M].
+__global__ void tile_outputs_kernel(zd* P, zf* P32, zdf* Pdf, const zdf* __restrict__ tiles,
+                                    int cmax, int k, int M, size_t total) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t r = e % M, ti = e / M;
+    size_t t = ti / k, i = ti % k;
+    zdf v = zdf_ld(tiles + (t * cmax + i) * M + r);
+    P[e] = {df_val(v.re), df_val(v.im)};
+    P32[e] = {df_to_float(v.re), df_to_float(v.im)};
+    if (Pdf) Pdf[e] = v;
+  }
+}
+
 __global__ void sigma_kernel(double* sig, int ldsig, const double* lam, int c, int kk, int ntiles) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ntiles * kk) return;
@@ -442,19 +511,21 @@ int make_blocking(Blocking& B, const int dims[4], const int block[4]) {
 }
 
 template <typename R>
-int chiral_gather(zd* tiles, int cmax, int col0, const cplx<R>* fields, int nvec,
-                  const Blocking& B, cudaStream_t st) {
+int chiral_gather(void* tiles, int cmax, int col0, const cplx<R>* fields, int nvec,
+                  const Blocking& B, cudaStream_t st, bool df64) {
   size_t total = (size_t)nvec * B.nd * B.d * 12;
   size_t g = (total + 255) / 256;
   size_t cap = (size_t)num_sms() * 16;
-  gather_kernel<R><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(tiles, cmax, col0, fields, nvec, B);
+  unsigned grid = (unsigned)(g < cap ? g : cap);
+  if (df64) gather_kernel<R, zdf><<<grid, 256, 0, st>>>((zdf*)tiles, cmax, col0, fields, nvec, B);
+  else gather_kernel<R, zd><<<grid, 256, 0, st>>>((zd*)tiles, cmax, col0, fields, nvec, B);
   WMG_LAUNCHED();
   return MG_OK;
 }
-template int chiral_gather<float>(zd*, int, int, const zf*, int, const Blocking&, cudaStream_t);
-template int chiral_gather<double>(zd*, int, int, const zd*, int, const Blocking&, cudaStream_t);
+template int chiral_gather<float>(void*, int, int, const zf*, int, const Blocking&, cudaStream_t, bool);
+template int chiral_gather<double>(void*, int, int, const zd*, int, const Blocking&, cudaStream_t, bool);
 
-int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaStream_t st,
+int tile_gram(zd* G, const void* tiles, int cmax, int c, const Blocking& B, cudaStream_t st,
               bool df64) {
   if (c > MAXC) return fail(MG_EINVAL, "tile_gram: more than 64 columns");
   size_t sh = sizeof(zd) * GR * c;
@@ -497,7 +568,7 @@ int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, do
   return MG_OK;
 }
 
-int tile_update(zd* out, int cmax_out, const zd* tiles, int cmax, int c, const zd* Vec,
+int tile_update(void* out, int cmax_out, const void* tiles, int cmax, int c, const zd* Vec,
                 const double* lam, int kout, int scale_inv, const Blocking& B, cudaStream_t st,
                 bool df64) {
   if (kout > UK || c > MAXC) return fail(MG_EINVAL, "tile_update: too many columns");
@@ -522,8 +593,21 @@ int tile_update(zd* out, int cmax_out, const zd* tiles, int cmax, int c, const z
   return MG_OK;
 }
 
-int tile_canonical_phase(zd* tiles, int cmax, int k, const Blocking& B, cudaStream_t st) {
-  phase_kernel<<<B.d * 2, GT, 0, st>>>(tiles, cmax, k, B.M);
+int tile_canonical_phase(void* tiles, int cmax, int k, const Blocking& B, cudaStream_t st,
+                         bool df64) {
+  if (df64) phase_df_kernel<<<B.d * 2, GT, 0, st>>>((zdf*)tiles, cmax, k, B.M);
+  else phase_kernel<<<B.d * 2, GT, 0, st>>>((zd*)tiles, cmax, k, B.M);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+int tile_outputs(zd* P, zf* P32, zdf* Pdf, const void* tiles, int cmax, int k, const Blocking& B,
+                 cudaStream_t st) {
+  size_t total = (size_t)B.d * 2 * k * B.M;
+  size_t g = (total + 255) / 256;
+  size_t cap = (size_t)num_sms() * 16;
+  tile_outputs_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(
+      P, P32, Pdf, (const zdf*)tiles, cmax, k, B.M, total);
   WMG_LAUNCHED();
   return MG_OK;
 }

@@ -417,7 +417,8 @@ int launch_hop_ne(dim3 grid, size_t sh, cudaStream_t st, zd* Op, zd* Xpart, cons
 }  // namespace
 
 int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, const zd* links,
-                   const zdf* Ldf, const Geom& g, const Blocking& B, cudaStream_t st, bool df64) {
+                   const zdf* Ldf, const Geom& g, const Blocking& B, cudaStream_t st, bool df64,
+                   bool pdf_ready) {
   if (4 * k * k > GTH * GMAXE) return fail(MG_EINVAL, "galerkin: k > 32");
   if (df64 && (!Pdf || !Ldf)) return fail(MG_EINVAL, "galerkin: double-float copies missing");
   HopGeom hg;
@@ -434,8 +435,12 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, con
   size_t sh = sizeof(zd) * 2 * GNB * 6 * 2 * k;
   dim3 grid(B.d, 4);
   // diagonal term P_j^dag P_j: the Gram matrix of every P tile (profiled as a Gram launch)
-  WMG_TRY(tile_gram(PtP, P, k, k, B, st, df64));
-  if (df64) WMG_TRY(to_df(Pdf, P, (size_t)B.d * 2 * k * B.M, st));
+  if (df64) {
+    if (!pdf_ready) WMG_TRY(to_df(Pdf, P, (size_t)B.d * 2 * k * B.M, st));
+    WMG_TRY(tile_gram(PtP, Pdf, k, k, B, st, true));
+  } else {
+    WMG_TRY(tile_gram(PtP, P, k, k, B, st, false));
+  }
   ProfScope ps(df64 ? "galerkin_df64" : "galerkin_fp64", 16.0 * (12.0 * B.nd * B.d * k * 5 + 36.0 * B.nd * B.d),
                768.0 * k * k * B.nd * B.d, st);
   if (df64) {

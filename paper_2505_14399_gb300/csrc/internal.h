@@ -237,13 +237,16 @@ struct Blocking {
 int make_blocking(Blocking& B, const int dims[4], const int block[4]);
 
 // ------------------------------------------------------------------ chiral SVD
-// Tile buffers: [tile][column][row] complex double, column stride M, tile stride cmax*M.
+// Tile buffers: [tile][column][row], column stride M, tile stride cmax*M; complex double, or
+// complex double-float (zdf, the same 16 bytes) when df64 is set: the double-float setup keeps
+// its tiles in that form from the gather to the prolongator, so nothing converts them on the
+// FP64 units.
 // gather: columns col0 .. col0+nvec-1 of every tile from nvec fields [v][site][12].
 template <typename R>
-int chiral_gather(zd* tiles, int cmax, int col0, const cplx<R>* fields, int nvec,
-                  const Blocking& B, cudaStream_t st);
-// G[t][c][c] = A_t^dag A_t over the first c columns.
-int tile_gram(zd* G, const zd* tiles, int cmax, int c, const Blocking& B, cudaStream_t st,
+int chiral_gather(void* tiles, int cmax, int col0, const cplx<R>* fields, int nvec,
+                  const Blocking& B, cudaStream_t st, bool df64 = false);
+// G[t][c][c] = A_t^dag A_t over the first c columns (df64: double-float tiles and sums).
+int tile_gram(zd* G, const void* tiles, int cmax, int c, const Blocking& B, cudaStream_t st,
               bool df64 = false);
 // Hermitian eigen-decomposition of every G_t (c x c) by parallel cyclic Jacobi; returns
 // eigenvalues descending in lam[t][c] and eigenvectors in Vec[t][c][c] (column i at
@@ -253,12 +256,17 @@ int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, do
              bool df64 = false);
 // out[t][i][row] = sum_c A[t][c][row] Vec[t][c][i] * (scale_inv ? 1/sqrt(lam[t][i]) : 1)
 // for i < kout; out tile stride cmax_out*M.
-// df64: sums of products in double-float arithmetic (df64.cuh) instead of FP64.
-int tile_update(zd* out, int cmax_out, const zd* tiles, int cmax, int c, const zd* Vec,
+// df64: double-float tiles in and out, sums of products in double-float arithmetic.
+int tile_update(void* out, int cmax_out, const void* tiles, int cmax, int c, const zd* Vec,
                 const double* lam, int kout, int scale_inv, const Blocking& B, cudaStream_t st,
                 bool df64 = false);
 // Multiply every column i < k of every tile by conj(q)/|q|, q = sum of its entries.
-int tile_canonical_phase(zd* tiles, int cmax, int k, const Blocking& B, cudaStream_t st);
+int tile_canonical_phase(void* tiles, int cmax, int k, const Blocking& B, cudaStream_t st,
+                         bool df64 = false);
+// The first k columns of double-float tiles as P [tile][k][M] in complex double, complex
+// float (rounded) and, if Pdf is not null, double-float.
+int tile_outputs(zd* P, zf* P32, zdf* Pdf, const void* tiles, int cmax, int k, const Blocking& B,
+                 cudaStream_t st);
 // sig[t*ldsig + i] = sqrt(max(lam[t][i], 0)), i < kk
 int tile_sigma(double* sig, int ldsig, const double* lam, int c, int kk, int ntiles,
                cudaStream_t st);
@@ -273,9 +281,11 @@ int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const
                    int nrhs, cudaStream_t st);
 // Galerkin: Op[j][blk][b][a] (column-major blocks; blk 0 = X, 1 + dir = Y_dir), FP64.
 // Scratch: Xpart (4 d (2k)^2), PtP (2 d k^2), and with df64 Pdf (P as (hi, lo) pairs, filled
-// here) and Ldf (the links as (hi, lo) pairs, filled by the caller).
+// here unless pdf_ready says the setup wrote it) and Ldf (the links as (hi, lo) pairs, filled
+// by the caller).
 int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, const zd* links,
-                   const zdf* Ldf, const Geom& g, const Blocking& B, cudaStream_t st, bool df64);
+                   const zdf* Ldf, const Geom& g, const Blocking& B, cudaStream_t st, bool df64,
+                   bool pdf_ready = false);
 // complex double -> (hi, lo) float pairs
 int to_df(zdf* out, const zd* in, size_t n, cudaStream_t st);
 template <typename R>

@@ -34,6 +34,7 @@ struct mg_handle {
   zdf* Pdf = nullptr;          // double-float Galerkin: P and the links as (hi, lo) pairs
   zdf* Ldf = nullptr;
   bool have_P = false, have_coarse = false;
+  bool pdf_ready = false;      // Pdf holds the double-float split of P64 already
   // solver state, sized for `nrhs`
   int nrhs = 0;
   Gmres<double> outer64, coarse64, post64;
@@ -201,7 +202,7 @@ int run_setup(mg_handle* h, cudaStream_t st) {
   const double eig_tol = df ? 1e-13 : 1e-15;
   for (int s = 0; s < p.n_s; ++s) {
     STEP(smooth_stream<R>(h, psi, phi, tmp, gm, s, st));
-    STEP(chiral_gather<R>(cur, cmax, kk, psi, r, h->B, st));
+    STEP(chiral_gather<R>(cur, cmax, kk, psi, r, h->B, st, df));
     int c = kk + r;
     int kn = c < k ? c : k;
     bool last = s == p.n_s - 1;
@@ -220,10 +221,18 @@ int run_setup(mg_handle* h, cudaStream_t st) {
     STEP(tile_sigma(h->hist + (size_t)s * ntile * k, k, lam, c, kn, (int)ntile, st));
     kk = kn;
   }
-  STEP(tile_canonical_phase(cur, cmax, k, h->B, st));
-  CSTEP(cudaMemcpy2DAsync(h->P64, (size_t)k * M * sizeof(zd), cur, (size_t)cmax * M * sizeof(zd),
-                          (size_t)k * M * sizeof(zd), ntile, cudaMemcpyDeviceToDevice, st));
-  STEP((convert<float, double>(h->P32, h->P64, nullptr, 0, ntile * k * M, 1, st)));
+  STEP(tile_canonical_phase(cur, cmax, k, h->B, st, df));
+  if (df) {
+    // double-float tiles: P, its FP32 copy and (for the double-float Galerkin) its
+    // double-float copy in one pass
+    STEP(tile_outputs(h->P64, h->P32, h->Pdf, cur, cmax, k, h->B, st));
+    h->pdf_ready = h->Pdf != nullptr;
+  } else {
+    CSTEP(cudaMemcpy2DAsync(h->P64, (size_t)k * M * sizeof(zd), cur, (size_t)cmax * M * sizeof(zd),
+                            (size_t)k * M * sizeof(zd), ntile, cudaMemcpyDeviceToDevice, st));
+    STEP((convert<float, double>(h->P32, h->P64, nullptr, 0, ntile * k * M, 1, st)));
+    h->pdf_ready = false;
+  }
   CSTEP(cudaMemcpyAsync(h->sigma, h->hist + (size_t)(p.n_s - 1) * ntile * k,
                         ntile * k * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CSTEP(cudaStreamSynchronize(st));
@@ -546,7 +555,7 @@ extern "C" int coarse_build(mg_handle* h, void* stream) {
   WMG_CUDA(cudaMallocAsync(&Xpart, (size_t)4 * h->B.d * ne * sizeof(zd), st));
   bool df = galerkin_df(h->p);
   int s = galerkin_build(h->Op64, Xpart, h->P64, h->Pdf, h->PtP, h->k, h->links64, h->Ldf, h->g,
-                         h->B, st, df);
+                         h->B, st, df, h->pdf_ready);
   cudaFreeAsync(Xpart, st);
   WMG_TRY(s);
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
@@ -607,7 +616,7 @@ extern "C" int coarse_build_noalloc(mg_handle* h, void* stream) {
   WMG_TRY(galerkin_scratch(&scratch));
   bool df = galerkin_df(h->p);
   WMG_TRY(galerkin_build(h->Op64, static_cast<zd*>(scratch), h->P64, h->Pdf, h->PtP, h->k,
-                         h->links64, h->Ldf, h->g, h->B, st, df));
+                         h->links64, h->Ldf, h->g, h->B, st, df, h->pdf_ready));
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
   WMG_CUDA(cudaStreamSynchronize(st));
   h->have_coarse = true;
@@ -758,6 +767,7 @@ extern "C" int mg_set_prolongator(mg_handle* h, const void* P, void* stream) {
   WMG_CUDA(cudaStreamSynchronize(st));
   h->have_P = true;
   h->have_coarse = false;
+  h->pdf_ready = false;
   return MG_OK;
 }
 
