@@ -127,6 +127,8 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, const zdf* __re
   T* sPt = gsm;                        // [GNB][6][n2k]
   T* sCh = gsm + GNB * 6 * n2k;        // [GNB][6][n2k]
   __shared__ int ssite[GNB], snb[GNB], sneg[GNB];
+  __shared__ size_t sox[GNB], soy[GNB];   // tile offsets (chirality 0, column 0) of x and y
+  __shared__ int slx[GNB], sly[GNB];      // local site of x and y in their aggregates
   int j = blockIdx.x, mu = blockIdx.y, dir = 2 * mu;
   double coef = -g.kappa * g.w[mu];
   int ne = n2k * n2k;
@@ -166,9 +168,17 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, const zdf* __re
         c[1] = r % g.L[1]; r /= g.L[1];
         c[2] = r % g.L[2]; c[3] = r / g.L[2];
         bool wrap = c[mu] == g.L[mu] - 1;
+        int y = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
         ssite[threadIdx.x] = x;
-        snb[threadIdx.x] = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
+        snb[threadIdx.x] = y;
         sneg[threadIdx.x] = (wrap && g.bc[mu] < 0) ? 1 : 0;
+        int jy, ly, jx, lx;
+        B.block_of(y, &jy, &ly);
+        B.block_of(x, &jx, &lx);
+        soy[threadIdx.x] = (size_t)(2 * jy) * k * B.M;
+        sox[threadIdx.x] = (size_t)(2 * jx) * k * B.M;
+        sly[threadIdx.x] = ly;
+        slx[threadIdx.x] = lx;
       }
       __syncthreads();
       // stage chi and Ptil
@@ -178,12 +188,11 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, const zdf* __re
         int bcol = e % n2k;
         int s = r / 3, cc = r % 3;
         int beta = bcol / k, ip = bcol % k;
-        int x = ssite[h], y = snb[h];
-        int jy, ly, jx, lx;
-        B.block_of(y, &jy, &ly);
-        B.block_of(x, &jx, &lx);
-        size_t oy = ((size_t)(2 * jy + beta) * k + ip) * B.M;
-        size_t ox = ((size_t)(2 * jx + beta) * k + ip) * B.M;
+        int x = ssite[h];
+        int ly = sly[h], lx = slx[h];
+        // column bcol = beta k + ip of the tile pair (chirality beta follows chirality 0)
+        size_t oy = soy[h] + (size_t)bcol * B.M;
+        size_t ox = sox[h] + (size_t)bcol * B.M;
         if constexpr (DF) {
           // half spinor of column bcol at y: chirality 0 keeps spin s of the upper pair;
           // chirality 1 gives i sigma_mu psi_dn (mu < 3) or -psi_dn (mu = 3)

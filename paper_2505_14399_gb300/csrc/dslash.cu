@@ -136,23 +136,6 @@ dslash_split_kernel(typename S::elem* __restrict__ out, const typename S::elem* 
   }
 }
 
-KGeom to_kgeom(const Geom& g) {
-  KGeom k;
-  for (int m = 0; m < 4; ++m) {
-    k.L[m] = g.L[m];
-    k.wf[m] = (float)g.w[m];
-    k.wd[m] = g.w[m];
-    k.bc[m] = g.bc[m];
-  }
-  k.stride[0] = 1;
-  k.stride[1] = g.L[0];
-  k.stride[2] = g.L[0] * g.L[1];
-  k.stride[3] = g.L[0] * g.L[1] * g.L[2];
-  k.V = g.V;
-  k.kappa = g.kappa;
-  return k;
-}
-
 // Launch shapes: threads per CTA and the minimum resident CTAs per SM requested from
 // the register allocator (register cap = 64K / (TPB * MINB)).  The autotuner below
 // picks one per (dtype, parity, dagger, volume, nrhs).

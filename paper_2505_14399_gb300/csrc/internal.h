@@ -134,6 +134,13 @@ using OpV = std::function<int(E* out, const E* in, cudaStream_t st)>;
 template <typename R>
 using Op = OpV<cplx<R>>;
 
+// The fine Wilson-Dirac operator in FP32 with lane-contiguous links ([mu][3x3 entry][site]),
+// for fixed-step GMRES runs that fuse it with their projection sweeps.
+struct FusedStencil {
+  const void* links;
+  Geom g;
+};
+
 template <typename E>
 class GmresV {
  public:
@@ -142,7 +149,10 @@ class GmresV {
   void release();
   // x = argmin ||b - A x|| over K_m(A, b), x0 = 0 (fixed number of steps, no host sync);
   // accumulate: x += that minimiser instead (x holds the caller's vector on entry)
-  int fixed(const OpV<E>& A, E* x, const E* b, int m, cudaStream_t st, bool accumulate = false);
+  // fused: A is this FP32 fine stencil, applied by one kernel together with each step's
+  // projection sweep (complex-float bases only; otherwise ignored)
+  int fixed(const OpV<E>& A, E* x, const E* b, int m, cudaStream_t st, bool accumulate = false,
+            const FusedStencil* fused = nullptr);
   // Restarted (F)GMRES from x0 = 0 until ||b - A x|| <= rtol ||b|| for every rhs.
   // M == nullptr: plain GMRES.  Returns MG_OK or MG_ENOCONV; *its = iterations.
   // check_every: host convergence check interval in Arnoldi steps; steps taken past
@@ -156,7 +166,7 @@ class GmresV {
 
  private:
   int arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st,
-                   bool single_pass = false);
+                   bool single_pass = false, const FusedStencil* fused = nullptr);
   double ip_scale() const { return VecT<E>::rms ? 1.0 / (double)n : 1.0; }
   E* V = nullptr;         // (m+1) x nrhs x n
   E* Z = nullptr;         // m x nrhs x n

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "reduce.cuh"
+#include "stencil.cuh"
 #include "tma.cuh"
 #include "vec.cuh"
 
@@ -466,6 +467,107 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
   }
 }
 
+// One fixed-step GMRES step's operator and projections in one kernel (single-pass classical
+// Gram-Schmidt, complex-float basis):  w = D v_j  (the FP32 Wilson-Dirac stencil, Eq. 1,
+// lane-contiguous links), h_i = V_i^dag w for i < nv = j + 1, ||w||^2, and in the last CTA
+// H[j+1, j]^2 = ||w||^2 - ||h||^2 as in stream_cgs_kernel<2>.  The basis reads at each
+// thread's own site do not depend on the stencil, so they overlap its latency-bound hops,
+// and w is not read back.  One thread per site and rhs row (blockIdx.y), a grid-stride
+// over 256-site blocks.
+template <int NVM>
+__global__ void __launch_bounds__(RT)
+dslash_proj_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_t n,
+                   const float2* __restrict__ links, stencil::KGeom g, zd* small, SmallLayout L,
+                   double* wnorm, double* partial, unsigned* counter, int maxvec) {
+  using namespace stencil;
+  dep_entry();
+  __shared__ float sh[(RT / 32) * NVM * 2];
+  const int rhs = blockIdx.y;
+  const int nsites = g.V;
+  const float2* vb = reinterpret_cast<const float2*>(V) + (size_t)rhs * n;
+  const float2* vin = vb + (size_t)(nv - 1) * vstride;   // v_j
+  float2* wr = reinterpret_cast<float2*>(w) + (size_t)rhs * n;
+  float ar[NVM], ai[NVM];
+#pragma unroll
+  for (int q = 0; q < NVM; ++q) { ar[q] = 0.f; ai[q] = 0.f; }
+  float ss = 0.f;
+  for (int site = blockIdx.x * RT + threadIdx.x; site < nsites; site += gridDim.x * RT) {
+    int c[4];
+    stencil_site(g, -1, site, c);
+    zf acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
+    hop_pair<0, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
+    hop_pair<1, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
+    hop_pair<2, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
+    hop_pair<3, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
+    zf p[12];
+    SiteIO<StC64>::load(vin, (size_t)site, p);
+    const float mk = (float)(-g.kappa);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      p[k].re = fmaf(mk, acc[k].re, p[k].re);
+      p[k].im = fmaf(mk, acc[k].im, p[k].im);
+      ss = fmaf(p[k].re, p[k].re, ss);
+      ss = fmaf(p[k].im, p[k].im, ss);
+    }
+    SiteIO<StC64>::store(wr, (size_t)site, p);
+#pragma unroll
+    for (int q = 0; q < NVM; ++q) {
+      if (q < nv) {
+        zf v[12];
+        SiteIO<StC64>::load(vb + (size_t)q * vstride, (size_t)site, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          ar[q] = fmaf(v[k].re, p[k].re, ar[q]);
+          ar[q] = fmaf(v[k].im, p[k].im, ar[q]);
+          ai[q] = fmaf(v[k].re, p[k].im, ai[q]);
+          ai[q] = fmaf(-v[k].im, p[k].re, ai[q]);
+        }
+      }
+    }
+  }
+  const int nblk = gridDim.x;
+  cta_store_partials<float, NVM>(ar, ai, nv, 0, rhs, maxvec, nblk, partials_as<float>(partial),
+                                 sh);
+  float zero = 0.f;
+  cta_store_partials<float, 1>(&ss, &zero, 1, nv, rhs, maxvec, nblk, partials_as<float>(partial),
+                               sh);
+  if (!last_cta(counter, rhs, nblk)) return;
+  // projections and H[j+1, j]; the Givens step follows in the normalising update
+  __shared__ zd g_h2[NVM + 1];
+  finish_partials(partials_as<float>(partial), nv + 1, nblk, maxvec, rhs, g_h2, nullptr, 0, 0);
+  __syncthreads();
+  zd* sm = small + (size_t)rhs * L.stride();
+  for (int i = threadIdx.x; i <= nv; i += RT) sm[L.h2() + i] = g_h2[i];
+  if (threadIdx.x == 0) {
+    counter[rhs] = 0;
+    double hh = 0;
+    for (int i = 0; i < nv; ++i) hh += norm2(g_h2[i]);
+    double b2 = g_h2[nv].re - hh;
+    wnorm[rhs] = b2 > 0 ? sqrt(b2) : 0.0;
+  }
+}
+
+int dslash_proj_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* small,
+                       SmallLayout L, int j, double* dnorm, ReduceWork& rw,
+                       const FusedStencil& fz, cudaStream_t st) {
+  stencil::KGeom kg = stencil::to_kgeom(fz.g);
+  int nv = j + 1;
+  int nb = (kg.V + RT - 1) / RT;
+  if (nb > rw.nblk) nb = rw.nblk;
+  const float2* L32 = static_cast<const float2*>(fz.links);
+  double byts = (double)nrhs * kg.V * 8.0 * (12.0 * (nv + 2) + 36.0);
+  ProfScope ps("dslash_proj", byts, (1320.0 + 48.0 * (nv + 1)) * kg.V * nrhs, st);
+  if (nv <= 4)
+    WMG_LAUNCH_DEP(dslash_proj_kernel<4>, dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec);
+  else if (nv <= 8)
+    WMG_LAUNCH_DEP(dslash_proj_kernel<8>, dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec);
+  else
+    WMG_LAUNCH_DEP(dslash_proj_kernel<16>, dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec);
+  return MG_OK;
+}
+
 template <int NVM>
 int stream_cgs_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* small,
                       SmallLayout L, int j, double* dnorm, double* reshist, ReduceWork& rw,
@@ -592,11 +694,18 @@ void GmresV<E>::release() {
 // dnorm layout: [0..nrhs) current ||w||, [nrhs..2nrhs) beta, [2nrhs..3nrhs) residual estimate
 template <typename E>
 int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st,
-                            bool single_pass) {
+                            bool single_pass, const FusedStencil* fused) {
   SmallLayout L{m};
   size_t fs = n * nrhs;
   E* vj = V + (size_t)j * fs;
-  if (M) {
+  bool fuse = false;
+  if constexpr (std::is_same<E, zf>::value)
+    fuse = fused && single_pass && !M && j + 1 <= ST_NV && n == (size_t)fused->g.V * 12;
+  if (fuse) {
+    // the stencil and the single-pass projections in one kernel
+    if constexpr (std::is_same<E, zf>::value)
+      WMG_TRY(dslash_proj_launch(w, V, fs, n, nrhs, small, L, j, dnorm, rw, *fused, st));
+  } else if (M) {
     E* zj = Z + (size_t)j * fs;
     WMG_TRY((*M)(zj, vj, st));
     WMG_TRY(A(w, zj, st));
@@ -607,9 +716,9 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
   // CGS2 in three sweeps: projections; update + re-projections + norm + Givens;
   // update + normalisation into column j + 1
   double fb = (double)nrhs * n * sizeof(E);
-  bool streamed = false;
+  bool streamed = fuse;
   if constexpr (std::is_same<E, zf>::value) {
-    if (j + 1 <= ST_NV && (n & 1) == 0) {
+    if (!fuse && j + 1 <= ST_NV && (n & 1) == 0) {
       WMG_TRY(stream_cgs(w, V, fs, n, nrhs, small, L, j, dnorm, reshist, rw, ip_scale(),
                          single_pass, st));
       streamed = true;
@@ -635,7 +744,7 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
 
 template <typename E>
 int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t st,
-                     bool accumulate) {
+                     bool accumulate, const FusedStencil* fused) {
   if (steps > m) return fail(MG_EINVAL, "gmres: more steps than allocated");
   SmallLayout L{m};
   size_t fs = n * nrhs;
@@ -649,7 +758,7 @@ int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t 
   // Pythagoras.  Over these few steps the basis stays orthogonal to ~eps_32 times the
   // conditioning of the small Krylov basis, which leaves the smoother's approximate
   // minimisation unchanged to FP32 rounding; the tolerance-driven solves keep CGS2.
-  for (int j = 0; j < steps; ++j) WMG_TRY(arnoldi_step(A, nullptr, j, st, true));
+  for (int j = 0; j < steps; ++j) WMG_TRY(arnoldi_step(A, nullptr, j, st, true, fused));
   WMG_LAUNCH_DEP(solve_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, steps, nrhs);
   WMG_TRY(multi_axpy_v<E>(x, V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
   return MG_OK;

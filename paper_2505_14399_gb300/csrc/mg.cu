@@ -161,7 +161,8 @@ int smooth_stream(mg_handle* h, cplx<R>* psi, cplx<R>* phi, cplx<R>* tmp, Gmres<
   WMG_TRY(D(tmp, phi, st));
   WMG_TRY(axpby<R>(tmp, 0.0, tmp, -1.0, h->nf * r, 1, st));   // tmp = -D phi
   WMG_TRY(gm.alloc(h->nf, r, p.sweeps > 0 ? p.sweeps : 1, false));
-  WMG_TRY(gm.fixed(D, psi, tmp, p.sweeps, st));
+  FusedStencil fz{h->links32L, h->g};   // FP32 runs fuse the stencil with the projections
+  WMG_TRY(gm.fixed(D, psi, tmp, p.sweeps, st, false, sizeof(R) == 4 ? &fz : nullptr));
   WMG_TRY(axpby<R>(psi, 1.0, phi, 1.0, h->nf * r, 1, st));     // psi = phi + psi'
   return MG_OK;
 }
@@ -399,7 +400,9 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
         if (p.solve_dtype == MG_BF16) return post_smooth_half<zbf>(h, h->postb, z, v, kw, nrhs, st);
       }
       WMG_TRY(axpby<R>(kw, 1.0, v, -1.0, h->nf * nrhs, 1, st));   // kw = v - D z
-      WMG_TRY(Lvl<R>::post(h).fixed(D, ke, kw, p.post_smooth, st));
+      FusedStencil fz{h->links32L, h->g};   // FP32 runs fuse the stencil with the projections
+      WMG_TRY(Lvl<R>::post(h).fixed(D, ke, kw, p.post_smooth, st, false,
+                                    sizeof(R) == 4 ? &fz : nullptr));
       WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, h->nf * nrhs, 1, st));    // z += e
     }
     return MG_OK;

@@ -75,7 +75,8 @@ __device__ __forceinline__ void finish_partials(const P* partial, int nv, int nb
 template <typename P>
 __device__ __forceinline__ P* partials_as(double* partial) { return reinterpret_cast<P*>(partial); }
 
-// CTA reduction of ni complex values held per thread (R precision) into the partial slots
+// CTA reduction (blockDim.x <= RT threads) of ni complex values held per thread (R precision)
+// into the partial slots
 // partial[((rhs*maxvec + i0 + q) * nblk + blockIdx.x) * 2 + {0,1}] (type R), q < ni <= G.
 template <typename R, int G>
 __device__ __forceinline__ void cta_store_partials(const R* ar, const R* ai, int ni, int i0,
@@ -94,7 +95,7 @@ __device__ __forceinline__ void cta_store_partials(const R* ar, const R* ai, int
   if ((int)threadIdx.x < 2 * ni) {
     int q = threadIdx.x >> 1, part = threadIdx.x & 1;
     R s = 0;
-    for (int wv = 0; wv < RT / 32; ++wv) s += shg[(wv * G + q) * 2 + part];
+    for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += shg[(wv * G + q) * 2 + part];
     partial[(((size_t)rhs * maxvec + i0 + q) * nblk + blockIdx.x) * 2 + part] = s;
     __threadfence();   // the writer publishes its partial before the CTA signals completion
   }

@@ -241,6 +241,23 @@ __device__ __forceinline__ int stencil_site(const KGeom& g, int parity, int i, i
   return site;
 }
 
+inline KGeom to_kgeom(const Geom& g) {
+  KGeom k;
+  for (int m = 0; m < 4; ++m) {
+    k.L[m] = g.L[m];
+    k.wf[m] = (float)g.w[m];
+    k.wd[m] = g.w[m];
+    k.bc[m] = g.bc[m];
+  }
+  k.stride[0] = 1;
+  k.stride[1] = g.L[0];
+  k.stride[2] = g.L[0] * g.L[1];
+  k.stride[3] = g.L[0] * g.L[1] * g.L[2];
+  k.V = g.V;
+  k.kappa = g.kappa;
+  return k;
+}
+
 // Stencil with 2 or 4 right-hand sides per thread (nr), defined in dslash_mrhs.cu for the four
 // storage types; layout 0: ABI links, 1: lane-contiguous links.
 template <typename S>
