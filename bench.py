@@ -128,6 +128,9 @@ def kernel_bound(name, alu, peaks, peak_kind):
         # double-float: one real multiply-add (2 FP64-equivalent flops) costs 12 FP32
         # instructions (1 mul, 3 fma, 8 add/sub), so the peak is the FP32 FMA rate / 12
         return "alu", alu["fp32"] / 12.0, "TFLOP/s", "measured FP32 FMA rate / 12"
+    if name.endswith("_tc"):
+        # exact bf16 digit-plane products on the tensor pipe, against the measured bf16 rate
+        return "tensor", peaks["bf16_tflops"], "TFLOP/s", peak_kind + " bf16 tensor"
     if name.endswith("_fp64") or name.startswith("galerkin"):
         return "alu", alu["fp64"], "TFLOP/s", "measured FP64 FMA rate"
     return "hbm", peaks["hbm_gbs"], "GB/s", peak_kind

@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "df64.cuh"
+#include "galerkin.cuh"
 #include "internal.h"
 
 namespace wmg {
@@ -79,12 +80,6 @@ __global__ void prolong_kernel(cplx<R>* v, const cplx<R>* __restrict__ vc,
   }
 }
 
-struct HopGeom {
-  int L[4], stride[4];
-  double w[4];
-  int bc[4];
-  double kappa;
-};
 
 // (i sigma_mu psi)[s] for a 2-spinor given by its two components: returns component s.
 __device__ __forceinline__ zd isigma(int mu, int s, zd p0, zd p1) {
@@ -93,16 +88,9 @@ __device__ __forceinline__ zd isigma(int mu, int s, zd p0, zd p1) {
   return s == 0 ? ti(p0) : tmi(p1);
 }
 
-constexpr int GNB = 8;       // fine sites staged per batch
 constexpr int GTH = 256;     // threads
 constexpr int GMAXE = 16;    // accumulator entries per thread ((2k)^2 <= 4096)
 
-// (i sigma_mu psi)[s] in df64 (sign changes and swaps only: exact)
-__device__ __forceinline__ zdf isigma_df(int mu, int s, zdf p0, zdf p1) {
-  if (mu == 0) return s == 0 ? zdf_ti(p1) : zdf_ti(p0);
-  if (mu == 1) return s == 0 ? p1 : zdf_neg(p0);
-  return s == 0 ? zdf_ti(p0) : zdf_tmi(p1);
-}
 
 // Forward hops x -> y = x + mu of D = 1 - kappa sum_mu w_mu [(1 - gamma_mu) U_mu(x) delta_{x+mu}
 // + ...]: the spin projector (1 - gamma_mu) reduces the 2k columns of P at y to a half
@@ -396,6 +384,9 @@ int to_df(zdf* out, const zd* in, size_t n, cudaStream_t st) {
   return MG_OK;
 }
 
+// raised by the tensor-pipe Galerkin kernel when a staged entry leaves its fixed-point range
+__device__ int g_galerkin_tc_range;
+
 namespace {
 template <bool DF, int NE>
 int launch_hop(dim3 grid, size_t sh, cudaStream_t st, zd* Op, zd* Xpart, const zd* P,
@@ -450,9 +441,28 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, con
   } else {
     WMG_TRY(tile_gram(PtP, P, k, k, B, st, false));
   }
-  ProfScope ps(df64 ? "galerkin_df64" : "galerkin_fp64", 16.0 * (12.0 * B.nd * B.d * k * 5 + 36.0 * B.nd * B.d),
-               768.0 * k * k * B.nd * B.d, st);
-  if (df64) {
+  const bool tc = df64 && galerkin_tc_supported(k);
+  // tensor path: the bf16 digit-plane products it issues (28 digit pairs of a (2 (2k)) x (2k)
+  // x 96 real product per 8-site batch, padded tiles, about n_d / 8 + 1 batches per CTA);
+  // otherwise FP64-equivalent flops
+  const double t4 = (k + 3) / 4;
+  const double tc_flops = 2.0 * (16 * t4) * (8 * t4) * 96.0 * 28.0 * 4.0 * B.d *
+                          ((double)B.nd / 8.0 + 1.0);
+  ProfScope ps(tc ? "galerkin_tc" : df64 ? "galerkin_df64" : "galerkin_fp64",
+               16.0 * (12.0 * B.nd * B.d * k * 5 + 36.0 * B.nd * B.d),
+               tc ? tc_flops : 768.0 * k * k * B.nd * B.d, st);
+  if (tc) {
+    // tensor pipe (exact digit-plane products); entries outside its fixed-point range (links
+    // that are not unitary, a prolongator that is not orthonormal) fall back to the FP32 units
+    int* flag = nullptr;
+    WMG_CUDA(cudaGetSymbolAddress((void**)&flag, g_galerkin_tc_range));
+    WMG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    WMG_TRY(galerkin_hops_tc(Op, Xpart, Pdf, k, Ldf, hg, B, flag, st));
+    int h_flag = 0;
+    WMG_CUDA(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    WMG_CUDA(cudaStreamSynchronize(st));
+    if (h_flag) WMG_TRY(launch_hop_ne<true>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B));
+  } else if (df64) {
     WMG_TRY(launch_hop_ne<true>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B));
   } else {
     WMG_TRY(launch_hop_ne<false>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B));

@@ -1,0 +1,349 @@
+// Forward-hop blocks of the Galerkin coarse operator (Eq. 5) on the tensor pipe, at
+// double-float accuracy.
+//
+// CTA (j, mu) accumulates, over the fine sites x of aggregate j, C[a][b] =
+// sum_{x,r} conj(Pt[x][r][a]) Ch[x][r][b] (the staged reconstruction-folded P(x) and the
+// spin-projected, colour-transported P(x + mu), as in the FP32-unit kernel of coarse.cu).
+// Every staged double-float entry v satisfies |v| < 2 (|P| <= 1 entrywise for orthonormal
+// columns; |U h| <= sqrt(3) for unitary U and |h| <= 1), so it is written exactly enough as
+// fixed-point digits in base 256,
+//     v = sum_{i < NS} s_i 2^{-6-8i},  s_i integers, |s_i| <= 129,  NS = 7 (error < 2^-55),
+// each digit exact in bfloat16.  A product of digit planes is an integer matrix product:
+// bf16 x bf16 tensor-core MMAs with FP32 accumulation are exact while the partial sums stay
+// below 2^24, which holds for one staging batch (<= 7 digit pairs x 96 stacked rows x 129^2).
+// Digit pairs i + j = d of the same weight 2^{-12-8d} share an FP32 accumulator; pairs with
+// i + j >= NS (weight below 2^-68) are dropped.  After every batch the exact FP32 sums are
+// scaled by their weights (exact) and added to double-float accumulators with error-free
+// two-sums, so the result carries double-float accuracy (~2^-48 relative), not bf16's.
+//
+// The complex product is one real GEMM per digit pair: with K = 48 rows (8 sites x 6 half-
+// spinor rows) per batch, stacked as k' = [re rows | im rows] (96),
+//     A'[b'][k'] : rows b < 2k = (Ch_re | Ch_im), rows 2k + b = (Ch_im | -Ch_re),
+//     B'[a][k']  : (Pt_re | Pt_im),
+// C'[b'][a] = sum_k' A'[b'][k'] B'[a][k'] gives Re C[a][b] (b' = b) and Im C[a][b] (b' = 2k+b).
+// mma.sync m16n8k16 (row.col) tiles: 16 rows b' x 8 columns a, one warp per tile.  The digit
+// planes are stored k'-major (SA[k'][b'], SB[k'][a]) so that staging threads with consecutive
+// columns write consecutive addresses, and read with ldmatrix .trans; every row stride is an
+// odd number of 16-byte units, so the eight rows of an ldmatrix phase hit distinct banks.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "df64.cuh"
+#include "galerkin.cuh"
+#include "internal.h"
+#include "tma.cuh"
+
+namespace wmg {
+
+namespace {
+
+constexpr int TC_NS = 7;               // digits per value
+constexpr int TC_KB = GNB * 6;         // staged rows per batch (48)
+constexpr int TC_K = 2 * TC_KB;        // stacked real rows (96)
+constexpr int TC_MAXW = 12;            // warps per CTA at most
+constexpr int TC_MAXT4 = 6;            // 2k <= 48
+
+__device__ __forceinline__ void ldm_x4t(unsigned r[4], const __nv_bfloat16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldm_x2t(unsigned r[2], const __nv_bfloat16* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(smem_addr(p)));
+}
+
+// Row strides (bf16) of the k'-major digit planes: odd multiples of 8 (16 bytes).
+__host__ __device__ constexpr int tc_lda(int t4) { return 16 * t4 + 8; }
+__host__ __device__ constexpr int tc_ldb(int t4) { return 8 * t4 + ((t4 & 1) ? 0 : 8); }
+__host__ __device__ constexpr size_t tc_smem(int t4) {
+  return sizeof(__nv_bfloat16) * (size_t)TC_NS * TC_K * (tc_lda(t4) + tc_ldb(t4));
+}
+// c += a b, 16x16 (row) x 16x8 (col) bf16, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// The base-256 digits of v (|v| < 2): v = sum_i s[i] 2^{-6-8i}, rounded to nearest at every
+// digit, so |s[i]| <= 128 (+1 when a remainder rounds up).  Exact remainders in double-float.
+__device__ __forceinline__ void tc_digits(df v, float s[TC_NS]) {
+  df x = {v.hi * 64.0f, v.lo * 64.0f};
+#pragma unroll
+  for (int i = 0; i < TC_NS; ++i) {
+    float d = rintf(x.hi);
+    s[i] = d;
+    df r = df_add(x, {-d, 0.0f});
+    x = {r.hi * 256.0f, r.lo * 256.0f};
+  }
+}
+
+// s + e += v with an error-free two-sum (v exact)
+__device__ __forceinline__ void acc_add(dfacc& a, float v) {
+  float s = __fadd_rn(a.s, v);
+  float bb = __fsub_rn(s, a.s);
+  float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+  a.s = s;
+  a.e = __fadd_rn(a.e, err);
+}
+
+__device__ __forceinline__ bool tc_in_range(df v) { return fabsf(v.hi) < 2.0f; }   // false for NaN
+
+__host__ __device__ constexpr int tc_warps(int t4) { return t4 * t4 < TC_MAXW ? t4 * t4 : TC_MAXW; }
+
+template <int T4>
+__global__ void __launch_bounds__(32 * tc_warps(T4), T4 <= 4 ? 2 : 1)
+galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
+                   const zdf* __restrict__ Ldf, HopGeom g, Blocking B, int* range_flag) {
+  constexpr int MR = 16 * T4;                 // rows b' (>= 4k)
+  constexpr int NR = 8 * T4;                  // columns a (>= 2k)
+  constexpr int NTILES = T4 * T4;
+  constexpr int NW = NTILES < TC_MAXW ? NTILES : TC_MAXW;
+  constexpr int TPW = (NTILES + NW - 1) / NW;   // tiles per warp
+  constexpr int ND = TC_NS;                   // digit-pair weights d = i + j < NS
+  constexpr int LDA = tc_lda(T4), LDB = tc_ldb(T4);
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(tc_raw);   // [NS][TC_K][LDA]
+  __nv_bfloat16* SB = SA + (size_t)TC_NS * TC_K * LDA;             // [NS][TC_K][LDB]
+  __shared__ int ssite[GNB], sneg[GNB], slx[GNB], sly[GNB];
+  __shared__ size_t sox[GNB], soy[GNB];
+  const int n2k = 2 * k;
+  const int j = blockIdx.x, mu = blockIdx.y, dir = 2 * mu;
+  const double coef = -g.kappa * g.w[mu];
+  const int ne = n2k * n2k;
+  const int bmu = B.b[mu];
+  const int* bb = B.b;
+  const size_t V = (size_t)B.nd * B.d;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const size_t plane16 = tc_smem(T4) / 16;   // 16-byte chunks of SA + SB
+  bool bad = false;
+
+  for (int pass = 0; pass < 2; ++pass) {  // 0: hops inside the aggregate, 1: crossing hops
+    // zero both digit planes: padding rows and columns stay zero for the whole pass
+    for (size_t e = threadIdx.x; e < plane16; e += blockDim.x)
+      reinterpret_cast<uint4*>(tc_raw)[e] = make_uint4(0u, 0u, 0u, 0u);
+    dfacc dacc[TPW][4];
+#pragma unroll
+    for (int t = 0; t < TPW; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) dacc[t][e] = {0.0f, 0.0f};
+    int l = 0;
+    while (true) {
+      // the next batch of local sites of this pass (same scan in every thread)
+      int nb = 0;
+      int lsel[GNB];
+      while (l < B.nd && nb < GNB) {
+        int q = l;
+        int lc[4];
+        lc[0] = q % bb[0]; q /= bb[0];
+        lc[1] = q % bb[1]; q /= bb[1];
+        lc[2] = q % bb[2]; lc[3] = q / bb[2];
+        bool cross = lc[mu] == bmu - 1;
+        if ((pass == 1) == cross) lsel[nb++] = l;
+        ++l;
+      }
+      if (nb == 0) break;
+      __syncthreads();   // the previous batch's digit planes have been read
+      if (threadIdx.x < nb) {
+        int x = B.site(j, lsel[threadIdx.x]);
+        int c[4];
+        c[0] = x % g.L[0];
+        int r = x / g.L[0];
+        c[1] = r % g.L[1]; r /= g.L[1];
+        c[2] = r % g.L[2]; c[3] = r / g.L[2];
+        bool wrap = c[mu] == g.L[mu] - 1;
+        int y = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
+        ssite[threadIdx.x] = x;
+        sneg[threadIdx.x] = (wrap && g.bc[mu] < 0) ? 1 : 0;
+        int jy, ly, jx, lx;
+        B.block_of(y, &jy, &ly);
+        B.block_of(x, &jx, &lx);
+        soy[threadIdx.x] = (size_t)(2 * jy) * k * B.M;
+        sox[threadIdx.x] = (size_t)(2 * jx) * k * B.M;
+        sly[threadIdx.x] = ly;
+        slx[threadIdx.x] = lx;
+      }
+      if (nb < GNB) {
+        // a short batch: its unused stacked rows k' are zero in every digit plane
+        const int k0 = nb * 6, kn = TC_KB - k0;
+        for (int e = threadIdx.x; e < TC_NS * 2 * kn * (LDA + LDB); e += blockDim.x) {
+          int col = e % (LDA + LDB), rr = e / (LDA + LDB);
+          int i = rr / (2 * kn), q = rr % (2 * kn);
+          int kk = (q < kn) ? k0 + q : TC_KB + k0 + (q - kn);
+          if (col < LDA) SA[((size_t)i * TC_K + kk) * LDA + col] = __float2bfloat16_rn(0.0f);
+          else SB[((size_t)i * TC_K + kk) * LDB + (col - LDA)] = __float2bfloat16_rn(0.0f);
+        }
+      }
+      __syncthreads();
+      // stage: Ch (spin-projected, transported P(y)) and Pt (reconstruction-folded P(x)) in
+      // double-float, written as digit planes
+      for (int e = threadIdx.x; e < nb * 6 * n2k; e += blockDim.x) {
+        int h = e / (6 * n2k);
+        int r = (e / n2k) % 6;
+        int bcol = e % n2k;
+        int s = r / 3, cc = r % 3;
+        int beta = bcol / k;
+        int x = ssite[h];
+        int ly = sly[h], lx = slx[h];
+        size_t oy = soy[h] + (size_t)bcol * B.M;
+        size_t ox = sox[h] + (size_t)bcol * B.M;
+        zdf hv[3];
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2) {
+          if (beta == 0) {
+            hv[c2] = zdf_ld(Pdf + oy + (ly * 2 + s) * 3 + c2);
+          } else {
+            zdf p0 = zdf_ld(Pdf + oy + (ly * 2 + 0) * 3 + c2);
+            zdf p1 = zdf_ld(Pdf + oy + (ly * 2 + 1) * 3 + c2);
+            hv[c2] = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
+          }
+        }
+        const zdf* U = Ldf + ((size_t)mu * V + x) * 9 + cc * 3;
+        zdfacc t{};
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2) zdf_fma(t, zdf_ld(U + c2), hv[c2]);
+        zdf ch = zdf_norm(t);
+        if (sneg[h]) ch = zdf_neg(ch);
+        zdf pt;
+        if (beta == 0) {
+          pt = zdf_ld(Pdf + ox + (lx * 2 + s) * 3 + cc);
+        } else {
+          zdf p0 = zdf_ld(Pdf + ox + (lx * 2 + 0) * 3 + cc);
+          zdf p1 = zdf_ld(Pdf + ox + (lx * 2 + 1) * 3 + cc);
+          pt = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
+        }
+        bad |= !(tc_in_range(ch.re) && tc_in_range(ch.im) && tc_in_range(pt.re) &&
+                 tc_in_range(pt.im));
+        const int kk = h * 6 + r;
+        float dr[TC_NS], di[TC_NS];
+        tc_digits(ch.re, dr);
+        tc_digits(ch.im, di);
+#pragma unroll
+        for (int i = 0; i < TC_NS; ++i) {
+          __nv_bfloat16* a0 = SA + ((size_t)i * TC_K + kk) * LDA;            // re rows k
+          __nv_bfloat16* a1 = SA + ((size_t)i * TC_K + TC_KB + kk) * LDA;    // im rows k
+          a0[bcol] = __float2bfloat16_rn(dr[i]);
+          a1[bcol] = __float2bfloat16_rn(di[i]);
+          a0[n2k + bcol] = __float2bfloat16_rn(di[i]);
+          a1[n2k + bcol] = __float2bfloat16_rn(-dr[i]);
+        }
+        tc_digits(pt.re, dr);
+        tc_digits(pt.im, di);
+#pragma unroll
+        for (int i = 0; i < TC_NS; ++i) {
+          SB[((size_t)i * TC_K + kk) * LDB + bcol] = __float2bfloat16_rn(dr[i]);
+          SB[((size_t)i * TC_K + TC_KB + kk) * LDB + bcol] = __float2bfloat16_rn(di[i]);
+        }
+      }
+      __syncthreads();
+      // exact digit-plane products of this warp's output tiles, folded into double-float
+#pragma unroll
+      for (int tt = 0; tt < TPW; ++tt) {
+        const int tile = wid + tt * NW;
+        if (tile < NTILES) {
+          const int mt = tile / T4, nt = tile % T4;
+          float acc[ND][4];
+#pragma unroll
+          for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[d][e] = 0.0f;
+          // ldmatrix .trans row addresses: A matrices (b' 0-7 | 8-15) x (k 0-7 | 8-15) in the
+          // order of the A fragment, B matrices k 0-7 | 8-15 for columns a of this tile
+          const int mq = lane >> 3, rr = lane & 7;
+          const __nv_bfloat16* arow = SA + (size_t)(8 * (mq >> 1) + rr) * LDA + 16 * mt + 8 * (mq & 1);
+          const __nv_bfloat16* brow = SB + (size_t)(8 * (mq & 1) + rr) * LDB + 8 * nt;
+#pragma unroll 1
+          for (int ks = 0; ks < TC_K / 16; ++ks) {
+            // B digit fragments for this k-step; A one digit at a time (registers: two CTAs
+            // per SM)
+            unsigned bfr[TC_NS][2];
+#pragma unroll
+            for (int i = 0; i < TC_NS; ++i)
+              ldm_x2t(bfr[i], brow + ((size_t)i * TC_K + 16 * ks) * LDB);
+#pragma unroll
+            for (int i = 0; i < TC_NS; ++i) {
+              unsigned af[4];
+              ldm_x4t(af, arow + ((size_t)i * TC_K + 16 * ks) * LDA);
+#pragma unroll
+              for (int jd = 0; jd < TC_NS; ++jd)
+                if (i + jd < ND) mma_bf16(acc[i + jd], af, bfr[jd]);
+            }
+          }
+          // weights 2^{-12-8d}: exact FP32 constants
+          float wgt = 1.0f / 4096.0f;
+#pragma unroll
+          for (int d = 0; d < ND; ++d) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc_add(dacc[tt][e], acc[d][e] * wgt);
+            wgt *= 1.0f / 256.0f;
+          }
+        }
+      }
+    }
+    // this pass's blocks: tiles -> shared memory (over the digit planes) -> Op / Xpart
+    __syncthreads();
+    df* sOut = reinterpret_cast<df*>(tc_raw);   // [MR][NR]
+#pragma unroll
+    for (int tt = 0; tt < TPW; ++tt) {
+      const int tile = wid + tt * NW;
+      if (tile < NTILES) {
+        const int mt = tile / T4, nt = tile % T4;
+        const int row = 16 * mt + (lane >> 2), col = 8 * nt + 2 * (lane & 3);
+        sOut[(size_t)row * NR + col] = df_norm(dacc[tt][0]);
+        sOut[(size_t)row * NR + col + 1] = df_norm(dacc[tt][1]);
+        sOut[(size_t)(row + 8) * NR + col] = df_norm(dacc[tt][2]);
+        sOut[(size_t)(row + 8) * NR + col + 1] = df_norm(dacc[tt][3]);
+      }
+    }
+    __syncthreads();
+    zd* out = pass == 1 ? Op + ((size_t)j * 9 + 1 + dir) * ne
+                        : Xpart + ((size_t)mu * B.d + j) * ne;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      int b = e / n2k, a = e % n2k;
+      df re = sOut[(size_t)b * NR + a], im = sOut[(size_t)(n2k + b) * NR + a];
+      out[(size_t)b * n2k + a] = {coef * df_val(re), coef * df_val(im)};   // column-major
+    }
+    __syncthreads();
+  }
+  if (bad) atomicExch(range_flag, 1);
+}
+
+template <int T4>
+int launch_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
+              const Blocking& B, int* range_flag, cudaStream_t st) {
+  constexpr int NW = tc_warps(T4);
+  size_t sh = tc_smem(T4);
+  static bool set = false;
+  if (!set) {
+    WMG_CUDA(cudaFuncSetAttribute(galerkin_tc_kernel<T4>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    set = true;
+  }
+  galerkin_tc_kernel<T4><<<dim3(B.d, 4), 32 * NW, sh, st>>>(Op, Xpart, Pdf, k, Ldf, g, B,
+                                                            range_flag);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+}  // namespace
+
+bool galerkin_tc_supported(int k) { return k >= 1 && (k + 3) / 4 <= TC_MAXT4; }
+
+int galerkin_hops_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
+                     const Blocking& B, int* range_flag, cudaStream_t st) {
+  switch ((k + 3) / 4) {
+    case 1: return launch_tc<1>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 2: return launch_tc<2>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 3: return launch_tc<3>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 4: return launch_tc<4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 5: return launch_tc<5>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 6: return launch_tc<6>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    default: return fail(MG_EINVAL, "galerkin (tensor pipe): 2k > 48");
+  }
+}
+
+}  // namespace wmg

@@ -37,6 +37,18 @@ def random_tiles(d, nd, k, seed):
     return rng.standard_normal((d, 2, k, 6 * nd)) + 1j * rng.standard_normal((d, 2, k, 6 * nd))
 
 
+def orthonormal_tiles(d, nd, k, seed):
+    """Seeded tiles (d, 2, k, 6 n_d) whose k rows are orthonormal (QR of complex Gaussians), so
+    every entry has modulus at most 1, as for the iCSVD prolongator -- an input, not an SVD."""
+    g = random_tiles(d, nd, k, seed)
+    out = np.empty_like(g)
+    for j in range(d):
+        for a in range(2):
+            q, _ = np.linalg.qr(g[j, a].T)
+            out[j, a] = q.T
+    return out
+
+
 def params_for(cfg, **kw):
     args = dict(dims=cfg["dims"], block=cfg["block"], kappa=cfg["kappa"], k=cfg["k"], r=cfg["r"],
                 n_s=cfg["n_s"], sweeps=cfg["sweeps"], seed=cfg["tv_seed"],

@@ -5,7 +5,7 @@ import torch
 
 from oracle import coarse, icsvd
 from paper_2505_14399_gb300 import api, synthetic
-from gpu_common import rel, random_tiles, to_dev
+from gpu_common import orthonormal_tiles, rel, random_tiles, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -16,14 +16,14 @@ CASES = [((4, 4, 4, 4), (2, 2, 2, 2), 4),
 
 
 def _handle(dims, block, k, seed, kappa=0.125, w=(1, 1, 1, 1 / 3.5), bc=(1, 1, 1, -1),
-            fp64_emulation=0):
+            fp64_emulation=0, tiles=random_tiles):
     U = synthetic.smooth_links(dims, seed)
     p = api.params(dims, block, kappa, k, k, 1, hop_weight=w, bc=bc, setup_dtype="c128",
                    solve_dtype="c128", fp64_emulation=fp64_emulation)
     h = api.Hierarchy(to_dev(U), p, setup=False)
     nd = int(np.prod(block))
     d = int(np.prod(dims)) // nd
-    P = random_tiles(d, nd, k, seed + 1)           # layout [j][alpha][i][row]
+    P = tiles(d, nd, k, seed + 1)                  # layout [j][alpha][i][row]
     h.set_prolongator(to_dev(P))
     Pt = np.ascontiguousarray(np.swapaxes(P, 2, 3))  # oracle layout [j][alpha][row][i]
     return h, U, Pt, (kappa, w, bc)
@@ -46,8 +46,25 @@ def test_restrict_prolong(dims, block, k):
 
 
 @pytest.mark.parametrize("dims,block,k", CASES)
+def test_galerkin_tensor_pipe_contraction(dims, block, k):
+    """Double-float Galerkin with an orthonormal prolongator and unitary links: every staged
+    entry is inside the fixed-point range, so the forward hops run as exact bf16 digit-plane
+    products on the tensor pipe; the operator must still match the FP64 oracle to double-float
+    accuracy."""
+    h, U, Pt, (kappa, w, bc) = _handle(dims, block, k, 9, fp64_emulation=1,
+                                       tiles=orthonormal_tiles)
+    h.coarse_build()
+    X, Y = h.coarse_op()
+    Xo, Yo = coarse.galerkin(Pt, U, dims, block, kappa, w, bc)
+    assert rel(X.cpu().numpy(), Xo) < 1e-11
+    assert rel(Y.cpu().numpy(), Yo) < 1e-11
+    h.close()
+
+
+@pytest.mark.parametrize("dims,block,k", CASES)
 def test_galerkin_double_float_contraction(dims, block, k):
-    """Galerkin contraction in double-float arithmetic on FP32 units vs the FP64 oracle."""
+    """Galerkin contraction in double-float arithmetic on FP32 units vs the FP64 oracle: Gaussian
+    tiles have entries beyond the tensor pipe's fixed-point range, so this runs the fallback."""
     h, U, Pt, (kappa, w, bc) = _handle(dims, block, k, 7, fp64_emulation=1)
     h.coarse_build()
     X, Y = h.coarse_op()
