@@ -441,7 +441,7 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, con
   } else {
     WMG_TRY(tile_gram(PtP, P, k, k, B, st, false));
   }
-  const bool tc = df64 && galerkin_tc_supported(k);
+  const bool tc = df64 && galerkin_tc_supported(k, B);
   // tensor path: the bf16 digit-plane products it issues (28 digit pairs of a (2 (2k)) x (2k)
   // x 96 real product per 8-site batch, padded tiles, about n_d / 8 + 1 batches per CTA);
   // otherwise FP64-equivalent flops

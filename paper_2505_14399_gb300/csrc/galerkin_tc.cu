@@ -41,7 +41,7 @@ constexpr int TC_NS = 7;               // digits per value
 constexpr int TC_KB = GNB * 6;         // staged rows per batch (48)
 constexpr int TC_K = 2 * TC_KB;        // stacked real rows (96)
 constexpr int TC_MAXW = 12;            // warps per CTA at most
-constexpr int TC_MAXT4 = 6;            // 2k <= 48
+constexpr int TC_MAXT4 = 3;            // 2k <= 24 (the digit planes and two raw buffers fit)
 
 __device__ __forceinline__ void ldm_x4t(unsigned r[4], const __nv_bfloat16* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -95,32 +95,124 @@ __device__ __forceinline__ bool tc_in_range(df v) { return fabsf(v.hi) < 2.0f; }
 
 __host__ __device__ constexpr int tc_warps(int t4) { return t4 * t4 < TC_MAXW ? t4 * t4 : TC_MAXW; }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared memory of one CTA beyond the digit planes: two raw input buffers (P(x + mu) and P(x)
+// column segments of 6 double-float values, U_mu(x)) and the per-site tables.
+__host__ __device__ constexpr size_t tc_raw_bytes(int t4) {
+  return sizeof(zdf) * 2 * ((size_t)2 * GNB * (8 * t4) * 6 + GNB * 9);
+}
+__host__ __device__ inline size_t tc_table_bytes(int nd) { return sizeof(int) * 8 * (size_t)nd + 16; }
+
 template <int T4>
-__global__ void __launch_bounds__(32 * tc_warps(T4), T4 <= 4 ? 2 : 1)
+__global__ void __launch_bounds__(32 * tc_warps(T4), 1)
 galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
                    const zdf* __restrict__ Ldf, HopGeom g, Blocking B, int* range_flag) {
-  constexpr int MR = 16 * T4;                 // rows b' (>= 4k)
   constexpr int NR = 8 * T4;                  // columns a (>= 2k)
   constexpr int NTILES = T4 * T4;
-  constexpr int NW = NTILES < TC_MAXW ? NTILES : TC_MAXW;
+  constexpr int NW = tc_warps(T4);
   constexpr int TPW = (NTILES + NW - 1) / NW;   // tiles per warp
   constexpr int ND = TC_NS;                   // digit-pair weights d = i + j < NS
   constexpr int LDA = tc_lda(T4), LDB = tc_ldb(T4);
   extern __shared__ __align__(16) unsigned char tc_raw[];
   __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(tc_raw);   // [NS][TC_K][LDA]
   __nv_bfloat16* SB = SA + (size_t)TC_NS * TC_K * LDA;             // [NS][TC_K][LDB]
-  __shared__ int ssite[GNB], sneg[GNB], slx[GNB], sly[GNB];
-  __shared__ size_t sox[GNB], soy[GNB];
+  zdf* sPy = reinterpret_cast<zdf*>(tc_raw + tc_smem(T4));         // [2][GNB][NR][6]
+  zdf* sPx = sPy + (size_t)2 * GNB * NR * 6;                       // [2][GNB][NR][6]
+  zdf* sU = sPx + (size_t)2 * GNB * NR * 6;                        // [2][GNB][9]
+  const int nd = B.nd;
+  int* tx = reinterpret_cast<int*>(tc_raw + tc_smem(T4) + tc_raw_bytes(T4));   // site x
+  int* toy = tx + nd;      // P offset of (2 j(y)) k M, y = x + mu
+  int* tox = toy + nd;     // P offset of (2 j(x)) k M
+  int* tly = tox + nd;     // local site of y, x
+  int* tlx = tly + nd;
+  int* tng = tlx + nd;     // antiperiodic sign of the hop
+  int* sel = tng + nd;     // [2][nd]: local sites of pass 0, then of pass 1
+  __shared__ int nsel[2];
   const int n2k = 2 * k;
   const int j = blockIdx.x, mu = blockIdx.y, dir = 2 * mu;
   const double coef = -g.kappa * g.w[mu];
   const int ne = n2k * n2k;
-  const int bmu = B.b[mu];
-  const int* bb = B.b;
+  const int M = B.M;
   const size_t V = (size_t)B.nd * B.d;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const size_t plane16 = tc_smem(T4) / 16;   // 16-byte chunks of SA + SB
   bool bad = false;
+
+  // ---- per-site tables of this aggregate, and the two passes' site lists
+  for (int l = threadIdx.x; l < nd; l += blockDim.x) {
+    int x = B.site(j, l);
+    int c[4];
+    c[0] = x % g.L[0];
+    int r = x / g.L[0];
+    c[1] = r % g.L[1]; r /= g.L[1];
+    c[2] = r % g.L[2]; c[3] = r / g.L[2];
+    bool wrap = c[mu] == g.L[mu] - 1;
+    int y = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
+    int jy, ly, jx, lx;
+    B.block_of(y, &jy, &ly);
+    B.block_of(x, &jx, &lx);
+    tx[l] = x;
+    toy[l] = 2 * jy * k * M;
+    tox[l] = 2 * jx * k * M;
+    tly[l] = ly;
+    tlx[l] = lx;
+    tng[l] = (wrap && g.bc[mu] < 0) ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // a hop crosses the aggregate when the local coordinate mu is the last one
+    int n0 = 0, n1 = 0;
+    const int bm = B.b[mu];
+    int stride = 1;
+    for (int m = 0; m < mu; ++m) stride *= B.b[m];
+    for (int l = 0; l < nd; ++l) {
+      bool cross = (l / stride) % bm == bm - 1;
+      if (cross) sel[nd + n1++] = l;
+      else sel[n0++] = l;
+    }
+    nsel[0] = n0;
+    nsel[1] = n1;
+  }
+  __syncthreads();
+
+  const int pps = 2 * n2k * 6 + 9;   // 16-byte pieces per site (one double-float complex each)
+  // issue the raw inputs of batch b of pass p into buffer buf (cp.async, one group)
+  auto prefetch = [&](int p, int b, int buf) {
+    const int* ls = sel + p * nd;
+    const int h0 = b * GNB;
+    const int nb = min(GNB, nsel[p] - h0);
+    for (int q = threadIdx.x; q < nb * pps; q += blockDim.x) {
+      int h = q / pps, rem = q - h * pps;
+      int l = ls[h0 + h];
+      const zdf* src;
+      zdf* dst;
+      if (rem < n2k * 6) {
+        int bcol = rem / 6, part = rem - bcol * 6;
+        src = Pdf + (size_t)toy[l] + (size_t)bcol * M + tly[l] * 6 + part;
+        dst = sPy + (((size_t)buf * GNB + h) * NR + bcol) * 6 + part;
+      } else if (rem < 2 * n2k * 6) {
+        rem -= n2k * 6;
+        int bcol = rem / 6, part = rem - bcol * 6;
+        src = Pdf + (size_t)tox[l] + (size_t)bcol * M + tlx[l] * 6 + part;
+        dst = sPx + (((size_t)buf * GNB + h) * NR + bcol) * 6 + part;
+      } else {
+        int part = rem - 2 * n2k * 6;
+        src = Ldf + ((size_t)mu * V + tx[l]) * 9 + part;
+        dst = sU + ((size_t)buf * GNB + h) * 9 + part;
+      }
+      cp_async16(dst, src);
+    }
+    cp_async_commit();
+  };
 
   for (int pass = 0; pass < 2; ++pass) {  // 0: hops inside the aggregate, 1: crossing hops
     // zero both digit planes: padding rows and columns stay zero for the whole pass
@@ -131,42 +223,19 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
     for (int t = 0; t < TPW; ++t)
 #pragma unroll
       for (int e = 0; e < 4; ++e) dacc[t][e] = {0.0f, 0.0f};
-    int l = 0;
-    while (true) {
-      // the next batch of local sites of this pass (same scan in every thread)
-      int nb = 0;
-      int lsel[GNB];
-      while (l < B.nd && nb < GNB) {
-        int q = l;
-        int lc[4];
-        lc[0] = q % bb[0]; q /= bb[0];
-        lc[1] = q % bb[1]; q /= bb[1];
-        lc[2] = q % bb[2]; lc[3] = q / bb[2];
-        bool cross = lc[mu] == bmu - 1;
-        if ((pass == 1) == cross) lsel[nb++] = l;
-        ++l;
+    const int nbat = (nsel[pass] + GNB - 1) / GNB;
+    if (nbat > 0) prefetch(pass, 0, 0);
+    for (int b = 0; b < nbat; ++b) {
+      const int buf = b & 1;
+      if (b + 1 < nbat) {
+        prefetch(pass, b + 1, buf ^ 1);   // its buffer was last read by batch b - 1's staging
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
-      if (nb == 0) break;
-      __syncthreads();   // the previous batch's digit planes have been read
-      if (threadIdx.x < nb) {
-        int x = B.site(j, lsel[threadIdx.x]);
-        int c[4];
-        c[0] = x % g.L[0];
-        int r = x / g.L[0];
-        c[1] = r % g.L[1]; r /= g.L[1];
-        c[2] = r % g.L[2]; c[3] = r / g.L[2];
-        bool wrap = c[mu] == g.L[mu] - 1;
-        int y = wrap ? x - (g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
-        ssite[threadIdx.x] = x;
-        sneg[threadIdx.x] = (wrap && g.bc[mu] < 0) ? 1 : 0;
-        int jy, ly, jx, lx;
-        B.block_of(y, &jy, &ly);
-        B.block_of(x, &jx, &lx);
-        soy[threadIdx.x] = (size_t)(2 * jy) * k * B.M;
-        sox[threadIdx.x] = (size_t)(2 * jx) * k * B.M;
-        sly[threadIdx.x] = ly;
-        slx[threadIdx.x] = lx;
-      }
+      __syncthreads();   // batch b's inputs are in; every warp finished batch b - 1's products
+      const int nb = min(GNB, nsel[pass] - b * GNB);
+      const int* ls = sel + pass * nd + b * GNB;
       if (nb < GNB) {
         // a short batch: its unused stacked rows k' are zero in every digit plane
         const int k0 = nb * 6, kn = TC_KB - k0;
@@ -178,42 +247,40 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
           else SB[((size_t)i * TC_K + kk) * LDB + (col - LDA)] = __float2bfloat16_rn(0.0f);
         }
       }
-      __syncthreads();
-      // stage: Ch (spin-projected, transported P(y)) and Pt (reconstruction-folded P(x)) in
-      // double-float, written as digit planes
+      // stage from shared memory: Ch (spin-projected, transported P(x + mu)) and Pt
+      // (reconstruction-folded P(x)) in double-float, written as digit planes
+      const zdf* py = sPy + (size_t)buf * GNB * NR * 6;
+      const zdf* px = sPx + (size_t)buf * GNB * NR * 6;
+      const zdf* pu = sU + (size_t)buf * GNB * 9;
       for (int e = threadIdx.x; e < nb * 6 * n2k; e += blockDim.x) {
         int h = e / (6 * n2k);
         int r = (e / n2k) % 6;
         int bcol = e % n2k;
         int s = r / 3, cc = r % 3;
         int beta = bcol / k;
-        int x = ssite[h];
-        int ly = sly[h], lx = slx[h];
-        size_t oy = soy[h] + (size_t)bcol * B.M;
-        size_t ox = sox[h] + (size_t)bcol * B.M;
+        const zdf* Py = py + ((size_t)h * NR + bcol) * 6;
+        const zdf* Px = px + ((size_t)h * NR + bcol) * 6;
         zdf hv[3];
 #pragma unroll
         for (int c2 = 0; c2 < 3; ++c2) {
           if (beta == 0) {
-            hv[c2] = zdf_ld(Pdf + oy + (ly * 2 + s) * 3 + c2);
+            hv[c2] = Py[s * 3 + c2];
           } else {
-            zdf p0 = zdf_ld(Pdf + oy + (ly * 2 + 0) * 3 + c2);
-            zdf p1 = zdf_ld(Pdf + oy + (ly * 2 + 1) * 3 + c2);
+            zdf p0 = Py[c2], p1 = Py[3 + c2];
             hv[c2] = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
           }
         }
-        const zdf* U = Ldf + ((size_t)mu * V + x) * 9 + cc * 3;
+        const zdf* U = pu + h * 9 + cc * 3;
         zdfacc t{};
 #pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2) zdf_fma(t, zdf_ld(U + c2), hv[c2]);
+        for (int c2 = 0; c2 < 3; ++c2) zdf_fma(t, U[c2], hv[c2]);
         zdf ch = zdf_norm(t);
-        if (sneg[h]) ch = zdf_neg(ch);
+        if (tng[ls[h]]) ch = zdf_neg(ch);
         zdf pt;
         if (beta == 0) {
-          pt = zdf_ld(Pdf + ox + (lx * 2 + s) * 3 + cc);
+          pt = Px[s * 3 + cc];
         } else {
-          zdf p0 = zdf_ld(Pdf + ox + (lx * 2 + 0) * 3 + cc);
-          zdf p1 = zdf_ld(Pdf + ox + (lx * 2 + 1) * 3 + cc);
+          zdf p0 = Px[cc], p1 = Px[3 + cc];
           pt = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
         }
         bad |= !(tc_in_range(ch.re) && tc_in_range(ch.im) && tc_in_range(pt.re) &&
@@ -258,8 +325,6 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
           const __nv_bfloat16* brow = SB + (size_t)(8 * (mq & 1) + rr) * LDB + 8 * nt;
 #pragma unroll 1
           for (int ks = 0; ks < TC_K / 16; ++ks) {
-            // B digit fragments for this k-step; A one digit at a time (registers: two CTAs
-            // per SM)
             unsigned bfr[TC_NS][2];
 #pragma unroll
             for (int i = 0; i < TC_NS; ++i)
@@ -286,7 +351,7 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
     }
     // this pass's blocks: tiles -> shared memory (over the digit planes) -> Op / Xpart
     __syncthreads();
-    df* sOut = reinterpret_cast<df*>(tc_raw);   // [MR][NR]
+    df* sOut = reinterpret_cast<df*>(tc_raw);   // [16 T4][NR]
 #pragma unroll
     for (int tt = 0; tt < TPW; ++tt) {
       const int tile = wid + tt * NW;
@@ -316,12 +381,12 @@ template <int T4>
 int launch_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
               const Blocking& B, int* range_flag, cudaStream_t st) {
   constexpr int NW = tc_warps(T4);
-  size_t sh = tc_smem(T4);
-  static bool set = false;
-  if (!set) {
+  size_t sh = tc_smem(T4) + tc_raw_bytes(T4) + tc_table_bytes(B.nd);
+  static size_t set = 0;
+  if (set < sh) {
     WMG_CUDA(cudaFuncSetAttribute(galerkin_tc_kernel<T4>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    set = true;
+    set = sh;
   }
   galerkin_tc_kernel<T4><<<dim3(B.d, 4), 32 * NW, sh, st>>>(Op, Xpart, Pdf, k, Ldf, g, B,
                                                             range_flag);
@@ -331,7 +396,13 @@ int launch_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const Ho
 
 }  // namespace
 
-bool galerkin_tc_supported(int k) { return k >= 1 && (k + 3) / 4 <= TC_MAXT4; }
+bool galerkin_tc_supported(int k, const Blocking& B) {
+  if (k < 1 || (k + 3) / 4 > TC_MAXT4) return false;
+  // shared memory of one CTA, and tile offsets that fit an int
+  const int t4 = (k + 3) / 4;
+  size_t sh = tc_smem(t4) + tc_raw_bytes(t4) + tc_table_bytes(B.nd);
+  return sh <= (size_t)227 * 1024 - 1024 && (size_t)B.d * 2 * k * B.M < ((size_t)1 << 31);
+}
 
 int galerkin_hops_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
                      const Blocking& B, int* range_flag, cudaStream_t st) {
@@ -339,10 +410,7 @@ int galerkin_hops_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, c
     case 1: return launch_tc<1>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
     case 2: return launch_tc<2>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
     case 3: return launch_tc<3>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    case 4: return launch_tc<4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    case 5: return launch_tc<5>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    case 6: return launch_tc<6>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    default: return fail(MG_EINVAL, "galerkin (tensor pipe): 2k > 48");
+    default: return fail(MG_EINVAL, "galerkin (tensor pipe): 2k > 24");
   }
 }
 
