@@ -94,6 +94,8 @@ __device__ __forceinline__ void acc_add(dfacc& a, float v) {
 __device__ __forceinline__ bool tc_in_range(df v) { return fabsf(v.hi) < 2.0f; }   // false for NaN
 
 __host__ __device__ constexpr int tc_warps(int t4) { return t4 * t4 < TC_MAXW ? t4 * t4 : TC_MAXW; }
+// Two warp groups: both stage; each takes half of the stacked rows k' of every product.
+constexpr int TC_WG = 2;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
@@ -113,7 +115,7 @@ __host__ __device__ constexpr size_t tc_raw_bytes(int t4) {
 __host__ __device__ inline size_t tc_table_bytes(int nd) { return sizeof(int) * 8 * (size_t)nd + 16; }
 
 template <int T4>
-__global__ void __launch_bounds__(32 * tc_warps(T4), 1)
+__global__ void __launch_bounds__(32 * TC_WG * tc_warps(T4), 1)
 galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
                    const zdf* __restrict__ Ldf, HopGeom g, Blocking B, int* range_flag) {
   constexpr int NR = 8 * T4;                  // columns a (>= 2k)
@@ -143,7 +145,8 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
   const int ne = n2k * n2k;
   const int M = B.M;
   const size_t V = (size_t)B.nd * B.d;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int wid = (threadIdx.x >> 5) % NW, grp = (threadIdx.x >> 5) / NW;   // tile slot, k' half
   const size_t plane16 = tc_smem(T4) / 16;   // 16-byte chunks of SA + SB
   bool bad = false;
 
@@ -324,7 +327,7 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
           const __nv_bfloat16* arow = SA + (size_t)(8 * (mq >> 1) + rr) * LDA + 16 * mt + 8 * (mq & 1);
           const __nv_bfloat16* brow = SB + (size_t)(8 * (mq & 1) + rr) * LDB + 8 * nt;
 #pragma unroll 1
-          for (int ks = 0; ks < TC_K / 16; ++ks) {
+          for (int ks = grp * (TC_K / 16 / TC_WG); ks < (grp + 1) * (TC_K / 16 / TC_WG); ++ks) {
             unsigned bfr[TC_NS][2];
 #pragma unroll
             for (int i = 0; i < TC_NS; ++i)
@@ -349,22 +352,30 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
         }
       }
     }
-    // this pass's blocks: tiles -> shared memory (over the digit planes) -> Op / Xpart
+    // this pass's blocks: tiles -> shared memory (over the digit planes) -> Op / Xpart; the
+    // second warp group adds its half of the rows to the first group's
     __syncthreads();
     df* sOut = reinterpret_cast<df*>(tc_raw);   // [16 T4][NR]
+    for (int g2 = 0; g2 < TC_WG; ++g2) {
+      if (grp == g2) {
 #pragma unroll
-    for (int tt = 0; tt < TPW; ++tt) {
-      const int tile = wid + tt * NW;
-      if (tile < NTILES) {
-        const int mt = tile / T4, nt = tile % T4;
-        const int row = 16 * mt + (lane >> 2), col = 8 * nt + 2 * (lane & 3);
-        sOut[(size_t)row * NR + col] = df_norm(dacc[tt][0]);
-        sOut[(size_t)row * NR + col + 1] = df_norm(dacc[tt][1]);
-        sOut[(size_t)(row + 8) * NR + col] = df_norm(dacc[tt][2]);
-        sOut[(size_t)(row + 8) * NR + col + 1] = df_norm(dacc[tt][3]);
+        for (int tt = 0; tt < TPW; ++tt) {
+          const int tile = wid + tt * NW;
+          if (tile < NTILES) {
+            const int mt = tile / T4, nt = tile % T4;
+            const int row = 16 * mt + (lane >> 2), col = 8 * nt + 2 * (lane & 3);
+            const size_t o[4] = {(size_t)row * NR + col, (size_t)row * NR + col + 1,
+                                 (size_t)(row + 8) * NR + col, (size_t)(row + 8) * NR + col + 1};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              df v = df_norm(dacc[tt][e]);
+              sOut[o[e]] = g2 == 0 ? v : df_add(sOut[o[e]], v);
+            }
+          }
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
     zd* out = pass == 1 ? Op + ((size_t)j * 9 + 1 + dir) * ne
                         : Xpart + ((size_t)mu * B.d + j) * ne;
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
@@ -380,7 +391,7 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
 template <int T4>
 int launch_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
               const Blocking& B, int* range_flag, cudaStream_t st) {
-  constexpr int NW = tc_warps(T4);
+  constexpr int NW = tc_warps(T4) * TC_WG;
   size_t sh = tc_smem(T4) + tc_raw_bytes(T4) + tc_table_bytes(B.nd);
   static size_t set = 0;
   if (set < sh) {
