@@ -109,8 +109,12 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Shared memory of one CTA beyond the digit planes: two raw input buffers (P(x + mu) and P(x)
 // column segments of 6 double-float values, U_mu(x)) and the per-site tables.
+// Raw P segments are stored [site][6 components][column], rows padded to 8 T4 + 1 columns so
+// that both the copies (consecutive components of one column) and the staging reads
+// (consecutive columns of one component) spread over the banks.
+__host__ __device__ constexpr int tc_nrp(int t4) { return 8 * t4 + 1; }
 __host__ __device__ constexpr size_t tc_raw_bytes(int t4) {
-  return sizeof(zdf) * 2 * ((size_t)2 * GNB * (8 * t4) * 6 + GNB * 9);
+  return sizeof(zdf) * 2 * ((size_t)2 * GNB * 6 * tc_nrp(t4) + GNB * 9);
 }
 __host__ __device__ inline size_t tc_table_bytes(int nd) { return sizeof(int) * 8 * (size_t)nd + 16; }
 
@@ -127,9 +131,10 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
   extern __shared__ __align__(16) unsigned char tc_raw[];
   __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(tc_raw);   // [NS][TC_K][LDA]
   __nv_bfloat16* SB = SA + (size_t)TC_NS * TC_K * LDA;             // [NS][TC_K][LDB]
-  zdf* sPy = reinterpret_cast<zdf*>(tc_raw + tc_smem(T4));         // [2][GNB][NR][6]
-  zdf* sPx = sPy + (size_t)2 * GNB * NR * 6;                       // [2][GNB][NR][6]
-  zdf* sU = sPx + (size_t)2 * GNB * NR * 6;                        // [2][GNB][9]
+  constexpr int NRP = tc_nrp(T4);
+  zdf* sPy = reinterpret_cast<zdf*>(tc_raw + tc_smem(T4));         // [2][GNB][6][NRP]
+  zdf* sPx = sPy + (size_t)2 * GNB * 6 * NRP;                      // [2][GNB][6][NRP]
+  zdf* sU = sPx + (size_t)2 * GNB * 6 * NRP;                       // [2][GNB][9]
   const int nd = B.nd;
   int* tx = reinterpret_cast<int*>(tc_raw + tc_smem(T4) + tc_raw_bytes(T4));   // site x
   int* toy = tx + nd;      // P offset of (2 j(y)) k M, y = x + mu
@@ -201,12 +206,12 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
       if (rem < n2k * 6) {
         int bcol = rem / 6, part = rem - bcol * 6;
         src = Pdf + (size_t)toy[l] + (size_t)bcol * M + tly[l] * 6 + part;
-        dst = sPy + (((size_t)buf * GNB + h) * NR + bcol) * 6 + part;
+        dst = sPy + (((size_t)buf * GNB + h) * 6 + part) * NRP + bcol;
       } else if (rem < 2 * n2k * 6) {
         rem -= n2k * 6;
         int bcol = rem / 6, part = rem - bcol * 6;
         src = Pdf + (size_t)tox[l] + (size_t)bcol * M + tlx[l] * 6 + part;
-        dst = sPx + (((size_t)buf * GNB + h) * NR + bcol) * 6 + part;
+        dst = sPx + (((size_t)buf * GNB + h) * 6 + part) * NRP + bcol;
       } else {
         int part = rem - 2 * n2k * 6;
         src = Ldf + ((size_t)mu * V + tx[l]) * 9 + part;
@@ -252,8 +257,8 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
       }
       // stage from shared memory: Ch (spin-projected, transported P(x + mu)) and Pt
       // (reconstruction-folded P(x)) in double-float, written as digit planes
-      const zdf* py = sPy + (size_t)buf * GNB * NR * 6;
-      const zdf* px = sPx + (size_t)buf * GNB * NR * 6;
+      const zdf* py = sPy + (size_t)buf * GNB * 6 * NRP;
+      const zdf* px = sPx + (size_t)buf * GNB * 6 * NRP;
       const zdf* pu = sU + (size_t)buf * GNB * 9;
       for (int e = threadIdx.x; e < nb * 6 * n2k; e += blockDim.x) {
         int h = e / (6 * n2k);
@@ -261,15 +266,16 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
         int bcol = e % n2k;
         int s = r / 3, cc = r % 3;
         int beta = bcol / k;
-        const zdf* Py = py + ((size_t)h * NR + bcol) * 6;
-        const zdf* Px = px + ((size_t)h * NR + bcol) * 6;
+        // component q of this column at this site: P*[q * NRP]
+        const zdf* Py = py + (size_t)h * 6 * NRP + bcol;
+        const zdf* Px = px + (size_t)h * 6 * NRP + bcol;
         zdf hv[3];
 #pragma unroll
         for (int c2 = 0; c2 < 3; ++c2) {
           if (beta == 0) {
-            hv[c2] = Py[s * 3 + c2];
+            hv[c2] = Py[(s * 3 + c2) * NRP];
           } else {
-            zdf p0 = Py[c2], p1 = Py[3 + c2];
+            zdf p0 = Py[c2 * NRP], p1 = Py[(3 + c2) * NRP];
             hv[c2] = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
           }
         }
@@ -281,9 +287,9 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
         if (tng[ls[h]]) ch = zdf_neg(ch);
         zdf pt;
         if (beta == 0) {
-          pt = Px[s * 3 + cc];
+          pt = Px[(s * 3 + cc) * NRP];
         } else {
-          zdf p0 = Px[cc], p1 = Px[3 + cc];
+          zdf p0 = Px[cc * NRP], p1 = Px[(3 + cc) * NRP];
           pt = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
         }
         bad |= !(tc_in_range(ch.re) && tc_in_range(ch.im) && tc_in_range(pt.re) &&
