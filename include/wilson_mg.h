@@ -99,7 +99,11 @@ typedef struct mg_params {
                                 and of the Galerkin contraction: 1 double-float on FP32
                                 units (~2^-48 relative), 0 native FP64; -1 double-float
                                 only in the mixed forms (SVD: setup_dtype MG_C64;
-                                Galerkin: solve_dtype other than MG_C128)                */
+                                Galerkin: solve_dtype other than MG_C128).  A double-float
+                                Galerkin with k <= 12 runs its contraction on the tensor
+                                pipe as exact bf16 digit products (same accuracy) when
+                                every entry is in range (orthonormal P, unitary links),
+                                else on the FP32 units                                   */
 } mg_params;
 
 typedef struct mg_solve_info {

@@ -384,9 +384,6 @@ int to_df(zdf* out, const zd* in, size_t n, cudaStream_t st) {
   return MG_OK;
 }
 
-// raised by the tensor-pipe Galerkin kernel when a staged entry leaves its fixed-point range
-__device__ int g_galerkin_tc_range;
-
 namespace {
 template <bool DF, int NE>
 int launch_hop(dim3 grid, size_t sh, cudaStream_t st, zd* Op, zd* Xpart, const zd* P,
@@ -418,7 +415,7 @@ int launch_hop_ne(dim3 grid, size_t sh, cudaStream_t st, zd* Op, zd* Xpart, cons
 
 int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, const zd* links,
                    const zdf* Ldf, const Geom& g, const Blocking& B, cudaStream_t st, bool df64,
-                   bool pdf_ready) {
+                   bool pdf_ready, int* range_flag) {
   if (4 * k * k > GTH * GMAXE) return fail(MG_EINVAL, "galerkin: k > 32");
   if (df64 && (!Pdf || !Ldf)) return fail(MG_EINVAL, "galerkin: double-float copies missing");
   HopGeom hg;
@@ -454,8 +451,8 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, con
   if (tc) {
     // tensor pipe (exact digit-plane products); entries outside its fixed-point range (links
     // that are not unitary, a prolongator that is not orthonormal) fall back to the FP32 units
-    int* flag = nullptr;
-    WMG_CUDA(cudaGetSymbolAddress((void**)&flag, g_galerkin_tc_range));
+    if (!range_flag) return fail(MG_EINVAL, "galerkin: no range flag");
+    int* flag = range_flag;
     WMG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
     WMG_TRY(galerkin_hops_tc(Op, Xpart, Pdf, k, Ldf, hg, B, flag, st));
     int h_flag = 0;

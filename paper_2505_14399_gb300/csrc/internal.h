@@ -291,11 +291,12 @@ int prolong_launch(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, int k, const
                    int nrhs, cudaStream_t st);
 // Galerkin: Op[j][blk][b][a] (column-major blocks; blk 0 = X, 1 + dir = Y_dir), FP64.
 // Scratch: Xpart (4 d (2k)^2), PtP (2 d k^2), and with df64 Pdf (P as (hi, lo) pairs, filled
-// here unless pdf_ready says the setup wrote it) and Ldf (the links as (hi, lo) pairs, filled
-// by the caller).
+// here unless pdf_ready says the setup wrote it), Ldf (the links as (hi, lo) pairs, filled
+// by the caller) and range_flag (one device int of the caller's, for the tensor path's range
+// check; synchronises `st` when that path runs).
 int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, const zd* links,
                    const zdf* Ldf, const Geom& g, const Blocking& B, cudaStream_t st, bool df64,
-                   bool pdf_ready = false);
+                   bool pdf_ready, int* range_flag);
 // complex double -> (hi, lo) float pairs
 int to_df(zdf* out, const zd* in, size_t n, cudaStream_t st);
 template <typename R>

@@ -1,10 +1,11 @@
 // Batched GMRES / flexible GMRES with all Krylov scalars resident on the device.
 //
 // Arnoldi uses classical Gram-Schmidt applied twice (CGS2: two batched dot passes and
-// two batched updates per step), the Hessenberg column is reduced by complex Givens
-// rotations in a one-thread-per-system kernel, and the residual estimates |g_{j+1}|
-// (one per step, kept on the device) are the only values the host reads, every
-// `check_every` steps of a tolerance-driven solve.  All nrhs systems advance in lockstep.
+// two batched updates per step; single-pass for the fixed-step FP32 smoothers), the
+// Hessenberg column is reduced by complex Givens rotations by one extra CTA of the step's
+// normalising update, and the residual estimates |g_{j+1}| (one per step, kept on the device)
+// are the only values the host reads, every `check_every` steps of a tolerance-driven solve.
+// All nrhs systems advance in lockstep.
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -123,8 +124,9 @@ __device__ void givens_deferred(zd* sm, SmallLayout L, int j, double beta, bool 
 //   w -= sum_i h1_i V_i,  then  h2_i = V_i^dag w (i < nv)  and  s = ||w||^2, one sweep over w.
 // The last CTA stores h2 and H[j+1, j]: with V orthonormal, the vector left after the pass 2
 // update, w - V h2, has squared norm s - ||h2||^2 (Pythagoras), so the pass 2 update needs no
-// reduction of its own (it also completes the Hessenberg column and the Givens step).  h2 is O(eps ||A v_j||) after pass 1, so the subtraction loses nothing unless
-// the Krylov space is (numerically) invariant, where H[j+1, j] ~ 0 ends the solve anyway.
+// reduction of its own (it also completes the Hessenberg column and the Givens step).  h2 is
+// O(eps ||A v_j||) after pass 1, so the subtraction loses nothing unless the Krylov space is
+// (numerically) invariant, where H[j+1, j] ~ 0 ends the solve anyway.
 template <typename E>
 __global__ void __launch_bounds__(RT, 3)
 cgs_update_dot_kernel(E* w, const E* __restrict__ V, size_t vstride, int nv,
@@ -713,8 +715,8 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
     WMG_TRY(A(w, vj, st));
   }
   zd* Hcol = small + L.H() + (size_t)j * (m + 1);
-  // CGS2 in three sweeps: projections; update + re-projections + norm + Givens;
-  // update + normalisation into column j + 1
+  // CGS2 in three sweeps: projections; update + re-projections + norm; update +
+  // normalisation into column j + 1, with the Givens step beside it
   double fb = (double)nrhs * n * sizeof(E);
   bool streamed = fuse;
   if constexpr (std::is_same<E, zf>::value) {

@@ -35,6 +35,7 @@ struct mg_handle {
   zdf* Ldf = nullptr;
   bool have_P = false, have_coarse = false;
   bool pdf_ready = false;      // Pdf holds the double-float split of P64 already
+  int* tc_flag = nullptr;      // device int: range flag of the tensor-pipe Galerkin
   // solver state, sized for `nrhs`
   int nrhs = 0;
   Gmres<double> outer64, coarse64, post64;
@@ -138,6 +139,7 @@ int create_handle(mg_handle** out, const void* links, const mg_params* p, bool n
     WMG_TRY(to_df(h->Ldf, h->links64, lb, st));
   }
   WMG_CUDA(cudaMemsetAsync(h->sigma, 0, ntile * h->k * sizeof(double), st));
+  WMG_TRY(dev_alloc(&h->tc_flag, sizeof(int)));
   int ns = p->n_s > 0 ? p->n_s : 1;
   WMG_TRY(dev_alloc(&h->hist, (size_t)ns * ntile * h->k * sizeof(double)));
   WMG_CUDA(cudaMemsetAsync(h->hist, 0, (size_t)ns * ntile * h->k * sizeof(double), st));
@@ -508,7 +510,7 @@ int check_ready(mg_handle* h, bool need_coarse) {
 mg_handle::~mg_handle() {
   free_solver();
   dfree(links64); dfree(links64L); dfree(links32L); dfree(links16L); dfree(P64); dfree(P32); dfree(sigma); dfree(hist);
-  dfree(Op64); dfree(Op32); dfree(PtP); dfree(Pdf); dfree(Ldf);
+  dfree(Op64); dfree(Op32); dfree(PtP); dfree(Pdf); dfree(Ldf); dfree(tc_flag);
 }
 
 void mg_handle::free_solver() {
@@ -558,7 +560,7 @@ extern "C" int coarse_build(mg_handle* h, void* stream) {
   WMG_CUDA(cudaMallocAsync(&Xpart, (size_t)4 * h->B.d * ne * sizeof(zd), st));
   bool df = galerkin_df(h->p);
   int s = galerkin_build(h->Op64, Xpart, h->P64, h->Pdf, h->PtP, h->k, h->links64, h->Ldf, h->g,
-                         h->B, st, df, h->pdf_ready);
+                         h->B, st, df, h->pdf_ready, h->tc_flag);
   cudaFreeAsync(Xpart, st);
   WMG_TRY(s);
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
@@ -619,7 +621,7 @@ extern "C" int coarse_build_noalloc(mg_handle* h, void* stream) {
   WMG_TRY(galerkin_scratch(&scratch));
   bool df = galerkin_df(h->p);
   WMG_TRY(galerkin_build(h->Op64, static_cast<zd*>(scratch), h->P64, h->Pdf, h->PtP, h->k,
-                         h->links64, h->Ldf, h->g, h->B, st, df, h->pdf_ready));
+                         h->links64, h->Ldf, h->g, h->B, st, df, h->pdf_ready, h->tc_flag));
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
   WMG_CUDA(cudaStreamSynchronize(st));
   h->have_coarse = true;
