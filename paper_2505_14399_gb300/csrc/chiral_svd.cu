@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
   T* rph = Vv + ce * ce;              // [np] e^{-i phi}
   TR* rcT = reinterpret_cast<TR*>(rph + np);   // [np] cos
   TR* rsT = rcT + np;                          // [np] sin
-  int* top = reinterpret_cast<int*>(rsT + np);   // [np]
-  int* bot = top + np;                           // [np]
-  int* rflag = bot + np;                         // [np] pair rotated in this round
+  int* pa = reinterpret_cast<int*>(rsT + np);    // [ce - 1][np] pair (a < b) of each round
+  int* pb = pa + (ce - 1) * np;
+  int* rflag = pb + (ce - 1) * np;               // [np] pair rotated in this round
   __shared__ double dg[MAXC];
   int t = blockIdx.x;
   const zd* Gt = G + (size_t)t * c * c;
@@ -169,9 +169,25 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
     A[e] = (i < c && j < c) ? J::from(Gt[i * c + j]) : J::zero();
     Vv[e] = (i == j) ? J::one() : J::zero();
   }
-  for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    top[p] = 2 * p;
-    bot[p] = 2 * p + 1;
+  // the round-robin schedule of all ce - 1 rounds of a sweep, once: pairs (top[p], bot[p])
+  // start as (2p, 2p + 1); after each round top[0] stays, the others move one place
+  if (threadIdx.x == 0) {
+    int top[MAXC / 2], bot[MAXC / 2];
+    for (int p = 0; p < np; ++p) { top[p] = 2 * p; bot[p] = 2 * p + 1; }
+    for (int round = 0; round < ce - 1; ++round) {
+      for (int p = 0; p < np; ++p) {
+        pa[round * np + p] = min(top[p], bot[p]);
+        pb[round * np + p] = max(top[p], bot[p]);
+      }
+      if (np > 1) {
+        int tlast = top[np - 1];
+        int b0 = bot[0];
+        for (int p = np - 1; p > 1; --p) top[p] = top[p - 1];
+        top[1] = b0;
+        for (int p = 0; p < np - 1; ++p) bot[p] = bot[p + 1];
+        bot[np - 1] = tlast;
+      }
+    }
   }
   __syncthreads();
   for (int sweep = 0; sweep < 30; ++sweep) {
@@ -179,7 +195,7 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
     for (int round = 0; round < ce - 1; ++round) {
       // rotation parameters
       for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+        const int a = pa[round * np + p], b = pb[round * np + p];
         int f = 0;
         if constexpr (DF) {
           // The angle comes from FP32 copies (the diagonal difference formed in df64 first,
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
       for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
         int p = e / ce, k = e % ce;
         if (!rflag[p]) continue;
-        int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+        const int a = pa[round * np + p], b = pb[round * np + p];
         T eph = rph[p];
         if constexpr (DF) eph.im = df_neg(eph.im);
         else eph.im = -eph.im;
@@ -254,7 +270,7 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
       for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
         int p = e / ce, k = e % ce;
         if (!rflag[p]) continue;
-        int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+        const int a = pa[round * np + p], b = pb[round * np + p];
         T mph = rph[p];
         T xa = A[k * ce + a], xb = A[k * ce + b];
         rot_pair(xa, xb, rcT[p], rsT[p], mph);
@@ -270,23 +286,13 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
         // with the exact FP64 angle the rotated pair's off-diagonal entries are zero
         for (int p = threadIdx.x; p < np; p += blockDim.x) {
           if (rflag[p]) {
-            int a = min(top[p], bot[p]), b = max(top[p], bot[p]);
+            const int a = pa[round * np + p], b = pb[round * np + p];
             A[a * ce + b] = J::zero();
             A[b * ce + a] = J::zero();
           }
         }
         __syncthreads();
       }
-      // round-robin: keep top[0], rotate the others
-      if (threadIdx.x == 0 && np > 1) {
-        int tlast = top[np - 1];
-        int b0 = bot[0];
-        for (int p = np - 1; p > 1; --p) top[p] = top[p - 1];
-        top[1] = b0;
-        for (int p = 0; p < np - 1; ++p) bot[p] = bot[p + 1];
-        bot[np - 1] = tlast;
-      }
-      __syncthreads();
     }
     // a barrier that also ORs the flags: every thread takes the same exit decision
     if (!__syncthreads_or(rotated)) break;
@@ -551,8 +557,10 @@ int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, do
              bool df64) {
   if (c > MAXC) return fail(MG_EINVAL, "tile_eig: more than 64 columns");
   int ce = c + (c & 1), np = ce / 2;
-  // A, V, phases (16-byte complex in both arithmetics), cos, sin (8 bytes), three int arrays
-  size_t sh = sizeof(zd) * (2 * ce * ce + np) + sizeof(double) * 2 * np + sizeof(int) * 3 * np + 64;
+  // A, V, phases (16-byte complex in both arithmetics), cos, sin (8 bytes), the round-robin
+  // schedule and the rotation flags
+  size_t sh = sizeof(zd) * (2 * ce * ce + np) + sizeof(double) * 2 * np +
+              sizeof(int) * (2 * (ce - 1) * np + np) + 64;
   static bool attr_set = false;
   if (!attr_set) {
     WMG_CUDA(cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
