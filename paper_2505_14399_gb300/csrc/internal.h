@@ -165,8 +165,10 @@ class GmresV {
   bool flexible = false;
 
  private:
+  // b0 (fused first step only): the unscaled right-hand side, scaled and written as v_0 there
   int arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st,
-                   bool single_pass = false, const FusedStencil* fused = nullptr);
+                   bool single_pass = false, const FusedStencil* fused = nullptr,
+                   const E* b0 = nullptr);
   double ip_scale() const { return VecT<E>::rms ? 1.0 / (double)n : 1.0; }
   E* V = nullptr;         // (m+1) x nrhs x n
   E* Z = nullptr;         // m x nrhs x n

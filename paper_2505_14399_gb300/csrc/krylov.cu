@@ -476,18 +476,27 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
 // thread's own site do not depend on the stencil, so they overlap its latency-bound hops,
 // and w is not read back.  One thread per site and rhs row (blockIdx.y), a grid-stride
 // over 256-site blocks.
-template <int NVM>
+template <int NVM, bool FIRST>
 __global__ void __launch_bounds__(RT)
-dslash_proj_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_t n,
+dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
                    const float2* __restrict__ links, stencil::KGeom g, zd* small, SmallLayout L,
-                   double* wnorm, double* partial, unsigned* counter, int maxvec) {
+                   double* wnorm, double* partial, unsigned* counter, int maxvec,
+                   const zf* __restrict__ b0, const double* beta0) {
   using namespace stencil;
   dep_entry();
   __shared__ float sh[(RT / 32) * NVM * 2];
   const int rhs = blockIdx.y;
   const int nsites = g.V;
-  const float2* vb = reinterpret_cast<const float2*>(V) + (size_t)rhs * n;
-  const float2* vin = vb + (size_t)(nv - 1) * vstride;   // v_j
+  float2* vb = reinterpret_cast<float2*>(V) + (size_t)rhs * n;
+  // FIRST (step 0): the stencil reads b and everything is scaled by 1 / ||b|| (linear),
+  // v_0 = b / ||b|| is written here (no separate scaling pass); otherwise the input is v_j
+  const float2* vin = FIRST ? reinterpret_cast<const float2*>(b0) + (size_t)rhs * n
+                            : vb + (size_t)(nv - 1) * vstride;
+  float sc = 1.0f;
+  if (FIRST) {
+    double bb = beta0[rhs];
+    sc = bb > 0 ? (float)(1.0 / bb) : 0.0f;
+  }
   float2* wr = reinterpret_cast<float2*>(w) + (size_t)rhs * n;
   float ar[NVM], ai[NVM];
 #pragma unroll
@@ -503,22 +512,30 @@ dslash_proj_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size
     hop_pair<1, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
     hop_pair<2, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
     hop_pair<3, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
-    zf p[12];
-    SiteIO<StC64>::load(vin, (size_t)site, p);
+    zf p[12], x0[12];
+    SiteIO<StC64>::load(vin, (size_t)site, x0);
     const float mk = (float)(-g.kappa);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      p[k].re = fmaf(mk, acc[k].re, p[k].re);
-      p[k].im = fmaf(mk, acc[k].im, p[k].im);
+      p[k].re = sc * fmaf(mk, acc[k].re, x0[k].re);
+      p[k].im = sc * fmaf(mk, acc[k].im, x0[k].im);
       ss = fmaf(p[k].re, p[k].re, ss);
       ss = fmaf(p[k].im, p[k].im, ss);
+      x0[k].re *= sc;
+      x0[k].im *= sc;
     }
     SiteIO<StC64>::store(wr, (size_t)site, p);
+    if (FIRST) SiteIO<StC64>::store(vb, (size_t)site, x0);   // v_0
 #pragma unroll
     for (int q = 0; q < NVM; ++q) {
       if (q < nv) {
         zf v[12];
-        SiteIO<StC64>::load(vb + (size_t)q * vstride, (size_t)site, v);
+        if (FIRST) {   // nv = 1: v_0 is in registers (just written, not read back)
+#pragma unroll
+          for (int k = 0; k < 12; ++k) v[k] = x0[k];
+        } else {
+          SiteIO<StC64>::load(vb + (size_t)q * vstride, (size_t)site, v);
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           ar[q] = fmaf(v[k].re, p[k].re, ar[q]);
@@ -551,9 +568,10 @@ dslash_proj_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size
   }
 }
 
-int dslash_proj_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* small,
+int dslash_proj_launch(zf* w, zf* V, size_t fs, size_t n, int nrhs, zd* small,
                        SmallLayout L, int j, double* dnorm, ReduceWork& rw,
-                       const FusedStencil& fz, cudaStream_t st) {
+                       const FusedStencil& fz, cudaStream_t st, const zf* b0 = nullptr,
+                       const double* beta0 = nullptr) {
   stencil::KGeom kg = stencil::to_kgeom(fz.g);
   int nv = j + 1;
   int nb = (kg.V + RT - 1) / RT;
@@ -561,12 +579,14 @@ int dslash_proj_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* sm
   const float2* L32 = static_cast<const float2*>(fz.links);
   double byts = (double)nrhs * kg.V * 8.0 * (12.0 * (nv + 2) + 36.0);
   ProfScope ps("dslash_proj", byts, (1320.0 + 48.0 * (nv + 1)) * kg.V * nrhs, st);
-  if (nv <= 4)
-    WMG_LAUNCH_DEP(dslash_proj_kernel<4>, dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec);
+  if (b0)
+    WMG_LAUNCH_DEP((dslash_proj_kernel<4, true>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
+  else if (nv <= 4)
+    WMG_LAUNCH_DEP((dslash_proj_kernel<4, false>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
   else if (nv <= 8)
-    WMG_LAUNCH_DEP(dslash_proj_kernel<8>, dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec);
+    WMG_LAUNCH_DEP((dslash_proj_kernel<8, false>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
   else
-    WMG_LAUNCH_DEP(dslash_proj_kernel<16>, dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec);
+    WMG_LAUNCH_DEP((dslash_proj_kernel<16, false>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
   return MG_OK;
 }
 
@@ -696,7 +716,7 @@ void GmresV<E>::release() {
 // dnorm layout: [0..nrhs) current ||w||, [nrhs..2nrhs) beta, [2nrhs..3nrhs) residual estimate
 template <typename E>
 int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st,
-                            bool single_pass, const FusedStencil* fused) {
+                            bool single_pass, const FusedStencil* fused, const E* b0) {
   SmallLayout L{m};
   size_t fs = n * nrhs;
   E* vj = V + (size_t)j * fs;
@@ -706,7 +726,8 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
   if (fuse) {
     // the stencil and the single-pass projections in one kernel
     if constexpr (std::is_same<E, zf>::value)
-      WMG_TRY(dslash_proj_launch(w, V, fs, n, nrhs, small, L, j, dnorm, rw, *fused, st));
+      WMG_TRY(dslash_proj_launch(w, V, fs, n, nrhs, small, L, j, dnorm, rw, *fused, st, b0,
+                                 b0 ? dnorm + nrhs : nullptr));
   } else if (M) {
     E* zj = Z + (size_t)j * fs;
     WMG_TRY((*M)(zj, vj, st));
@@ -754,13 +775,17 @@ int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t 
   if (steps == 0) return MG_OK;
   WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, b, n, nrhs, rw, st, ip_scale()));
   WMG_LAUNCH_DEP(init_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
-  WMG_TRY(scale_inv_v<E>(V, b, dnorm + nrhs, 1, n, nrhs, st));
+  // the fused first step scales b itself and writes v_0 (see dslash_proj_kernel)
+  bool fuse0 = false;
+  if constexpr (std::is_same<E, zf>::value) fuse0 = fused && n == (size_t)fused->g.V * 12;
+  if (!fuse0) WMG_TRY(scale_inv_v<E>(V, b, dnorm + nrhs, 1, n, nrhs, st));
   // A fixed number of steps from zero (the smoothers): complex-float bases of up to 16
   // columns orthogonalise with a single classical Gram-Schmidt pass, H[j+1, j] from
   // Pythagoras.  Over these few steps the basis stays orthogonal to ~eps_32 times the
   // conditioning of the small Krylov basis, which leaves the smoother's approximate
   // minimisation unchanged to FP32 rounding; the tolerance-driven solves keep CGS2.
-  for (int j = 0; j < steps; ++j) WMG_TRY(arnoldi_step(A, nullptr, j, st, true, fused));
+  for (int j = 0; j < steps; ++j)
+    WMG_TRY(arnoldi_step(A, nullptr, j, st, true, fused, fuse0 && j == 0 ? b : nullptr));
   WMG_LAUNCH_DEP(solve_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, steps, nrhs);
   WMG_TRY(multi_axpy_v<E>(x, V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
   return MG_OK;
