@@ -175,10 +175,10 @@ galerkin_hop_kernel(zd* Op, zd* Xpart, const zd* __restrict__ P, const zdf* __re
         int r = (e / n2k) % 6;
         int bcol = e % n2k;
         int s = r / 3, cc = r % 3;
-        int beta = bcol / k, ip = bcol % k;
+        int beta = bcol / k;
         int x = ssite[h];
         int ly = sly[h], lx = slx[h];
-        // column bcol = beta k + ip of the tile pair (chirality beta follows chirality 0)
+        // column bcol = beta k + i of the tile pair (chirality beta follows chirality 0)
         size_t oy = soy[h] + (size_t)bcol * B.M;
         size_t ox = sox[h] + (size_t)bcol * B.M;
         if constexpr (DF) {
