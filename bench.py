@@ -122,6 +122,11 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# DRAM bytes per launch (read + write) from one ncu capture of the bench step on its workload
+# (profiles/dslash_proj_16x16x16x32_traffic.md); reported as roofline.traffic for that kernel.
+NCU_TRAFFIC = {("dslash_proj", "c2_16^3x32_near_critical"): 135.4e6}
+
+
 def kernel_bound(name, alu, peaks, peak_kind):
     """(bound, peak, unit, source) of a library kernel, by the arithmetic it runs on."""
     if name.endswith("_df64"):
@@ -361,7 +366,8 @@ def gpu_arm(args):
             ach = v["bytes"] / max(v["launches"], 1e-9) / per_launch_s / 1e9
             roof = {"kernel": name, "bound": bound, "achieved": ach, "peak": pk,
                     "unit": unit, "frac": ach / pk, "peak_source": src,
-                    "traffic": None, "avg_launch_us": per_launch_s * 1e6,
+                    "traffic": NCU_TRAFFIC.get((name, WORKLOAD)),
+                    "avg_launch_us": per_launch_s * 1e6,
                     "algorithmic_bytes_per_launch": v["bytes"] / max(v["launches"], 1e-9)}
     if roof is None:
         roof = {"kernel": "dslash_c64 (16^3x32, L2 flushed)", "bound": "hbm", "achieved": gbs,
