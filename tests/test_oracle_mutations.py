@@ -1,0 +1,245 @@
+"""Planted mistakes in the oracle must fail its pins (mutation checks, CPU only).
+
+Each mutant rewrites one or two expressions in the source of one oracle function — a flipped
+sign, a dropped conjugate or transpose, a neighbour taken on the wrong side, a missing factor
+— compiles the rewritten function against the oracle module's own globals, installs it in
+every oracle module that refers to the original for the duration of one test, and runs the
+pins chosen to catch that kind of mistake: at least one of them must fail.  Every rewritten
+snippet must occur exactly once in the original source, so that a later edit of the oracle
+cannot silently turn a mutant into the original function.
+"""
+import inspect
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+import oracle.adjoint
+import oracle.coarse
+import oracle.icsvd
+import oracle.krylov
+import oracle.mg
+import oracle.philox
+import oracle.wilson
+import test_oracle_numerics as TN
+import test_oracle_wilson as TW
+
+ANISO_T = ((1, 1, 1, -1), TW.ANISO)
+ANTI_X = ((-1, 1, 1, 1), (1.0, 0.5, 1.0, 1.0))
+# x antiperiodic and weighted: on the 4x2x2x2 lattice only x has momenta with sin p != 0
+FREE_X = ((-1, 1, 1, 1), (0.5, 1.0, 1.0, 1.0))
+
+
+def _free_spectrum_small(bc, w):
+    """The closed-form free-field spectrum on a 4x2x2x2 lattice (cheaper than the 4x2x2x4 pin)."""
+    from paper_2505_14399_gb300 import synthetic
+    dims = (4, 2, 2, 2)
+    D = oracle.wilson.dense_dirac(synthetic.unit_links(dims), dims, 0.11, w, bc)
+    ev = np.sort_complex(np.round(np.linalg.eigvals(D), 10))
+    ref = np.sort_complex(np.round(oracle.wilson.free_spectrum(dims, 0.11, w, bc), 10))
+    assert np.abs(ev - ref).max() < 1e-9
+
+
+def _link_gradient_fd(n_dirs=2):
+    """Central finite differences of |x|^2, x = D^{-1} b, against the oracle's link gradient."""
+    from paper_2505_14399_gb300 import synthetic
+    W = oracle.wilson
+    dims = (2, 2, 2, 2)
+    U = synthetic.smooth_links(dims, 4)
+    w, bc, kappa = (1, 1, 1, 0.5), (1, 1, 1, -1), 0.12
+    b = synthetic.gaussian_rhs(dims, 5)[0].reshape(-1)
+
+    def loss(links):
+        x = np.linalg.solve(W.dense_dirac(links, dims, kappa, w, bc), b)
+        return float(np.vdot(x, x).real), x
+
+    x = loss(U)[1]
+    D = W.dense_dirac(U, dims, kappa, w, bc)
+    g_b = np.linalg.solve(D.conj().T, 2 * x)
+    G = oracle.adjoint.grad_link_angles(g_b, x, U, dims, kappa, w, bc)
+    rng = np.random.default_rng(6)
+    h = 1e-4
+    for _ in range(n_dirs):
+        om = rng.standard_normal((4, W.volume(dims), 8))
+        fd = (loss(oracle.adjoint.perturb_links(U, h * om))[0]
+              - loss(oracle.adjoint.perturb_links(U, -h * om))[0]) / (2 * h)
+        assert abs(fd - float((G * om).sum())) < 1e-6 * max(1, abs(fd))
+
+
+def _galerkin(dims, block):
+    return lambda: TN.test_galerkin_stencil_equals_dense_product(dims, block)
+
+
+GAL_A = _galerkin((4, 4, 2, 2), (2, 2, 2, 2))
+GAL_B = _galerkin((6, 2, 2, 4), (2, 2, 1, 2))
+HERM = [lambda: TW.test_gamma5_hermiticity_dense(*ANISO_T)]
+PLANE = [TW.test_plane_wave_momentum_space_form]
+COV = [TW.test_gauge_covariance]
+
+# (id, module, function or Class.method, [(original snippet, replacement)], pins)
+MUTANTS = [
+    # Wilson-Dirac operator (Eq. 1 with the documented conventions)
+    ("projector_sign_forward", oracle.wilson, "hopping",
+     [("eye + sgn * GAMMA[mu], up", "eye - sgn * GAMMA[mu], up")], HERM + PLANE),
+    ("projectors_swapped", oracle.wilson, "hopping",
+     [("eye + sgn * GAMMA[mu], up", "eye - sgn * GAMMA[mu], up"),
+      ("eye - sgn * GAMMA[mu], bwd", "eye + sgn * GAMMA[mu], bwd")], HERM + PLANE),
+    ("backward_link_not_conjugated", oracle.wilson, "hopping",
+     [("'xba,xsb->xsa', U.conj()", "'xba,xsb->xsa', U")], HERM + COV),
+    ("backward_link_not_transposed", oracle.wilson, "hopping",
+     [("'xba,xsb->xsa', U.conj()", "'xab,xsb->xsa', U.conj()")], HERM + COV),
+    ("backward_hop_from_wrong_side", oracle.wilson, "hopping",
+     [("_shift(Udag_psi, dims, mu, -1, bc)", "_shift(Udag_psi, dims, mu, +1, bc)")],
+     HERM + PLANE),
+    ("backward_hop_weight_dropped", oracle.wilson, "hopping",
+     [("out += hop_weight[mu] * np.einsum('st,xtb->xsb', eye - sgn",
+       "out += np.einsum('st,xtb->xsb', eye - sgn")], HERM + PLANE),
+    ("forward_link_taken_at_neighbour", oracle.wilson, "hopping",
+     [("up = np.einsum('xab,xsb->xsa', U, fwd)",
+       "up = _shift(np.einsum('xab,xsb->xsa', U, psi), dims, mu, +1, bc)")], HERM + COV),
+    ("boundary_phase_on_wrong_slice", oracle.wilson, "_shift",
+     [("sl[ax] = dims[mu] - 1 if direction > 0 else 0",
+       "sl[ax] = 0 if direction > 0 else dims[mu] - 1")],
+     # on unit links the free spectrum cannot see this mistake (the Wilson projectors
+     # annihilate back-tracking paths, the only closed paths that feel it); gamma_5
+     # hermiticity on random links with an antiperiodic direction of extent 4 does
+     [lambda: TW.test_gamma5_hermiticity_dense(*ANTI_X)]),
+    ("kappa_sign", oracle.wilson, "dslash",
+     [("psi - kappa * hopping", "psi + kappa * hopping")], PLANE),
+    ("parity_output_swapped", oracle.wilson, "dslash_parity",
+     [("h[par == parity]", "h[par == 1 - parity]")],
+     [TW.test_parity_split_reassembles_full_operator]),
+    ("free_spectrum_missing_weight", oracle.wilson, "free_spectrum",
+     [("(w[m] * np.sin(P[m])) ** 2", "np.sin(P[m]) ** 2")],
+     [lambda: _free_spectrum_small(*FREE_X)]),
+    # Philox4x32-10 (published definition) and the Gaussian map
+    ("philox_key_bump_swapped", oracle.philox, "philox4x32_10",
+     [("(int(k0) + W0)", "(int(k0) + W1)")], [TN.test_philox_known_answers]),
+    ("philox_output_permutation", oracle.philox, "philox4x32_10",
+     [("c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]",
+       "c = [hi0 ^ c[1] ^ k0, lo0, hi1 ^ c[3] ^ k1, lo1]")], [TN.test_philox_known_answers]),
+    # Krylov smoother / solvers (Sec. 4)
+    ("gmres_rhs_squared", oracle.krylov, "gmres_fixed",
+     [("rhs[0] = beta", "rhs[0] = beta * beta")], [TN.test_gmres_full_krylov_is_exact_solve]),
+    ("gmres_projection_conjugated", oracle.krylov, "gmres_fixed",
+     [("H[i, j] = np.vdot(V[i], w)", "H[i, j] = np.vdot(w, V[i])")],
+     [TN.test_gmres_full_krylov_is_exact_solve, TN.test_gmres_minimises_over_krylov_space]),
+    ("gmres_coefficients_conjugated", oracle.krylov, "gmres_fixed",
+     [("x = x + y[i] * V[i]", "x = x + np.conj(y[i]) * V[i]")],
+     [TN.test_gmres_full_krylov_is_exact_solve]),
+    ("fgmres_updates_with_v_not_z", oracle.krylov, "fgmres",
+     [("x = x + y[i] * Z[i]", "x = x + y[i] * V[i]")], [TN.test_gmres_tol_and_fgmres]),
+    # test vectors (Eq. 2), chiral split (Eq. 3), streaming SVD (Alg. 3, Eqs. 6-8)
+    ("test_vector_source_sign", oracle.icsvd, "smooth",
+     [("b = -A(phi.reshape(-1))", "b = A(phi.reshape(-1))")], [TN.test_test_vectors_follow_eq2]),
+    ("chiral_split_spin_offset", oracle.icsvd, "chiral_split",
+     [("vectors[:, :, 2 * a:2 * a + 2, :]", "vectors[:, :, a:a + 2, :]")],
+     [TN.test_chiral_split_places_spins, TN.test_prolongator_is_orthonormal_and_chiral]),
+    ("phi_without_sigma", oracle.icsvd, "icsvd_tiles",
+     [("Phi[j][a] = Uk * Sk[None, :]", "Phi[j][a] = Uk")],
+     [TN.test_icsvd_exact_when_stream_lies_in_rank_k_subspace,
+      TN.test_icsvd_stream_recursion_and_energy_identity]),
+    ("phi_with_sigma_squared", oracle.icsvd, "icsvd_tiles",
+     [("Phi[j][a] = Uk * Sk[None, :]", "Phi[j][a] = Uk * (Sk ** 2)[None, :]")],
+     [TN.test_icsvd_exact_when_stream_lies_in_rank_k_subspace,
+      TN.test_icsvd_stream_recursion_and_energy_identity]),
+    ("stream_memory_dropped", oracle.icsvd, "icsvd_tiles",
+     [("Phi[j][a] = Uk * Sk[None, :]", "Phi[j][a] = Phi[j][a]")],
+     [TN.test_icsvd_stream_recursion_and_energy_identity]),
+    ("keeps_smallest_singular_vectors", oracle.icsvd, "rank_k_svd",
+     [("return U[:, :kk], S[:kk]", "return U[:, -kk:], S[-kk:]")],
+     [TN.test_icsvd_single_stream_is_csvd]),
+    ("phase_not_conjugated", oracle.icsvd, "canonical_phase",
+     [("np.conj(q) / np.where", "q / np.where")],
+     [TN.test_icsvd_singular_values_bounded_by_dense_svd]),
+    # restriction, prolongation, Galerkin operator (Eqs. 4-6), coarse stencil
+    ("restrict_without_conjugate", oracle.coarse, "restrict",
+     [("Ps.conj(), v)", "Ps, v)")], [GAL_A]),
+    ("galerkin_transpose_not_adjoint", oracle.coarse, "galerkin",
+     [("C = np.einsum('xra,xrb->xab', Ps[sl].conj(), B)",
+       "C = np.einsum('xra,xrb->xab', Ps[sl], B)")], [GAL_A, GAL_B]),
+    ("galerkin_backward_projector_sign", oracle.coarse, "galerkin",
+     [("spin = eye + wilson.GAMMA[mu]", "spin = eye - wilson.GAMMA[mu]")], [GAL_A, GAL_B]),
+    ("galerkin_block_crossing_off_by_one", oracle.coarse, "galerkin",
+     [("cross = (xm % block[mu]) == block[mu] - 1", "cross = (xm % block[mu]) == 0")],
+     [GAL_A, GAL_B]),
+    ("galerkin_boundary_phase_dropped", oracle.coarse, "galerkin",
+     [("phase = np.where(wrap, float(bc[mu]), 1.0)", "phase = np.ones(V)")], [GAL_A, GAL_B]),
+    ("galerkin_diagonal_dropped", oracle.coarse, "galerkin",
+     [("np.add.at(X, coarse, np.einsum('xra,xrb->xab', Ps.conj(), Ps))", "pass")],
+     [GAL_A, GAL_B]),
+    ("coarse_apply_neighbours_swapped", oracle.coarse, "coarse_apply",
+     [("vc[nbr[dr]]", "vc[nbr[dr ^ 1]]")], [GAL_B]),
+    ("coarse_neighbour_direction", oracle.coarse, "coarse_neighbours",
+     [("(n[:, mu] + sgn) % cd[mu]", "(n[:, mu] - sgn) % cd[mu]")], [GAL_B]),
+    # K-cycle (Sec. 2.1 end, Sec. 4)
+    ("kcycle_residual_sign", oracle.mg, "TwoLevel.kcycle",
+     [("r = np.asarray(v).reshape(-1) - self.D(e)", "r = self.D(e) - np.asarray(v).reshape(-1)")],
+     [TN.test_kcycle_with_exact_coarse_solve_is_coarse_grid_correction]),
+    ("kcycle_prolongation_dropped", oracle.mg, "TwoLevel.kcycle",
+     [("return e + gmres_fixed(self.D, r, self.post)", "return gmres_fixed(self.D, r, self.post)")],
+     [TN.test_kcycle_with_exact_coarse_solve_is_coarse_grid_correction]),
+    # link-angle gradient of the adjoint
+    ("gradient_backward_projector_sign", oracle.adjoint, "grad_link_angles",
+     [("eye + wilson.GAMMA[mu], t2", "eye - wilson.GAMMA[mu], t2")], [_link_gradient_fd]),
+    ("gradient_neighbour_term_dropped", oracle.adjoint, "grad_link_angles",
+     [("+ np.einsum('xsb,xsb->x', g_b[nb].conj(), t2))", ")")], [_link_gradient_fd]),
+    ("gradient_generator_not_daggered", oracle.adjoint, "grad_link_angles",
+     [("dUd = np.conj(np.swapaxes(dU, 1, 2))", "dUd = np.swapaxes(dU, 1, 2)")],
+     [_link_gradient_fd]),
+]
+
+
+def _lookup(module, qual):
+    obj = module
+    for part in qual.split("."):
+        obj = getattr(obj, part)
+    return obj
+
+
+def _build_mutant(module, qual, subs):
+    orig = _lookup(module, qual)
+    src = textwrap.dedent(inspect.getsource(orig))
+    for old, new in subs:
+        assert src.count(old) == 1, "snippet %r must occur once in %s.%s" % (old, module.__name__, qual)
+        src = src.replace(old, new)
+    ns = {}
+    exec(compile(src, "<mutant of %s.%s>" % (module.__name__, qual), "exec"), module.__dict__, ns)
+    return orig, ns[qual.split(".")[-1]]
+
+
+def _install(monkeypatch, module, qual, orig, mutant):
+    if "." in qual:
+        cls_name, meth = qual.split(".")
+        monkeypatch.setattr(getattr(module, cls_name), meth, mutant)
+        return
+    for name, mod in list(sys.modules.items()):
+        if name == "oracle" or name.startswith("oracle."):
+            if getattr(mod, qual, None) is orig:
+                monkeypatch.setattr(mod, qual, mutant)
+
+
+@pytest.mark.parametrize("mid,module,qual,subs,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(monkeypatch, mid, module, qual, subs, pins):
+    orig, mutant = _build_mutant(module, qual, subs)
+    _install(monkeypatch, module, qual, orig, mutant)
+    caught = []
+    for pin in pins:
+        try:
+            pin()
+        except Exception as e:          # a failed assertion, or a pin that cannot even run
+            caught.append((pin, e))
+            break
+    assert caught, "mutant %s passed every pin meant to catch it" % mid
+
+
+def test_unmutated_pins_pass():
+    """Every pin the mutants are run against holds for the oracle as it stands, so a mutant
+    counts as caught only because of what it changed."""
+    seen = set()
+    for m in MUTANTS:
+        for pin in m[4]:
+            if id(pin) not in seen:
+                seen.add(id(pin))
+                pin()

@@ -149,6 +149,37 @@ def test_icsvd_singular_values_bounded_by_dense_svd():
     assert hist[0].shape[-1] == 4 and hist[1].shape[-1] == 6
 
 
+def test_icsvd_stream_recursion_and_energy_identity():
+    """Stream by stream (Alg. 3, Eqs. 7-8): Phi_s Phi_s^dag is the rank-k spectral truncation
+    of A_s A_s^dag = Phi_{s-1} Phi_{s-1}^dag + Psi_s Psi_s^dag, and the energy identity
+    ||Phi_final||_F^2 + sum_s sum_{i>k} sigma_i(A_s)^2 = sum_s ||Psi_s||_F^2 holds.
+
+    Phi_s is read off the oracle's public output for the first s + 1 streams (P Sigma); the
+    reference route is the Hermitian eigen-decomposition of the Gram matrix, not an SVD."""
+    rng = np.random.default_rng(12)
+    k, n_s = 5, 4
+    tiles = [rng.standard_normal((2, 2, 30, 3 + s)) + 1j * rng.standard_normal((2, 2, 30, 3 + s))
+             for s in range(n_s)]
+    for j in range(2):
+        for a in range(2):
+            G_prev = np.zeros((30, 30), dtype=np.complex128)
+            lost = 0.0
+            for s in range(n_s):
+                Pt, S, _ = icsvd.icsvd_tiles(tiles[:s + 1], k)
+                Phi = Pt[j, a] * S[j, a][None, :]
+                Psi = tiles[s][j, a]
+                lam, vec = np.linalg.eigh(G_prev + Psi @ Psi.conj().T)
+                lam, vec = lam[::-1], vec[:, ::-1]
+                kk = min(k, np.count_nonzero(lam > 1e-9 * lam[0]))
+                trunc = (vec[:, :kk] * lam[:kk]) @ vec[:, :kk].conj().T
+                G = Phi @ Phi.conj().T
+                assert np.abs(G - trunc).max() < 1e-11 * lam[0]
+                lost += lam[kk:].clip(min=0).sum()
+                G_prev = G
+            total = sum(np.vdot(t[j, a], t[j, a]).real for t in tiles)
+            assert abs(np.trace(G_prev).real + lost - total) < 1e-11 * total
+
+
 def test_single_stream_r_equals_k_spans_gram_schmidt_basis():
     """n_s = 1, r = k: the SVD basis spans the same space as block orthonormalisation (Alg. 1)."""
     rng = np.random.default_rng(4)
@@ -265,6 +296,41 @@ def test_two_level_solve_matches_direct_solve():
     xs = np.linalg.solve(D, b)
     assert np.linalg.norm(x - xs) <= 1e-8 * np.linalg.norm(xs)
     assert info['outer'] > 0 and info['coarse'] > 0
+
+
+def test_kcycle_with_exact_coarse_solve_is_coarse_grid_correction():
+    """One K-cycle (Sec. 2.1 end) with the coarse system solved exactly and no post-smoothing
+    is the coarse-grid correction P (P^dag D P)^{-1} P^dag v; with a post-smoother that spans
+    the whole space it is D^{-1} v; with a full-rank P (k = 6 n_d) the correction alone is
+    D^{-1} v and FGMRES stops after one iteration."""
+    dims, block = (4, 2, 2, 2), (2, 2, 2, 2)
+    U, w, bc, Pt, S = _tiny_setup(dims, block, 3, 3, 2)
+    kappa = 0.12
+    n = 12 * wilson.volume(dims)
+    P = icsvd.dense_prolongator(Pt, dims, block)
+    D = wilson.dense_dirac(U, dims, kappa, w, bc)
+    rng = np.random.default_rng(14)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    tl = mg.TwoLevel(U, dims, kappa, w, bc, block, Pt, coarse_tol=1e-14, coarse_restart=64,
+                     post=0)
+    cgc = P @ np.linalg.solve(P.conj().T @ D @ P, P.conj().T @ v)
+    assert np.abs(tl.kcycle(v) - cgc).max() < 1e-10 * np.abs(cgc).max()
+    tl.post = n
+    x = np.linalg.solve(D, v)
+    assert np.abs(tl.kcycle(v) - x).max() < 1e-8 * np.abs(x).max()
+    # full rank: n_d = 2, k = 12
+    dims, block = (2, 2, 2, 2), (2, 1, 1, 1)
+    U = synthetic.haar_links(dims, 5)
+    t = rng.standard_normal((8, 2, 12, 12)) + 1j * rng.standard_normal((8, 2, 12, 12))
+    Pt, S, _ = icsvd.icsvd_tiles([t], 12)
+    tl = mg.TwoLevel(U, dims, kappa, (1, 1, 1, 1), (1, 1, 1, 1), block, Pt, coarse_tol=1e-14,
+                     coarse_restart=200, post=0)
+    D = wilson.dense_dirac(U, dims, kappa)
+    v = rng.standard_normal(192) + 1j * rng.standard_normal(192)
+    x = np.linalg.solve(D, v)
+    assert np.abs(tl.kcycle(v) - x).max() < 1e-10 * np.abs(x).max()
+    xs, info = tl.solve(v, tol=1e-10)
+    assert info['outer'] == 1 and np.linalg.norm(xs - x) < 1e-9 * np.linalg.norm(x)
 
 
 # ----------------------------------------------------------------------------- adjoint

@@ -19,7 +19,8 @@ def test_gamma_algebra_and_chirality():
     assert np.allclose(g5, np.diag([1, 1, -1, -1]))
 
 
-@pytest.mark.parametrize("bc,w", [((1, 1, 1, 1), (1, 1, 1, 1)), ((1, 1, 1, -1), ANISO)])
+@pytest.mark.parametrize("bc,w", [((1, 1, 1, 1), (1, 1, 1, 1)), ((1, 1, 1, -1), ANISO),
+                                  ((-1, 1, 1, 1), (1.0, 0.5, 1.0, 1.0))])
 def test_gamma5_hermiticity_dense(bc, w):
     dims = (4, 2, 2, 2)
     U = synthetic.haar_links(dims, 7)
