@@ -204,6 +204,15 @@ def dslash_32(api, synthetic, dev, flush, peaks, peak_kind, reps=20):
             "algorithmic_bytes": V * 480.0}
 
 
+def bench_config(cfg, world):
+    """The `config` object of the JSON line (both arms): the workload and its parameters."""
+    return {"workload": WORKLOAD, "dims": list(cfg["dims"]), "block": list(cfg["block"]),
+            "k": cfg["k"], "r": cfg["r"], "n_s": cfg["n_s"], "sweeps": cfg["sweeps"],
+            "kappa": cfg["kappa"], "tol": 1e-10, "nrhs": 1,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "256 MB buffer written, then a second 256 MB buffer read, before every timed step"}
+
+
 def workload():
     from paper_2505_14399_gb300 import synthetic
     cfg = dict(synthetic.WORKLOADS[WORKLOAD])
@@ -414,11 +423,7 @@ def gpu_arm(args):
             "vs_baseline": None,
             "dtype": "c64+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "dims": list(dims), "block": list(cfg["block"]),
-                       "k": cfg["k"], "r": cfg["r"], "n_s": cfg["n_s"], "sweeps": cfg["sweeps"],
-                       "kappa": cfg["kappa"], "tol": 1e-10, "nrhs": 1,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "256 MB buffer written, then a second 256 MB buffer read, before every timed step"},
+            "config": bench_config(cfg, world),
             "fp64_seconds": t_fp64,
             "mixed_over_fp64_speedup": t_fp64 / t_mixed,
             "profiled_step_seconds": t_prof,
@@ -554,7 +559,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "dims": list(cfg["dims"])},
+            "data": "synthetic", "config": bench_config(cfg, world),
             "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
