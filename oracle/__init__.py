@@ -16,6 +16,9 @@ for Wilson fermions in lattice QCD", arXiv:2505.14399):
 * ``coarse``   -- restriction R = P^dag, prolongation, the Galerkin operator of Eq. (5)
                   as a nearest-neighbour coarse stencil, and its application.
 * ``mg``       -- the two-level K-cycle preconditioned FGMRES solve of Eq. (1).
+* ``multilevel`` -- the same setup and Galerkin product applied to a coarse operator
+                  (sigma_3 as its chirality) and the K-cycle on every level of a deeper
+                  hierarchy (Sec. 2.1 end, Sec. 4).
 * ``adjoint``  -- gradients of |x|^2, x = D^{-1} b, with respect to b and link angles.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may

@@ -48,16 +48,23 @@ def philox4x32_10(ctr, key):
     return np.stack(c, axis=-1)
 
 
-def gaussian_vectors(seed, vec_ids, volume):
-    """Complex Gaussian spinor fields, shape (len(vec_ids), volume, 4, 3), complex128."""
+def gaussian_field(seed, vec_ids, nsites, ncomp, word3=0):
+    """Complex Gaussian fields, shape (len(vec_ids), nsites, ncomp), complex128.
+
+    Counter (site, component, vector id, word3), key (seed mod 2^32, seed >> 32), then the
+    53-bit uniforms and Box-Muller of the module header.  word3 = 0 for the fine-level
+    spinors; a coarse level of the hierarchy uses its level index, so its fields are
+    independent of the fine ones drawn with the same seed and vector ids.
+    """
     vec_ids = np.asarray(vec_ids, dtype=np.uint64)
     nv = len(vec_ids)
-    s = np.arange(volume, dtype=np.uint64)
-    c = np.arange(12, dtype=np.uint64)
-    ctr = np.zeros((nv, volume, 12, 4), dtype=np.uint64)
+    s = np.arange(nsites, dtype=np.uint64)
+    c = np.arange(ncomp, dtype=np.uint64)
+    ctr = np.zeros((nv, nsites, ncomp, 4), dtype=np.uint64)
     ctr[..., 0] = s[None, :, None]
     ctr[..., 1] = c[None, None, :]
     ctr[..., 2] = vec_ids[:, None, None]
+    ctr[..., 3] = np.uint64(word3)
     key = (seed & MASK, (seed >> 32) & MASK)
     w = philox4x32_10(ctr, key)
     two26 = np.float64(67108864.0)
@@ -68,5 +75,10 @@ def gaussian_vectors(seed, vec_ids, volume):
           + (w[..., 3] >> np.uint64(6)).astype(np.float64)) * scale
     rho = np.sqrt(-2.0 * np.log(1.0 - ua))
     th = 2.0 * np.pi * ub
-    z = rho * np.cos(th) + 1j * (rho * np.sin(th))
-    return z.reshape(nv, volume, 4, 3)
+    return rho * np.cos(th) + 1j * (rho * np.sin(th))
+
+
+def gaussian_vectors(seed, vec_ids, volume):
+    """Complex Gaussian spinor fields, shape (len(vec_ids), volume, 4, 3), complex128
+    (component c = 3 * spin + colour, counter word 3 = 0)."""
+    return gaussian_field(seed, vec_ids, volume, 12, 0).reshape(len(vec_ids), volume, 4, 3)

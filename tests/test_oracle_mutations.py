@@ -20,8 +20,10 @@ import oracle.coarse
 import oracle.icsvd
 import oracle.krylov
 import oracle.mg
+import oracle.multilevel
 import oracle.philox
 import oracle.wilson
+import test_oracle_multilevel as TM
 import test_oracle_numerics as TN
 import test_oracle_wilson as TW
 
@@ -73,6 +75,8 @@ def _galerkin(dims, block):
 
 GAL_A = _galerkin((4, 4, 2, 2), (2, 2, 2, 2))
 GAL_B = _galerkin((6, 2, 2, 4), (2, 2, 1, 2))
+# aggregates of two level-1 sites with two aggregates along x: hops inside and across them
+ML_GAL = lambda: TM.test_coarse_level_galerkin_equals_dense_product(*TM.CASES[2])
 HERM = [lambda: TW.test_gamma5_hermiticity_dense(*ANISO_T)]
 PLANE = [TW.test_plane_wave_momentum_space_form]
 COV = [TW.test_gauge_covariance]
@@ -180,6 +184,26 @@ MUTANTS = [
     ("kcycle_prolongation_dropped", oracle.mg, "TwoLevel.kcycle",
      [("return e + gmres_fixed(self.D, r, self.post)", "return gmres_fixed(self.D, r, self.post)")],
      [TN.test_kcycle_with_exact_coarse_solve_is_coarse_grid_correction]),
+    # deeper levels: chiral SVD and Galerkin product on a coarse operator, multilevel K-cycle
+    ("level_split_half_offset", oracle.multilevel, "chiral_split",
+     [("vectors[:, :, a * k:(a + 1) * k]", "vectors[:, :, a:a + k]")],
+     [TM.test_coarse_chiral_split_places_components]),
+    ("level_prolongator_swaps_chirality", oracle.multilevel, "site_prolongator",
+     [("Ps[:, a, :, a, :] = T[agg, a, local]", "Ps[:, a, :, 1 - a, :] = T[agg, a, local]")],
+     [ML_GAL]),
+    ("level_galerkin_edge_off_by_one", oracle.multilevel, "galerkin",
+     [("edge = block[mu] - 1 if sgn > 0 else 0", "edge = 0 if sgn > 0 else block[mu] - 1")],
+     [ML_GAL]),
+    ("level_galerkin_neighbour_p_at_site", oracle.multilevel, "galerkin",
+     [("Y[dr], Ps[nbr[dr]])", "Y[dr], Ps)")], [ML_GAL]),
+    ("level_restrict_without_conjugate", oracle.multilevel, "restrict",
+     [("Ps.conj(), v)", "Ps, v)")], [ML_GAL]),
+    ("level_test_vector_level_word", oracle.multilevel, "test_vectors",
+     [("gaussian_field(seed, ids, d, n, level)", "gaussian_field(seed, ids, d, n, 0)")],
+     [TM.test_coarse_test_vectors_follow_eq2]),
+    ("multilevel_kcycle_prolongation_dropped", oracle.multilevel, "Hierarchy.kcycle",
+     [("return e + gmres_fixed(D, v - D(e), self.post)", "return gmres_fixed(D, v - D(e), self.post)")],
+     [TM.test_level1_kcycle_with_exact_coarsest_solve_is_coarse_grid_correction]),
     # link-angle gradient of the adjoint
     ("gradient_backward_projector_sign", oracle.adjoint, "grad_link_angles",
      [("eye + wilson.GAMMA[mu], t2", "eye - wilson.GAMMA[mu], t2")], [_link_gradient_fd]),
