@@ -19,6 +19,8 @@ for Wilson fermions in lattice QCD", arXiv:2505.14399):
 * ``multilevel`` -- the same setup and Galerkin product applied to a coarse operator
                   (sigma_3 as its chirality) and the K-cycle on every level of a deeper
                   hierarchy (Sec. 2.1 end, Sec. 4).
+* ``schur``    -- the even-odd Schur-complement form of D x = b (Sec. 1 lists even-odd
+                  preconditioning): D_hat = 1 - kappa^2 H_eo H_oe and the reconstruction.
 * ``adjoint``  -- gradients of |x|^2, x = D^{-1} b, with respect to b and link angles.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may

@@ -22,9 +22,11 @@ import oracle.krylov
 import oracle.mg
 import oracle.multilevel
 import oracle.philox
+import oracle.schur
 import oracle.wilson
 import test_oracle_multilevel as TM
 import test_oracle_numerics as TN
+import test_oracle_schur as TS
 import test_oracle_wilson as TW
 
 ANISO_T = ((1, 1, 1, -1), TW.ANISO)
@@ -204,6 +206,16 @@ MUTANTS = [
     ("multilevel_kcycle_prolongation_dropped", oracle.multilevel, "Hierarchy.kcycle",
      [("return e + gmres_fixed(D, v - D(e), self.post)", "return gmres_fixed(D, v - D(e), self.post)")],
      [TM.test_level1_kcycle_with_exact_coarsest_solve_is_coarse_grid_correction]),
+    # even-odd Schur form
+    ("schur_second_hop_parity", oracle.schur, "schur_op",
+     [("return v - hop(t, links, dims, kappa, 0,", "return v + hop(t, links, dims, kappa, 0,")],
+     [lambda: TS.test_schur_complement_of_the_dense_blocks((1, 1, 1, 1), (1, 1, 1, 1))]),
+    ("schur_rhs_sign", oracle.schur, "prepare",
+     [("return be - hop(bo,", "return be + hop(bo,")],
+     [TS.test_schur_solve_reconstructs_the_full_solution]),
+    ("schur_reconstruction_sign", oracle.schur, "reconstruct",
+     [("xo = bo - hop(x_even,", "xo = bo + hop(x_even,")],
+     [TS.test_schur_solve_reconstructs_the_full_solution]),
     # link-angle gradient of the adjoint
     ("gradient_backward_projector_sign", oracle.adjoint, "grad_link_angles",
      [("eye + wilson.GAMMA[mu], t2", "eye - wilson.GAMMA[mu], t2")], [_link_gradient_fd]),
