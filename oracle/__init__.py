@@ -21,6 +21,8 @@ for Wilson fermions in lattice QCD", arXiv:2505.14399):
                   hierarchy (Sec. 2.1 end, Sec. 4).
 * ``schur``    -- the even-odd Schur-complement form of D x = b (Sec. 1 lists even-odd
                   preconditioning): D_hat = 1 - kappa^2 H_eo H_oe and the reconstruction.
+* ``clover``   -- the Wilson-clover term (the action of Configuration B, Sec. 4): clover-leaf
+                  field strength, sigma_mu_nu F_mu_nu, and D_clover.
 * ``adjoint``  -- gradients of |x|^2, x = D^{-1} b, with respect to b and link angles.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may

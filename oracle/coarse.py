@@ -8,7 +8,8 @@
   1 for -mu), each (2k) x (2k) with rows/columns ordered (alpha, i).  Entry (a, b) of the
   block linking coarse site j to j' is sum_{x in L_j, y in L_j'} P(x)_a^dag D_{x,y} P(y)_b,
   accumulated here term by term over the nonzeros of D:
-    - the diagonal 1 of D contributes P(x)^dag P(x) to X(j(x));
+    - the diagonal 1 of D contributes P(x)^dag P(x) to X(j(x)), and a site-local clover
+      term C(x) (``oracle.clover``), when given, P(x)^dag C(x) P(x);
     - the hop x -> x + mu contributes -kappa w_mu P(x)^dag (1 - gamma_mu) U_mu(x) P(x+mu)
       (with bc[mu] when it wraps the lattice) to X if x+mu stays in the aggregate of x
       and to Y_{+mu}(j(x)) otherwise; the hop x -> x - mu likewise with
@@ -55,8 +56,10 @@ def prolong(Pt, vc, dims, block):
 
 
 def galerkin(Pt, links, dims, block, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1, 1, 1),
-             chunk=4096):
-    """Eq. 5 as a coarse stencil. Returns X (d, 2k, 2k), Y (8, d, 2k, 2k)."""
+             chunk=4096, clover=None):
+    """Eq. 5 as a coarse stencil. Returns X (d, 2k, 2k), Y (8, d, 2k, 2k).
+
+    clover: optional site-local term C (V, 12, 12) of D (the Wilson-clover operator)."""
     coarse, local, cd, nd = block_geometry(dims, block)
     d = Pt.shape[0]
     c = wilson.coords(dims)
@@ -69,6 +72,8 @@ def galerkin(Pt, links, dims, block, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1, 1
     strides = [1, dims[0], dims[0] * dims[1], dims[0] * dims[1] * dims[2]]
     # diagonal of D
     np.add.at(X, coarse, np.einsum('xra,xrb->xab', Ps.conj(), Ps))
+    if clover is not None:
+        np.add.at(X, coarse, np.einsum('xra,xrs,xsb->xab', Ps.conj(), clover, Ps))
     for mu in range(4):
         for sgn in (+1, -1):
             xm = c[:, mu]

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import oracle.adjoint
+import oracle.clover
 import oracle.coarse
 import oracle.icsvd
 import oracle.krylov
@@ -24,6 +25,7 @@ import oracle.multilevel
 import oracle.philox
 import oracle.schur
 import oracle.wilson
+import test_oracle_clover as TC
 import test_oracle_multilevel as TM
 import test_oracle_numerics as TN
 import test_oracle_schur as TS
@@ -216,6 +218,29 @@ MUTANTS = [
     ("schur_reconstruction_sign", oracle.schur, "reconstruct",
      [("xo = bo - hop(x_even,", "xo = bo + hop(x_even,")],
      [TS.test_schur_solve_reconstructs_the_full_solution]),
+    # Wilson-clover term
+    ("sigma_anticommutator", oracle.clover, "sigma",
+     [("0.5j * (g[mu] @ g[nu] - g[nu] @ g[mu])", "0.5j * (g[mu] @ g[nu] + g[nu] @ g[mu])")],
+     [TC.test_sigma_hermitian_and_chiral]),
+    ("field_strength_hermitian_part", oracle.clover, "field_strength",
+     [("f = (Q - _dag(Q)) / 8j", "f = (Q + _dag(Q)) / 8j")], [TC.test_field_strength_of_abelian_fields]),
+    ("field_strength_trace_kept", oracle.clover, "field_strength",
+     [("F[p] = f - (tr / 3.0)[:, None, None] * np.eye(3)", "F[p] = f")],
+     [TC.test_clover_term_is_hermitian_and_chirally_block_diagonal]),
+    ("leaf_two_open", oracle.clover, "field_strength",
+     [("_dag(_at(Um, dims, [(nu, 1), (mu, -1)]))", "_dag(_at(Um, dims, [(nu, 1)]))")],
+     [TC.test_clover_gauge_covariance]),
+    ("leaf_three_last_link_unshifted", oracle.clover, "field_strength",
+     [("@ _at(Un, dims, [(nu, -1)]))", "@ Un)")], [TC.test_clover_gauge_covariance]),
+    ("leaf_four_wrong_corner", oracle.clover, "field_strength",
+     [("_at(Un, dims, [(nu, -1), (mu, 1)])", "_at(Un, dims, [(nu, -1)])")],
+     [TC.test_clover_gauge_covariance]),
+    ("clover_sign", oracle.clover, "clover_term",
+     [("(-kappa * csw) * C", "(kappa * csw) * C")],
+     [TC.test_clover_term_is_hermitian_and_chirally_block_diagonal]),
+    ("galerkin_clover_dropped", oracle.coarse, "galerkin",
+     [("np.add.at(X, coarse, np.einsum('xra,xrs,xsb->xab', Ps.conj(), clover, Ps))", "pass")],
+     [TC.test_galerkin_with_clover_equals_dense_product]),
     # link-angle gradient of the adjoint
     ("gradient_backward_projector_sign", oracle.adjoint, "grad_link_angles",
      [("eye + wilson.GAMMA[mu], t2", "eye - wilson.GAMMA[mu], t2")], [_link_gradient_fd]),
