@@ -353,12 +353,7 @@ int restrict_launch(cplx<R>* vc, const cplx<R>* v, const cplx<R>* P, int k, cons
   dim3 grid(B.d * 2, nrhs);
   size_t sh = sizeof(cplx<R>) * B.M;
   if (sh > 200 * 1024) return fail(MG_EINVAL, "restrict: aggregate too large");
-  static bool set = false;
-  if (!set) {
-    WMG_CUDA(cudaFuncSetAttribute(restrict_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
-    set = true;
-  }
+  WMG_TRY(smem_attr(restrict_kernel<R>, sh));
   ProfScope ps("restrict", (double)sizeof(cplx<R>) * (12.0 * B.nd * B.d * (k + nrhs) + 2.0 * B.d * k * nrhs),
                8.0 * 12 * B.nd * B.d * k * nrhs, st);
   WMG_LAUNCH_DEP(restrict_kernel<R>, grid, 256, sh, st, vc, v, P, k, B);
@@ -389,12 +384,7 @@ template <bool DF, int NE>
 int launch_hop(dim3 grid, size_t sh, cudaStream_t st, zd* Op, zd* Xpart, const zd* P,
                const zdf* Pdf, int k, const zd* links, const zdf* Ldf, const HopGeom& hg,
                const Blocking& B) {
-  static bool set = false;
-  if (!set) {
-    WMG_CUDA(cudaFuncSetAttribute(galerkin_hop_kernel<DF, NE>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    set = true;
-  }
+  WMG_TRY(smem_attr(galerkin_hop_kernel<DF, NE>, sh));
   galerkin_hop_kernel<DF, NE><<<grid, GTH, sh, st>>>(Op, Xpart, P, Pdf, k, links, Ldf, hg, B);
   WMG_LAUNCHED();
   return MG_OK;
@@ -439,15 +429,16 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, con
     WMG_TRY(tile_gram(PtP, P, k, k, B, st, false));
   }
   const bool tc = df64 && galerkin_tc_supported(k, B);
-  // tensor path: the bf16 digit-plane products it issues (28 digit pairs of a (2 (2k)) x (2k)
-  // x 96 real product per 8-site batch, padded tiles, about n_d / 8 + 1 batches per CTA);
-  // otherwise FP64-equivalent flops
+  // flops: the method's work, 768 k^2 FP64-equivalent flops per fine site (4 forward hops x
+  // 6 rows x (2k)^2 complex multiply-adds); the tensor path also records the bf16 digit-plane
+  // products it issues for them (28 digit pairs of a (2 (2k)) x (2k) x 96 real product per
+  // 8-site batch, padded tiles, about n_d / 8 + 1 batches per CTA)
   const double t4 = (k + 3) / 4;
   const double tc_flops = 2.0 * (16 * t4) * (8 * t4) * 96.0 * 28.0 * 4.0 * B.d *
                           ((double)B.nd / 8.0 + 1.0);
   ProfScope ps(tc ? "galerkin_tc" : df64 ? "galerkin_df64" : "galerkin_fp64",
                16.0 * (12.0 * B.nd * B.d * k * 5 + 36.0 * B.nd * B.d),
-               tc ? tc_flops : 768.0 * k * k * B.nd * B.d, st);
+               768.0 * k * k * B.nd * B.d, tc ? tc_flops : 0.0, st);
   if (tc) {
     // tensor pipe (exact digit-plane products); entries outside its fixed-point range (links
     // that are not unitary, a prolongator that is not orthonormal) fall back to the FP32 units

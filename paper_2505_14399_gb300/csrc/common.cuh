@@ -103,13 +103,19 @@ cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // on its own stream; mg_profile_report() aggregates durations with the launch's
 // algorithmic bytes and flops per kernel name.  Disabled: one branch per launch.
 bool prof_enabled();
-void prof_begin(const char* name, double bytes, double flops, cudaStream_t st);
+// bytes, flops: the algorithmic figures of the launch; issued: flops the tensor pipe executes
+// for them, when that differs (exact digit-plane products), else 0
+void prof_begin(const char* name, double bytes, double flops, double issued, cudaStream_t st);
 void prof_end(cudaStream_t st);
 struct ProfScope {
   bool on;
   cudaStream_t st;
   ProfScope(const char* name, double bytes, double flops, cudaStream_t s) : on(prof_enabled()), st(s) {
-    if (on) prof_begin(name, bytes, flops, s);
+    if (on) prof_begin(name, bytes, flops, 0.0, s);
+  }
+  ProfScope(const char* name, double bytes, double flops, double issued, cudaStream_t s)
+      : on(prof_enabled()), st(s) {
+    if (on) prof_begin(name, bytes, flops, issued, s);
   }
   ~ProfScope() {
     if (on) prof_end(st);
@@ -245,6 +251,15 @@ int make_geom(Geom& g, const int dims[4], double kappa, const double w[4], const
               bool need_even);
 
 int num_sms();
+
+// Raises the dynamic shared-memory limit of kernel `fn` on the current device to at least
+// `bytes`: the attribute is per device, so the record of what was set is kept per (device,
+// kernel), under a lock.
+int smem_attr_raw(const void* fn, size_t bytes);
+template <typename F>
+inline int smem_attr(F* fn, size_t bytes) {
+  return smem_attr_raw(reinterpret_cast<const void*>(fn), bytes);
+}
 
 // ------------------------------------------------------------------ host staging
 // A field argument that may live on the host: returns a device pointer (the same

@@ -577,7 +577,11 @@ int dslash_proj_launch(zf* w, zf* V, size_t fs, size_t n, int nrhs, zd* small,
   int nb = (kg.V + RT - 1) / RT;
   if (nb > rw.nblk) nb = rw.nblk;
   const float2* L32 = static_cast<const float2*>(fz.links);
-  double byts = (double)nrhs * kg.V * 8.0 * (12.0 * (nv + 2) + 36.0);
+  // algorithmic bytes: per right-hand side the nv basis columns read (v_j, the stencil input,
+  // is one of them) and w written -- the first step reads b and writes v_0 and w instead --
+  // and the 36 complex link entries of a site once per launch
+  const double fields = b0 ? 3.0 : (double)(nv + 1);
+  double byts = (double)kg.V * 8.0 * (12.0 * fields * nrhs + 36.0);
   ProfScope ps("dslash_proj", byts, (1320.0 + 48.0 * (nv + 1)) * kg.V * nrhs, st);
   if (b0)
     WMG_LAUNCH_DEP((dslash_proj_kernel<4, true>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
@@ -594,16 +598,11 @@ template <int NVM>
 int stream_cgs_launch(zf* w, const zf* V, size_t fs, size_t n, int nrhs, zd* small,
                       SmallLayout L, int j, double* dnorm, double* reshist, ReduceWork& rw,
                       double scale, int* err, bool cgs1, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    int mx = (int)st_smem(NVM);
-    WMG_CUDA(cudaFuncSetAttribute(stream_cgs_kernel<0, NVM>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    WMG_CUDA(cudaFuncSetAttribute(stream_cgs_kernel<1, NVM>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    WMG_CUDA(cudaFuncSetAttribute(stream_cgs_kernel<2, NVM>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    attr = true;
+  {
+    size_t mx = st_smem(NVM);
+    WMG_TRY(smem_attr(stream_cgs_kernel<0, NVM>, mx));
+    WMG_TRY(smem_attr(stream_cgs_kernel<1, NVM>, mx));
+    WMG_TRY(smem_attr(stream_cgs_kernel<2, NVM>, mx));
   }
   int nv = j + 1;
   int per_sm = NVM <= 8 ? 2 : 1;

@@ -147,6 +147,19 @@ void dev_free(void* p) { cached_free(p, false); }
 int host_alloc_bytes(void** p, size_t bytes) { return cached_alloc(p, bytes, true); }
 void host_free(void* p) { cached_free(p, true); }
 
+int smem_attr_raw(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = 0;
+  WMG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{dev, fn}];
+  if (have >= bytes) return MG_OK;
+  WMG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
+  return MG_OK;
+}
+
 int num_sms() {
   static int n = 0;
   if (n == 0) {
@@ -215,7 +228,7 @@ int stage_out_finish(Staged& s, void* p, size_t bytes, cudaStream_t st) {
 namespace {
 struct ProfRec {
   const char* name;
-  double bytes, flops;
+  double bytes, flops, issued;
   int ev0, ev1;
 };
 std::mutex g_prof_mu;
@@ -229,7 +242,7 @@ std::string g_prof_json;
 
 bool prof_enabled() { return g_prof_on; }
 
-void prof_begin(const char* name, double bytes, double flops, cudaStream_t st) {
+void prof_begin(const char* name, double bytes, double flops, double issued, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (g_prof_next + 2 > g_prof_events.size()) {
     g_prof_open.push_back(-1);
@@ -237,7 +250,7 @@ void prof_begin(const char* name, double bytes, double flops, cudaStream_t st) {
   }
   int e0 = (int)g_prof_next++, e1 = (int)g_prof_next++;
   cudaEventRecord(g_prof_events[e0], st);
-  g_prof_recs.push_back({name, bytes, flops, e0, e1});
+  g_prof_recs.push_back({name, bytes, flops, issued, e0, e1});
   g_prof_open.push_back((int)g_prof_recs.size() - 1);
 }
 
@@ -274,7 +287,7 @@ extern "C" const char* mg_profile_report(void) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   struct Agg {
     long long n = 0;
-    double ms = 0, bytes = 0, flops = 0;
+    double ms = 0, bytes = 0, flops = 0, issued = 0;
   };
   std::map<std::string, Agg> agg;
   for (auto& r : g_prof_recs) {
@@ -289,6 +302,7 @@ extern "C" const char* mg_profile_report(void) {
     a.ms += ms;
     a.bytes += r.bytes;
     a.flops += r.flops;
+    a.issued += r.issued;
   }
   std::ostringstream os;
   os << "{";
@@ -297,7 +311,9 @@ extern "C" const char* mg_profile_report(void) {
     if (!first) os << ",";
     first = false;
     os << "\"" << kv.first << "\":{\"launches\":" << kv.second.n << ",\"ms\":" << kv.second.ms
-       << ",\"bytes\":" << kv.second.bytes << ",\"flops\":" << kv.second.flops << "}";
+       << ",\"bytes\":" << kv.second.bytes << ",\"flops\":" << kv.second.flops;
+    if (kv.second.issued > 0) os << ",\"issued_flops\":" << kv.second.issued;
+    os << "}";
   }
   os << "}";
   g_prof_json = os.str();

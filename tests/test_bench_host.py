@@ -12,7 +12,8 @@ def _kern():
     return {
         "coarse_gmres": {"launches": 30, "ms": 20.0, "bytes": 1.0e8, "flops": 0.0},
         "dslash_proj": {"launches": 260, "ms": 13.0, "bytes": 260 * 172e6, "flops": 260 * 8e8},
-        "galerkin_tc": {"launches": 1, "ms": 4.4, "bytes": 1.6e9, "flops": 4.2e14 * 4.4e-3},
+        "galerkin_tc": {"launches": 1, "ms": 4.4, "bytes": 1.6e9, "flops": 1.45e10,
+                        "issued_flops": 4.2e14 * 4.4e-3},
         "svd_gram_df64": {"launches": 5, "ms": 2.8, "bytes": 1.9e9, "flops": 3.0e12 * 2.8e-3},
         "svd_jacobi_df64": {"launches": 4, "ms": 2.2, "bytes": 3.5e7, "flops": 0.0},
         "dslash_c128": {"launches": 3, "ms": 0.7, "bytes": 3 * 126e6, "flops": 3 * 1.73e8},
@@ -40,8 +41,12 @@ def test_each_kernel_against_its_own_unit():
     assert list(kernels)[0] == "coarse_gmres"                    # sorted by time
     assert kernels["coarse_gmres"]["bound"] == "latency" and kernels["coarse_gmres"]["frac"] is None
     assert kernels["svd_jacobi_df64"]["frac"] is None
-    assert kernels["galerkin_tc"]["bound"] == "tensor"
-    assert kernels["galerkin_tc"]["frac"] == pytest.approx(420.0 / PEAKS["bf16_tflops"])
+    # the method's FP64-equivalent flops against the double-float (FP32 / 12) staging peak;
+    # the bf16 digit-plane products it issues against the bf16 tensor peak, as extra fields
+    assert kernels["galerkin_tc"]["bound"] == "alu"
+    assert kernels["galerkin_tc"]["frac"] == pytest.approx(1.45e10 / 4.4e-3 / 1e12 / (ALU["fp32"] / 12))
+    assert kernels["galerkin_tc"]["tensor_issued_TFLOPs"] == pytest.approx(420.0)
+    assert kernels["galerkin_tc"]["tensor_issued_frac_of_bf16"] == pytest.approx(420.0 / PEAKS["bf16_tflops"])
     assert kernels["svd_gram_df64"]["bound"] == "alu"
     assert kernels["svd_gram_df64"]["frac"] == pytest.approx(3.0 / (ALU["fp32"] / 12))
     assert kernels["dslash_c128"]["bound"] == "alu"
