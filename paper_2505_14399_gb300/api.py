@@ -98,7 +98,10 @@ def link_gradient(g_b, x, links, dims, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1,
 class Hierarchy:
     """Owner of an mg_handle: iCSVD prolongator, Galerkin coarse operator, K-cycle solver."""
 
-    def __init__(self, links, p, setup=True):
+    def __init__(self, links, p, setup=True, vectors=None, smooth=False):
+        """setup: run the iCSVD setup (Philox test vectors), else only create the handle.
+        vectors: (n_s r, V, 4, 3) complex128 / complex64 fields for mg_setup_from_vectors
+        (smooth: they are initial guesses phi of Eq. 2, else the test vectors themselves)."""
         self.p = p
         self.dims = tuple(p.dims)
         self.block = tuple(p.block)
@@ -108,6 +111,12 @@ class Hierarchy:
         self.d = self.V // self.nd
         self.device = links.device
         self._h = C.c_void_p()
+        if vectors is not None:
+            vdt = _DT[vectors.dtype]
+            L.check(L.lib().mg_setup_from_vectors(C.byref(self._h), _ptr(links), C.byref(p),
+                                                  _ptr(vectors), vdt, int(bool(smooth)),
+                                                  _stream(links)), "mg_setup_from_vectors")
+            return
         fn = L.lib().mg_setup_streaming_svd if setup else L.lib().mg_create
         L.check(fn(C.byref(self._h), _ptr(links), C.byref(p), _stream(links)),
                 "mg_setup_streaming_svd" if setup else "mg_create")
@@ -201,10 +210,17 @@ class MGSolve(torch.autograd.Function):
     Forward: mg_solve.  Backward (recomputed, nothing stored but b, x): g_b = D^{-dag} g_x
     via mg_solve_adjoint (gamma_5-hermiticity, D^dag = gamma_5 D gamma_5), and the link-angle
     gradient -Re[g_b^dag dD x] for U_mu(y) -> exp(i omega^a T^a) U_mu(y) at omega = 0.
+
+    omega marks the point of differentiation and must be zero: the hierarchy and the solve
+    use the links as given (the rotated links exp(i omega T) U are never formed), so a
+    non-zero omega is rejected rather than silently solved at omega = 0.
     """
 
     @staticmethod
     def forward(ctx, b, omega, hier, links, tol):
+        if omega is not None and bool(torch.any(omega != 0)):
+            raise ValueError("MGSolve: omega must be zero (gradients are taken at the given "
+                             "links; rotate the links and rebuild the hierarchy instead)")
         x, _ = hier.solve(b.contiguous(), tol=tol)
         ctx.hier, ctx.links, ctx.tol = hier, links, tol
         ctx.save_for_backward(x)

@@ -146,3 +146,15 @@ def test_dslash_rejects_bad_arguments_before_any_device_call(lib, dims, bc, pari
                            parity, 0, dtype, nrhs, None)
     assert st == _lib.MG_EINVAL
     assert msg.encode() in lib.mg_last_error()
+
+
+def test_autograd_rejects_nonzero_link_angles():
+    """MGSolve differentiates at the given links (omega = 0); any other omega is an error,
+    raised on the host before any solve."""
+    import torch
+    from paper_2505_14399_gb300 import api
+    b = torch.zeros((1, 16, 4, 3), dtype=torch.complex128)
+    om = torch.zeros((4, 16, 8), dtype=torch.float64)
+    om[1, 3, 2] = 1e-3
+    with pytest.raises(ValueError, match="omega must be zero"):
+        api.mg_solve_autograd(b, om, None, None)
