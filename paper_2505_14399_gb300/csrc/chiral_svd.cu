@@ -561,14 +561,7 @@ int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, do
   // schedule and the rotation flags
   size_t sh = sizeof(zd) * (2 * ce * ce + np) + sizeof(double) * 2 * np +
               sizeof(int) * (2 * (ce - 1) * np + np) + 64;
-  static bool attr_set = false;
-  if (!attr_set) {
-    WMG_CUDA(cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
-    WMG_CUDA(cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  200 * 1024));
-    attr_set = true;
-  }
+  WMG_TRY(smem_attr(df64 ? jacobi_kernel<true> : jacobi_kernel<false>, sh));
   ProfScope ps(df64 ? "svd_jacobi_df64" : "svd_jacobi_fp64", 32.0 * c * c * ntiles, 0.0, st);
   if (df64) jacobi_kernel<true><<<ntiles, GT, sh, st>>>(lam, Vec, G, c, rtol);
   else jacobi_kernel<false><<<ntiles, GT, sh, st>>>(lam, Vec, G, c, rtol);
@@ -581,14 +574,7 @@ int tile_update(void* out, int cmax_out, const void* tiles, int cmax, int c, con
                 bool df64) {
   if (kout > UK || c > MAXC) return fail(MG_EINVAL, "tile_update: too many columns");
   size_t sh = sizeof(zd) * c * kout;
-  static bool attr_set = false;
-  if (!attr_set) {
-    WMG_CUDA(cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  100 * 1024));
-    WMG_CUDA(cudaFuncSetAttribute(update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  100 * 1024));
-    attr_set = true;
-  }
+  WMG_TRY(smem_attr(df64 ? update_kernel<true> : update_kernel<false>, sh));
   ProfScope ps(df64 ? "svd_update_df64" : "svd_update_fp64", 16.0 * B.M * (c + kout) * B.d * 2,
                8.0 * B.M * c * kout * B.d * 2, st);
   if (df64)

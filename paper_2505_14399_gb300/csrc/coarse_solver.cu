@@ -521,8 +521,7 @@ int CoarseSolver<R>::solve(const cplx<R>* Op, const Blocking& B, int k, cplx<R>*
     op_in_smem = 1;
   if (CLayout(restart, spc, n2k, csz, 1, op_in_smem).total <= cap) v_in_smem = 1;
   size_t sh = CLayout(restart, spc, n2k, csz, v_in_smem, op_in_smem).total + 16;
-  WMG_CUDA(cudaFuncSetAttribute(coarse_gmres_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sh));
+  WMG_TRY(smem_attr(coarse_gmres_kernel<R>, sh));
   int per_sm = 0;
   WMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_gmres_kernel<R>, CT, sh));
   if (per_sm < 1 || grid > per_sm * num_sms())

@@ -399,12 +399,7 @@ int launch_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const Ho
               const Blocking& B, int* range_flag, cudaStream_t st) {
   constexpr int NW = tc_warps(T4) * TC_WG;
   size_t sh = tc_smem(T4) + tc_raw_bytes(T4) + tc_table_bytes(B.nd);
-  static size_t set = 0;
-  if (set < sh) {
-    WMG_CUDA(cudaFuncSetAttribute(galerkin_tc_kernel<T4>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-    set = sh;
-  }
+  WMG_TRY(smem_attr(galerkin_tc_kernel<T4>, sh));
   galerkin_tc_kernel<T4><<<dim3(B.d, 4), 32 * NW, sh, st>>>(Op, Xpart, Pdf, k, Ldf, g, B,
                                                             range_flag);
   WMG_LAUNCHED();
