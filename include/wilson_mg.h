@@ -104,6 +104,17 @@ typedef struct mg_params {
                                 pipe as exact bf16 digit products (same accuracy) when
                                 every entry is in range (orthonormal P, unitary links),
                                 else on the FP32 units                                   */
+  int link_compress;         /* link copies of the FP32 / half stencils: 1 keep the first
+                                two rows of each link and rebuild the third as the complex
+                                conjugate of their cross product (exact for SU(3): 12 of
+                                the 18 reals per link are read); 0 keep all three rows;
+                                -1 two rows when every link is SU(3) to 1e-9, else three.
+                                1 on links that are not SU(3) to 1e-9 gives MG_EINVAL.
+                                The FP64 stencil always keeps three rows               */
+  int schur_smoother;        /* 1: the K-cycle post-smoother solves the even-odd Schur
+                                system D_hat e_e = r_e + kappa H_eo r_o with post_smooth
+                                GMRES steps and reconstructs e_o = r_o + kappa H_oe e_e
+                                (even-odd preconditioning, Sec. 1); 0: GMRES on D      */
 } mg_params;
 
 typedef struct mg_solve_info {
@@ -117,7 +128,7 @@ typedef struct mg_solve_info {
 /* Defaults: k = 24, r = 24, n_s = 2, sweeps = 5, post_smooth = 8, coarse_tol = 0.03,
  * coarse_restart = 32, coarse_maxiter = 2000, outer_restart = 16, inner_tol = 1e-5,
  * setup_dtype = MG_C64, solve_dtype = MG_C64, svd_refine = -1, coarse_persistent = 1,
- * fp64_emulation = -1,
+ * fp64_emulation = -1, link_compress = -1, schur_smoother = 0,
  * isotropic periodic. */
 void mg_params_default(mg_params* p);
 
@@ -165,6 +176,20 @@ int wilson_dslash(void* out, const void* in, const void* links, const int dims[4
                   int parity, int dagger, int dtype, int nrhs, void* stream);
 
 /* ---------------------------------------------------------------------------------
+ * wilson_schur -- the even-odd Schur complement of D (even-odd preconditioning, Sec. 1):
+ *   out_e = D_hat in_e = in_e - kappa^2 H_eo H_oe in_e   (dagger: D_hat^dag in_e),
+ * where -kappa H_{p,1-p} is the single-parity hop of wilson_dslash(parity = p).  With it,
+ * D x = b is solved as D_hat x_e = b_e + kappa H_eo b_o, x_o = b_o + kappa H_oe x_e.
+ *   in, out: even half-lattice fields of V/2 sites (checkerboard index site / 2), nrhs of
+ *   them; links: [mu][site][3][3] in the same dtype; every dims[mu] even.
+ * Allocates one odd half-lattice temporary on `stream` (stream-ordered).
+ * Returns MG_EINVAL for bad dims / dtype / nrhs < 1 / NULL or aliased pointers.
+ * ------------------------------------------------------------------------------- */
+int wilson_schur(void* out, const void* in, const void* links, const int dims[4],
+                 double kappa, const double hop_weight[4], const int bc_phase[4],
+                 int dagger, int dtype, int nrhs, void* stream);
+
+/* ---------------------------------------------------------------------------------
  * mg_setup_streaming_svd -- Algorithm 4 up to P: iCSVD (Algorithm 3) on the fine
  * operator.  For s = 0..n_s-1: r Philox complex-Gaussian phi_i (vector ids s*r+i),
  * psi_i = phi_i + GMRES_sweeps(D, -D phi_i) (Eq. 2); chiral split into aggregates
@@ -178,6 +203,24 @@ int wilson_dslash(void* out, const void* in, const void* links, const int dims[4
  * ------------------------------------------------------------------------------- */
 int mg_setup_streaming_svd(mg_handle** h, const void* links, const mg_params* p,
                            void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * mg_setup_from_vectors -- the same iCSVD setup (Algorithm 3) on vectors the caller
+ * supplies instead of the Philox fields: stream s takes fields s*r .. s*r+r-1 of
+ *   vectors: n_s * r fields [field][site][4][3], complex double (vec_dtype MG_C128) or
+ *            complex float (MG_C64), device or host memory, read only during the call;
+ *   smooth = 1: each field is an initial guess phi, smoothed into psi = phi +
+ *            GMRES_sweeps(D, -D phi) (Eq. 2) in setup_dtype arithmetic;
+ *   smooth = 0: each field is used as the test vector psi itself (Eq. 3 split onward).
+ * The fields are rounded to setup_dtype first (an MG_C64 field is exact in either), and
+ * the SVD then runs exactly as in mg_setup_streaming_svd (same arithmetic, same kernels):
+ * this is how the streaming SVD of a given set of test vectors is checked against a
+ * reference, and how an application supplies its own near-null vectors.
+ * MG_EINVAL: as mg_setup_streaming_svd, plus NULL vectors, vec_dtype other than MG_C128 /
+ * MG_C64, smooth other than 0 / 1.  Creates *h (NULL on entry); synchronises `stream`.
+ * ------------------------------------------------------------------------------- */
+int mg_setup_from_vectors(mg_handle** h, const void* links, const mg_params* p,
+                          const void* vectors, int vec_dtype, int smooth, void* stream);
 
 /* Creates a handle with links and parameters but no prolongator (for mg_set_prolongator). */
 int mg_create(mg_handle** h, const void* links, const mg_params* p, void* stream);
@@ -195,8 +238,8 @@ int coarse_build(mg_handle* h, void* stream);
  * library allocate device memory while they run -- e.g. an application that has handed
  * nearly all of HBM to its own pool allocator (a library cudaMalloc would then fail or
  * fragment that pool), or one that must keep a fixed device-memory footprint after
- * start-up.  It recomputes D_c = P^dag D P (Eq. 5) into the handle's existing
- * coarse-operator storage, e.g. after mg_set_prolongator.
+ * start-up.  It performs the same coarse-operator rebuild as coarse_build, into the
+ * handle's existing coarse-operator storage, e.g. after mg_set_prolongator.
  *   Scratch: the Galerkin forward-hop partials, 4 * d * (2k)^2 complex doubles
  *     (d = coarse sites), live in one fixed 24 MiB device array inside the library, so
  *     d * k^2 must not exceed 98304 (the 16^3x32 lattice with 4^4 aggregates fits up to
@@ -208,7 +251,9 @@ int coarse_build(mg_handle* h, void* stream);
  *     MG_EINVAL.
  *   Set-up: the first call on each device looks up the device address of the scratch
  *     array (once, with that device current) and caches it; make that first call before
- *     any stream capture begins.
+ *     any stream capture begins.  Like every other device state of the library (handles,
+ *     its allocation cache), the cached address belongs to the device's primary context:
+ *     a cudaDeviceReset of that device while the library is loaded invalidates it.
  *   Concurrency: the scratch is shared by every handle of the process on a device, so
  *     calls on the same device must not overlap (e.g. from two host threads): two
  *     overlapping calls race on the scratch and both results are undefined.
@@ -248,6 +293,10 @@ int mg_test_vectors(void* out, const void* links, const mg_params* p, int stream
  * MG_F16 / MG_BF16 fields (half links) on a handle whose solve_dtype is that type. */
 int mg_apply_fine(mg_handle* h, void* out, const void* in, int nrhs, int dtype, int dagger,
                   void* stream);
+
+/* Rows per link kept by the handle's FP32 / half stencil copies (2 or 3; link_compress);
+ * 0 for a NULL handle. */
+int mg_link_rows(const mg_handle* h);
 
 /* P tiles: P[j][alpha][i][row], row = (local site * 2 + spin in chirality) * 3 + colour,
  * local site lexicographic inside the aggregate; complex double.  sigma[j][alpha][k]

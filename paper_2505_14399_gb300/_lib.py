@@ -39,6 +39,8 @@ class MgParams(C.Structure):
         ("svd_refine", C.c_int),
         ("coarse_persistent", C.c_int),
         ("fp64_emulation", C.c_int),
+        ("link_compress", C.c_int),
+        ("schur_smoother", C.c_int),
     ]
 
 
@@ -67,7 +69,11 @@ SIGNATURES = {
     "mg_profile_report": (C.c_char_p, []),
     "wilson_dslash": (I, [P, P, P, C.POINTER(C.c_int), D, C.POINTER(C.c_double),
                           C.POINTER(C.c_int), I, I, I, I, P]),
+    "wilson_schur": (I, [P, P, P, C.POINTER(C.c_int), D, C.POINTER(C.c_double),
+                         C.POINTER(C.c_int), I, I, I, P]),
     "mg_setup_streaming_svd": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),
+    "mg_setup_from_vectors": (I, [C.POINTER(P), P, C.POINTER(MgParams), P, I, I, P]),
+    "mg_link_rows": (I, [P]),
     "mg_create": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),
     "coarse_build": (I, [P, P]),
     "coarse_build_noalloc": (I, [P, P]),

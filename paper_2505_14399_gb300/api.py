@@ -33,7 +33,8 @@ def _ptr(t):
 def params(dims, block, kappa, k, r, n_s, sweeps=5, seed=3000, hop_weight=(1, 1, 1, 1),
            bc=(1, 1, 1, 1), setup_dtype="c64", solve_dtype="c64", post_smooth=8,
            coarse_tol=0.03, coarse_restart=32, coarse_maxiter=2000, outer_restart=16,
-           inner_tol=1e-5, svd_refine=-1, coarse_persistent=1, fp64_emulation=-1):
+           inner_tol=1e-5, svd_refine=-1, coarse_persistent=1, fp64_emulation=-1,
+           link_compress=-1, schur_smoother=0):
     """Build an mg_params structure (paper symbols k, r, n_s; aggregates of extent `block`)."""
     p = L.MgParams()
     L.lib().mg_params_default(C.byref(p))
@@ -56,6 +57,8 @@ def params(dims, block, kappa, k, r, n_s, sweeps=5, seed=3000, hop_weight=(1, 1,
     p.svd_refine = int(svd_refine)
     p.coarse_persistent = int(coarse_persistent)
     p.fp64_emulation = int(fp64_emulation)
+    p.link_compress = int(link_compress)
+    p.schur_smoother = int(schur_smoother)
     return p
 
 
@@ -73,6 +76,22 @@ def dslash(inp, links, dims, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1, 1, 1), pa
     L.check(L.lib().wilson_dslash(_ptr(out), _ptr(inp), _ptr(links), L.ivec(dims), float(kappa),
                                   L.dvec(hop_weight), L.ivec(bc), int(parity), int(dagger), dt,
                                   int(nrhs), _stream(inp)), "wilson_dslash")
+    return out
+
+
+def schur(inp, links, dims, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1, 1, 1), dagger=False,
+          out=None):
+    """out = D_hat in (even-odd Schur complement) on even half-lattice fields."""
+    dt = _DT[inp.dtype]
+    if links.dtype != inp.dtype:
+        raise ValueError("links and fields must share a dtype")
+    if out is None:
+        out = torch.empty_like(inp)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    nrhs = inp.numel() // ((V // 2) * 12 * (2 if dt >= L.MG_F16 else 1))
+    L.check(L.lib().wilson_schur(_ptr(out), _ptr(inp), _ptr(links), L.ivec(dims), float(kappa),
+                                 L.dvec(hop_weight), L.ivec(bc), int(dagger), dt, int(nrhs),
+                                 _stream(inp)), "wilson_schur")
     return out
 
 

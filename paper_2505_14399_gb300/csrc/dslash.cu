@@ -5,6 +5,9 @@
 // chiral basis, multiplies by U_mu(x) or U_mu(x-mu)^dag, and reconstructs the lower
 // spin pair from the upper one.  Spinor loads are 16-byte vector loads of the
 // [site][spin][colour] layout; links are read through the read-only path.
+#include <cstring>
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "stencil.cuh"
@@ -188,15 +191,23 @@ int launch_typed(void* out, const void* in, const void* links, const Geom& g, in
     if (layout == 0) {
       if (dagger) launch_variant<S, 1, 0>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
       else launch_variant<S, 0, 0>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
-    } else {
+    } else if (layout == 1) {
       if (dagger) launch_variant<S, 1, 1>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
       else launch_variant<S, 0, 1>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+    } else if constexpr (!std::is_same<S, StC128>::value) {
+      // two stored rows (FP32 and half storage only: the FP64 stencil is bound by its FMA
+      // rate, where rebuilding the third row would cost more than the bytes it saves)
+      if (dagger) launch_variant<S, 1, 2>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
+      else launch_variant<S, 0, 2>(v, out, in, links, k, parity, nsites, nrhs, st, in_stride, out_stride);
     }
   };
+  if (layout == 2 && std::is_same<S, StC128>::value)
+    return fail(MG_EINVAL, "dslash: two-row links are not used with complex double fields");
   int v = tuned_variant(dtype + 16 * layout, parity, dagger, g.V, nrhs, st,
                         nrhs > 1 ? kNumShapes : kNumSingle, run);
   if (v < 0) return fail(MG_ECUDA, "dslash autotune failed");
-  // algorithmic bytes: in + out spinors per rhs and each link once (parity: all 4V links)
+  // algorithmic bytes: in + out spinors per rhs and each link once (parity: all 4V links),
+  // 18 reals per link whatever the stored form
   double real_bytes = (double)sizeof(typename S::real) * (sizeof(typename S::elem) == 4 ? 0.5 : 1.0);
   double per_site = parity < 0 ? 48.0 * nrhs + 72.0 : 48.0 * nrhs + 144.0;
   ProfScope ps(dtype == MG_C128 ? "dslash_c128" : dtype == MG_C64 ? "dslash_c64"
@@ -208,14 +219,14 @@ int launch_typed(void* out, const void* in, const void* links, const Geom& g, in
 }
 
 template <typename E>
-__global__ void link_to_lanes_kernel(E* dst, const zd* __restrict__ src, int V) {
+__global__ void link_to_lanes_kernel(E* dst, const zd* __restrict__ src, int V, int ne) {
   typedef typename VecT<E>::R R;
-  size_t total = (size_t)4 * V * 9;
+  size_t total = (size_t)4 * V * ne;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
-    // e enumerates the destination [mu][entry][site]
+    // e enumerates the destination [mu][entry][site], entries 0 .. ne - 1 (row-major)
     size_t site = e % V, rest = e / V;
-    int entry = (int)(rest % 9), mu = (int)(rest / 9);
+    int entry = (int)(rest % ne), mu = (int)(rest / ne);
     zd v = src[((size_t)mu * V + site) * 9 + entry];
     VecT<E>::st(dst, e, cplx<R>{(R)v.re, (R)v.im});
   }
@@ -224,17 +235,62 @@ __global__ void link_to_lanes_kernel(E* dst, const zd* __restrict__ src, int V) 
 }  // namespace
 
 template <typename E>
-int link_to_lanes_v(E* dst, const zd* src, int V, cudaStream_t st) {
-  size_t total = (size_t)4 * V * 9;
+int link_to_lanes_v(E* dst, const zd* src, int V, cudaStream_t st, int rows) {
+  size_t total = (size_t)4 * V * 3 * rows;
   size_t g = (total + 255) / 256, cap = (size_t)num_sms() * 16;
-  link_to_lanes_kernel<E><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(dst, src, V);
+  link_to_lanes_kernel<E><<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(dst, src, V, 3 * rows);
   WMG_LAUNCHED();
   return MG_OK;
 }
-template int link_to_lanes_v<zd>(zd*, const zd*, int, cudaStream_t);
-template int link_to_lanes_v<zf>(zf*, const zd*, int, cudaStream_t);
-template int link_to_lanes_v<zh>(zh*, const zd*, int, cudaStream_t);
-template int link_to_lanes_v<zbf>(zbf*, const zd*, int, cudaStream_t);
+template int link_to_lanes_v<zd>(zd*, const zd*, int, cudaStream_t, int);
+template int link_to_lanes_v<zf>(zf*, const zd*, int, cudaStream_t, int);
+template int link_to_lanes_v<zh>(zh*, const zd*, int, cudaStream_t, int);
+template int link_to_lanes_v<zbf>(zbf*, const zd*, int, cudaStream_t, int);
+
+namespace {
+// Largest deviation of any link from SU(3): max over links of max(|U U^dag - 1|_max,
+// |det U - 1|), as the bits of a non-negative double (ordered like the values) in *out.
+__global__ void su3_deviation_kernel(unsigned long long* out, const zd* __restrict__ L, size_t n) {
+  double worst = 0;
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (size_t)gridDim.x * blockDim.x) {
+    zd u[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) u[i] = L[l * 9 + i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        zd s = {0, 0};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s = s + u[a * 3 + c] * conj(u[b * 3 + c]);
+        if (a == b) s.re -= 1.0;
+        worst = fmax(worst, fmax(fabs(s.re), fabs(s.im)));
+      }
+    zd det = u[0] * (u[4] * u[8] - u[5] * u[7]) - u[1] * (u[3] * u[8] - u[5] * u[6]) +
+             u[2] * (u[3] * u[7] - u[4] * u[6]);
+    det.re -= 1.0;
+    worst = fmax(worst, sqrt(det.re * det.re + det.im * det.im));
+  }
+  if (!(worst == worst)) worst = 1e300;   // NaN: not SU(3)
+  atomicMax(out, (unsigned long long)__double_as_longlong(worst));
+}
+}  // namespace
+
+int su3_deviation(double* dev_out, const zd* links, size_t nlinks, cudaStream_t st) {
+  unsigned long long* d = nullptr;
+  WMG_CUDA(cudaMallocAsync(&d, sizeof(*d), st));
+  WMG_CUDA(cudaMemsetAsync(d, 0, sizeof(*d), st));
+  size_t g = (nlinks + 255) / 256, cap = (size_t)num_sms() * 8;
+  su3_deviation_kernel<<<(unsigned)(g < cap ? (g < 1 ? 1 : g) : cap), 256, 0, st>>>(d, links, nlinks);
+  WMG_LAUNCHED();
+  unsigned long long bits = 0;
+  WMG_CUDA(cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  cudaFreeAsync(d, st);
+  std::memcpy(dev_out, &bits, sizeof(double));
+  return MG_OK;
+}
 
 int dslash_launch(int dtype, void* out, const void* in, const void* links, const Geom& g,
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,

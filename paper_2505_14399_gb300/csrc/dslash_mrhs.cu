@@ -2,6 +2,8 @@
 // once and applied to NR spinors (the test-vector streams of the setup smoothing, Eq. 2, and
 // batched solves), so link bytes are shared across the right-hand sides and every thread
 // keeps NR independent neighbour loads in flight per hop.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "stencil.cuh"
@@ -153,9 +155,12 @@ void launch_dslash_mrhs(int nr, int dagger, int layout, void* out, const void* i
   if (layout == 0) {
     if (dagger) launch_dl<S, 1, 0>(nr, out, in, links, k, parity, nsites, nrhs, st, is, os);
     else launch_dl<S, 0, 0>(nr, out, in, links, k, parity, nsites, nrhs, st, is, os);
-  } else {
+  } else if (layout == 1) {
     if (dagger) launch_dl<S, 1, 1>(nr, out, in, links, k, parity, nsites, nrhs, st, is, os);
     else launch_dl<S, 0, 1>(nr, out, in, links, k, parity, nsites, nrhs, st, is, os);
+  } else if constexpr (!std::is_same<S, StC128>::value) {
+    if (dagger) launch_dl<S, 1, 2>(nr, out, in, links, k, parity, nsites, nrhs, st, is, os);
+    else launch_dl<S, 0, 2>(nr, out, in, links, k, parity, nsites, nrhs, st, is, os);
   }
 }
 

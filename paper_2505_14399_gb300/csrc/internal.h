@@ -12,17 +12,22 @@ namespace wmg {
 
 // ------------------------------------------------------------------ Dslash
 // in/out strides are in complex elements between right-hand sides (0 = field size).
-// link_layout 0: ABI [mu][site][3][3]; 1: lane-contiguous [mu][9][site] (link_to_lanes).
+// link_layout 0: ABI [mu][site][3][3]; 1: lane-contiguous [mu][9][site] (link_to_lanes);
+// 2: lane-contiguous first two rows [mu][6][site], third row rebuilt (SU(3) links, not C128).
 int dslash_launch(int dtype, void* out, const void* in, const void* links, const Geom& g,
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,
                   size_t out_stride, int link_layout = 0);
-// dst[mu][e][site] = src[mu][site][e] (e < 9), converting complex double to E (vec.cuh).
+// dst[mu][e][site] = src[mu][site][e] (e < 3 rows, rows 3 or 2), converting complex double to E
+// (vec.cuh); link_layout 1 reads rows = 3, link_layout 2 rows = 2.
 template <typename E>
-int link_to_lanes_v(E* dst, const zd* src, int V, cudaStream_t st);
+int link_to_lanes_v(E* dst, const zd* src, int V, cudaStream_t st, int rows = 3);
 template <typename To>
-inline int link_to_lanes(cplx<To>* dst, const zd* src, int V, cudaStream_t st) {
-  return link_to_lanes_v<cplx<To>>(dst, src, V, st);
+inline int link_to_lanes(cplx<To>* dst, const zd* src, int V, cudaStream_t st, int rows = 3) {
+  return link_to_lanes_v<cplx<To>>(dst, src, V, st, rows);
 }
+// *dev = the largest deviation of the nlinks 3x3 complex-double links from SU(3):
+// max(|U U^dag - 1|_max, |det U - 1|) (synchronises st).
+int su3_deviation(double* dev, const zd* links, size_t nlinks, cudaStream_t st);
 
 // Autotuned launch shape for a kernel with `nvar` candidate shapes; `run(v)` launches
 // shape v on the caller's arguments.  Returns the chosen shape or -1 on a CUDA error.
@@ -139,6 +144,7 @@ using Op = OpV<cplx<R>>;
 struct FusedStencil {
   const void* links;
   Geom g;
+  int layout = 1;   // 1: [mu][9][site]; 2: first two rows [mu][6][site] (SU(3) links)
 };
 
 template <typename E>
@@ -304,6 +310,19 @@ int to_df(zdf* out, const zd* in, size_t n, cudaStream_t st);
 template <typename R>
 int coarse_apply_launch(cplx<R>* y, const cplx<R>* x, const cplx<R>* Op, int k, const Blocking& B,
                         int nrhs, cudaStream_t st);
+
+// ------------------------------------------------------------------ even-odd (Schur) form
+// even/odd half-lattice fields (checkerboard index site / 2) of nrhs full-lattice fields;
+// split skips a NULL output
+template <typename E>
+int eo_split(E* even, E* odd, const E* full, const Geom& g, int nrhs, cudaStream_t st);
+template <typename E>
+int eo_join(E* full, const E* even, const E* odd, const Geom& g, int nrhs, cudaStream_t st);
+// out = D_hat in = (1 - kappa^2 H_eo H_oe) in on even fields (dagger: D_hat^dag); tmp: odd
+// field per rhs; links in `layout` (dslash_launch)
+template <typename E>
+int schur_apply(E* out, const E* in, E* tmp, const void* links, int layout, const Geom& g,
+                int dagger, int nrhs, cudaStream_t st);
 
 // ------------------------------------------------------------------ gradient
 int link_gradient_launch(double* out, const zd* gb, const zd* x, const zd* links, const Geom& g,

@@ -476,8 +476,8 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
 // thread's own site do not depend on the stencil, so they overlap its latency-bound hops,
 // and w is not read back.  One thread per site and rhs row (blockIdx.y), a grid-stride
 // over 256-site blocks.
-template <int NVM, bool FIRST>
-__global__ void __launch_bounds__(RT)
+template <int NVM, bool FIRST, int LL>
+__global__ void __launch_bounds__(RT, 2)
 dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
                    const float2* __restrict__ links, stencil::KGeom g, zd* small, SmallLayout L,
                    double* wnorm, double* partial, unsigned* counter, int maxvec,
@@ -508,10 +508,10 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
     zf acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
-    hop_pair<0, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
-    hop_pair<1, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
-    hop_pair<2, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
-    hop_pair<3, 0, StC64, 1>(g, site, c, vin, 0, false, links, acc);
+    hop_pair<0, 0, StC64, LL>(g, site, c, vin, 0, false, links, acc);
+    hop_pair<1, 0, StC64, LL>(g, site, c, vin, 0, false, links, acc);
+    hop_pair<2, 0, StC64, LL>(g, site, c, vin, 0, false, links, acc);
+    hop_pair<3, 0, StC64, LL>(g, site, c, vin, 0, false, links, acc);
     zf p[12], x0[12];
     SiteIO<StC64>::load(vin, (size_t)site, x0);
     const float mk = (float)(-g.kappa);
@@ -568,6 +568,21 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
   }
 }
 
+template <int LL>
+int launch_proj(int nv, bool first, int nb, int nrhs, cudaStream_t st, zf* w, zf* V, size_t fs,
+                size_t n, const float2* L32, const stencil::KGeom& kg, zd* small, SmallLayout L,
+                double* dnorm, ReduceWork& rw, const zf* b0, const double* beta0) {
+  if (first)
+    WMG_LAUNCH_DEP((dslash_proj_kernel<4, true, LL>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
+  else if (nv <= 4)
+    WMG_LAUNCH_DEP((dslash_proj_kernel<4, false, LL>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
+  else if (nv <= 8)
+    WMG_LAUNCH_DEP((dslash_proj_kernel<8, false, LL>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
+  else
+    WMG_LAUNCH_DEP((dslash_proj_kernel<16, false, LL>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
+  return MG_OK;
+}
+
 int dslash_proj_launch(zf* w, zf* V, size_t fs, size_t n, int nrhs, zd* small,
                        SmallLayout L, int j, double* dnorm, ReduceWork& rw,
                        const FusedStencil& fz, cudaStream_t st, const zf* b0 = nullptr,
@@ -583,15 +598,8 @@ int dslash_proj_launch(zf* w, zf* V, size_t fs, size_t n, int nrhs, zd* small,
   const double fields = b0 ? 3.0 : (double)(nv + 1);
   double byts = (double)kg.V * 8.0 * (12.0 * fields * nrhs + 36.0);
   ProfScope ps("dslash_proj", byts, (1320.0 + 48.0 * (nv + 1)) * kg.V * nrhs, st);
-  if (b0)
-    WMG_LAUNCH_DEP((dslash_proj_kernel<4, true>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
-  else if (nv <= 4)
-    WMG_LAUNCH_DEP((dslash_proj_kernel<4, false>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
-  else if (nv <= 8)
-    WMG_LAUNCH_DEP((dslash_proj_kernel<8, false>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
-  else
-    WMG_LAUNCH_DEP((dslash_proj_kernel<16, false>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
-  return MG_OK;
+  if (fz.layout == 2) return launch_proj<2>(nv, b0 != nullptr, nb, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0);
+  return launch_proj<1>(nv, b0 != nullptr, nb, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0);
 }
 
 template <int NVM>

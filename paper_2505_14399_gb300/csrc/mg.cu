@@ -24,6 +24,7 @@ struct mg_handle {
   zd* links64L = nullptr;      // lane-contiguous [mu][9][site] copies for the stencil
   zf* links32L = nullptr;
   void* links16L = nullptr;    // half-storage solve: zh or zbf lane-contiguous links
+  int llay = 1;                // layout of links32L / links16L: 1 three rows, 2 two rows
   zd* P64 = nullptr;
   zf* P32 = nullptr;
   double* sigma = nullptr;   // [tile][k]
@@ -44,6 +45,9 @@ struct mg_handle {
   CoarseSolver<float> csol32;
   GmresV<zh> posth;            // half-storage post-smoother (solve_dtype MG_F16)
   GmresV<zbf> postb;           // (solve_dtype MG_BF16)
+  Gmres<double> posts64;       // Schur-form post-smoother on even half-lattice fields
+  Gmres<float> posts32;
+  void* sbuf[5] = {};          // its half-lattice fields: r_e, r_o, r_hat, x_e, odd temporary
   void *kwh = nullptr, *keh = nullptr;
   zd *x64 = nullptr, *r64 = nullptr, *t64 = nullptr;
   zf *e32 = nullptr, *r32 = nullptr;
@@ -93,6 +97,8 @@ int validate(const mg_params* p, bool need_svd) {
       p->solve_dtype != MG_BF16)
     return fail(MG_EINVAL, "solve_dtype must be MG_C128, MG_C64, MG_F16 or MG_BF16");
   if (p->post_smooth < 0 || p->post_smooth > 64) return fail(MG_EINVAL, "post_smooth in [0, 64]");
+  if (p->schur_smoother && p->solve_dtype != MG_C128 && p->solve_dtype != MG_C64)
+    return fail(MG_EINVAL, "schur_smoother needs solve_dtype MG_C128 or MG_C64");
   if (p->coarse_restart < 1 || p->coarse_restart > 128) return fail(MG_EINVAL, "coarse_restart in [1, 128]");
   if (p->outer_restart < 1 || p->outer_restart > 128) return fail(MG_EINVAL, "outer_restart in [1, 128]");
   if (!(p->coarse_tol > 0 && p->coarse_tol < 1)) return fail(MG_EINVAL, "coarse_tol in (0, 1)");
@@ -117,16 +123,28 @@ int create_handle(mg_handle** out, const void* links, const mg_params* p, bool n
   size_t lb = (size_t)4 * h->g.V * 9;
   WMG_TRY(dev_alloc(&h->links64, lb * sizeof(zd)));
   WMG_TRY(dev_alloc(&h->links64L, lb * sizeof(zd)));
-  WMG_TRY(dev_alloc(&h->links32L, lb * sizeof(zf)));
   Staged sl;
   WMG_TRY(stage_in(sl, links, lb * sizeof(zd), st));
   WMG_CUDA(cudaMemcpyAsync(h->links64, sl.dev, lb * sizeof(zd), cudaMemcpyDeviceToDevice, st));
   WMG_TRY(link_to_lanes<double>(h->links64L, h->links64, h->g.V, st));
-  WMG_TRY(link_to_lanes<float>(h->links32L, h->links64, h->g.V, st));
+  // the FP32 / half stencil copies keep two rows per link when the links are SU(3)
+  int rows = 3;
+  if (p->link_compress != 0) {
+    double dev = 0;
+    WMG_TRY(su3_deviation(&dev, h->links64, (size_t)4 * h->g.V, st));
+    if (dev <= 1e-9) rows = 2;
+    else if (p->link_compress > 0)
+      return fail(MG_EINVAL, "link_compress = 1 needs SU(3) links (deviation " +
+                                 std::to_string(dev) + " > 1e-9)");
+  }
+  h->llay = rows == 2 ? 2 : 1;
+  size_t lbc = (size_t)4 * h->g.V * 3 * rows;
+  WMG_TRY(dev_alloc(&h->links32L, lbc * sizeof(zf)));
+  WMG_TRY(link_to_lanes<float>(h->links32L, h->links64, h->g.V, st, rows));
   if (p->solve_dtype == MG_F16 || p->solve_dtype == MG_BF16) {
-    WMG_TRY(dev_alloc(&h->links16L, lb * 4));
-    if (p->solve_dtype == MG_F16) WMG_TRY(link_to_lanes_v<zh>((zh*)h->links16L, h->links64, h->g.V, st));
-    else WMG_TRY(link_to_lanes_v<zbf>((zbf*)h->links16L, h->links64, h->g.V, st));
+    WMG_TRY(dev_alloc(&h->links16L, lbc * 4));
+    if (p->solve_dtype == MG_F16) WMG_TRY(link_to_lanes_v<zh>((zh*)h->links16L, h->links64, h->g.V, st, rows));
+    else WMG_TRY(link_to_lanes_v<zbf>((zbf*)h->links16L, h->links64, h->g.V, st, rows));
   }
   size_t ntile = (size_t)h->B.d * 2;
   WMG_TRY(dev_alloc(&h->P64, ntile * h->k * h->B.M * sizeof(zd)));
@@ -148,29 +166,55 @@ int create_handle(mg_handle** out, const void* links, const mg_params* p, bool n
   return MG_OK;
 }
 
-// b = -D phi ; psi = phi + GMRES_sweeps(D, b)   (Eq. 2) for r fields, in precision R
+// Caller-supplied vectors of mg_setup_from_vectors: n_s r fields on the device, stream s
+// using fields s r .. s r + r - 1; smooth = 1: they are the initial guesses phi of Eq. 2,
+// 0: they are the test vectors psi themselves.
+struct SetupSource {
+  const void* fields;
+  int dtype;
+  int smooth;
+};
+
+// b = -D phi ; psi = phi + GMRES_sweeps(D, b)   (Eq. 2) for r fields, in precision R; phi is
+// the stream's Philox field, or the caller's fields when src is given
 template <typename R>
 int smooth_stream(mg_handle* h, cplx<R>* psi, cplx<R>* phi, cplx<R>* tmp, Gmres<R>& gm, int s,
-                  cudaStream_t st) {
+                  cudaStream_t st, const SetupSource* src = nullptr) {
   const mg_params& p = h->p;
   int r = p.r;
-  WMG_TRY(gaussian_fill<R>(phi, p.seed, (unsigned)(s * r), r, h->g.V, st));
+  if (src) {
+    size_t off = (size_t)s * r * h->nf;
+    if (src->dtype == MG_C128)
+      WMG_TRY((convert<R, double>(phi, static_cast<const zd*>(src->fields) + off, nullptr, 0,
+                                  h->nf * r, 1, st)));
+    else
+      WMG_TRY((convert<R, float>(phi, static_cast<const zf*>(src->fields) + off, nullptr, 0,
+                                 h->nf * r, 1, st)));
+    if (!src->smooth) {
+      WMG_CUDA(cudaMemcpyAsync(psi, phi, h->nf * r * sizeof(cplx<R>), cudaMemcpyDeviceToDevice,
+                               st));
+      return MG_OK;
+    }
+  } else {
+    WMG_TRY(gaussian_fill<R>(phi, p.seed, (unsigned)(s * r), r, h->g.V, st));
+  }
   int dt = sizeof(R) == 8 ? MG_C128 : MG_C64;
   const void* L = sizeof(R) == 8 ? (const void*)h->links64L : (const void*)h->links32L;
-  Op<R> D = [h, dt, L, r](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
-    return dslash_launch(dt, out, in, L, h->g, -1, 0, r, s2, h->nf, h->nf, 1);
+  const int lay = sizeof(R) == 8 ? 1 : h->llay;
+  Op<R> D = [h, dt, L, r, lay](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
+    return dslash_launch(dt, out, in, L, h->g, -1, 0, r, s2, h->nf, h->nf, lay);
   };
   WMG_TRY(D(tmp, phi, st));
   WMG_TRY(axpby<R>(tmp, 0.0, tmp, -1.0, h->nf * r, 1, st));   // tmp = -D phi
   WMG_TRY(gm.alloc(h->nf, r, p.sweeps > 0 ? p.sweeps : 1, false));
-  FusedStencil fz{h->links32L, h->g};   // FP32 runs fuse the stencil with the projections
+  FusedStencil fz{h->links32L, h->g, h->llay};   // FP32 runs fuse the stencil with the projections
   WMG_TRY(gm.fixed(D, psi, tmp, p.sweeps, st, false, sizeof(R) == 4 ? &fz : nullptr));
   WMG_TRY(axpby<R>(psi, 1.0, phi, 1.0, h->nf * r, 1, st));     // psi = phi + psi'
   return MG_OK;
 }
 
 template <typename R>
-int run_setup(mg_handle* h, cudaStream_t st) {
+int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr) {
   const mg_params& p = h->p;
   int r = p.r, k = h->k;
   int cmax = k + r;
@@ -204,7 +248,7 @@ int run_setup(mg_handle* h, cudaStream_t st) {
   // rotate only above the accuracy of the Gram sums (FP64 ~1e-16, double-float ~1e-14)
   const double eig_tol = df ? 1e-13 : 1e-15;
   for (int s = 0; s < p.n_s; ++s) {
-    STEP(smooth_stream<R>(h, psi, phi, tmp, gm, s, st));
+    STEP(smooth_stream<R>(h, psi, phi, tmp, gm, s, st, src));
     STEP(chiral_gather<R>(cur, cmax, kk, psi, r, h->B, st, df));
     int c = kk + r;
     int kn = c < k ? c : k;
@@ -292,6 +336,13 @@ int ensure_solver(mg_handle* h, int nrhs) {
       WMG_TRY(h->post32.alloc(h->nf, nrhs, ps, false));
     }
   }
+  if (p.schur_smoother) {
+    size_t eh = (h->nf / 2) * nrhs * (p.solve_dtype == MG_C128 ? sizeof(zd) : sizeof(zf));
+    for (auto& b : h->sbuf) WMG_TRY(dev_alloc(&b, eh));
+    int ps = p.post_smooth > 0 ? p.post_smooth : 1;
+    if (p.solve_dtype == MG_C128) WMG_TRY(h->posts64.alloc(h->nf / 2, nrhs, ps, false));
+    else WMG_TRY(h->posts32.alloc(h->nf / 2, nrhs, ps, false));
+  }
   h->nrhs = nrhs;
   return MG_OK;
 }
@@ -300,11 +351,13 @@ int ensure_solver(mg_handle* h, int nrhs) {
 template <typename R> struct Lvl;
 template <> struct Lvl<double> {
   static const void* links(mg_handle* h) { return h->links64L; }
+  static int layout(mg_handle*) { return 1; }
   static const zd* P(mg_handle* h) { return h->P64; }
   static const zd* Op(mg_handle* h) { return h->Op64; }
   static Gmres<double>& coarse(mg_handle* h) { return h->coarse64; }
   static CoarseSolver<double>& csol(mg_handle* h) { return h->csol64; }
   static Gmres<double>& post(mg_handle* h) { return h->post64; }
+  static Gmres<double>& posts(mg_handle* h) { return h->posts64; }
   static Gmres<double>& outer(mg_handle* h) { return h->outer64; }
   static zd* vc(mg_handle* h) { return h->vc64; }
   static zd* ec(mg_handle* h) { return h->ec64; }
@@ -314,11 +367,13 @@ template <> struct Lvl<double> {
 };
 template <> struct Lvl<float> {
   static const void* links(mg_handle* h) { return h->links32L; }
+  static int layout(mg_handle* h) { return h->llay; }
   static const zf* P(mg_handle* h) { return h->P32; }
   static const zf* Op(mg_handle* h) { return h->Op32; }
   static Gmres<float>& coarse(mg_handle* h) { return h->coarse32; }
   static CoarseSolver<float>& csol(mg_handle* h) { return h->csol32; }
   static Gmres<float>& post(mg_handle* h) { return h->post32; }
+  static Gmres<float>& posts(mg_handle* h) { return h->posts32; }
   static Gmres<float>& outer(mg_handle* h) { return h->outer32; }
   static zf* vc(mg_handle* h) { return h->vc32; }
   static zf* ec(mg_handle* h) { return h->ec32; }
@@ -331,7 +386,7 @@ template <typename R>
 Op<R> fine_op(mg_handle* h, int nrhs) {
   return [h, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t st) -> int {
     return dslash_launch(Lvl<R>::dtype, out, in, Lvl<R>::links(h), h->g, -1, 0, nrhs, st, h->nf,
-                         h->nf, 1);
+                         h->nf, Lvl<R>::layout(h));
   };
 }
 
@@ -340,7 +395,7 @@ template <typename H>
 OpV<H> fine_op_half(mg_handle* h, int nrhs) {
   int dt = std::is_same<H, zh>::value ? MG_F16 : MG_BF16;
   return [h, nrhs, dt](H* out, const H* in, cudaStream_t st) -> int {
-    return dslash_launch(dt, out, in, h->links16L, h->g, -1, 0, nrhs, st, h->nf, h->nf, 1);
+    return dslash_launch(dt, out, in, h->links16L, h->g, -1, 0, nrhs, st, h->nf, h->nf, h->llay);
   };
 }
 
@@ -356,6 +411,37 @@ int post_smooth_half(mg_handle* h, GmresV<H>& gm, zf* z, const zf* v, zf* kw, in
   WMG_TRY((lincomb_v<H, zf>((H*)h->kwh, s, v, -s, kw, f, st)));   // kw holds D z
   WMG_TRY(gm.fixed(fine_op_half<H>(h, nrhs), (H*)h->keh, (const H*)h->kwh, h->p.post_smooth, st));
   WMG_TRY((axpy_mixed<zf, H>(z, 1.0 / s, (const H*)h->keh, f, st)));
+  return MG_OK;
+}
+
+// Post-smoother on the even-odd Schur system (even-odd preconditioning, Sec. 1): with the
+// residual r = v - D z split into r_e, r_o,
+//   r_hat = r_e + kappa H_eo r_o,  e_e = GMRES_post(D_hat, r_hat),  e_o = r_o + kappa H_oe e_e,
+// and z += (e_e, e_o).  (D e)_o = r_o holds exactly for any number of steps.
+template <typename R>
+int post_smooth_schur(mg_handle* h, cplx<R>* z, const cplx<R>* r, int nrhs, cudaStream_t st) {
+  const Geom& g = h->g;
+  const size_t nh = h->nf / 2;
+  cplx<R>* re = static_cast<cplx<R>*>(h->sbuf[0]);
+  cplx<R>* ro = static_cast<cplx<R>*>(h->sbuf[1]);
+  cplx<R>* rh = static_cast<cplx<R>*>(h->sbuf[2]);
+  cplx<R>* xe = static_cast<cplx<R>*>(h->sbuf[3]);
+  cplx<R>* to = static_cast<cplx<R>*>(h->sbuf[4]);
+  const void* L = Lvl<R>::links(h);
+  const int lay = Lvl<R>::layout(h);
+  const int dt = Lvl<R>::dtype;
+  WMG_TRY(eo_split<cplx<R>>(re, ro, r, g, nrhs, st));
+  WMG_TRY(dslash_launch(dt, rh, ro, L, g, 0, 0, nrhs, st, nh, nh, lay));   // -kappa H_eo r_o
+  WMG_TRY(axpby<R>(rh, 1.0, re, -1.0, nh * nrhs, 1, st));                 // r_hat
+  Op<R> Dhat = [h, to, L, lay, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
+    return schur_apply<cplx<R>>(out, in, to, L, lay, h->g, 0, nrhs, s2);
+  };
+  WMG_TRY(Lvl<R>::posts(h).fixed(Dhat, xe, rh, h->p.post_smooth, st));
+  WMG_TRY(dslash_launch(dt, to, xe, L, g, 1, 0, nrhs, st, nh, nh, lay));   // -kappa H_oe e_e
+  WMG_TRY(axpby<R>(to, 1.0, ro, -1.0, nh * nrhs, 1, st));                 // e_o
+  cplx<R>* ke = Lvl<R>::ke(h);
+  WMG_TRY(eo_join<cplx<R>>(ke, xe, to, g, nrhs, st));
+  WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, h->nf * nrhs, 1, st));                // z += e
   return MG_OK;
 }
 
@@ -402,7 +488,8 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
         if (p.solve_dtype == MG_BF16) return post_smooth_half<zbf>(h, h->postb, z, v, kw, nrhs, st);
       }
       WMG_TRY(axpby<R>(kw, 1.0, v, -1.0, h->nf * nrhs, 1, st));   // kw = v - D z
-      FusedStencil fz{h->links32L, h->g};   // FP32 runs fuse the stencil with the projections
+      if (p.schur_smoother) return post_smooth_schur<R>(h, z, kw, nrhs, st);
+      FusedStencil fz{h->links32L, h->g, h->llay};   // FP32 runs fuse the stencil with the projections
       WMG_TRY(Lvl<R>::post(h).fixed(D, ke, kw, p.post_smooth, st, false,
                                     sizeof(R) == 4 ? &fz : nullptr));
       WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, h->nf * nrhs, 1, st));    // z += e
@@ -518,6 +605,8 @@ void mg_handle::free_solver() {
   outer32.release(); coarse32.release(); post32.release();
   csol64.release(); csol32.release();
   posth.release(); postb.release();
+  posts64.release(); posts32.release();
+  for (auto& b : sbuf) dfree(b);
   dfree(kwh); dfree(keh);
   dfree(x64); dfree(r64); dfree(t64); dfree(e32); dfree(r32);
   dfree(vc64); dfree(ec64); dfree(kw64); dfree(ke64);
@@ -539,6 +628,32 @@ extern "C" int mg_setup_streaming_svd(mg_handle** h, const void* links, const mg
   cudaStream_t st = (cudaStream_t)stream;
   WMG_TRY(create_handle(h, links, p, true, st));
   int s = p->setup_dtype == MG_C128 ? run_setup<double>(*h, st) : run_setup<float>(*h, st);
+  if (s != MG_OK) {
+    std::string msg = mg_last_error();
+    delete *h;
+    *h = nullptr;
+    return fail(s, msg);
+  }
+  return MG_OK;
+}
+
+extern "C" int mg_setup_from_vectors(mg_handle** h, const void* links, const mg_params* p,
+                                     const void* vectors, int vec_dtype, int smooth,
+                                     void* stream) {
+  if (!vectors) return fail(MG_EINVAL, "mg_setup_from_vectors: NULL vectors");
+  if (vec_dtype != MG_C128 && vec_dtype != MG_C64)
+    return fail(MG_EINVAL, "mg_setup_from_vectors: vec_dtype must be MG_C128 or MG_C64");
+  if (smooth != 0 && smooth != 1) return fail(MG_EINVAL, "mg_setup_from_vectors: smooth is 0 or 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  WMG_TRY(create_handle(h, links, p, true, st));
+  size_t bytes = (size_t)p->n_s * p->r * (*h)->nf * dtype_bytes(vec_dtype);
+  Staged sv;
+  int s = stage_in(sv, vectors, bytes, st);
+  if (s == MG_OK) {
+    SetupSource src{sv.dev, vec_dtype, smooth};
+    s = p->setup_dtype == MG_C128 ? run_setup<double>(*h, st, &src)
+                                  : run_setup<float>(*h, st, &src);
+  }
   if (s != MG_OK) {
     std::string msg = mg_last_error();
     delete *h;
@@ -721,6 +836,8 @@ extern "C" int mg_test_vectors(void* out, const void* links, const mg_params* p,
   return MG_OK;
 }
 
+extern "C" int mg_link_rows(const mg_handle* h) { return h ? (h->llay == 2 ? 2 : 3) : 0; }
+
 extern "C" int mg_apply_fine(mg_handle* h, void* out, const void* in, int nrhs, int dtype,
                              int dagger, void* stream) {
   if (!h || !out || !in || nrhs < 1) return fail(MG_EINVAL, "mg_apply_fine: bad arguments");
@@ -736,7 +853,8 @@ extern "C" int mg_apply_fine(mg_handle* h, void* out, const void* in, int nrhs, 
   WMG_TRY(stage_out_alloc(so, out, bytes, st));
   const void* L = dtype == MG_C128 ? (const void*)h->links64L
                   : dtype == MG_C64 ? (const void*)h->links32L : (const void*)h->links16L;
-  WMG_TRY(dslash_launch(dtype, so.dev, si.dev, L, h->g, -1, dagger, nrhs, st, h->nf, h->nf, 1));
+  WMG_TRY(dslash_launch(dtype, so.dev, si.dev, L, h->g, -1, dagger, nrhs, st, h->nf, h->nf,
+                        dtype == MG_C128 ? 1 : h->llay));
   WMG_TRY(stage_out_finish(so, out, bytes, st));
   return MG_OK;
 }

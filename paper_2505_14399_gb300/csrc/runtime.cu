@@ -350,4 +350,6 @@ extern "C" void mg_params_default(mg_params* p) {
   p->svd_refine = -1;
   p->coarse_persistent = 1;
   p->fp64_emulation = -1;
+  p->link_compress = -1;
+  p->schur_smoother = 0;
 }

@@ -71,7 +71,10 @@ template <> struct SiteIO<StBF16> : SiteIOHalf<__nv_bfloat162, StBF16> {};
 
 // Load the 3x3 link U_mu(site).  LL = 0: ABI layout [mu][site][3][3] (one link contiguous);
 // LL = 1: lane-contiguous layout [mu][3x3 entry][site], so a warp reading one entry for 32
-// consecutive sites touches one contiguous 32 x element_size span (the solver's copy).
+// consecutive sites touches one contiguous 32 x element_size span (the solver's copy);
+// LL = 2: the same with the first two rows only, [mu][6 entry][site]: for U in SU(3) the rows
+// are orthonormal and det U = 1, so the third row is the complex conjugate of the cross
+// product of the first two (12 of the 18 reals cross HBM).
 template <typename S, int LL>
 __device__ __forceinline__ void load_link(const typename S::elem* L, int V, int mu, int site,
                                           cplx<typename S::real> u[9]) {
@@ -79,9 +82,15 @@ __device__ __forceinline__ void load_link(const typename S::elem* L, int V, int 
     size_t idx = ((size_t)mu * V + site) * 9;
 #pragma unroll
     for (int i = 0; i < 9; ++i) u[i] = S::ld(L, idx + i);
-  } else {
+  } else if (LL == 1) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) u[i] = S::ld(L, ((size_t)mu * 9 + i) * V + site);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) u[i] = S::ld(L, ((size_t)mu * 6 + i) * V + site);
+    u[6] = conj(u[1] * u[5] - u[2] * u[4]);
+    u[7] = conj(u[2] * u[3] - u[0] * u[5]);
+    u[8] = conj(u[0] * u[4] - u[1] * u[3]);
   }
 }
 
