@@ -15,9 +15,9 @@ oracle function on its own unit.  The sequential FGMRES iteration runs in one pr
 Two uses:
 * ``full_step``: the whole step, with the oracle's own iteration counts (minutes at
   16^3 x 32).  ``python -m oracle.full_step <workload> [workers] [out.json]``.
-* ``sampled_step``: a bounded piece of every part, timed, each scaled by its share of the
-  whole step (the number of test vectors, aggregates and coarse slabs; the outer iteration
-  count of a recorded full step), giving the estimated seconds of one whole step.
+* ``SampledStep``: a bounded piece of every part, timed, each scaled by its share of the
+  whole step (the number of test vectors and coarse slabs; the outer iteration count of a
+  recorded full step), giving the estimated seconds of one whole step.
 """
 import json
 import math
@@ -113,50 +113,104 @@ def full_step(links, b, cfg, kappa, workers=1, tol=1e-10, log=None):
     return info, parts
 
 
-def sampled_step(links, b, cfg, kappa, workers, outer_its, n_outer=1):
-    """A bounded sample of every part of the step, scaled to one whole step.
+class SampledStep:
+    """A bounded sample of every part of the step, each part timed and scaled to its share of
+    one whole step on `workers` host cores:
 
-    * test vectors: `workers` of the r n_s vectors smoothed at full volume, one per process,
-      scaled by ceil(r n_s / workers) rounds;
-    * streaming SVD: every aggregate and stream, on the sampled vectors (the stream tiles are
-      the sampled vectors taken r at a time, cycled when fewer than r n_s were smoothed);
-    * Galerkin product: the full lattice (one process);
-    * solve: `n_outer` FGMRES iterations of the K-cycle-preconditioned solve on the sampled
-      prolongator, scaled by `outer_its` (the outer iterations of a recorded full step).
-    Returns (estimated seconds of one step, per-part seconds as run, description).
+    * ``vectors``: `workers` of the r n_s test vectors smoothed at full volume (Eq. 2), one per
+      process; scaled by ceil(r n_s / workers) rounds;
+    * ``svd``: the streaming SVD of all aggregates and streams (Algorithm 3) on the sampled
+      vectors (stream tiles take them r at a time, cycled), aggregates spread over the pool;
+    * ``galerkin``: the Galerkin product (Eq. 5) of one coarse time slab, computed as a
+      periodic lattice of that slab's extent (the same work per site as the whole lattice);
+      scaled by ceil(slabs / workers), the slabs being independent units;
+    * ``solve``: one outer FGMRES iteration of the K-cycle preconditioned solve on the full
+      lattice with the sampled prolongator (its coarse operator: the slab's, repeated over the
+      slabs); scaled by `outer_its`, the outer iterations of a recorded full step.
+
+    `run(part)` measures one part; `estimate()` sums the latest scaled measurement of every
+    part (None until each part has been measured once).
     """
-    dims, block, k, r, n_s = cfg["dims"], cfg["block"], cfg["k"], cfg["r"], cfg["n_s"]
-    w, bc = cfg["hop_weight"], cfg["bc"]
-    m = r * n_s
-    nv = max(1, min(workers, m))
-    run = {}
-    with _pool(workers, links) as pool:
-        t0 = time.perf_counter()
-        vecs, _ = _vectors(pool, cfg, kappa, range(nv))
-        run["test_vectors"] = time.perf_counter() - t0
-        tiles = []
-        for s in range(n_s):
-            idx = [(s * r + i) % nv for i in range(r)]
-            tiles.append(icsvd.chiral_split(vecs[idx], dims, block))
-        t0 = time.perf_counter()
-        Pt, _ = _icsvd(pool, tiles, k, workers)
-        run["icsvd"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    XY = coarse.galerkin(Pt, links, dims, block, kappa, w, bc)
-    run["galerkin"] = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    lvl = mg.TwoLevel(links, dims, kappa, w, bc, block, Pt, XY=XY)
-    lvl.solve(np.asarray(b).reshape(-1), tol=1e-30, maxiter=n_outer)
-    run["solve"] = time.perf_counter() - t0
-    scaled = {"test_vectors": run["test_vectors"] * math.ceil(m / nv),
-              "icsvd": run["icsvd"], "galerkin": run["galerkin"],
-              "solve": run["solve"] * outer_its / n_outer}
-    desc = ("%d of %d test vectors smoothed at full volume (one per process, scaled by %d "
-            "rounds); streaming SVD of all %d aggregates; full Galerkin product; %d of %d "
-            "outer FGMRES iterations (scaled)" % (nv, m, math.ceil(m / nv),
-                                                   int(np.prod(dims)) // int(np.prod(block)),
-                                                   n_outer, outer_its))
-    return sum(scaled.values()), run, scaled, desc
+    PARTS = ("vectors", "svd", "galerkin", "solve")
+
+    def __init__(self, links, b, cfg, kappa, workers, outer_its):
+        self.links, self.b, self.cfg, self.kappa = links, np.asarray(b).reshape(-1), cfg, kappa
+        self.workers, self.outer_its = workers, outer_its
+        dims, block = cfg["dims"], cfg["block"]
+        self.m = cfg["r"] * cfg["n_s"]
+        self.nv = max(1, min(workers, self.m))
+        self.nslab = dims[3] // block[3]
+        self.run_s, self.scaled_s = {}, {}
+        self.vecs = self.Pt = self.XY = None
+
+    def _slab(self):
+        dims, block = self.cfg["dims"], self.cfg["block"]
+        sub = (dims[0], dims[1], dims[2], block[3])
+        vs = int(np.prod(sub))
+        nb = vs // int(np.prod(block))
+        return sub, np.ascontiguousarray(self.links[:, :vs]), nb
+
+    def run(self, part, pool=None):
+        cfg, dims, block, k, r = (self.cfg, self.cfg["dims"], self.cfg["block"], self.cfg["k"],
+                                  self.cfg["r"])
+        w, bc = cfg["hop_weight"], cfg["bc"]
+        own = pool is None and part in ("vectors", "svd")
+        if own:
+            pool = _pool(self.workers, self.links)
+        try:
+            t0 = time.perf_counter()
+            if part == "vectors":
+                self.vecs, _ = _vectors(pool, cfg, self.kappa, range(self.nv))
+                t = time.perf_counter() - t0
+                scaled = t * math.ceil(self.m / self.nv)
+            elif part == "svd":
+                tiles = []
+                for s in range(cfg["n_s"]):
+                    idx = [(s * r + i) % self.nv for i in range(r)]
+                    tiles.append(icsvd.chiral_split(self.vecs[idx], dims, block))
+                t0 = time.perf_counter()
+                self.Pt, _ = _icsvd(pool, tiles, k, self.workers)
+                t = scaled = time.perf_counter() - t0
+            elif part == "galerkin":
+                sub, Ls, nb = self._slab()
+                X, Y = coarse.galerkin(self.Pt[:nb], Ls, sub, block, self.kappa, w, bc)
+                t = time.perf_counter() - t0
+                scaled = t * math.ceil(self.nslab / self.workers)
+                self.XY = (np.concatenate([X] * self.nslab, axis=0),
+                           np.concatenate([Y] * self.nslab, axis=1))
+            else:
+                lvl = mg.TwoLevel(self.links, dims, self.kappa, w, bc, block, self.Pt, XY=self.XY)
+                t0 = time.perf_counter()
+                lvl.solve(self.b, tol=1e-30, maxiter=1)
+                t = time.perf_counter() - t0
+                scaled = t * self.outer_its
+        finally:
+            if own:
+                pool.close()
+                pool.join()
+        self.run_s[part], self.scaled_s[part] = t, scaled
+        return t
+
+    def run_all(self):
+        with _pool(self.workers, self.links) as pool:
+            self.run("vectors", pool)
+            self.run("svd", pool)
+        self.run("galerkin")
+        self.run("solve")
+
+    def estimate(self):
+        if any(p not in self.scaled_s for p in self.PARTS):
+            return None
+        return sum(self.scaled_s.values())
+
+    def describe(self):
+        dims, block = self.cfg["dims"], self.cfg["block"]
+        return ("%d of %d test vectors smoothed at full volume on %d processes (x%d rounds); "
+                "streaming SVD of all %d aggregates; Galerkin product of 1 of %d coarse time "
+                "slabs (x%d); 1 outer FGMRES iteration (x%d)"
+                % (self.nv, self.m, self.workers, math.ceil(self.m / self.nv),
+                   int(np.prod(dims)) // int(np.prod(block)), self.nslab,
+                   math.ceil(self.nslab / self.workers), self.outer_its))
 
 
 if __name__ == "__main__":

@@ -12,6 +12,11 @@ levels one application of the preconditioner to v is:
 
 Readings the paper leaves open (restart lengths, iteration caps) are parameters.
 
+Schur-form post-smoother (``schur=True``; the introduction lists even-odd preconditioning
+among the standard ones, Sec. 1): the post-smoother solves D e = r through the Schur
+complement on the even sites, GMRES_post on D_hat r_hat with r_hat = r_e + kappa H_eo r_o,
+then e_o = r_o + kappa H_oe e_e (``oracle.schur``).
+
 Parity status: the pieces are pinned individually (Krylov, Dslash, Galerkin); the
 solve itself is pinned by the true residual computed with the dense D and by a direct
 dense solve on tiny lattices.  Iteration counts of the paper's Tables 1-3 need the
@@ -22,11 +27,12 @@ import numpy as np
 from . import wilson
 from .coarse import coarse_apply, galerkin, prolong, restrict
 from .krylov import fgmres, gmres_fixed, gmres_tol
+from . import schur as _schur
 
 
 class TwoLevel:
     def __init__(self, links, dims, kappa, hop_weight, bc, block, Pt, coarse_tol=0.03,
-                 coarse_restart=32, coarse_maxiter=1000, post=8, XY=None):
+                 coarse_restart=32, coarse_maxiter=1000, post=8, XY=None, schur=False):
         self.links, self.dims, self.kappa = links, dims, kappa
         self.w, self.bc, self.block, self.Pt = hop_weight, bc, block, Pt
         self.cd = [dims[m] // block[m] for m in range(4)]
@@ -34,6 +40,7 @@ class TwoLevel:
                                                           hop_weight, bc)
         self.coarse_tol, self.coarse_restart = coarse_tol, coarse_restart
         self.coarse_maxiter, self.post = coarse_maxiter, post
+        self.schur = schur
         self.coarse_its = 0
         self.kcycles = 0
 
@@ -51,7 +58,17 @@ class TwoLevel:
         self.kcycles += 1
         e = prolong(self.Pt, ec, self.dims, self.block).reshape(-1)
         r = np.asarray(v).reshape(-1) - self.D(e)
-        return e + gmres_fixed(self.D, r, self.post)
+        return e + self.smooth(r)
+
+    def smooth(self, r):
+        """post GMRES steps on D e = r from zero: on D itself, or on the Schur system."""
+        if not self.schur:
+            return gmres_fixed(self.D, r, self.post)
+        a = (self.links, self.dims, self.kappa, self.w, self.bc)
+        Dh = lambda u: _schur.schur_op(u, *a).reshape(-1)
+        rh = _schur.prepare(r, *a).reshape(-1)
+        ee = gmres_fixed(Dh, rh, self.post)
+        return _schur.reconstruct(ee, r, *a).reshape(-1)
 
     def solve(self, b, tol=1e-10, restart=16, maxiter=500):
         x, its, res = fgmres(self.D, self.kcycle, np.asarray(b).reshape(-1), tol, restart,

@@ -63,6 +63,15 @@ def gaussian_rhs(dims, seed, nrhs=1):
     return _cgauss(rng, (nrhs, V, 4, 3))
 
 
+def graded_fields(dims, m, decades, seed):
+    """m complex-Gaussian fields (m, V, 4, 3), field i scaled by 10^(-decades i / (m - 1)):
+    stand-in test vectors whose aggregate tiles have singular values spread over `decades`."""
+    rng = np.random.default_rng(seed)
+    V = volume(dims)
+    scale = 10.0 ** (-decades * np.arange(m) / max(m - 1, 1))
+    return _cgauss(rng, (m, V, 4, 3)) * scale[:, None, None, None]
+
+
 # Workload definitions.  Seeds: links 1000+i, sources 2000+i, test vectors 3000+i.
 # kappa=None marks a near-critical workload: kappa = kappa_factor * KAPPA_CRIT[name].
 WORKLOADS = {

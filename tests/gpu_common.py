@@ -59,3 +59,15 @@ def params_for(cfg, **kw):
 
 def links_for(cfg):
     return synthetic.make_links(cfg)
+
+
+def record(name, **values):
+    """Append measured errors and their bounds to the JSON-lines file named by
+    WMG_PARITY_LOG (nothing when it is unset)."""
+    import json
+    import os
+    path = os.environ.get("WMG_PARITY_LOG")
+    if not path:
+        return
+    with open(path, "a") as f:
+        f.write(json.dumps(dict(test=name, **{k: float(v) for k, v in values.items()})) + "\n")

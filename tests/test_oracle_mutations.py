@@ -186,7 +186,7 @@ MUTANTS = [
      [("r = np.asarray(v).reshape(-1) - self.D(e)", "r = self.D(e) - np.asarray(v).reshape(-1)")],
      [TN.test_kcycle_with_exact_coarse_solve_is_coarse_grid_correction]),
     ("kcycle_prolongation_dropped", oracle.mg, "TwoLevel.kcycle",
-     [("return e + gmres_fixed(self.D, r, self.post)", "return gmres_fixed(self.D, r, self.post)")],
+     [("return e + self.smooth(r)", "return self.smooth(r)")],
      [TN.test_kcycle_with_exact_coarse_solve_is_coarse_grid_correction]),
     # deeper levels: chiral SVD and Galerkin product on a coarse operator, multilevel K-cycle
     ("level_split_half_offset", oracle.multilevel, "chiral_split",
@@ -227,6 +227,13 @@ MUTANTS = [
     ("field_strength_trace_kept", oracle.clover, "field_strength",
      [("F[p] = f - (tr / 3.0)[:, None, None] * np.eye(3)", "F[p] = f")],
      [TC.test_clover_term_is_hermitian_and_chirally_block_diagonal]),
+    ("schur_smoother_not_reconstructed", oracle.mg, "TwoLevel.smooth",
+     [("return _schur.reconstruct(ee, r, *a).reshape(-1)",
+       "return _schur.join(ee, 0 * ee, self.dims).reshape(-1)")],
+     [TS.test_schur_smoother_satisfies_the_odd_equations]),
+    ("schur_smoother_unprepared_rhs", oracle.mg, "TwoLevel.smooth",
+     [("rh = _schur.prepare(r, *a).reshape(-1)", "rh = _schur.split(r, self.dims)[0].reshape(-1)")],
+     [TS.test_schur_smoother_with_a_spanning_krylov_space_is_the_exact_inverse]),
     ("leaf_two_open", oracle.clover, "field_strength",
      [("_dag(_at(Um, dims, [(nu, 1), (mu, -1)]))", "_dag(_at(Um, dims, [(nu, 1)]))")],
      [TC.test_clover_gauge_covariance]),

@@ -73,3 +73,55 @@ def test_schur_solve_reconstructs_the_full_solution():
     bh = schur.prepare(b, U, dims, kappa, w, bc)
     assert np.abs(schur.schur_op(xe, U, dims, kappa, w, bc) - bh).max() < 1e-10
     assert np.array_equal(schur.join(xe, xo, dims), x)
+
+
+def _tiny_level(schur, post):
+    from oracle import icsvd, mg
+    dims, block, kappa = (4, 2, 2, 2), (2, 2, 2, 2), 0.12
+    U = synthetic.haar_links(dims, 9)
+    Pt, _, _ = icsvd.icsvd(U, dims, kappa, (1, 1, 1, 1), (1, 1, 1, 1), block, 4, 4, 1, 2, 3000)
+    return mg.TwoLevel(U, dims, kappa, (1, 1, 1, 1), (1, 1, 1, 1), block, Pt, post=post,
+                       schur=schur), U, dims, kappa
+
+
+def test_schur_smoother_satisfies_the_odd_equations():
+    """For any number of steps the Schur-form correction e solves the odd rows exactly:
+    (D e)_o = r_o, because e_o = r_o + kappa H_oe e_e."""
+    lvl, U, dims, kappa = _tiny_level(True, 3)
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(12 * wilson.volume(dims)) + 1j * rng.standard_normal(12 * wilson.volume(dims))
+    e = lvl.smooth(r)
+    De = wilson.dslash(e, U, dims, kappa).reshape(-1, 4, 3)
+    _, ro = schur.split(r, dims)
+    _, Deo = schur.split(De, dims)
+    assert np.abs(Deo - ro).max() < 1e-13
+    # and the even rows only approximately after 3 steps (the smoother is not a solve)
+    de, re = schur.split(De, dims)[0], schur.split(r, dims)[0]
+    assert np.abs(de - re).max() > 1e-6
+
+
+def test_schur_smoother_with_a_spanning_krylov_space_is_the_exact_inverse():
+    """GMRES with as many steps as the even space has dimensions solves D_hat exactly, so the
+    Schur-form smoother returns D^{-1} r (to rounding); the plain smoother with the same number
+    of steps does not (its space has twice the dimension)."""
+    n_even = 12 * 32 // 2
+    lvl, U, dims, kappa = _tiny_level(True, n_even)
+    rng = np.random.default_rng(5)
+    n = 12 * wilson.volume(dims)
+    r = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x = np.linalg.solve(wilson.dense_dirac(U, dims, kappa, (1, 1, 1, 1), (1, 1, 1, 1)), r)
+    e = lvl.smooth(r)
+    assert np.linalg.norm(e - x) / np.linalg.norm(x) < 1e-9
+
+
+def test_schur_smoothed_kcycle_solve():
+    """The two-level FGMRES with the Schur-form post-smoother reaches 1e-10 and matches the
+    dense solve."""
+    lvl, U, dims, kappa = _tiny_level(True, 4)
+    rng = np.random.default_rng(6)
+    n = 12 * wilson.volume(dims)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, info = lvl.solve(b, tol=1e-10)
+    xd = np.linalg.solve(wilson.dense_dirac(U, dims, kappa, (1, 1, 1, 1), (1, 1, 1, 1)), b)
+    assert info["residual"] <= 1e-10
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8

@@ -61,6 +61,28 @@ def test_two_calls_in_a_row_match_coarse_build(solve_dtype):
     h.close()
 
 
+def test_calls_allocate_no_device_memory():
+    """Around two calls in a row, neither the device's free memory (cudaMemGetInfo: the
+    library's own allocations, the stream-ordered pool, lazily loaded code) nor torch's
+    allocator changes.  The first call comes before the measurement: it may load the library's
+    module with the fixed scratch array in it."""
+    import torch
+    dims, block, k = (8, 8, 8, 8), (2, 2, 2, 2), 9
+    h, _, _ = _handle(dims, block, k, 61)
+    h.coarse_build()
+    _noalloc(h)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    _noalloc(h)
+    _noalloc(h)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert torch.cuda.memory_allocated() == alloc0
+    h.close()
+
+
 def test_scratch_left_by_a_larger_hierarchy_is_harmless():
     big, _, _ = _handle((8, 8, 8, 8), (2, 2, 2, 2), 12, 21)
     big.coarse_build()
