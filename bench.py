@@ -316,10 +316,14 @@ def gpu_arm(args):
                           setup_dtype="c64" if mixed else "c128",
                           solve_dtype="c64" if mixed else "c128")
 
-    def step(p, links, rhs):
+    def step(p, links, rhs, levels=()):
         h = api.Hierarchy(links, p)
         h.coarse_build()
+        for blk, kl, rl, nsl, tl in levels:
+            h.add_level(blk, kl, rl, nsl, tl)
         x, info = h.solve(rhs, tol=1e-10, maxiter=4000)
+        if levels:
+            info = dict(info, level_iterations=h.level_iterations())
         h.close()
         return x, info
 
@@ -425,24 +429,50 @@ def gpu_arm(args):
                 "peak_source": peak_kind, "traffic": None, "avg_launch_us": t_d * 1e6,
                 "algorithmic_bytes_per_launch": bytes_d}
 
-    # fine-level outer iterations, Regular (k test vectors, n_s = 1) vs iCSVD streams of r = 8,
-    # FP64 solve on the same field and source (the comparison of Table 2, synthetic lattice),
-    # at the timed step's smoothing (5 GMRES steps per test vector) and at 20 steps
+    # The comparison of Table 2 on the synthetic near-critical lattice: fine-level outer
+    # iterations of Regular (k test vectors, one stream) and iCSVD (streams of r = 8, n_s = 4
+    # and 8), together with the setup + solve seconds of the mixed and the plain FP64 form on
+    # the same configuration, at the timed smoothing (5 GMRES steps per test vector) and at 20,
+    # on two levels and on four (level 2: 2^4 aggregates of the level-1 lattice, k = 16;
+    # level 3: the rest, k = 16; level tolerances 0.03 / 0.06 / 0.6 as at the critical mass in
+    # Sec. 4.5).
+    def timed_once(p, levels=()):
+        step(p, Ud, bd, levels)            # warm-up (autotuner, allocation cache)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, inf = step(p, Ud, bd, levels)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, inf
+
     fine = {}
-    for sw in (cfg["sweeps"], 20):
-        row = {}
-        for tag, r, ns in (("regular_ns1", cfg["k"], 1), ("icsvd_ns4", cfg["r"], 4),
-                           ("icsvd_ns8", cfg["r"], 8)):
-            pf = api.params(dims, cfg["block"], cfg["kappa"], cfg["k"], r, ns, sw,
-                            cfg["tv_seed"], cfg["hop_weight"], cfg["bc"], setup_dtype="c128",
-                            solve_dtype="c128")
-            _, inf = step(pf, Ud, bd)
-            row[tag] = {"outer": inf["outer"], "coarse": inf["coarse"], "test_vectors": r * ns}
-        row["reduction_regular_over_icsvd_ns4"] = (row["regular_ns1"]["outer"]
-                                                   / max(row["icsvd_ns4"]["outer"], 1))
-        row["reduction_regular_over_icsvd_ns8"] = (row["regular_ns1"]["outer"]
-                                                   / max(row["icsvd_ns8"]["outer"], 1))
-        fine["sweeps_%d" % sw] = row
+    lc = [dims[m] // cfg["block"][m] for m in range(4)]
+    four = lambda reg: ((2, 2, 2, 2), 16, 16 if reg else 8, 1 if reg else 4, 0.06), \
+        ((lc[0] // 2, lc[1] // 2, lc[2] // 2, lc[3] // 2), 16, 16 if reg else 8,
+         1 if reg else 4, 0.6)
+    for depth in (2, 4):
+        for sw in (cfg["sweeps"], 20):
+            row = {}
+            for tag, r, ns in (("regular_ns1", cfg["k"], 1), ("icsvd_ns4", cfg["r"], 4),
+                               ("icsvd_ns8", cfg["r"], 8)):
+                levels = four(tag == "regular_ns1") if depth == 4 else ()
+                ent = {"test_vectors": r * ns}
+                for form, sd in (("fp64", "c128"), ("mixed", "c64")):
+                    pf = api.params(dims, cfg["block"], cfg["kappa"], cfg["k"], r, ns, sw,
+                                    cfg["tv_seed"], cfg["hop_weight"], cfg["bc"], setup_dtype=sd,
+                                    solve_dtype=sd)
+                    t, inf = timed_once(pf, levels)
+                    ent[form] = {"seconds": t, "outer": inf["outer"], "coarse": inf["coarse"]}
+                    if "level_iterations" in inf:
+                        ent[form]["level_iterations"] = inf["level_iterations"]
+                ent["mixed_over_fp64_speedup"] = ent["fp64"]["seconds"] / ent["mixed"]["seconds"]
+                row[tag] = ent
+            for t in ("icsvd_ns4", "icsvd_ns8"):
+                row["reduction_regular_over_" + t] = (row["regular_ns1"]["fp64"]["outer"]
+                                                      / max(row[t]["fp64"]["outer"], 1))
+            fine["levels_%d_sweeps_%d" % (depth, sw)] = row
 
     # anisotropic 16^3 x 64 (w_t = 1/3.5): FP16 and BF16 smoother storage vs plain FP64
     aniso = anisotropic_leg(api, synthetic, dev, step) if args.aniso else None

@@ -263,6 +263,42 @@ int coarse_build(mg_handle* h, void* stream);
 int coarse_build_noalloc(mg_handle* h, void* stream);
 
 /* ---------------------------------------------------------------------------------
+ * mg_add_level -- one more level of the hierarchy (Sec. 2.1 end; Sec. 4 uses three and, near
+ * the critical mass, four levels): the coarsest operator so far, D_l (l = 1 after
+ * coarse_build), takes the place of D in Algorithm 3 and Eq. 5 --
+ *   test vectors psi = phi + GMRES_sweeps(D_l, -D_l phi) (Eq. 2), phi complex-Gaussian
+ *     Philox fields with counter (site, component, vector id, l), vector ids s r .. s r + r - 1;
+ *   chiral split with sigma_3 as the chirality (gamma_5 P = P sigma_3): each level-l site
+ *     vector [alpha][k_l] gives k_l rows of chirality alpha, rows (local site, i) inside the
+ *     aggregates of extent `block` on the level-l lattice;
+ *   streaming SVD over n_s streams of r vectors, k kept (FP64);
+ *   D_{l+1} = P_l^dag D_l P_l as a nearest-neighbour stencil on the lattice of aggregates.
+ * The K-cycle then recurses: the level-l system of the cycle is solved to its tolerance by
+ * FGMRES preconditioned by the K-cycle of level l (GMRES on the coarsest level, restart
+ * coarse_restart), with post_smooth GMRES steps on D_l; `tol` is the relative tolerance of the
+ * new coarsest level's solve (the paper: 0.03; near the critical mass 0.06 and 0.6 on its
+ * third and fourth level).  Requires coarse_build; coarse_build and mg_set_prolongator drop the
+ * added levels.  sweeps, seed and svd_refine come from the handle's parameters.
+ * MG_EINVAL: block not dividing the level-l lattice, k > min(32, n_d k_l), k + r > 64,
+ * n_s r < k, tol outside (0, 1), more than 8 levels.  Synchronises `stream`.
+ * ------------------------------------------------------------------------------- */
+int mg_add_level(mg_handle* h, const int block[4], int k, int r, int n_s, double tol,
+                 void* stream);
+
+/* Number of levels: 1 before coarse_build, 2 after it, + 1 per mg_add_level. */
+int mg_num_levels(const mg_handle* h);
+
+/* Iterations of the last solve on levels 1 .. L-1 (its[l - 1], summed over K-cycles and
+ * right-hand sides), at most nmax of them. */
+int mg_level_iterations(const mg_handle* h, long long* its, int nmax);
+
+/* Level l >= 2 added by mg_add_level: P_{l-1} tiles P[J][alpha][i][row] (row = local site *
+ * k_{l-1} + component, complex double), their singular values sigma[J][alpha][i] (double), and
+ * the level-l operator X[j][a][b], Y[dir][j][a][b] (complex double, row a, column b).  Any of P,
+ * sigma may be NULL; X and Y are both given or both NULL. */
+int mg_get_level(mg_handle* h, int level, void* P, void* sigma, void* X, void* Y, void* stream);
+
+/* ---------------------------------------------------------------------------------
  * mg_solve -- x = D^{-1} b to ||b - D x|| <= tol ||b|| (checked in FP64) with FGMRES
  * preconditioned by the two-level K-cycle (restrict, coarse GMRES to coarse_tol,
  * prolong, post_smooth GMRES steps).  solve_dtype MG_C128: one FP64 FGMRES;

@@ -140,10 +140,14 @@ class Hierarchy:
 
     def __init__(self, links, dims, kappa, hop_weight, bc, blocks, ks, rs=None, n_ss=None,
                  sweeps=5, seed=3000, Pts=None, coarse_tol=0.03, coarse_restart=32,
-                 coarse_maxiter=1000, post=8):
+                 coarse_maxiter=1000, post=8, level_tols=None):
         from .icsvd import icsvd
         self.links, self.dims, self.kappa, self.w, self.bc = links, dims, kappa, hop_weight, bc
         self.blocks, self.post = blocks, post
+        # relative tolerance of the solve on level l + 1 inside the K-cycle of level l: the
+        # paper uses 0.03 on levels 1 and 2, and near the critical mass 0.06 on level 2 and 0.6
+        # on level 3 (Sec. 4.5)
+        self.level_tols = list(level_tols) if level_tols is not None else [coarse_tol] * len(blocks)
         self.coarse_tol, self.coarse_restart, self.coarse_maxiter = (coarse_tol, coarse_restart,
                                                                      coarse_maxiter)
         nl = len(blocks)
@@ -199,11 +203,11 @@ class Hierarchy:
         v = np.asarray(v, dtype=np.complex128).reshape(-1)
         vc = self.restrict(l, v)
         A = self.op(l + 1)
+        tol = self.level_tols[l]
         if l + 1 == len(self.blocks):
-            ec, its, _ = gmres_tol(A, vc, self.coarse_tol, self.coarse_restart,
-                                   self.coarse_maxiter)
+            ec, its, _ = gmres_tol(A, vc, tol, self.coarse_restart, self.coarse_maxiter)
         else:
-            ec, its, _ = fgmres(A, lambda u: self.kcycle(l + 1, u), vc, self.coarse_tol,
+            ec, its, _ = fgmres(A, lambda u: self.kcycle(l + 1, u), vc, tol,
                                 self.coarse_restart, self.coarse_maxiter)
         self.coarse_its += its
         e = self.prolong(l, ec)

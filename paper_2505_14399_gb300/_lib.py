@@ -74,6 +74,10 @@ SIGNATURES = {
     "mg_setup_streaming_svd": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),
     "mg_setup_from_vectors": (I, [C.POINTER(P), P, C.POINTER(MgParams), P, I, I, P]),
     "mg_link_rows": (I, [P]),
+    "mg_add_level": (I, [P, C.POINTER(C.c_int), I, I, I, D, P]),
+    "mg_num_levels": (I, [P]),
+    "mg_level_iterations": (I, [P, C.POINTER(C.c_longlong), I]),
+    "mg_get_level": (I, [P, I, P, P, P, P, P]),
     "mg_create": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),
     "coarse_build": (I, [P, P]),
     "coarse_build_noalloc": (I, [P, P]),

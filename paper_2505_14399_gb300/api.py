@@ -8,6 +8,7 @@ stream; CPU tensors are staged by the library itself.
 """
 import ctypes as C
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -153,6 +154,7 @@ class Hierarchy:
 
     def coarse_build(self):
         L.check(L.lib().coarse_build(self._h, _stream()), "coarse_build")
+        self.levels = []          # the library drops levels built on the old operator
 
     def coarse_build_noalloc(self):
         L.check(L.lib().coarse_build_noalloc(self._h, _stream()), "coarse_build_noalloc")
@@ -194,6 +196,7 @@ class Hierarchy:
 
     def set_prolongator(self, P):
         L.check(L.lib().mg_set_prolongator(self._h, _ptr(P), _stream(P)), "mg_set_prolongator")
+        self.levels = []
 
     def restrict(self, v):
         nrhs = v.numel() // (self.V * 12)
@@ -213,6 +216,40 @@ class Hierarchy:
         Y = torch.empty((8, self.d, n2k, n2k), dtype=torch.complex128, device=self.device)
         L.check(L.lib().mg_get_coarse_op(self._h, _ptr(X), _ptr(Y), _stream(X)), "mg_get_coarse_op")
         return X, Y
+
+    def add_level(self, block, k, r, n_s, tol=0.03):
+        """One more level below the coarsest (Algorithm 3 + Eq. 5 on the coarse operator)."""
+        L.check(L.lib().mg_add_level(self._h, L.ivec(block), int(k), int(r), int(n_s), float(tol),
+                                     _stream()), "mg_add_level")
+        self.levels = getattr(self, "levels", [])
+        prev = self.levels[-1] if self.levels else dict(dims=[self.dims[m] // self.block[m]
+                                                              for m in range(4)], k=self.k)
+        dims = [prev["dims"][m] // block[m] for m in range(4)]
+        self.levels.append(dict(dims=dims, k=int(k), k_in=prev["k"], block=tuple(block),
+                                nd=int(np.prod(block))))
+
+    def num_levels(self):
+        return L.lib().mg_num_levels(self._h)
+
+    def level_iterations(self):
+        n = max(self.num_levels() - 1, 1)
+        buf = (C.c_longlong * n)()
+        L.check(L.lib().mg_level_iterations(self._h, buf, n), "mg_level_iterations")
+        return [int(v) for v in buf]
+
+    def level(self, l):
+        """(P tiles (d', 2, k, n_d k_in), sigma (d', 2, k), X (d', 2k, 2k), Y (8, d', 2k, 2k))
+        of level l >= 2 (P: from level l - 1 to l; X, Y: the level-l operator)."""
+        lv = self.levels[l - 2]
+        d = int(np.prod(lv["dims"]))
+        k = lv["k"]
+        P = torch.empty((d, 2, k, lv["nd"] * lv["k_in"]), dtype=torch.complex128, device=self.device)
+        S = torch.empty((d, 2, k), dtype=torch.float64, device=self.device)
+        X = torch.empty((d, 2 * k, 2 * k), dtype=torch.complex128, device=self.device)
+        Y = torch.empty((8, d, 2 * k, 2 * k), dtype=torch.complex128, device=self.device)
+        L.check(L.lib().mg_get_level(self._h, int(l), _ptr(P), _ptr(S), _ptr(X), _ptr(Y),
+                                     _stream(P)), "mg_get_level")
+        return P, S, X, Y
 
     def coarse_apply(self, vc):
         dt = _DT[vc.dtype]

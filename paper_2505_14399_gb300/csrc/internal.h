@@ -311,6 +311,22 @@ template <typename R>
 int coarse_apply_launch(cplx<R>* y, const cplx<R>* x, const cplx<R>* Op, int k, const Blocking& B,
                         int nrhs, cudaStream_t st);
 
+// ------------------------------------------------------------------ deeper levels
+// B: L = level-l lattice, b = aggregate, C = level-(l+1) lattice, M = n_d k (k = k_l); level-l
+// vectors [site][alpha][k], level-(l+1) vectors [J][alpha][kp]; P tiles [2J + alpha][kp][M].
+template <typename R>
+int coarse_gather(void* tiles, int cmax, int col0, const cplx<R>* fields, int nvec,
+                  const Blocking& B, int k, cudaStream_t st, bool df64);
+template <typename R>
+int coarse_restrict(cplx<R>* vc, const cplx<R>* v, const cplx<R>* P, const Blocking& B, int k,
+                    int kp, int nrhs, cudaStream_t st);
+template <typename R>
+int coarse_prolong(cplx<R>* v, const cplx<R>* vc, const cplx<R>* P, const Blocking& B, int k,
+                   int kp, int nrhs, cudaStream_t st);
+// Op2 = P^dag Op P (Eq. 5) as the level-(l+1) stencil, from the level-l stencil Op; FP64
+int coarse_galerkin(zd* Op2, const zd* Op, const zd* P, const Blocking& B, int k, int kp,
+                    cudaStream_t st);
+
 // ------------------------------------------------------------------ even-odd (Schur) form
 // even/odd half-lattice fields (checkerboard index site / 2) of nrhs full-lattice fields;
 // split skips a NULL output
@@ -334,5 +350,10 @@ int link_gradient_launch(double* out, const zd* gb, const zd* x, const zd* links
 template <typename R>
 int gaussian_fill(cplx<R>* out, unsigned long long seed, unsigned id0, int nvec, int V,
                   cudaStream_t st);
+// out[v][site][c] for nsites sites of ncomp components, counter (site, c, id0 + v, word3)
+// (word3: 0 on the fine lattice, the level index on a coarse level)
+template <typename R>
+int gaussian_fill_n(cplx<R>* out, unsigned long long seed, unsigned id0, int nvec, int nsites,
+                    int ncomp, unsigned word3, cudaStream_t st);
 
 }  // namespace wmg

@@ -13,6 +13,36 @@
 
 using namespace wmg;
 
+// A level below level 1 (Sec. 2.1 end; Sec. 4 uses three and four levels): built by
+// mg_add_level from the coarsest operator so far, level l, with the setup of Algorithm 3 and
+// the Galerkin product of Eq. 5; it holds P_l (level l -> l + 1) and the operator of level
+// l + 1, and the solver state of the K-cycle of level l.
+struct CLevel {
+  Blocking B;              // L: level-l lattice, b: aggregate, C: level-(l+1) lattice,
+                           // M = n_d k_in rows per tile
+  int k_in = 0, k = 0;     // k_l and k_{l+1}
+  double tol = 0.03;       // relative tolerance of the level-(l+1) solve
+  zd* P64 = nullptr;       // [2 d'][k][M]
+  zf* P32 = nullptr;
+  double* sigma = nullptr; // [2 d'][k]
+  zd* Op64 = nullptr;      // level-(l+1) stencil [d'][9][2k][2k] (column-major blocks)
+  zf* Op32 = nullptr;
+  size_t n_in = 0, n = 0;  // complex entries of a level-l / level-(l+1) vector
+  Gmres<double> solve64, post64;   // level-(l+1) solve, level-l post-smoother
+  Gmres<float> solve32, post32;
+  void *vc = nullptr, *ec = nullptr, *kw = nullptr, *ke = nullptr;   // solve precision
+  long long its = 0;       // level-(l+1) iterations of the current solve
+  void free_solver() {
+    solve64.release(); post64.release(); solve32.release(); post32.release();
+    dev_free(vc); dev_free(ec); dev_free(kw); dev_free(ke);
+    vc = ec = kw = ke = nullptr;
+  }
+  ~CLevel() {
+    free_solver();
+    dev_free(P64); dev_free(P32); dev_free(sigma); dev_free(Op64); dev_free(Op32);
+  }
+};
+
 struct mg_handle {
   mg_params p;
   Geom g;
@@ -56,6 +86,7 @@ struct mg_handle {
   double* dscal = nullptr;     // device scalars [4][nrhs]
   double* hscal = nullptr;     // pinned
   ReduceWork rw;
+  std::vector<std::unique_ptr<CLevel>> lv;   // levels 2, 3, ... (mg_add_level)
   // counters of the last solve
   long long coarse_its = 0;
   int kcycles = 0;
@@ -313,7 +344,7 @@ int ensure_solver(mg_handle* h, int nrhs) {
     WMG_TRY(dev_alloc(&h->kw64, f * sizeof(zd)));
     WMG_TRY(dev_alloc(&h->ke64, f * sizeof(zd)));
     WMG_TRY(h->outer64.alloc(h->nf, nrhs, p.outer_restart, true));
-    WMG_TRY(h->coarse64.alloc(h->nc, nrhs, p.coarse_restart, false));
+    WMG_TRY(h->coarse64.alloc(h->nc, nrhs, p.coarse_restart, !h->lv.empty()));
     if (p.coarse_persistent) WMG_TRY(h->csol64.alloc(h->nc, p.coarse_restart));
     WMG_TRY(h->post64.alloc(h->nf, nrhs, p.post_smooth > 0 ? p.post_smooth : 1, false));
   } else {
@@ -324,7 +355,7 @@ int ensure_solver(mg_handle* h, int nrhs) {
     WMG_TRY(dev_alloc(&h->kw32, f * sizeof(zf)));
     WMG_TRY(dev_alloc(&h->ke32, f * sizeof(zf)));
     WMG_TRY(h->outer32.alloc(h->nf, nrhs, p.outer_restart, true));
-    WMG_TRY(h->coarse32.alloc(h->nc, nrhs, p.coarse_restart, false));
+    WMG_TRY(h->coarse32.alloc(h->nc, nrhs, p.coarse_restart, !h->lv.empty()));
     if (p.coarse_persistent) WMG_TRY(h->csol32.alloc(h->nc, p.coarse_restart));
     int ps = p.post_smooth > 0 ? p.post_smooth : 1;
     if (p.solve_dtype == MG_F16 || p.solve_dtype == MG_BF16) {
@@ -334,6 +365,23 @@ int ensure_solver(mg_handle* h, int nrhs) {
       else WMG_TRY(h->postb.alloc(h->nf, nrhs, ps, false));
     } else {
       WMG_TRY(h->post32.alloc(h->nf, nrhs, ps, false));
+    }
+  }
+  for (auto& L : h->lv) {
+    const bool d64 = p.solve_dtype == MG_C128;
+    const size_t es = d64 ? sizeof(zd) : sizeof(zf);
+    WMG_TRY(dev_alloc(&L->vc, L->n * nrhs * es));
+    WMG_TRY(dev_alloc(&L->ec, L->n * nrhs * es));
+    WMG_TRY(dev_alloc(&L->kw, L->n_in * nrhs * es));
+    WMG_TRY(dev_alloc(&L->ke, L->n_in * nrhs * es));
+    const bool coarsest = L.get() == h->lv.back().get();
+    int ps = p.post_smooth > 0 ? p.post_smooth : 1;
+    if (d64) {
+      WMG_TRY(L->solve64.alloc(L->n, nrhs, p.coarse_restart, !coarsest));
+      WMG_TRY(L->post64.alloc(L->n_in, nrhs, ps, false));
+    } else {
+      WMG_TRY(L->solve32.alloc(L->n, nrhs, p.coarse_restart, !coarsest));
+      WMG_TRY(L->post32.alloc(L->n_in, nrhs, ps, false));
     }
   }
   if (p.schur_smoother) {
@@ -452,6 +500,67 @@ Op<R> coarse_op(mg_handle* h, int nrhs) {
   };
 }
 
+// D_l on level-l vectors (l >= 1): the level-1 operator, or that of a level added by
+// mg_add_level
+template <typename R>
+Op<R> level_op(mg_handle* h, int l, int nrhs) {
+  if (l == 1) return coarse_op<R>(h, nrhs);
+  CLevel* L = h->lv[l - 2].get();
+  return [L, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t st) -> int {
+    const cplx<R>* Op = std::is_same<R, double>::value ? (const cplx<R>*)L->Op64
+                                                        : (const cplx<R>*)L->Op32;
+    return coarse_apply_launch<R>(out, in, Op, L->k, L->B, nrhs, st);
+  };
+}
+
+template <typename R>
+Gmres<R>& lv_solve(CLevel* L);
+template <> Gmres<double>& lv_solve<double>(CLevel* L) { return L->solve64; }
+template <> Gmres<float>& lv_solve<float>(CLevel* L) { return L->solve32; }
+template <typename R>
+Gmres<R>& lv_post(CLevel* L);
+template <> Gmres<double>& lv_post<double>(CLevel* L) { return L->post64; }
+template <> Gmres<float>& lv_post<float>(CLevel* L) { return L->post32; }
+
+// K-cycle of level l >= 1 (Sec. 2.1 end): z = M_l v -- restrict with P_l, solve level l + 1
+// to its tolerance (FGMRES preconditioned by the K-cycle of level l + 1, GMRES on the
+// coarsest level), prolong, post_smooth GMRES steps on D_l.
+template <typename R>
+Op<R> kcycle_level(mg_handle* h, int l, int nrhs) {
+  return [h, l, nrhs](cplx<R>* z, const cplx<R>* v, cudaStream_t st) -> int {
+    const mg_params& p = h->p;
+    CLevel* L = h->lv[l - 1].get();
+    const cplx<R>* P = std::is_same<R, double>::value ? (const cplx<R>*)L->P64
+                                                       : (const cplx<R>*)L->P32;
+    cplx<R>* vc = static_cast<cplx<R>*>(L->vc);
+    cplx<R>* ec = static_cast<cplx<R>*>(L->ec);
+    cplx<R>* kw = static_cast<cplx<R>*>(L->kw);
+    cplx<R>* ke = static_cast<cplx<R>*>(L->ke);
+    WMG_TRY(coarse_restrict<R>(vc, v, P, L->B, L->k_in, L->k, nrhs, st));
+    Op<R> A = level_op<R>(h, l + 1, nrhs);
+    int its = 0, s;
+    if (l == (int)h->lv.size()) {
+      s = lv_solve<R>(L).solve(A, nullptr, ec, vc, L->tol, p.coarse_restart, p.coarse_maxiter,
+                               &its, st, 8);
+    } else {
+      Op<R> M = kcycle_level<R>(h, l + 1, nrhs);
+      s = lv_solve<R>(L).solve(A, &M, ec, vc, L->tol, p.coarse_restart, p.coarse_maxiter, &its,
+                               st);
+    }
+    if (s != MG_OK && s != MG_ENOCONV) return s;
+    L->its += (long long)its * nrhs;
+    WMG_TRY(coarse_prolong<R>(z, ec, P, L->B, L->k_in, L->k, nrhs, st));
+    if (p.post_smooth > 0) {
+      Op<R> D = level_op<R>(h, l, nrhs);
+      WMG_TRY(D(kw, z, st));
+      WMG_TRY(axpby<R>(kw, 1.0, v, -1.0, L->n_in * nrhs, 1, st));   // kw = v - D_l z
+      WMG_TRY(lv_post<R>(L).fixed(D, ke, kw, p.post_smooth, st));
+      WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, L->n_in * nrhs, 1, st));    // z += e
+    }
+    return MG_OK;
+  };
+}
+
 // z = M v: restrict, coarse GMRES to coarse_tol, prolong, post-smooth (Sec. 2.1 K-cycle, Sec. 4)
 template <typename R>
 Op<R> kcycle_op(mg_handle* h, int nrhs) {
@@ -463,7 +572,15 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
     cplx<R>* ke = Lvl<R>::ke(h);
     WMG_TRY(restrict_launch<R>(vc, v, Lvl<R>::P(h), h->k, h->B, nrhs, st));
     int its = 0;
-    if (p.coarse_persistent && Lvl<R>::csol(h).fits(h->B, h->k)) {
+    if (!h->lv.empty()) {
+      // deeper hierarchy: FGMRES on level 1 preconditioned by the K-cycle of level 1
+      Op<R> Dc = coarse_op<R>(h, nrhs);
+      Op<R> M1 = kcycle_level<R>(h, 1, nrhs);
+      int s = Lvl<R>::coarse(h).solve(Dc, &M1, ec, vc, p.coarse_tol, p.coarse_restart,
+                                      p.coarse_maxiter, &its, st);
+      if (s != MG_OK && s != MG_ENOCONV) return s;
+      its *= nrhs;
+    } else if (p.coarse_persistent && Lvl<R>::csol(h).fits(h->B, h->k)) {
       // one cooperative launch per system: the whole restarted coarse GMRES on the device
       // (its iteration count accumulates there and is read once per solve)
       for (int r = 0; r < nrhs; ++r)
@@ -512,6 +629,7 @@ int solve_impl(mg_handle* h, zd* x, const zd* b, int nrhs, double tol, int maxit
   WMG_TRY(ensure_solver(h, nrhs));
   h->coarse_its = 0;
   h->kcycles = 0;
+  for (auto& L : h->lv) L->its = 0;
   WMG_TRY(h->csol64.take_iterations(nullptr, st));   // drop counts of an unfinished solve
   WMG_TRY(h->csol32.take_iterations(nullptr, st));
   std::vector<double> bn(nrhs), rn(nrhs);
@@ -585,6 +703,76 @@ int solve_impl(mg_handle* h, zd* x, const zd* b, int nrhs, double tol, int maxit
   return MG_OK;
 }
 
+// Algorithm 3 on the coarsest operator so far, D_l (l >= 1): test vectors psi = phi +
+// GMRES_sweeps(D_l, -D_l phi) (Eq. 2) from Philox fields with counter word 3 = l, chiral split
+// (sigma_3 halves of each site's vector) into the aggregates of L->B, streaming SVD in FP64;
+// P_l (canonical phase) and its last-stream singular values into L.
+int setup_level(mg_handle* h, CLevel* L, int l, int r, int n_s, cudaStream_t st) {
+  const mg_params& p = h->p;
+  const int k = L->k, cmax = k + r;
+  const size_t ntile = (size_t)L->B.d * 2, M = L->B.M;
+  const size_t fr = L->n_in * r;
+  const int nsites = L->B.L[0] * L->B.L[1] * L->B.L[2] * L->B.L[3];
+  zd *phi = nullptr, *psi = nullptr, *tmp = nullptr, *T0 = nullptr, *T1 = nullptr, *G = nullptr,
+     *Vec = nullptr;
+  double* lam = nullptr;
+  Gmres<double> gm;
+  int status = MG_OK;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    dfree(phi); dfree(psi); dfree(tmp); dfree(T0); dfree(T1); dfree(G); dfree(Vec); dfree(lam);
+  };
+#define STEP(x) do { status = (x); if (status != MG_OK) { cleanup(); return status; } } while (0)
+  STEP(dev_alloc(&phi, fr * sizeof(zd)));
+  STEP(dev_alloc(&psi, fr * sizeof(zd)));
+  STEP(dev_alloc(&tmp, fr * sizeof(zd)));
+  STEP(dev_alloc(&T0, ntile * cmax * M * sizeof(zd)));
+  STEP(dev_alloc(&T1, ntile * cmax * M * sizeof(zd)));
+  STEP(dev_alloc(&G, ntile * cmax * cmax * sizeof(zd)));
+  STEP(dev_alloc(&Vec, ntile * cmax * cmax * sizeof(zd)));
+  STEP(dev_alloc(&lam, ntile * cmax * sizeof(double)));
+  Op<double> D = level_op<double>(h, l, r);
+  STEP(gm.alloc(L->n_in, r, p.sweeps > 0 ? p.sweeps : 1, false));
+  zd *cur = T0, *oth = T1;
+  int kk = 0;
+  for (int s = 0; s < n_s; ++s) {
+    STEP(gaussian_fill_n<double>(phi, p.seed, (unsigned)(s * r), r, nsites, 2 * L->k_in,
+                                 (unsigned)l, st));
+    STEP(D(tmp, phi, st));
+    STEP(axpby<double>(tmp, 0.0, tmp, -1.0, fr, 1, st));        // tmp = -D_l phi
+    STEP(gm.fixed(D, psi, tmp, p.sweeps, st));
+    STEP(axpby<double>(psi, 1.0, phi, 1.0, fr, 1, st));         // psi = phi + psi'
+    STEP(coarse_gather<double>(cur, cmax, kk, psi, r, L->B, L->k_in, st, false));
+    const int c = kk + r, kn = c < k ? c : k;
+    const bool last = s == n_s - 1;
+    STEP(tile_gram(G, cur, cmax, c, L->B, st, false));
+    STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, 1e-15, false));
+    if (p.svd_refine != 0) {
+      STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, c, 0, L->B, st, false));
+      STEP(tile_gram(G, oth, cmax, c, L->B, st, false));
+      STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, 1e-15, false));
+      STEP(tile_update(cur, cmax, oth, cmax, c, Vec, lam, kn, last ? 1 : 0, L->B, st, false));
+    } else {
+      STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, kn, last ? 1 : 0, L->B, st, false));
+      zd* t = cur; cur = oth; oth = t;
+    }
+    if (last) STEP(tile_sigma(L->sigma, k, lam, c, kn, (int)ntile, st));
+    kk = kn;
+  }
+  STEP(tile_canonical_phase(cur, cmax, k, L->B, st, false));
+  {
+    cudaError_t e = cudaMemcpy2DAsync(L->P64, (size_t)k * M * sizeof(zd), cur,
+                                      (size_t)cmax * M * sizeof(zd), (size_t)k * M * sizeof(zd),
+                                      ntile, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) { cleanup(); return fail(MG_ECUDA, cudaGetErrorString(e)); }
+  }
+  STEP((convert<float, double>(L->P32, L->P64, nullptr, 0, ntile * k * M, 1, st)));
+  cleanup();
+  if (take_device_error()) return fail(MG_ETIMEOUT, "mg_add_level: a bounded wait gave up");
+#undef STEP
+  return MG_OK;
+}
+
 int check_ready(mg_handle* h, bool need_coarse) {
   if (!h) return fail(MG_EINVAL, "NULL handle");
   if (!h->have_P) return fail(MG_EINVAL, "handle has no prolongator");
@@ -607,6 +795,7 @@ void mg_handle::free_solver() {
   posth.release(); postb.release();
   posts64.release(); posts32.release();
   for (auto& b : sbuf) dfree(b);
+  for (auto& L : lv) L->free_solver();
   dfree(kwh); dfree(keh);
   dfree(x64); dfree(r64); dfree(t64); dfree(e32); dfree(r32);
   dfree(vc64); dfree(ec64); dfree(kw64); dfree(ke64);
@@ -663,6 +852,58 @@ extern "C" int mg_setup_from_vectors(mg_handle** h, const void* links, const mg_
   return MG_OK;
 }
 
+extern "C" int mg_add_level(mg_handle* h, const int block[4], int k, int r, int n_s, double tol,
+                            void* stream) {
+  WMG_TRY(check_ready(h, true));
+  if (!block) return fail(MG_EINVAL, "mg_add_level: NULL block");
+  if (h->lv.size() >= 6) return fail(MG_EINVAL, "mg_add_level: at most 8 levels");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int l = 1 + (int)h->lv.size();      // the level the new P starts from
+  const Blocking& Bp = h->lv.empty() ? h->B : h->lv.back()->B;
+  const int k_in = h->lv.empty() ? h->k : h->lv.back()->k;
+  const zd* Op_in = h->lv.empty() ? h->Op64 : h->lv.back()->Op64;
+  std::unique_ptr<CLevel> L(new CLevel());
+  WMG_TRY(make_blocking(L->B, Bp.C, block));
+  const int nd = L->B.nd;
+  if (k < 1 || k > 32 || k > nd * k_in) return fail(MG_EINVAL, "mg_add_level: k in [1, min(32, n_d k_l)]");
+  if (r < 1 || n_s < 1 || k + r > 64 || (long long)r * n_s < k)
+    return fail(MG_EINVAL, "mg_add_level: need r, n_s >= 1, k + r <= 64, n_s r >= k");
+  if (!(tol > 0 && tol < 1)) return fail(MG_EINVAL, "mg_add_level: tol in (0, 1)");
+  L->B.M = nd * k_in;
+  L->k_in = k_in;
+  L->k = k;
+  L->tol = tol;
+  L->n_in = (size_t)L->B.d * nd * 2 * k_in;
+  L->n = (size_t)L->B.d * 2 * k;
+  const size_t ntile = (size_t)L->B.d * 2;
+  WMG_TRY(dev_alloc(&L->P64, ntile * k * L->B.M * sizeof(zd)));
+  WMG_TRY(dev_alloc(&L->P32, ntile * k * L->B.M * sizeof(zf)));
+  WMG_TRY(dev_alloc(&L->sigma, ntile * k * sizeof(double)));
+  const size_t ne = (size_t)L->B.d * 9 * 4 * k * k;
+  WMG_TRY(dev_alloc(&L->Op64, ne * sizeof(zd)));
+  WMG_TRY(dev_alloc(&L->Op32, ne * sizeof(zf)));
+  if (h->nrhs) cudaDeviceSynchronize();
+  h->free_solver();                       // the solver state is rebuilt for the new depth
+  WMG_TRY(setup_level(h, L.get(), l, r, n_s, st));
+  WMG_TRY(coarse_galerkin(L->Op64, Op_in, L->P64, L->B, k_in, k, st));
+  WMG_TRY((convert<float, double>(L->Op32, L->Op64, nullptr, 0, ne, 1, st)));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  h->lv.push_back(std::move(L));
+  return MG_OK;
+}
+
+extern "C" int mg_num_levels(const mg_handle* h) {
+  if (!h) return 0;
+  return h->have_coarse ? 2 + (int)h->lv.size() : 1;
+}
+
+extern "C" int mg_level_iterations(const mg_handle* h, long long* its, int nmax) {
+  if (!h || !its) return fail(MG_EINVAL, "mg_level_iterations: NULL argument");
+  int n = 1 + (int)h->lv.size();
+  for (int i = 0; i < n && i < nmax; ++i) its[i] = i == 0 ? h->coarse_its : h->lv[i - 1]->its;
+  return MG_OK;
+}
+
 extern "C" int coarse_build(mg_handle* h, void* stream) {
   WMG_TRY(check_ready(h, false));
   cudaStream_t st = (cudaStream_t)stream;
@@ -670,6 +911,12 @@ extern "C" int coarse_build(mg_handle* h, void* stream) {
   if (!h->Op64) {
     WMG_TRY(dev_alloc(&h->Op64, (size_t)h->B.d * 9 * ne * sizeof(zd)));
     WMG_TRY(dev_alloc(&h->Op32, (size_t)h->B.d * 9 * ne * sizeof(zf)));
+  }
+  if (!h->lv.empty()) {
+    // the levels below were built from the operator this call replaces
+    cudaDeviceSynchronize();
+    h->free_solver();
+    h->lv.clear();
   }
   zd* Xpart = nullptr;
   WMG_CUDA(cudaMallocAsync(&Xpart, (size_t)4 * h->B.d * ne * sizeof(zd), st));
@@ -732,6 +979,10 @@ extern "C" int coarse_build_noalloc(mg_handle* h, void* stream) {
   if (!h->Op64 || !h->Op32)
     return fail(MG_EINVAL, "coarse_build_noalloc: the handle has no coarse-operator storage "
                            "yet; call coarse_build once first (it allocates that storage)");
+  if (!h->lv.empty())
+    return fail(MG_EINVAL, "coarse_build_noalloc: the handle has levels below level 1 "
+                           "(mg_add_level), which a new level-1 operator would leave stale; "
+                           "use coarse_build, which drops them");
   void* scratch = nullptr;
   WMG_TRY(galerkin_scratch(&scratch));
   bool df = galerkin_df(h->p);
@@ -891,6 +1142,11 @@ extern "C" int mg_set_prolongator(mg_handle* h, const void* P, void* stream) {
   h->have_P = true;
   h->have_coarse = false;
   h->pdf_ready = false;
+  if (!h->lv.empty()) {
+    cudaDeviceSynchronize();
+    h->free_solver();
+    h->lv.clear();
+  }
   return MG_OK;
 }
 
@@ -947,6 +1203,31 @@ extern "C" int mg_get_coarse_op(mg_handle* h, void* X, void* Y, void* stream) {
   WMG_LAUNCHED();
   WMG_TRY(stage_out_finish(sx, X, (size_t)h->B.d * ne * sizeof(zd), st));
   WMG_TRY(stage_out_finish(sy, Y, (size_t)8 * h->B.d * ne * sizeof(zd), st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+extern "C" int mg_get_level(mg_handle* h, int level, void* P, void* sigma, void* X, void* Y,
+                            void* stream) {
+  if (!h) return fail(MG_EINVAL, "NULL handle");
+  if (level < 2 || level - 2 >= (int)h->lv.size())
+    return fail(MG_EINVAL, "mg_get_level: level must be one added by mg_add_level (>= 2)");
+  CLevel* L = h->lv[level - 2].get();
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ntile = (size_t)L->B.d * 2;
+  if (P) WMG_CUDA(cudaMemcpyAsync(P, L->P64, ntile * L->k * L->B.M * sizeof(zd), cudaMemcpyDefault, st));
+  if (sigma) WMG_CUDA(cudaMemcpyAsync(sigma, L->sigma, ntile * L->k * sizeof(double), cudaMemcpyDefault, st));
+  if (X || Y) {
+    if (!X || !Y) return fail(MG_EINVAL, "mg_get_level: X and Y go together");
+    size_t ne = (size_t)4 * L->k * L->k;
+    Staged sx, sy;
+    WMG_TRY(stage_out_alloc(sx, X, (size_t)L->B.d * ne * sizeof(zd), st));
+    WMG_TRY(stage_out_alloc(sy, Y, (size_t)8 * L->B.d * ne * sizeof(zd), st));
+    export_coarse_kernel<<<256, 256, 0, st>>>((zd*)sx.dev, (zd*)sy.dev, L->Op64, 2 * L->k, L->B.d);
+    WMG_LAUNCHED();
+    WMG_TRY(stage_out_finish(sx, X, (size_t)L->B.d * ne * sizeof(zd), st));
+    WMG_TRY(stage_out_finish(sy, Y, (size_t)8 * L->B.d * ne * sizeof(zd), st));
+  }
   WMG_CUDA(cudaStreamSynchronize(st));
   return MG_OK;
 }

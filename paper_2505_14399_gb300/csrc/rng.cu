@@ -38,13 +38,13 @@ __device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1
 // integer 2^53 - m_a before rounding to float, so the tail is not lost to cancellation;
 // small u_a goes through log1pf.  Relative error against the FP64 map ~1e-7.
 __global__ void gaussian_kernel_f32(zf* out, uint32_t k0, uint32_t k1, unsigned id0, int V,
-                                    size_t total) {
+                                    int nc, uint32_t w3, size_t total) {
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
-    size_t per = (size_t)V * 12;
+    size_t per = (size_t)V * nc;
     unsigned v = (unsigned)(e / per);
     size_t rem = e % per;
-    uint32_t c[4] = {(uint32_t)(rem / 12), (uint32_t)(rem % 12), id0 + v, 0u};
+    uint32_t c[4] = {(uint32_t)(rem / nc), (uint32_t)(rem % nc), id0 + v, w3};
     philox10(c, k0, k1);
     unsigned long long ma = ((unsigned long long)(c[0] >> 5) << 26) | (c[1] >> 6);
     unsigned long long mb = ((unsigned long long)(c[2] >> 5) << 26) | (c[3] >> 6);
@@ -63,13 +63,13 @@ __global__ void gaussian_kernel_f32(zf* out, uint32_t k0, uint32_t k1, unsigned 
 
 template <typename R>
 __global__ void gaussian_kernel(cplx<R>* out, uint32_t k0, uint32_t k1, unsigned id0, int V,
-                                size_t total) {
+                                int nc, uint32_t w3, size_t total) {
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
-    size_t per = (size_t)V * 12;
+    size_t per = (size_t)V * nc;
     unsigned v = (unsigned)(e / per);
     size_t rem = e % per;
-    uint32_t c[4] = {(uint32_t)(rem / 12), (uint32_t)(rem % 12), id0 + v, 0u};
+    uint32_t c[4] = {(uint32_t)(rem / nc), (uint32_t)(rem % nc), id0 + v, w3};
     philox10(c, k0, k1);
     const double s53 = 1.1102230246251565e-16;  // 2^-53
     double ua = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6)) * s53;
@@ -84,22 +84,32 @@ __global__ void gaussian_kernel(cplx<R>* out, uint32_t k0, uint32_t k1, unsigned
 }  // namespace
 
 template <typename R>
-int gaussian_fill(cplx<R>* out, unsigned long long seed, unsigned id0, int nvec, int V,
-                  cudaStream_t st) {
-  size_t total = (size_t)nvec * V * 12;
+int gaussian_fill_n(cplx<R>* out, unsigned long long seed, unsigned id0, int nvec, int nsites,
+                    int ncomp, unsigned word3, cudaStream_t st) {
+  size_t total = (size_t)nvec * nsites * ncomp;
   size_t g = (total + 255) / 256;
   size_t cap = (size_t)num_sms() * 16;
-  unsigned grid = (unsigned)(g < cap ? g : cap);
+  unsigned grid = (unsigned)(g < cap ? (g < 1 ? 1 : g) : cap);
   uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
   if (sizeof(R) == 4)
-    gaussian_kernel_f32<<<grid, 256, 0, st>>>((zf*)out, k0, k1, id0, V, total);
+    gaussian_kernel_f32<<<grid, 256, 0, st>>>((zf*)out, k0, k1, id0, nsites, ncomp, word3, total);
   else
-    gaussian_kernel<R><<<grid, 256, 0, st>>>(out, k0, k1, id0, V, total);
+    gaussian_kernel<R><<<grid, 256, 0, st>>>(out, k0, k1, id0, nsites, ncomp, word3, total);
   WMG_LAUNCHED();
   return MG_OK;
 }
 
+template <typename R>
+int gaussian_fill(cplx<R>* out, unsigned long long seed, unsigned id0, int nvec, int V,
+                  cudaStream_t st) {
+  return gaussian_fill_n<R>(out, seed, id0, nvec, V, 12, 0u, st);
+}
+
 template int gaussian_fill<float>(zf*, unsigned long long, unsigned, int, int, cudaStream_t);
 template int gaussian_fill<double>(zd*, unsigned long long, unsigned, int, int, cudaStream_t);
+template int gaussian_fill_n<float>(zf*, unsigned long long, unsigned, int, int, int, unsigned,
+                                    cudaStream_t);
+template int gaussian_fill_n<double>(zd*, unsigned long long, unsigned, int, int, int, unsigned,
+                                     cudaStream_t);
 
 }  // namespace wmg
