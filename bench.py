@@ -449,9 +449,10 @@ def gpu_arm(args):
 
     fine = {}
     lc = [dims[m] // cfg["block"][m] for m in range(4)]
-    four = lambda reg: ((2, 2, 2, 2), 16, 16 if reg else 8, 1 if reg else 4, 0.06), \
-        ((lc[0] // 2, lc[1] // 2, lc[2] // 2, lc[3] // 2), 16, 16 if reg else 8,
-         1 if reg else 4, 0.6)
+    def four(reg):
+        return (((2, 2, 2, 2), 16, 16 if reg else 8, 1 if reg else 4, 0.06),
+                ((lc[0] // 2, lc[1] // 2, lc[2] // 2, lc[3] // 2), 16, 16 if reg else 8,
+                 1 if reg else 4, 0.6))
     for depth in (2, 4):
         for sw in (cfg["sweeps"], 20):
             row = {}

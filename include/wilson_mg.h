@@ -111,6 +111,11 @@ typedef struct mg_params {
                                 -1 two rows when every link is SU(3) to 1e-9, else three.
                                 1 on links that are not SU(3) to 1e-9 gives MG_EINVAL.
                                 The FP64 stencil always keeps three rows               */
+  double csw;                /* clover coefficient c_sw: 0 for the Wilson operator, else
+                                D = D_W + C with the clover term C of wilson_clover_field
+                                in every stencil, the setup and the Galerkin diagonal
+                                (Configuration B of Sec. 4); needs schur_smoother = 0 and
+                                solve_dtype MG_C128 / MG_C64                             */
   int schur_smoother;        /* 1: the K-cycle post-smoother solves the even-odd Schur
                                 system D_hat e_e = r_e + kappa H_eo r_o with post_smooth
                                 GMRES steps and reconstructs e_o = r_o + kappa H_oe e_e
@@ -190,6 +195,26 @@ int wilson_schur(void* out, const void* in, const void* links, const int dims[4]
                  int dagger, int dtype, int nrhs, void* stream);
 
 /* ---------------------------------------------------------------------------------
+ * wilson_clover_field -- the clover term of the Wilson-clover operator (the action of
+ * Configuration B, Sec. 4; the paper writes no term, this is the textbook form):
+ *   C(x) = -kappa c_sw sum_{mu<nu} sigma_mu_nu (x) F_mu_nu(x),  sigma_mu_nu = (i/2)[g_mu, g_nu],
+ *   F_mu_nu(x) = traceless part of (Q - Q^dag) / (8 i), Q the four plaquettes of the mu-nu
+ *   plane that start and end at x, counter-clockwise; periodic gauge field.
+ * sigma_mu_nu commutes with gamma_5, so C is two 6 x 6 Hermitian blocks per site:
+ *   clover: out, [site][alpha][6][6] complex double, rows/columns (spin within the
+ *   chirality, colour), alpha = 0 for spins 1,2 and 1 for spins 3,4;
+ *   links: complex double [mu][site][3][3].  FP64 arithmetic.
+ * ------------------------------------------------------------------------------- */
+int wilson_clover_field(void* clover, const void* links, const int dims[4], double kappa,
+                        double csw, void* stream);
+
+/* out = D_W in + C in (dagger: D_W^dag in + C in; C is Hermitian), full-lattice fields,
+ * dtype MG_C128 or MG_C64 for out, in, links and clover (layouts as above). */
+int wilson_clover_apply(void* out, const void* in, const void* links, const void* clover,
+                        const int dims[4], double kappa, const double hop_weight[4],
+                        const int bc_phase[4], int dagger, int dtype, int nrhs, void* stream);
+
+/* ---------------------------------------------------------------------------------
  * mg_setup_streaming_svd -- Algorithm 4 up to P: iCSVD (Algorithm 3) on the fine
  * operator.  For s = 0..n_s-1: r Philox complex-Gaussian phi_i (vector ids s*r+i),
  * psi_i = phi_i + GMRES_sweeps(D, -D phi_i) (Eq. 2); chiral split into aggregates
@@ -221,6 +246,21 @@ int mg_setup_streaming_svd(mg_handle** h, const void* links, const mg_params* p,
  * ------------------------------------------------------------------------------- */
 int mg_setup_from_vectors(mg_handle** h, const void* links, const mg_params* p,
                           const void* vectors, int vec_dtype, int smooth, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * mg_setup_ls -- the setup with the least-squares interpolation prolongator of Eq. 9
+ * (Sec. 5): per aggregate and chirality, with the tile V_f of the r test vectors (Eq. 2,
+ * Philox, as in mg_setup_streaming_svd), its SVD V_f = U Sigma V^dag and V_c = Sigma_k V_k^dag,
+ *   P_j = V_f Omega V_c^dag (V_c Omega V_c^dag)^{-1},   Omega = diag(omega),
+ * each column with the canonical phase.  omega = 1 gives U_k (the iCSVD prolongator); other
+ * weights (the paper names energy norms of the test vectors) give a prolongator whose columns
+ * are not orthonormal (the Galerkin product and R = P^dag handle that).
+ *   omega: r positive doubles, host or device, one per test vector, the same for every
+ *   aggregate.  Requires n_s = 1 and r >= k; one Gram pass (svd_refine is ignored).
+ * MG_EINVAL: as mg_setup_streaming_svd, plus n_s != 1, r < k, a weight <= 0.
+ * ------------------------------------------------------------------------------- */
+int mg_setup_ls(mg_handle** h, const void* links, const mg_params* p, const double* omega,
+                void* stream);
 
 /* Creates a handle with links and parameters but no prolongator (for mg_set_prolongator). */
 int mg_create(mg_handle** h, const void* links, const mg_params* p, void* stream);

@@ -13,6 +13,8 @@
   are kept as Phi_s = U_kk Sigma_kk; after the last stream U_k is the prolongator block
   of Eq. (6).  All blocks and both chiralities are updated in every stream (the loop
   nesting of Algorithm 3 read that way).
+* Least-squares interpolation (Eq. 9): P_j = V_f Omega V_c^dag (V_c Omega V_c^dag)^{-1} with
+  V_c = Sigma_k V_k^dag; the weights Omega (positive, one per test vector) are an input.
 * Canonical phase (library convention; singular vectors are only defined up to a phase):
   every kept column u is multiplied by conj(q)/|q| with q = sum of its entries, so
   that the sum of its entries is real and positive.
@@ -37,19 +39,24 @@ def block_geometry(dims, block):
     return coarse, local, cd, nd
 
 
-def smooth(phi, links, dims, kappa, w, bc, sweeps):
-    """psi = phi + GMRES_sweeps(D, -D phi, x0 = 0)  (Eq. 2)."""
-    A = lambda v: wilson.dslash(v, links, dims, kappa, w, bc).reshape(-1)
+def smooth(phi, links, dims, kappa, w, bc, sweeps, clover=None):
+    """psi = phi + GMRES_sweeps(D, -D phi, x0 = 0)  (Eq. 2); D = D_W + C with a clover term
+    C (V, 12, 12) when given."""
+    if clover is None:
+        A = lambda v: wilson.dslash(v, links, dims, kappa, w, bc).reshape(-1)
+    else:
+        from . import clover as _cl
+        A = lambda v: _cl.dslash(v, links, dims, kappa, 0.0, w, bc, C=clover).reshape(-1)
     b = -A(phi.reshape(-1))
     return phi.reshape(-1) + gmres_fixed(A, b, sweeps)
 
 
-def test_vectors(links, dims, kappa, w, bc, seed, r, stream, sweeps):
+def test_vectors(links, dims, kappa, w, bc, seed, r, stream, sweeps, clover=None):
     """The r smoothed test vectors of one stream, shape (r, V, 4, 3)."""
     V = wilson.volume(dims)
     ids = np.arange(stream * r, stream * r + r)
     phis = gaussian_vectors(seed, ids, V)
-    return np.stack([smooth(phis[i], links, dims, kappa, w, bc, sweeps).reshape(V, 4, 3)
+    return np.stack([smooth(phis[i], links, dims, kappa, w, bc, sweeps, clover).reshape(V, 4, 3)
                      for i in range(r)])
 
 
@@ -112,11 +119,32 @@ def icsvd_tiles(stream_tiles, k):
     return Pt, Sig, hist
 
 
-def icsvd(links, dims, kappa, w, bc, block, k, r, n_s, sweeps, seed):
+def ls_prolongator_tiles(tiles, k, omega):
+    """Least-squares interpolation (Eq. 9, Sec. 5) on every tile (d, 2, rows, m) of m test
+    vectors: P_j = V_f Omega V_c^dag (V_c Omega V_c^dag)^{-1} with V_f the tile, V_c =
+    Sigma_k V_k^dag from its SVD, Omega = diag(omega) (m positive weights, the same on every
+    tile).  Columns get the canonical phase (the SVD fixes V_k only up to a phase per column,
+    which P inherits).  Omega = I gives U_k.  Returns (P tiles (d, 2, rows, k), Sigma_k)."""
+    d, _, rows, m = tiles.shape
+    Om = np.diag(np.asarray(omega, dtype=np.float64))
+    P = np.zeros((d, 2, rows, k), dtype=np.complex128)
+    S = np.zeros((d, 2, k))
+    for j in range(d):
+        for a in range(2):
+            Vf = tiles[j, a]
+            _, s, Vh = np.linalg.svd(Vf, full_matrices=False)
+            Vc = np.diag(s[:k]) @ Vh[:k]
+            Pj = Vf @ Om @ Vc.conj().T @ np.linalg.inv(Vc @ Om @ Vc.conj().T)
+            P[j, a] = canonical_phase(Pj)
+            S[j, a] = s[:k]
+    return P, S
+
+
+def icsvd(links, dims, kappa, w, bc, block, k, r, n_s, sweeps, seed, clover=None):
     """Algorithm 3 end to end: smooth, split, stream. Returns (P tiles, Sigma, history)."""
     tiles = []
     for s in range(n_s):
-        vecs = test_vectors(links, dims, kappa, w, bc, seed, r, s, sweeps)
+        vecs = test_vectors(links, dims, kappa, w, bc, seed, r, s, sweeps, clover)
         tiles.append(chiral_split(vecs, dims, block))
     return icsvd_tiles(tiles, k)
 

@@ -12,6 +12,9 @@ levels one application of the preconditioner to v is:
 
 Readings the paper leaves open (restart lengths, iteration caps) are parameters.
 
+Wilson-clover operator (``clover=C``, the site-local term of ``oracle.clover``): D = D_W + C
+in the solve, the smoother and the Galerkin diagonal.
+
 Schur-form post-smoother (``schur=True``; the introduction lists even-odd preconditioning
 among the standard ones, Sec. 1): the post-smoother solves D e = r through the Schur
 complement on the even sites, GMRES_post on D_hat r_hat with r_hat = r_e + kappa H_eo r_o,
@@ -32,12 +35,14 @@ from . import schur as _schur
 
 class TwoLevel:
     def __init__(self, links, dims, kappa, hop_weight, bc, block, Pt, coarse_tol=0.03,
-                 coarse_restart=32, coarse_maxiter=1000, post=8, XY=None, schur=False):
+                 coarse_restart=32, coarse_maxiter=1000, post=8, XY=None, schur=False,
+                 clover=None):
         self.links, self.dims, self.kappa = links, dims, kappa
         self.w, self.bc, self.block, self.Pt = hop_weight, bc, block, Pt
         self.cd = [dims[m] // block[m] for m in range(4)]
+        self.clover = clover
         self.X, self.Y = XY if XY is not None else galerkin(Pt, links, dims, block, kappa,
-                                                          hop_weight, bc)
+                                                          hop_weight, bc, clover=clover)
         self.coarse_tol, self.coarse_restart = coarse_tol, coarse_restart
         self.coarse_maxiter, self.post = coarse_maxiter, post
         self.schur = schur
@@ -45,7 +50,11 @@ class TwoLevel:
         self.kcycles = 0
 
     def D(self, v):
-        return wilson.dslash(v, self.links, self.dims, self.kappa, self.w, self.bc).reshape(-1)
+        out = wilson.dslash(v, self.links, self.dims, self.kappa, self.w, self.bc).reshape(-1)
+        if self.clover is not None:
+            out = out + np.einsum('xrc,xc->xr', self.clover,
+                                  np.asarray(v).reshape(-1, 12)).reshape(-1)
+        return out
 
     def Dc(self, vc):
         return coarse_apply(self.X, self.Y, vc, self.cd).reshape(-1)

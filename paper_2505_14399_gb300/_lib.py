@@ -40,6 +40,7 @@ class MgParams(C.Structure):
         ("coarse_persistent", C.c_int),
         ("fp64_emulation", C.c_int),
         ("link_compress", C.c_int),
+        ("csw", C.c_double),
         ("schur_smoother", C.c_int),
     ]
 
@@ -71,9 +72,13 @@ SIGNATURES = {
                           C.POINTER(C.c_int), I, I, I, I, P]),
     "wilson_schur": (I, [P, P, P, C.POINTER(C.c_int), D, C.POINTER(C.c_double),
                          C.POINTER(C.c_int), I, I, I, P]),
+    "wilson_clover_field": (I, [P, P, C.POINTER(C.c_int), D, D, P]),
+    "wilson_clover_apply": (I, [P, P, P, P, C.POINTER(C.c_int), D, C.POINTER(C.c_double),
+                                C.POINTER(C.c_int), I, I, I, P]),
     "mg_setup_streaming_svd": (I, [C.POINTER(P), P, C.POINTER(MgParams), P]),
     "mg_setup_from_vectors": (I, [C.POINTER(P), P, C.POINTER(MgParams), P, I, I, P]),
     "mg_link_rows": (I, [P]),
+    "mg_setup_ls": (I, [C.POINTER(P), P, C.POINTER(MgParams), P, P]),
     "mg_add_level": (I, [P, C.POINTER(C.c_int), I, I, I, D, P]),
     "mg_num_levels": (I, [P]),
     "mg_level_iterations": (I, [P, C.POINTER(C.c_longlong), I]),

@@ -35,7 +35,7 @@ def params(dims, block, kappa, k, r, n_s, sweeps=5, seed=3000, hop_weight=(1, 1,
            bc=(1, 1, 1, 1), setup_dtype="c64", solve_dtype="c64", post_smooth=8,
            coarse_tol=0.03, coarse_restart=32, coarse_maxiter=2000, outer_restart=16,
            inner_tol=1e-5, svd_refine=-1, coarse_persistent=1, fp64_emulation=-1,
-           link_compress=-1, schur_smoother=0):
+           link_compress=-1, schur_smoother=0, csw=0.0):
     """Build an mg_params structure (paper symbols k, r, n_s; aggregates of extent `block`)."""
     p = L.MgParams()
     L.lib().mg_params_default(C.byref(p))
@@ -60,6 +60,7 @@ def params(dims, block, kappa, k, r, n_s, sweeps=5, seed=3000, hop_weight=(1, 1,
     p.fp64_emulation = int(fp64_emulation)
     p.link_compress = int(link_compress)
     p.schur_smoother = int(schur_smoother)
+    p.csw = float(csw)
     return p
 
 
@@ -96,6 +97,32 @@ def schur(inp, links, dims, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1, 1, 1), dag
     return out
 
 
+def clover_field(links, dims, kappa, csw):
+    """The clover term C(x) as (V, 2, 6, 6) complex128 chiral blocks."""
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    out = torch.empty((V, 2, 6, 6), dtype=torch.complex128, device=links.device)
+    L.check(L.lib().wilson_clover_field(_ptr(out), _ptr(links), L.ivec(dims), float(kappa),
+                                        float(csw), _stream(links)), "wilson_clover_field")
+    return out
+
+
+def clover_dslash(inp, links, clover, dims, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1, 1, 1),
+                  dagger=False, out=None):
+    """out = (D_W + C) in (dagger: D_W^dag in + C in)."""
+    dt = _DT[inp.dtype]
+    if links.dtype != inp.dtype or clover.dtype != inp.dtype:
+        raise ValueError("links, clover and fields must share a dtype")
+    if out is None:
+        out = torch.empty_like(inp)
+    V = dims[0] * dims[1] * dims[2] * dims[3]
+    nrhs = inp.numel() // (V * 12)
+    L.check(L.lib().wilson_clover_apply(_ptr(out), _ptr(inp), _ptr(links), _ptr(clover),
+                                        L.ivec(dims), float(kappa), L.dvec(hop_weight),
+                                        L.ivec(bc), int(dagger), dt, int(nrhs), _stream(inp)),
+            "wilson_clover_apply")
+    return out
+
+
 def test_vectors(links, p, stream_index, device=None):
     """The r smoothed test vectors of one stream (Eq. 2), complex128 (r, V, 4, 3)."""
     V = p.dims[0] * p.dims[1] * p.dims[2] * p.dims[3]
@@ -118,7 +145,7 @@ def link_gradient(g_b, x, links, dims, kappa, hop_weight=(1, 1, 1, 1), bc=(1, 1,
 class Hierarchy:
     """Owner of an mg_handle: iCSVD prolongator, Galerkin coarse operator, K-cycle solver."""
 
-    def __init__(self, links, p, setup=True, vectors=None, smooth=False):
+    def __init__(self, links, p, setup=True, vectors=None, smooth=False, ls_omega=None):
         """setup: run the iCSVD setup (Philox test vectors), else only create the handle.
         vectors: (n_s r, V, 4, 3) complex128 / complex64 fields for mg_setup_from_vectors
         (smooth: they are initial guesses phi of Eq. 2, else the test vectors themselves)."""
@@ -131,6 +158,11 @@ class Hierarchy:
         self.d = self.V // self.nd
         self.device = links.device
         self._h = C.c_void_p()
+        if ls_omega is not None:
+            w = np.ascontiguousarray(np.asarray(ls_omega, dtype=np.float64))
+            L.check(L.lib().mg_setup_ls(C.byref(self._h), _ptr(links), C.byref(p),
+                                        C.c_void_p(w.ctypes.data), _stream(links)), "mg_setup_ls")
+            return
         if vectors is not None:
             vdt = _DT[vectors.dtype]
             L.check(L.lib().mg_setup_from_vectors(C.byref(self._h), _ptr(links), C.byref(p),
@@ -274,6 +306,9 @@ class MGSolve(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, b, omega, hier, links, tol):
+        if getattr(getattr(hier, "p", None), "csw", 0.0) != 0.0:
+            raise ValueError("MGSolve: link-angle gradients of the clover term are not "
+                             "implemented (csw must be 0)")
         if omega is not None and bool(torch.any(omega != 0)):
             raise ValueError("MGSolve: omega must be zero (gradients are taken at the given "
                              "links; rotate the links and rebuild the hierarchy instead)")

@@ -490,6 +490,78 @@ __global__ void tile_outputs_kernel(zd* P, zf* P32, zdf* Pdf, const zdf* __restr
   }
 }
 
+// Least-squares interpolation weights (Eq. 9): with the tile A = U Sigma V^dag (V and
+// Sigma^2 from the Gram eigen-decomposition), V_c = Sigma_k V_k^dag and Omega = diag(omega),
+//   P = A Omega V_c^dag (V_c Omega V_c^dag)^{-1} = A W,  W = Omega V_k B^{-1} Sigma_k^{-1},
+//   B = V_k^dag Omega V_k (k x k, Hermitian positive definite for omega > 0).
+// One CTA per tile: B in shared memory, inverted by Gauss-Jordan elimination with partial
+// pivoting in FP64; W[t][row][i] (leading dimension c, columns i < k) for tile_update.
+__global__ void __launch_bounds__(GT) ls_weights_kernel(zd* W, const zd* __restrict__ Vec,
+                                                        const double* __restrict__ lam,
+                                                        const double* __restrict__ omega, int c,
+                                                        int k) {
+  extern __shared__ zd lsm[];
+  zd* Bm = lsm;                  // [k][2k]: B | I, reduced to I | B^-1
+  zd* fc = Bm + (size_t)k * 2 * k;   // [k] the pivot column's factors of one elimination step
+  __shared__ int piv;
+  __shared__ double pmax;
+  const int t = blockIdx.x, w2 = 2 * k;
+  const zd* V = Vec + (size_t)t * c * c;   // V[row * c + i]
+  for (int e = threadIdx.x; e < k * w2; e += blockDim.x) {
+    int a = e / w2, b = e % w2;
+    zd s = {0, 0};
+    if (b < k) {
+      for (int r = 0; r < c; ++r) cfmac(s, V[r * c + a], omega[r] * V[r * c + b]);
+    } else {
+      s = {(b - k) == a ? 1.0 : 0.0, 0.0};
+    }
+    Bm[e] = s;
+  }
+  __syncthreads();
+  for (int col = 0; col < k; ++col) {
+    if (threadIdx.x == 0) {
+      int p = col;
+      double m = -1;
+      for (int r = col; r < k; ++r) {
+        double v = norm2(Bm[r * w2 + col]);
+        if (v > m) { m = v; p = r; }
+      }
+      piv = p;
+      pmax = m;
+    }
+    __syncthreads();
+    if (piv != col)
+      for (int b = threadIdx.x; b < w2; b += blockDim.x) {
+        zd x = Bm[col * w2 + b];
+        Bm[col * w2 + b] = Bm[piv * w2 + b];
+        Bm[piv * w2 + b] = x;
+      }
+    __syncthreads();
+    zd pv = Bm[col * w2 + col];
+    double d = norm2(pv);
+    zd inv = d > 0 ? zd{pv.re / d, -pv.im / d} : zd{0, 0};
+    __syncthreads();
+    for (int b = threadIdx.x; b < w2; b += blockDim.x) Bm[col * w2 + b] = Bm[col * w2 + b] * inv;
+    for (int r = threadIdx.x; r < k; r += blockDim.x) fc[r] = Bm[r * w2 + col];
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * w2; e += blockDim.x) {
+      int r = e / w2, b = e % w2;
+      if (r == col) continue;
+      Bm[e] = Bm[e] - fc[r] * Bm[col * w2 + b];
+    }
+    __syncthreads();
+  }
+  zd* Wt = W + (size_t)t * c * c;
+  for (int e = threadIdx.x; e < c * k; e += blockDim.x) {
+    int r = e / k, i = e % k;
+    zd s = {0, 0};
+    for (int a = 0; a < k; ++a) cfma(s, V[r * c + a], Bm[a * w2 + k + i]);
+    double l = lam[(size_t)t * c + i];
+    double f = l > 0 ? omega[r] / sqrt(l) : 0.0;
+    Wt[r * c + i] = f * s;
+  }
+}
+
 __global__ void sigma_kernel(double* sig, int ldsig, const double* lam, int c, int kk, int ntiles) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ntiles * kk) return;
@@ -602,6 +674,16 @@ int tile_outputs(zd* P, zf* P32, zdf* Pdf, const void* tiles, int cmax, int k, c
   size_t cap = (size_t)num_sms() * 16;
   tile_outputs_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(
       P, P32, Pdf, (const zdf*)tiles, cmax, k, B.M, total);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+int tile_ls_weights(zd* W, const zd* Vec, const double* lam, const double* omega, int c, int k,
+                    int ntiles, cudaStream_t st) {
+  if (k > c || c > MAXC) return fail(MG_EINVAL, "tile_ls_weights: bad sizes");
+  size_t sh = sizeof(zd) * ((size_t)k * 2 * k + k);
+  WMG_TRY(smem_attr(ls_weights_kernel, sh));
+  ls_weights_kernel<<<ntiles, GT, sh, st>>>(W, Vec, lam, omega, c, k);
   WMG_LAUNCHED();
   return MG_OK;
 }

@@ -285,6 +285,10 @@ int tile_canonical_phase(void* tiles, int cmax, int k, const Blocking& B, cudaSt
 // float (rounded) and, if Pdf is not null, double-float.
 int tile_outputs(zd* P, zf* P32, zdf* Pdf, const void* tiles, int cmax, int k, const Blocking& B,
                  cudaStream_t st);
+// Eq. 9 weights: W[t][row][i] = omega_row (V_k B^-1)[row][i] / sqrt(lam_i), B = V_k^dag Omega V_k,
+// so that A W is the least-squares interpolation prolongator (leading dimension c, i < k)
+int tile_ls_weights(zd* W, const zd* Vec, const double* lam, const double* omega, int c, int k,
+                    int ntiles, cudaStream_t st);
 // sig[t*ldsig + i] = sqrt(max(lam[t][i], 0)), i < kk
 int tile_sigma(double* sig, int ldsig, const double* lam, int c, int kk, int ntiles,
                cudaStream_t st);
@@ -339,6 +343,15 @@ int eo_join(E* full, const E* even, const E* odd, const Geom& g, int nrhs, cudaS
 template <typename E>
 int schur_apply(E* out, const E* in, E* tmp, const void* links, int layout, const Geom& g,
                 int dagger, int nrhs, cudaStream_t st);
+
+// ------------------------------------------------------------------ Wilson-clover term
+// C[site][alpha][6][6] = -kappa c_sw sum_{mu<nu} sigma_mu_nu (x) F_mu_nu (chiral blocks), FP64
+int clover_field(zd* C, const zd* links, const Geom& g, double csw, cudaStream_t st);
+// out[rhs][x] += C(x) in[rhs][x]
+template <typename R>
+int clover_add(cplx<R>* out, const cplx<R>* in, const cplx<R>* C, int V, int nrhs, cudaStream_t st);
+// X_j += sum_{x in Lambda_j} P(x)^dag C(x) P(x) on the chirality-diagonal blocks of Op
+int clover_galerkin_add(zd* Op, const zd* P, const zd* C, int k, const Blocking& B, cudaStream_t st);
 
 // ------------------------------------------------------------------ gradient
 int link_gradient_launch(double* out, const zd* gb, const zd* x, const zd* links, const Geom& g,

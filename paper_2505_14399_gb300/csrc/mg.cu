@@ -55,6 +55,8 @@ struct mg_handle {
   zf* links32L = nullptr;
   void* links16L = nullptr;    // half-storage solve: zh or zbf lane-contiguous links
   int llay = 1;                // layout of links32L / links16L: 1 three rows, 2 two rows
+  zd* clov64 = nullptr;        // clover term C(x) [site][2][6][6] (csw != 0), FP64 and FP32
+  zf* clov32 = nullptr;
   zd* P64 = nullptr;
   zf* P32 = nullptr;
   double* sigma = nullptr;   // [tile][k]
@@ -130,6 +132,10 @@ int validate(const mg_params* p, bool need_svd) {
   if (p->post_smooth < 0 || p->post_smooth > 64) return fail(MG_EINVAL, "post_smooth in [0, 64]");
   if (p->schur_smoother && p->solve_dtype != MG_C128 && p->solve_dtype != MG_C64)
     return fail(MG_EINVAL, "schur_smoother needs solve_dtype MG_C128 or MG_C64");
+  if (p->csw != 0 && (p->schur_smoother || p->solve_dtype == MG_F16 || p->solve_dtype == MG_BF16))
+    return fail(MG_EINVAL, "csw != 0: the clover term is applied in FP64 / FP32 without the "
+                           "Schur-form smoother (schur_smoother = 0, solve_dtype MG_C128 / MG_C64)");
+  if (!std::isfinite(p->csw)) return fail(MG_EINVAL, "csw must be finite");
   if (p->coarse_restart < 1 || p->coarse_restart > 128) return fail(MG_EINVAL, "coarse_restart in [1, 128]");
   if (p->outer_restart < 1 || p->outer_restart > 128) return fail(MG_EINVAL, "outer_restart in [1, 128]");
   if (!(p->coarse_tol > 0 && p->coarse_tol < 1)) return fail(MG_EINVAL, "coarse_tol in (0, 1)");
@@ -176,6 +182,12 @@ int create_handle(mg_handle** out, const void* links, const mg_params* p, bool n
     WMG_TRY(dev_alloc(&h->links16L, lbc * 4));
     if (p->solve_dtype == MG_F16) WMG_TRY(link_to_lanes_v<zh>((zh*)h->links16L, h->links64, h->g.V, st, rows));
     else WMG_TRY(link_to_lanes_v<zbf>((zbf*)h->links16L, h->links64, h->g.V, st, rows));
+  }
+  if (p->csw != 0) {
+    WMG_TRY(dev_alloc(&h->clov64, (size_t)h->g.V * 72 * sizeof(zd)));
+    WMG_TRY(dev_alloc(&h->clov32, (size_t)h->g.V * 72 * sizeof(zf)));
+    WMG_TRY(clover_field(h->clov64, h->links64, h->g, p->csw, st));
+    WMG_TRY((convert<float, double>(h->clov32, h->clov64, nullptr, 0, (size_t)h->g.V * 72, 1, st)));
   }
   size_t ntile = (size_t)h->B.d * 2;
   WMG_TRY(dev_alloc(&h->P64, ntile * h->k * h->B.M * sizeof(zd)));
@@ -232,20 +244,26 @@ int smooth_stream(mg_handle* h, cplx<R>* psi, cplx<R>* phi, cplx<R>* tmp, Gmres<
   int dt = sizeof(R) == 8 ? MG_C128 : MG_C64;
   const void* L = sizeof(R) == 8 ? (const void*)h->links64L : (const void*)h->links32L;
   const int lay = sizeof(R) == 8 ? 1 : h->llay;
-  Op<R> D = [h, dt, L, r, lay](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
-    return dslash_launch(dt, out, in, L, h->g, -1, 0, r, s2, h->nf, h->nf, lay);
+  const cplx<R>* Cl = sizeof(R) == 8 ? (const cplx<R>*)h->clov64 : (const cplx<R>*)h->clov32;
+  Op<R> D = [h, dt, L, r, lay, Cl](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
+    WMG_TRY(dslash_launch(dt, out, in, L, h->g, -1, 0, r, s2, h->nf, h->nf, lay));
+    if (Cl) WMG_TRY(clover_add<R>(out, in, Cl, h->g.V, r, s2));
+    return MG_OK;
   };
   WMG_TRY(D(tmp, phi, st));
   WMG_TRY(axpby<R>(tmp, 0.0, tmp, -1.0, h->nf * r, 1, st));   // tmp = -D phi
   WMG_TRY(gm.alloc(h->nf, r, p.sweeps > 0 ? p.sweeps : 1, false));
-  FusedStencil fz{h->links32L, h->g, h->llay};   // FP32 runs fuse the stencil with the projections
-  WMG_TRY(gm.fixed(D, psi, tmp, p.sweeps, st, false, sizeof(R) == 4 ? &fz : nullptr));
+  FusedStencil fz{h->links32L, h->g, h->llay};   // FP32 Wilson runs fuse the stencil with the projections
+  WMG_TRY(gm.fixed(D, psi, tmp, p.sweeps, st, false, sizeof(R) == 4 && !Cl ? &fz : nullptr));
   WMG_TRY(axpby<R>(psi, 1.0, phi, 1.0, h->nf * r, 1, st));     // psi = phi + psi'
   return MG_OK;
 }
 
+// ls_omega (device, r weights): the final update is the least-squares interpolation of Eq. 9
+// instead of U_k (one stream, one Gram pass)
 template <typename R>
-int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr) {
+int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr,
+              const double* ls_omega = nullptr) {
   const mg_params& p = h->p;
   int r = p.r, k = h->k;
   int cmax = k + r;
@@ -286,7 +304,12 @@ int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr) {
     bool last = s == p.n_s - 1;
     STEP(tile_gram(G, cur, cmax, c, h->B, st, df));
     STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, eig_tol, df));
-    if (p.svd_refine > 0 || (p.svd_refine < 0 && sizeof(R) == 8)) {
+    if (ls_omega) {
+      // P = A W with W = Omega V_k B^-1 Sigma_k^-1 (Eq. 9); G is free after the eigensolver
+      STEP(tile_ls_weights(G, Vec, lam, ls_omega, c, kn, (int)ntile, st));
+      STEP(tile_update(oth, cmax, cur, cmax, c, G, lam, kn, 0, h->B, st, df));
+      zd* t = cur; cur = oth; oth = t;
+    } else if (p.svd_refine > 0 || (p.svd_refine < 0 && sizeof(R) == 8)) {
       // B = A V (all c columns), then a second Gram/eig pass on B
       STEP(tile_update(oth, cmax, cur, cmax, c, Vec, lam, c, 0, h->B, st, df));
       STEP(tile_gram(G, oth, cmax, c, h->B, st, df));
@@ -433,8 +456,11 @@ template <> struct Lvl<float> {
 template <typename R>
 Op<R> fine_op(mg_handle* h, int nrhs) {
   return [h, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t st) -> int {
-    return dslash_launch(Lvl<R>::dtype, out, in, Lvl<R>::links(h), h->g, -1, 0, nrhs, st, h->nf,
-                         h->nf, Lvl<R>::layout(h));
+    WMG_TRY(dslash_launch(Lvl<R>::dtype, out, in, Lvl<R>::links(h), h->g, -1, 0, nrhs, st, h->nf,
+                          h->nf, Lvl<R>::layout(h)));
+    const cplx<R>* Cl = sizeof(R) == 8 ? (const cplx<R>*)h->clov64 : (const cplx<R>*)h->clov32;
+    if (Cl) WMG_TRY(clover_add<R>(out, in, Cl, h->g.V, nrhs, st));
+    return MG_OK;
   };
 }
 
@@ -606,9 +632,9 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
       }
       WMG_TRY(axpby<R>(kw, 1.0, v, -1.0, h->nf * nrhs, 1, st));   // kw = v - D z
       if (p.schur_smoother) return post_smooth_schur<R>(h, z, kw, nrhs, st);
-      FusedStencil fz{h->links32L, h->g, h->llay};   // FP32 runs fuse the stencil with the projections
+      FusedStencil fz{h->links32L, h->g, h->llay};   // FP32 Wilson runs fuse the stencil with the projections
       WMG_TRY(Lvl<R>::post(h).fixed(D, ke, kw, p.post_smooth, st, false,
-                                    sizeof(R) == 4 ? &fz : nullptr));
+                                    sizeof(R) == 4 && !h->clov32 ? &fz : nullptr));
       WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, h->nf * nrhs, 1, st));    // z += e
     }
     return MG_OK;
@@ -786,6 +812,7 @@ mg_handle::~mg_handle() {
   free_solver();
   dfree(links64); dfree(links64L); dfree(links32L); dfree(links16L); dfree(P64); dfree(P32); dfree(sigma); dfree(hist);
   dfree(Op64); dfree(Op32); dfree(PtP); dfree(Pdf); dfree(Ldf); dfree(tc_flag);
+  dfree(clov64); dfree(clov32);
 }
 
 void mg_handle::free_solver() {
@@ -904,6 +931,44 @@ extern "C" int mg_level_iterations(const mg_handle* h, long long* its, int nmax)
   return MG_OK;
 }
 
+extern "C" int mg_setup_ls(mg_handle** h, const void* links, const mg_params* p,
+                           const double* omega, void* stream) {
+  if (!p || !omega) return fail(MG_EINVAL, "mg_setup_ls: NULL argument");
+  if (p->n_s != 1) return fail(MG_EINVAL, "mg_setup_ls: Eq. 9 uses every test vector at once: n_s = 1");
+  if (p->r < p->k) return fail(MG_EINVAL, "mg_setup_ls: r >= k");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> w(p->r);
+  {
+    cudaPointerAttributes at{};
+    bool dev = cudaPointerGetAttributes(&at, omega) == cudaSuccess &&
+               (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (dev) WMG_CUDA(cudaMemcpy(w.data(), omega, p->r * sizeof(double), cudaMemcpyDeviceToHost));
+    else std::memcpy(w.data(), omega, p->r * sizeof(double));
+  }
+  for (double x : w)
+    if (!(x > 0) || !std::isfinite(x)) return fail(MG_EINVAL, "mg_setup_ls: weights must be positive");
+  WMG_TRY(create_handle(h, links, p, true, st));
+  double* dw = nullptr;
+  int s = dev_alloc(&dw, p->r * sizeof(double));
+  if (s == MG_OK) {
+    cudaError_t e = cudaMemcpyAsync(dw, w.data(), p->r * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) s = fail(MG_ECUDA, cudaGetErrorString(e));
+  }
+  if (s == MG_OK)
+    s = p->setup_dtype == MG_C128 ? run_setup<double>(*h, st, nullptr, dw)
+                                  : run_setup<float>(*h, st, nullptr, dw);
+  cudaStreamSynchronize(st);
+  dfree(dw);
+  if (s != MG_OK) {
+    std::string msg = mg_last_error();
+    delete *h;
+    *h = nullptr;
+    return fail(s, msg);
+  }
+  return MG_OK;
+}
+
 extern "C" int coarse_build(mg_handle* h, void* stream) {
   WMG_TRY(check_ready(h, false));
   cudaStream_t st = (cudaStream_t)stream;
@@ -925,6 +990,7 @@ extern "C" int coarse_build(mg_handle* h, void* stream) {
                          h->B, st, df, h->pdf_ready, h->tc_flag);
   cudaFreeAsync(Xpart, st);
   WMG_TRY(s);
+  if (h->clov64) WMG_TRY(clover_galerkin_add(h->Op64, h->P64, h->clov64, h->k, h->B, st));
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
   WMG_CUDA(cudaStreamSynchronize(st));
   h->have_coarse = true;
@@ -988,6 +1054,7 @@ extern "C" int coarse_build_noalloc(mg_handle* h, void* stream) {
   bool df = galerkin_df(h->p);
   WMG_TRY(galerkin_build(h->Op64, static_cast<zd*>(scratch), h->P64, h->Pdf, h->PtP, h->k,
                          h->links64, h->Ldf, h->g, h->B, st, df, h->pdf_ready, h->tc_flag));
+  if (h->clov64) WMG_TRY(clover_galerkin_add(h->Op64, h->P64, h->clov64, h->k, h->B, st));
   WMG_TRY((convert<float, double>(h->Op32, h->Op64, nullptr, 0, (size_t)h->B.d * 9 * ne, 1, st)));
   WMG_CUDA(cudaStreamSynchronize(st));
   h->have_coarse = true;
@@ -1106,6 +1173,11 @@ extern "C" int mg_apply_fine(mg_handle* h, void* out, const void* in, int nrhs, 
                   : dtype == MG_C64 ? (const void*)h->links32L : (const void*)h->links16L;
   WMG_TRY(dslash_launch(dtype, so.dev, si.dev, L, h->g, -1, dagger, nrhs, st, h->nf, h->nf,
                         dtype == MG_C128 ? 1 : h->llay));
+  // the clover term is Hermitian: the same for D and D^dag
+  if (dtype == MG_C128 && h->clov64)
+    WMG_TRY(clover_add<double>((zd*)so.dev, (const zd*)si.dev, h->clov64, h->g.V, nrhs, st));
+  else if (dtype == MG_C64 && h->clov32)
+    WMG_TRY(clover_add<float>((zf*)so.dev, (const zf*)si.dev, h->clov32, h->g.V, nrhs, st));
   WMG_TRY(stage_out_finish(so, out, bytes, st));
   return MG_OK;
 }

@@ -151,3 +151,40 @@ def test_supplied_initial_guesses_are_smoothed():
         tiles.append(icsvd.chiral_split(tv, cfg["dims"], cfg["block"]))
     _check("supplied_phi_c5", P.cpu().numpy(), H, tiles, cfg["k"], svd_bounds.U64)
     h.close()
+
+
+@pytest.mark.parametrize("cfg", [C1, C5], ids=["c1", "c5"])
+@pytest.mark.parametrize("weights", ["ones", "graded"])
+def test_least_squares_interpolation_prolongator(cfg, weights):
+    """Eq. 9 on the GPU (FP64 setup, one stream of r test vectors) against the oracle's
+    P_j = V_f Omega V_c^dag (V_c Omega V_c^dag)^{-1} on the same vectors.  The GPU computes V_k
+    from the Gram matrix: its error is the subspace bound of a single stream times the
+    condition number of V_k^dag Omega V_k; with Omega = 1 the result is U_k."""
+    U = links_for(cfg)
+    r = cfg["r"] * cfg["n_s"]
+    k = cfg["k"]
+    omega = np.ones(r) if weights == "ones" else 10.0 ** (-np.arange(r) / (r - 1))
+    p = params_for(cfg, setup_dtype="c128", n_s=1, r=r, fp64_emulation=0, svd_refine=0)
+    h = api.Hierarchy(to_dev(U), p, ls_omega=omega)
+    P, _ = h.prolongator()
+    P = P.cpu().numpy()
+    tv = icsvd.test_vectors(U, cfg["dims"], cfg["kappa"], cfg["hop_weight"], cfg["bc"],
+                            cfg["tv_seed"], r, 0, cfg["sweeps"])
+    tiles = icsvd.chiral_split(tv, cfg["dims"], cfg["block"])
+    Po, _ = icsvd.ls_prolongator_tiles(tiles, k, omega)
+    spectra = svd_bounds.stream_spectra([tiles], k)
+    bp = svd_bounds.arithmetic_bounds(spectra, svd_bounds.U64, tiles.shape[2])[-1][0]
+    worst = 0.0
+    for j in range(P.shape[0]):
+        for a in range(2):
+            _, s, Vh = np.linalg.svd(tiles[j, a], full_matrices=False)
+            Vk = Vh[:k].conj().T
+            cond = np.linalg.cond(Vk.conj().T @ np.diag(omega) @ Vk)
+            e = np.abs(P[j, a].T - Po[j, a]).max() / np.abs(Po[j, a]).max()
+            assert e <= 4 * cond * bp[j, a], (j, a, e, cond * bp[j, a])
+            worst = max(worst, e)
+    if weights == "ones":
+        Pu, _, _ = icsvd.icsvd_tiles([tiles], k)
+        assert np.all(svd_bounds.projector_errors(P, Pu) <= bp)
+    record("ls_%s_%s" % (cfg["link_seed"], weights), rel_err=worst)
+    h.close()

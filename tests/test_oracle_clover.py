@@ -124,3 +124,40 @@ def test_galerkin_with_clover_equals_dense_product():
     d = Pt.shape[0]
     s3 = np.kron(np.eye(d), np.kron(np.diag([1, -1]), np.eye(k)))
     assert np.abs(s3 @ Dc @ s3 - Dc.conj().T).max() < 1e-13
+
+
+def test_clover_test_vectors_follow_eq2():
+    """Test vectors of the clover operator: psi - phi is the 4-step Krylov minimiser of
+    ||-D phi - D psi'|| with the dense D_clover (Eq. 2 with D = D_W + C)."""
+    from oracle import philox
+    dims = (2, 2, 2, 4)
+    U = synthetic.haar_links(dims, 13)
+    C = clover.clover_term(U, dims, 0.12, CSW)
+    tv = icsvd.test_vectors(U, dims, 0.12, (1, 1, 1, 1), (1, 1, 1, 1), 99, 2, 1, 4, clover=C)
+    phi = philox.gaussian_vectors(99, [2, 3], wilson.volume(dims))
+    D = clover.dense_dirac(U, dims, 0.12, CSW)
+    for i in range(2):
+        p = phi[i].reshape(-1)
+        corr = tv[i].reshape(-1) - p
+        K = np.stack([np.linalg.matrix_power(D, j) @ (-D @ p) for j in range(4)], axis=1)
+        y = np.linalg.lstsq(D @ K, -D @ p, rcond=None)[0]
+        assert np.abs(corr - K @ y).max() < 1e-8 * np.abs(corr).max()
+
+
+def test_clover_two_level_solve():
+    """The two-level K-cycle FGMRES with D = D_W + C solves the clover system: true residual
+    1e-10 and the dense solution."""
+    from oracle import mg
+    dims, block, kappa = (4, 2, 2, 2), (2, 2, 2, 2), 0.12
+    U = synthetic.smooth_links(dims, 14)
+    C = clover.clover_term(U, dims, kappa, CSW)
+    Pt, _, _ = icsvd.icsvd(U, dims, kappa, (1, 1, 1, 1), (1, 1, 1, 1), block, 4, 4, 1, 2, 3000,
+                           clover=C)
+    lvl = mg.TwoLevel(U, dims, kappa, (1, 1, 1, 1), (1, 1, 1, 1), block, Pt, clover=C)
+    rng = np.random.default_rng(7)
+    n = 12 * wilson.volume(dims)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, info = lvl.solve(b, tol=1e-10)
+    xd = np.linalg.solve(clover.dense_dirac(U, dims, kappa, CSW), b)
+    assert info["residual"] <= 1e-10
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8

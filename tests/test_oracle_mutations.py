@@ -234,6 +234,12 @@ MUTANTS = [
     ("schur_smoother_unprepared_rhs", oracle.mg, "TwoLevel.smooth",
      [("rh = _schur.prepare(r, *a).reshape(-1)", "rh = _schur.split(r, self.dims)[0].reshape(-1)")],
      [TS.test_schur_smoother_with_a_spanning_krylov_space_is_the_exact_inverse]),
+    ("ls_weights_dropped_in_normal_matrix", oracle.icsvd, "ls_prolongator_tiles",
+     [("np.linalg.inv(Vc @ Om @ Vc.conj().T)", "np.linalg.inv(Vc @ Vc.conj().T)")],
+     [TN.test_ls_prolongator_minimises_the_weighted_interpolation_error]),
+    ("ls_coarse_vectors_without_sigma", oracle.icsvd, "ls_prolongator_tiles",
+     [("Vc = np.diag(s[:k]) @ Vh[:k]", "Vc = Vh[:k]")],
+     [TN.test_ls_prolongator_reduces_to_left_singular_vectors]),
     ("leaf_two_open", oracle.clover, "field_strength",
      [("_dag(_at(Um, dims, [(nu, 1), (mu, -1)]))", "_dag(_at(Um, dims, [(nu, 1)]))")],
      [TC.test_clover_gauge_covariance]),

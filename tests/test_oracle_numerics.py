@@ -374,3 +374,44 @@ def test_gell_mann_normalisation():
         assert np.allclose(T[a], T[a].conj().T) and abs(np.trace(T[a])) < 1e-15
         for b in range(8):
             assert abs(np.trace(T[a] @ T[b]) - 0.5 * (a == b)) < 1e-15
+
+
+def _ls_tiles(seed, m=10, rows=30):
+    rng = np.random.default_rng(seed)
+    t = rng.standard_normal((2, 2, rows, m)) + 1j * rng.standard_normal((2, 2, rows, m))
+    return t * (10.0 ** (-np.arange(m) / (m - 1)))[None, None, None, :]
+
+
+def test_ls_prolongator_reduces_to_left_singular_vectors():
+    """Eq. 9 with Omega = c I (any c > 0) gives U_k: the Omega = I identity of the paper,
+    with the weights' scale cancelling."""
+    t = _ls_tiles(8)
+    Pu, Su, _ = icsvd.icsvd_tiles([t], 4)
+    for c in (1.0, 3.7):
+        P, S = icsvd.ls_prolongator_tiles(t, 4, c * np.ones(t.shape[3]))
+        assert np.abs(P - Pu).max() < 1e-12
+        assert np.abs(S - Su).max() < 1e-12
+
+
+def test_ls_prolongator_minimises_the_weighted_interpolation_error():
+    """P_j minimises sum_i omega_i ||v_f,i - P v_c,i||^2: it equals (up to the phase of each
+    column, which the canonical phase fixes) the solution of that weighted least-squares problem
+    by an independent route (a library least-squares solve of the row-scaled system), and the
+    unweighted minimiser differs from it."""
+    t = _ls_tiles(9)
+    rng = np.random.default_rng(10)
+    omega = rng.uniform(0.2, 5.0, t.shape[3])
+    P, _ = icsvd.ls_prolongator_tiles(t, 4, omega)
+    P1, _ = icsvd.ls_prolongator_tiles(t, 4, np.ones(t.shape[3]))
+    w = np.sqrt(omega)
+    for j in range(2):
+        for a in range(2):
+            Vf = t[j, a]
+            _, s, Vh = np.linalg.svd(Vf, full_matrices=False)
+            Vc = np.diag(s[:4]) @ Vh[:4]
+            Q = np.linalg.lstsq((Vc * w[None, :]).T, (Vf * w[None, :]).T, rcond=None)[0].T
+            for i in range(4):
+                ov = abs(np.vdot(Q[:, i], P[j, a][:, i]))
+                assert abs(ov - np.linalg.norm(Q[:, i]) * np.linalg.norm(P[j, a][:, i])) < 1e-10 * ov
+                assert abs(np.linalg.norm(Q[:, i]) - np.linalg.norm(P[j, a][:, i])) < 1e-10 * ov ** 0.5
+            assert np.abs(P[j, a] - P1[j, a]).max() > 1e-3
