@@ -449,11 +449,12 @@ def gpu_arm(args):
 
     fine = {}
     lc = [dims[m] // cfg["block"][m] for m in range(4)]
+    depths = (2, 4) if args.extras else ()
     def four(reg):
         return (((2, 2, 2, 2), 16, 16 if reg else 8, 1 if reg else 4, 0.06),
                 ((lc[0] // 2, lc[1] // 2, lc[2] // 2, lc[3] // 2), 16, 16 if reg else 8,
                  1 if reg else 4, 0.6))
-    for depth in (2, 4):
+    for depth in depths:
         for sw in (cfg["sweeps"], 20):
             row = {}
             for tag, r, ns in (("regular_ns1", cfg["k"], 1), ("icsvd_ns4", cfg["r"], 4),
@@ -478,7 +479,7 @@ def gpu_arm(args):
     # anisotropic 16^3 x 64 (w_t = 1/3.5): FP16 and BF16 smoother storage vs plain FP64
     aniso = anisotropic_leg(api, synthetic, dev, step) if args.aniso else None
 
-    d32 = dslash_32(api, synthetic, dev, flush, peaks, peak_kind)
+    d32 = dslash_32(api, synthetic, dev, flush, peaks, peak_kind) if args.extras else None
 
     if rank == 0:
         line = {
@@ -510,6 +511,7 @@ def gpu_arm(args):
             "roofline": roof,
             "kernels": kernels,
             "alu_peaks_tflops": alu,
+            "autotune": json.loads(_lib.lib().mg_autotune_report().decode()),
             "fine_iterations": fine,
             "anisotropic_16^3x64": aniso,
             "dslash_roofline_32^3x64": d32,
@@ -631,6 +633,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aniso", dest="aniso", action="store_false",
                     help="skip the anisotropic 16^3 x 64 half-storage leg")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the legs outside the timed step (Regular vs iCSVD iterations, "
+                         "32^3 x 64 stencil)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

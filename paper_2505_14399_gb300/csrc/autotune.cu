@@ -5,6 +5,12 @@
 // each, CUDA events on the caller's stream) and keeps the fastest; later calls reuse the
 // choice.  Calls made while the stream is being captured into a graph never tune (they use
 // the default shape).  WMG_DSLASH_VARIANT=<i> in the environment forces a shape.
+//
+// Persistence: with WMG_AUTOTUNE_CACHE=<file> the choices are also kept in that file, one JSON
+// object per line ({"device": ..., "dtype": ..., "parity": ..., "dagger": ..., "volume": ...,
+// "nrhs": ..., "variant": ..., "ms": ...}); the file is read once per process and every new
+// choice is appended, so later processes on the same kind of GPU skip the timing.  Entries of
+// other device names are ignored.
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -23,6 +29,58 @@ typedef std::tuple<int, int, int, int, int> Key;
 std::map<Key, std::pair<int, float>> g_cache;
 std::mutex g_mu;
 std::string g_report;
+bool g_loaded = false;
+
+std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp pr{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string n = pr.name;
+  for (auto& ch : n)
+    if (ch == '"' || ch == '\\') ch = '_';
+  return n;
+}
+
+// caller holds g_mu
+void load_cache_file() {
+  if (g_loaded) return;
+  g_loaded = true;
+  const char* path = std::getenv("WMG_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  const std::string want = "{\"device\":\"" + device_name() + "\",";
+  char line[512];
+  while (std::fgets(line, sizeof(line), f)) {
+    std::string s(line);
+    if (s.compare(0, want.size(), want) != 0) continue;
+    int dt, par, dag, V, nrhs, var;
+    float ms;
+    if (std::sscanf(s.c_str() + want.size(),
+                    "\"dtype\":%d,\"parity\":%d,\"dagger\":%d,\"volume\":%d,\"nrhs\":%d,"
+                    "\"variant\":%d,\"ms\":%f",
+                    &dt, &par, &dag, &V, &nrhs, &var, &ms) == 7)
+      g_cache[Key(dt, par, dag, V, nrhs)] = std::make_pair(var, ms);
+  }
+  std::fclose(f);
+}
+
+// caller holds g_mu
+void append_cache_file(const Key& k, int var, float ms) {
+  const char* path = std::getenv("WMG_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f,
+               "{\"device\":\"%s\",\"dtype\":%d,\"parity\":%d,\"dagger\":%d,\"volume\":%d,"
+               "\"nrhs\":%d,\"variant\":%d,\"ms\":%.6g}\n",
+               device_name().c_str(), std::get<0>(k), std::get<1>(k), std::get<2>(k),
+               std::get<3>(k), std::get<4>(k), var, ms);
+  std::fclose(f);
+}
 }  // namespace
 
 int tuned_variant(int dtype, int parity, int dagger, int V, int nrhs, cudaStream_t st, int nvar,
@@ -35,7 +93,12 @@ int tuned_variant(int dtype, int parity, int dagger, int V, int nrhs, cudaStream
   Key key(dtype, parity, dagger, V, nrhs);
   {
     std::lock_guard<std::mutex> lk(g_mu);
+    load_cache_file();
     auto it = g_cache.find(key);
+    if (it != g_cache.end() && (it->second.first < 0 || it->second.first >= nvar)) {
+      g_cache.erase(it);
+      it = g_cache.end();
+    }
     if (it != g_cache.end()) return it->second.first;
   }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -69,6 +132,7 @@ int tuned_variant(int dtype, int parity, int dagger, int V, int nrhs, cudaStream
   cudaEventDestroy(e1);
   std::lock_guard<std::mutex> lk(g_mu);
   g_cache[key] = std::make_pair(best, best_ms / 3.0f);
+  append_cache_file(key, best, best_ms / 3.0f);
   return best;
 }
 

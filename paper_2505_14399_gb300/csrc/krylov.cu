@@ -475,16 +475,17 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
 // H[j+1, j]^2 = ||w||^2 - ||h||^2 as in stream_cgs_kernel<2>.  The basis reads at each
 // thread's own site do not depend on the stencil, so they overlap its latency-bound hops,
 // and w is not read back.  One thread per site and rhs row (blockIdx.y), a grid-stride
-// over 256-site blocks.
-template <int NVM, bool FIRST, int LL>
-__global__ void __launch_bounds__(RT, 2)
+// over BT-site blocks; BT and the register budget (MINB resident CTAs) are launch shapes the
+// autotuner picks per (columns, link layout, volume, rhs).
+template <int NVM, bool FIRST, int LL, int BT, int MINB>
+__global__ void __launch_bounds__(BT, MINB)
 dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
                    const float2* __restrict__ links, stencil::KGeom g, zd* small, SmallLayout L,
                    double* wnorm, double* partial, unsigned* counter, int maxvec,
                    const zf* __restrict__ b0, const double* beta0) {
   using namespace stencil;
   dep_entry();
-  __shared__ float sh[(RT / 32) * NVM * 2];
+  __shared__ float sh[(BT / 32) * NVM * 2];
   const int rhs = blockIdx.y;
   const int nsites = g.V;
   float2* vb = reinterpret_cast<float2*>(V) + (size_t)rhs * n;
@@ -502,7 +503,7 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
 #pragma unroll
   for (int q = 0; q < NVM; ++q) { ar[q] = 0.f; ai[q] = 0.f; }
   float ss = 0.f;
-  for (int site = blockIdx.x * RT + threadIdx.x; site < nsites; site += gridDim.x * RT) {
+  for (int site = blockIdx.x * BT + threadIdx.x; site < nsites; site += gridDim.x * BT) {
     int c[4];
     stencil_site(g, -1, site, c);
     zf acc[12];
@@ -558,7 +559,7 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
   finish_partials(partials_as<float>(partial), nv + 1, nblk, maxvec, rhs, g_h2, nullptr, 0, 0);
   __syncthreads();
   zd* sm = small + (size_t)rhs * L.stride();
-  for (int i = threadIdx.x; i <= nv; i += RT) sm[L.h2() + i] = g_h2[i];
+  for (int i = threadIdx.x; i <= nv; i += BT) sm[L.h2() + i] = g_h2[i];
   if (threadIdx.x == 0) {
     counter[rhs] = 0;
     double hh = 0;
@@ -568,18 +569,57 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
   }
 }
 
+// launch shapes of the fused kernel: threads per CTA and resident CTAs per SM asked of the
+// register allocator (register cap 64K / (BT MINB)): 256 x 2 and 128 x 4 (128 registers),
+// 128 x 5 (102), 128 x 6 (85)
+constexpr int kProjShapes = 4;
+
+template <int NVM, bool FIRST, int LL, int BT, int MINB>
+void launch_proj_shape(int nv, int V, int nblk, int nrhs, cudaStream_t st, zf* w, zf* V_,
+                       size_t fs, size_t n, const float2* L32, const stencil::KGeom& kg, zd* small,
+                       SmallLayout L, double* dnorm, ReduceWork& rw, const zf* b0,
+                       const double* beta0, cudaError_t* err) {
+  int nb = (V + BT - 1) / BT;
+  if (nb > nblk) nb = nblk;
+  *err = launch_dep(dslash_proj_kernel<NVM, FIRST, LL, BT, MINB>, dim3(nb, nrhs), BT, 0, st, w,
+                    V_, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec,
+                    b0, beta0);
+}
+
+template <int NVM, bool FIRST, int LL>
+void launch_proj_v(int v, int nv, int nrhs, cudaStream_t st, zf* w, zf* V_, size_t fs, size_t n,
+                   const float2* L32, const stencil::KGeom& kg, zd* small, SmallLayout L,
+                   double* dnorm, ReduceWork& rw, const zf* b0, const double* beta0,
+                   cudaError_t* err) {
+  switch (v) {
+    case 1: launch_proj_shape<NVM, FIRST, LL, 128, 4>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
+    case 2: launch_proj_shape<NVM, FIRST, LL, 128, 5>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
+    case 3: launch_proj_shape<NVM, FIRST, LL, 128, 6>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
+    default: launch_proj_shape<NVM, FIRST, LL, 256, 2>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
+  }
+}
+
 template <int LL>
-int launch_proj(int nv, bool first, int nb, int nrhs, cudaStream_t st, zf* w, zf* V, size_t fs,
+int launch_proj(int nv, bool first, int nrhs, cudaStream_t st, zf* w, zf* V, size_t fs,
                 size_t n, const float2* L32, const stencil::KGeom& kg, zd* small, SmallLayout L,
                 double* dnorm, ReduceWork& rw, const zf* b0, const double* beta0) {
-  if (first)
-    WMG_LAUNCH_DEP((dslash_proj_kernel<4, true, LL>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
-  else if (nv <= 4)
-    WMG_LAUNCH_DEP((dslash_proj_kernel<4, false, LL>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
-  else if (nv <= 8)
-    WMG_LAUNCH_DEP((dslash_proj_kernel<8, false, LL>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
-  else
-    WMG_LAUNCH_DEP((dslash_proj_kernel<16, false, LL>), dim3(nb, nrhs), RT, 0, st, w, V, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec, b0, beta0);
+  const int nvm = first ? 0 : nv <= 4 ? 4 : nv <= 8 ? 8 : 16;
+  cudaError_t err = cudaSuccess;
+  auto run = [&](int v) {
+    if (first) launch_proj_v<4, true, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, &err);
+    else if (nvm == 4) launch_proj_v<4, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, &err);
+    else if (nvm == 8) launch_proj_v<8, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, &err);
+    else launch_proj_v<16, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, &err);
+  };
+  // tuning key: a dtype code of its own per (columns class, link layout), parity -2; the
+  // kernel is idempotent (it rewrites w, its partials and its Hessenberg column from inputs
+  // it does not modify), so the tuner may run it several times
+  int v = tuned_variant(1000 + 10 * nvm + LL, -2, 0, kg.V, nrhs, st, kProjShapes, run);
+  if (v < 0) return fail(MG_ECUDA, "fused stencil autotune failed");
+  run(v);
+  count_launch();
+  if (err != cudaSuccess)
+    return fail(MG_ECUDA, std::string("dslash_proj launch: ") + cudaGetErrorString(err));
   return MG_OK;
 }
 
@@ -589,8 +629,6 @@ int dslash_proj_launch(zf* w, zf* V, size_t fs, size_t n, int nrhs, zd* small,
                        const double* beta0 = nullptr) {
   stencil::KGeom kg = stencil::to_kgeom(fz.g);
   int nv = j + 1;
-  int nb = (kg.V + RT - 1) / RT;
-  if (nb > rw.nblk) nb = rw.nblk;
   const float2* L32 = static_cast<const float2*>(fz.links);
   // algorithmic bytes: per right-hand side the nv basis columns read (v_j, the stencil input,
   // is one of them) and w written -- the first step reads b and writes v_0 and w instead --
@@ -598,8 +636,8 @@ int dslash_proj_launch(zf* w, zf* V, size_t fs, size_t n, int nrhs, zd* small,
   const double fields = b0 ? 3.0 : (double)(nv + 1);
   double byts = (double)kg.V * 8.0 * (12.0 * fields * nrhs + 36.0);
   ProfScope ps("dslash_proj", byts, (1320.0 + 48.0 * (nv + 1)) * kg.V * nrhs, st);
-  if (fz.layout == 2) return launch_proj<2>(nv, b0 != nullptr, nb, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0);
-  return launch_proj<1>(nv, b0 != nullptr, nb, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0);
+  if (fz.layout == 2) return launch_proj<2>(nv, b0 != nullptr, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0);
+  return launch_proj<1>(nv, b0 != nullptr, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0);
 }
 
 template <int NVM>
