@@ -571,8 +571,9 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
 
 // launch shapes of the fused kernel: threads per CTA and resident CTAs per SM asked of the
 // register allocator (register cap 64K / (BT MINB)): 256 x 2 and 128 x 4 (128 registers),
-// 128 x 5 (102), 128 x 6 (85)
-constexpr int kProjShapes = 4;
+// 128 x 5 (102).  (128 x 6, 85 registers, spilled 250-330 bytes per thread and doubled the
+// kernel's DRAM writes; it is not a candidate.)
+constexpr int kProjShapes = 3;
 
 template <int NVM, bool FIRST, int LL, int BT, int MINB>
 void launch_proj_shape(int nv, int V, int nblk, int nrhs, cudaStream_t st, zf* w, zf* V_,
@@ -594,7 +595,6 @@ void launch_proj_v(int v, int nv, int nrhs, cudaStream_t st, zf* w, zf* V_, size
   switch (v) {
     case 1: launch_proj_shape<NVM, FIRST, LL, 128, 4>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
     case 2: launch_proj_shape<NVM, FIRST, LL, 128, 5>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
-    case 3: launch_proj_shape<NVM, FIRST, LL, 128, 6>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
     default: launch_proj_shape<NVM, FIRST, LL, 256, 2>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
   }
 }
