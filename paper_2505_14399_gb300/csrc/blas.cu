@@ -288,9 +288,11 @@ int ReduceWork::alloc(size_t n, int nrhs, int mv) {
   size_t nb = (n + 4 * RT - 1) / (4 * RT);
   size_t cap = (size_t)num_sms() * 6;
   nblk = (int)(nb < 1 ? 1 : (nb > cap ? cap : nb));
+  size_t per128 = (n / 12 + 127) / 128;
+  this->cap = (int)(per128 > (size_t)nblk ? per128 : (size_t)nblk);
   maxvec = mv;
   nrhs_cap = nrhs;
-  WMG_TRY(dev_alloc(&partial, sizeof(double) * 2 * (size_t)nblk * maxvec * nrhs));
+  WMG_TRY(dev_alloc(&partial, sizeof(double) * 2 * (size_t)this->cap * maxvec * nrhs));
   WMG_TRY(dev_alloc(&counter, sizeof(unsigned) * nrhs));
   WMG_CUDA(cudaMemset(counter, 0, sizeof(unsigned) * nrhs));
   return MG_OK;

@@ -42,6 +42,8 @@ struct ReduceWork {
   double* partial = nullptr;   // [nrhs][maxvec][nblk] (re, im interleaved)
   unsigned* counter = nullptr; // [nrhs]
   int nblk = 0;
+  int cap = 0;        // partial slots per vector: >= nblk, and one per 128 sites of a fine
+                      // field, so the fused stencil kernel may launch a CTA per 128 sites
   int maxvec = 0;
   int nrhs_cap = 0;
   int alloc(size_t n, int nrhs, int maxvec);

@@ -593,9 +593,9 @@ void launch_proj_v(int v, int nv, int nrhs, cudaStream_t st, zf* w, zf* V_, size
                    double* dnorm, ReduceWork& rw, const zf* b0, const double* beta0,
                    cudaError_t* err) {
   switch (v) {
-    case 1: launch_proj_shape<NVM, FIRST, LL, 128, 4>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
-    case 2: launch_proj_shape<NVM, FIRST, LL, 128, 5>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
-    default: launch_proj_shape<NVM, FIRST, LL, 256, 2>(nv, kg.V, rw.nblk, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
+    case 1: launch_proj_shape<NVM, FIRST, LL, 128, 4>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
+    case 2: launch_proj_shape<NVM, FIRST, LL, 128, 5>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
+    default: launch_proj_shape<NVM, FIRST, LL, 256, 2>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
   }
 }
 
