@@ -25,6 +25,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "c2_16^3x32_near_critical"
 METRIC = "MG setup+solve seconds to 1e-10 residual (mixed precision); Dslash GB/s"
+# The timed step's K-cycle post-smoother runs its 8 GMRES steps on the even-odd Schur system
+# (even-odd preconditioning, Sec. 1), in both the mixed and the FP64 form; the same step with
+# the smoother on the full system is timed beside it.
+SCHUR_SMOOTHER = True
 
 
 def _dist():
@@ -277,6 +281,8 @@ def bench_config(cfg, world):
     return {"workload": WORKLOAD, "dims": list(cfg["dims"]), "block": list(cfg["block"]),
             "k": cfg["k"], "r": cfg["r"], "n_s": cfg["n_s"], "sweeps": cfg["sweeps"],
             "kappa": cfg["kappa"], "tol": 1e-10, "nrhs": 1,
+            "post_smoother": ("8 GMRES steps on the even-odd Schur system" if SCHUR_SMOOTHER
+                              else "8 GMRES steps on D"),
             "parallelism": "replicas" if world > 1 else "single",
             "l2": "256 MB buffer written, then a second 256 MB buffer read, before every timed step"}
 
@@ -310,11 +316,11 @@ def gpu_arm(args):
     bd = torch.from_numpy(b).to(dev)
     flush = L2Flush(dev)
 
-    def make_params(mixed):
+    def make_params(mixed, schur=SCHUR_SMOOTHER):
         return api.params(dims, cfg["block"], cfg["kappa"], cfg["k"], cfg["r"], cfg["n_s"],
                           cfg["sweeps"], cfg["tv_seed"], cfg["hop_weight"], cfg["bc"],
                           setup_dtype="c64" if mixed else "c128",
-                          solve_dtype="c64" if mixed else "c128")
+                          solve_dtype="c64" if mixed else "c128", schur_smoother=int(schur))
 
     def step(p, links, rhs, levels=()):
         h = api.Hierarchy(links, p)
@@ -388,6 +394,10 @@ def gpu_arm(args):
     torch.cuda.nvtx.range_push("fp64")
     t_fp64, info_64, _, _, _ = timed(p64, Ud, bd, max(1, min(args.steps, 2)), 1)
     torch.cuda.nvtx.range_pop()
+    # the same steps with the post-smoother on the full system
+    t_plain, info_plain, _, _, _ = timed(make_params(True, False), Ud, bd, args.steps, 1)
+    t_plain64, info_plain64, _, _, _ = timed(make_params(False, False), Ud, bd,
+                                             max(1, min(args.steps, 2)), 1)
 
     # end to end through the C ABI with host buffers (links, b on the host; x back to host)
     Uh = torch.from_numpy(U).pin_memory()
@@ -476,6 +486,47 @@ def gpu_arm(args):
                                                       / max(row[t]["fp64"]["outer"], 1))
             fine["levels_%d_sweeps_%d" % (depth, sw)] = row
 
+    # the next rows on the timed workload: the Schur-form post-smoother (even-odd
+    # preconditioning, Sec. 1), the Wilson-clover operator (c_sw = 1.7, at kappa = 0.125 since
+    # the clover term moves the critical point) and the Eq. 9 prolongator (one stream of 32
+    # test vectors, weights 10^(-i/31)): setup + Galerkin + solve seconds and iterations,
+    # mixed and FP64
+    variants = {}
+    if args.extras:
+        m32 = cfg["r"] * cfg["n_s"]
+        omega = [10.0 ** (-i / (m32 - 1)) for i in range(m32)]
+        for tag, extra, kap in (("schur_smoother", dict(schur_smoother=1), cfg["kappa"]),
+                                ("clover_csw1.7", dict(csw=1.7), 0.125),
+                                ("wilson_kappa0.125", {}, 0.125),
+                                ("ls_interpolation", dict(n_s=1, r=m32), cfg["kappa"])):
+            ent = {}
+            for form, sd in (("fp64", "c128"), ("mixed", "c64")):
+                args_p = dict(dims=dims, block=cfg["block"], kappa=kap, k=cfg["k"], r=cfg["r"],
+                              n_s=cfg["n_s"], sweeps=cfg["sweeps"], seed=cfg["tv_seed"],
+                              hop_weight=cfg["hop_weight"], bc=cfg["bc"], setup_dtype=sd,
+                              solve_dtype=sd)
+                args_p.update(extra)
+                pv = api.params(**args_p)
+                ls = omega if tag == "ls_interpolation" else None
+
+                def run_v():
+                    h = api.Hierarchy(Ud, pv, ls_omega=ls)
+                    h.coarse_build()
+                    x, inf = h.solve(bd, tol=1e-10, maxiter=4000)
+                    h.close()
+                    return inf
+                run_v()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                inf = run_v()
+                e1.record()
+                torch.cuda.synchronize()
+                ent[form] = {"seconds": e0.elapsed_time(e1) / 1e3, "outer": inf["outer"],
+                             "coarse": inf["coarse"], "residual": inf["residual"]}
+            variants[tag] = ent
+
     # anisotropic 16^3 x 64 (w_t = 1/3.5): FP16 and BF16 smoother storage vs plain FP64
     aniso = anisotropic_leg(api, synthetic, dev, step) if args.aniso else None
 
@@ -499,6 +550,9 @@ def gpu_arm(args):
             "config": bench_config(cfg, world),
             "fp64_seconds": t_fp64,
             "mixed_over_fp64_speedup": t_fp64 / t_mixed,
+            "full_system_smoother": {"mixed_seconds": t_plain, "fp64_seconds": t_plain64,
+                                     "solve_info_mixed": info_plain,
+                                     "solve_info_fp64": info_plain64},
             "profiled_step_seconds": t_prof,
             "solve_info_mixed": info_m,
             "solve_info_fp64": info_64,
@@ -513,6 +567,7 @@ def gpu_arm(args):
             "alu_peaks_tflops": alu,
             "autotune": json.loads(_lib.lib().mg_autotune_report().decode()),
             "fine_iterations": fine,
+            "next_rows_16^3x32": variants,
             "anisotropic_16^3x64": aniso,
             "dslash_roofline_32^3x64": d32,
             "dslash_roofline": {"kernel": "dslash_c64 (16^3x32, L2 flushed, standalone)",
@@ -545,7 +600,8 @@ def host_info():
             "arch": platform.machine(), "available_cores": len(os.sched_getaffinity(0))}
 
 
-FULL_STEP_RECORD = os.path.join(ROOT, "oracle", "records", "full_step_c2_16x16x16x32.json")
+FULL_STEP_RECORD = os.path.join(ROOT, "oracle", "records",
+                                "full_step_c2_16x16x16x32%s.json" % ("_schur" if SCHUR_SMOOTHER else ""))
 
 
 def oracle_outer_iterations(cfg, fallback):
@@ -555,7 +611,8 @@ def oracle_outer_iterations(cfg, fallback):
     try:
         with open(FULL_STEP_RECORD) as f:
             rec = json.load(f)
-        if rec.get("workload") == WORKLOAD and abs(rec["kappa"] - cfg["kappa"]) < 1e-12:
+        if (rec.get("workload") == WORKLOAD and abs(rec["kappa"] - cfg["kappa"]) < 1e-12
+                and bool(rec.get("schur_smoother", False)) == SCHUR_SMOOTHER):
             return int(rec["info"]["outer"]), "oracle full step (recorded)", rec
     except Exception:
         pass
@@ -573,7 +630,7 @@ def cpu_baseline(cfg, U, b, outer_fallback):
     from oracle import full_step
     workers = len(os.sched_getaffinity(0))
     outer, src, rec = oracle_outer_iterations(cfg, outer_fallback)
-    s = full_step.SampledStep(U, b[0], cfg, cfg["kappa"], workers, outer)
+    s = full_step.SampledStep(U, b[0], cfg, cfg["kappa"], workers, outer, schur=SCHUR_SMOOTHER)
     t0 = time.perf_counter()
     s.run_all()
     out = {"value": s.estimate(), "unit": "s", "cores": workers, "kind": "oracle",
@@ -599,7 +656,7 @@ def reference_arm(args):
     cfg = workload()
     U = synthetic.make_links(cfg)
     b = synthetic.gaussian_rhs(cfg["dims"], cfg["rhs_seed"])
-    r, s = cpu_baseline(cfg, U, b, outer_fallback=30)
+    r, s = cpu_baseline(cfg, U, b, outer_fallback=15 if SCHUR_SMOOTHER else 30)
     vals, walls = [], []
     for i in range(args.steps):
         part = s.PARTS[i % len(s.PARTS)]

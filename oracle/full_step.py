@@ -14,7 +14,8 @@ oracle function on its own unit.  The sequential FGMRES iteration runs in one pr
 
 Two uses:
 * ``full_step``: the whole step, with the oracle's own iteration counts (minutes at
-  16^3 x 32).  ``python -m oracle.full_step <workload> [workers] [out.json]``.
+  16^3 x 32).  ``python -m oracle.full_step <workload> [workers] [out.json] [schur]``
+  (``schur``: the Schur-form post-smoother).
 * ``SampledStep``: a bounded piece of every part, timed, each scaled by its share of the
   whole step (the number of test vectors and coarse slabs; the outer iteration count of a
   recorded full step), giving the estimated seconds of one whole step.
@@ -85,8 +86,9 @@ def _icsvd(pool, stream_tiles, k, workers):
     return np.concatenate([r[0] for r in res]), np.concatenate([r[1] for r in res])
 
 
-def full_step(links, b, cfg, kappa, workers=1, tol=1e-10, log=None):
-    """The whole step on `workers` processes.  Returns the solve info, per-part seconds."""
+def full_step(links, b, cfg, kappa, workers=1, tol=1e-10, log=None, schur=False):
+    """The whole step on `workers` processes (schur: the K-cycle's post-smoother on the
+    even-odd Schur system).  Returns the solve info, per-part seconds."""
     dims, block, k, r, n_s = cfg["dims"], cfg["block"], cfg["k"], cfg["r"], cfg["n_s"]
     w, bc = cfg["hop_weight"], cfg["bc"]
     parts = {}
@@ -106,7 +108,7 @@ def full_step(links, b, cfg, kappa, workers=1, tol=1e-10, log=None):
     XY = coarse.galerkin(Pt, links, dims, block, kappa, w, bc)
     parts["galerkin"] = time.perf_counter() - t0
     t0 = time.perf_counter()
-    lvl = mg.TwoLevel(links, dims, kappa, w, bc, block, Pt, XY=XY)
+    lvl = mg.TwoLevel(links, dims, kappa, w, bc, block, Pt, XY=XY, schur=schur)
     _, info = lvl.solve(np.asarray(b).reshape(-1), tol=tol, maxiter=4000)
     parts["solve"] = time.perf_counter() - t0
     info = dict(info, kcycles=lvl.kcycles)
@@ -133,9 +135,9 @@ class SampledStep:
     """
     PARTS = ("vectors", "svd", "galerkin", "solve")
 
-    def __init__(self, links, b, cfg, kappa, workers, outer_its):
+    def __init__(self, links, b, cfg, kappa, workers, outer_its, schur=False):
         self.links, self.b, self.cfg, self.kappa = links, np.asarray(b).reshape(-1), cfg, kappa
-        self.workers, self.outer_its = workers, outer_its
+        self.workers, self.outer_its, self.schur = workers, outer_its, schur
         dims, block = cfg["dims"], cfg["block"]
         self.m = cfg["r"] * cfg["n_s"]
         self.nv = max(1, min(workers, self.m))
@@ -179,7 +181,8 @@ class SampledStep:
                 self.XY = (np.concatenate([X] * self.nslab, axis=0),
                            np.concatenate([Y] * self.nslab, axis=1))
             else:
-                lvl = mg.TwoLevel(self.links, dims, self.kappa, w, bc, block, self.Pt, XY=self.XY)
+                lvl = mg.TwoLevel(self.links, dims, self.kappa, w, bc, block, self.Pt, XY=self.XY,
+                                  schur=self.schur)
                 t0 = time.perf_counter()
                 lvl.solve(self.b, tol=1e-30, maxiter=1)
                 t = time.perf_counter() - t0
@@ -219,13 +222,15 @@ if __name__ == "__main__":
     name = sys.argv[1]
     workers = int(sys.argv[2]) if len(sys.argv) > 2 else 1
     out = sys.argv[3] if len(sys.argv) > 3 else None
+    schur = len(sys.argv) > 4 and sys.argv[4] == "schur"
     cfg = synthetic.WORKLOADS[name]
     kappa = synthetic.kappa_of(name)
     U = synthetic.make_links(cfg)
     b = synthetic.gaussian_rhs(cfg["dims"], cfg["rhs_seed"])[0]
     t0 = time.perf_counter()
-    info, parts = full_step(U, b, cfg, kappa, workers, log=lambda s: print(s, flush=True))
-    rec = {"workload": name, "kappa": kappa, "workers": workers,
+    info, parts = full_step(U, b, cfg, kappa, workers, log=lambda s: print(s, flush=True),
+                            schur=schur)
+    rec = {"workload": name, "kappa": kappa, "workers": workers, "schur_smoother": schur,
            "seconds": time.perf_counter() - t0, "parts_s": parts, "info": info,
            "host_cores": len(os.sched_getaffinity(0))}
     print(json.dumps(rec), flush=True)

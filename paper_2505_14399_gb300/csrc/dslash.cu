@@ -72,6 +72,7 @@ dslash_kernel(typename S::elem* __restrict__ out, const typename S::elem* __rest
   } else {
 #pragma unroll
     for (int k = 0; k < 12; ++k) res[k] = mk * acc[k];
+    apply_sub<S>(g, rhs * out_stride, i, res);
     SiteIO<S>::store(out + rhs * out_stride, (size_t)i, res);
   }
 }
@@ -135,6 +136,7 @@ dslash_split_kernel(typename S::elem* __restrict__ out, const typename S::elem* 
   } else {
 #pragma unroll
     for (int k = 0; k < 12; ++k) res[k] = mk * acc[k];
+    apply_sub<S>(g, rhs * out_stride, i, res);
     SiteIO<S>::store(out + rhs * out_stride, (size_t)i, res);
   }
 }
@@ -184,8 +186,9 @@ void launch_variant(int v, void* out, const void* in, const void* links, const K
 template <typename S>
 int launch_typed(void* out, const void* in, const void* links, const Geom& g, int parity,
                  int dagger, int nrhs, cudaStream_t st, size_t in_stride, size_t out_stride,
-                 int dtype, int layout) {
+                 int dtype, int layout, const void* subf) {
   KGeom k = to_kgeom(g);
+  k.sub = parity >= 0 ? subf : nullptr;
   int nsites = parity < 0 ? g.V : g.V / 2;
   auto run = [&](int v) {
     if (layout == 0) {
@@ -294,23 +297,23 @@ int su3_deviation(double* dev_out, const zd* links, size_t nlinks, cudaStream_t 
 
 int dslash_launch(int dtype, void* out, const void* in, const void* links, const Geom& g,
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,
-                  size_t out_stride, int link_layout) {
+                  size_t out_stride, int link_layout, const void* sub) {
   size_t half = (size_t)12 * (parity < 0 ? g.V : g.V / 2);
   if (in_stride == 0) in_stride = half;
   if (out_stride == 0) out_stride = half;
   switch (dtype) {
     case MG_C128:
       return launch_typed<StC128>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype,
-                                  link_layout);
+                                  link_layout, sub);
     case MG_C64:
       return launch_typed<StC64>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype,
-                                  link_layout);
+                                  link_layout, sub);
     case MG_F16:
       return launch_typed<StF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype,
-                                  link_layout);
+                                  link_layout, sub);
     case MG_BF16:
       return launch_typed<StBF16>(out, in, links, g, parity, dagger, nrhs, st, in_stride, out_stride, dtype,
-                                  link_layout);
+                                  link_layout, sub);
   }
   return fail(MG_EINVAL, "dslash: unknown dtype");
 }

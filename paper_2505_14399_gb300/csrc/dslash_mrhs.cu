@@ -120,6 +120,7 @@ dslash_mrhs_kernel(typename S::elem* __restrict__ out, const typename S::elem* _
       } else {
 #pragma unroll
         for (int k = 0; k < 12; ++k) res[k] = mk * acc[r][k];
+        apply_sub<S>(g, (size_t)(r0 + r) * out_stride, i, res);
         SiteIO<S>::store(o, (size_t)i, res);
       }
     }

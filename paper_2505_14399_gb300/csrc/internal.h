@@ -14,9 +14,11 @@ namespace wmg {
 // in/out strides are in complex elements between right-hand sides (0 = field size).
 // link_layout 0: ABI [mu][site][3][3]; 1: lane-contiguous [mu][9][site] (link_to_lanes);
 // 2: lane-contiguous first two rows [mu][6][site], third row rebuilt (SU(3) links, not C128).
+// sub (single-parity form only, may be NULL): out_p = sub_p - (-kappa H_{p,1-p} in), sub with
+// out's layout and stride.
 int dslash_launch(int dtype, void* out, const void* in, const void* links, const Geom& g,
                   int parity, int dagger, int nrhs, cudaStream_t st, size_t in_stride,
-                  size_t out_stride, int link_layout = 0);
+                  size_t out_stride, int link_layout = 0, const void* sub = nullptr);
 // dst[mu][e][site] = src[mu][site][e] (e < 3 rows, rows 3 or 2), converting complex double to E
 // (vec.cuh); link_layout 1 reads rows = 3, link_layout 2 rows = 2.
 template <typename E>

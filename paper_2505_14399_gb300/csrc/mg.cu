@@ -505,14 +505,12 @@ int post_smooth_schur(mg_handle* h, cplx<R>* z, const cplx<R>* r, int nrhs, cuda
   const int lay = Lvl<R>::layout(h);
   const int dt = Lvl<R>::dtype;
   WMG_TRY(eo_split<cplx<R>>(re, ro, r, g, nrhs, st));
-  WMG_TRY(dslash_launch(dt, rh, ro, L, g, 0, 0, nrhs, st, nh, nh, lay));   // -kappa H_eo r_o
-  WMG_TRY(axpby<R>(rh, 1.0, re, -1.0, nh * nrhs, 1, st));                 // r_hat
+  WMG_TRY(dslash_launch(dt, rh, ro, L, g, 0, 0, nrhs, st, nh, nh, lay, re));   // r_hat
   Op<R> Dhat = [h, to, L, lay, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
     return schur_apply<cplx<R>>(out, in, to, L, lay, h->g, 0, nrhs, s2);
   };
   WMG_TRY(Lvl<R>::posts(h).fixed(Dhat, xe, rh, h->p.post_smooth, st));
-  WMG_TRY(dslash_launch(dt, to, xe, L, g, 1, 0, nrhs, st, nh, nh, lay));   // -kappa H_oe e_e
-  WMG_TRY(axpby<R>(to, 1.0, ro, -1.0, nh * nrhs, 1, st));                 // e_o
+  WMG_TRY(dslash_launch(dt, to, xe, L, g, 1, 0, nrhs, st, nh, nh, lay, ro));   // e_o
   cplx<R>* ke = Lvl<R>::ke(h);
   WMG_TRY(eo_join<cplx<R>>(ke, xe, to, g, nrhs, st));
   WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, h->nf * nrhs, 1, st));                // z += e

@@ -98,8 +98,8 @@ int schur_apply(E* out, const E* in, E* tmp, const void* links, int layout, cons
                                                   : MG_BF16;
   size_t nh = (size_t)(g.V / 2) * 12;
   WMG_TRY(dslash_launch(dt, tmp, in, links, g, 1, dagger, nrhs, st, nh, nh, layout));
-  WMG_TRY(dslash_launch(dt, out, tmp, links, g, 0, dagger, nrhs, st, nh, nh, layout));
-  WMG_TRY(axpby_v<E>(out, 1.0, in, -1.0, nh * nrhs, 1, st));
+  // out = in - (-kappa H_eo) tmp, the subtraction fused into the second hop
+  WMG_TRY(dslash_launch(dt, out, tmp, links, g, 0, dagger, nrhs, st, nh, nh, layout, in));
   return MG_OK;
 }
 

@@ -169,7 +169,15 @@ struct KGeom {
   double wd[4];
   int bc[4];
   double kappa;
+  // single-parity form only: when set, out_p = sub_p - (-kappa H_{p,1-p} in) (the even-odd
+  // Schur complement and its source / reconstruction steps), sub with out's layout and stride
+  const void* sub = nullptr;
 };
+
+// res <- sub[rhs][i] - res for the single-parity form with a subtrahend field
+template <typename S>
+__device__ __forceinline__ void apply_sub(const KGeom& g, size_t rhs_off, int i,
+                                          cplx<typename S::real> res[12]);
 
 template <typename R> __device__ __forceinline__ R wgt(const KGeom& g, int mu);
 template <> __device__ __forceinline__ double wgt<double>(const KGeom& g, int mu) { return g.wd[mu]; }
@@ -248,6 +256,16 @@ __device__ __forceinline__ int stencil_site(const KGeom& g, int parity, int i, i
   c[2] = rest % g.L[2];
   c[3] = rest / g.L[2];
   return site;
+}
+
+template <typename S>
+__device__ __forceinline__ void apply_sub(const KGeom& g, size_t rhs_off, int i,
+                                          cplx<typename S::real> res[12]) {
+  if (!g.sub) return;
+  cplx<typename S::real> b[12];
+  SiteIO<S>::load(static_cast<const typename S::elem*>(g.sub) + rhs_off, (size_t)i, b);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) res[k] = b[k] - res[k];
 }
 
 inline KGeom to_kgeom(const Geom& g) {
