@@ -149,6 +149,10 @@ struct FusedStencil {
   const void* links;
   Geom g;
   int layout = 1;   // 1: [mu][9][site]; 2: first two rows [mu][6][site] (SU(3) links)
+  // the even-odd Schur operator D_hat on even half-lattice fields instead of D: its first
+  // hop into the odd field `odd` (nrhs of them), the second fused with the projections
+  bool schur = false;
+  void* odd = nullptr;
 };
 
 template <typename E>

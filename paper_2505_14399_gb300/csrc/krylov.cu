@@ -482,12 +482,15 @@ __global__ void __launch_bounds__(BT, MINB)
 dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
                    const float2* __restrict__ links, stencil::KGeom g, zd* small, SmallLayout L,
                    double* wnorm, double* partial, unsigned* counter, int maxvec,
-                   const zf* __restrict__ b0, const double* beta0) {
+                   const zf* __restrict__ b0, const double* beta0, const zf* __restrict__ sin,
+                   int par) {
   using namespace stencil;
   dep_entry();
   __shared__ float sh[(BT / 32) * NVM * 2];
   const int rhs = blockIdx.y;
-  const int nsites = g.V;
+  // par: the even-odd Schur operator's second hop, w = x - (-kappa H_eo) t_o on even
+  // half-lattice fields, with t_o = -kappa H_oe x (the odd field sin) computed by the caller
+  const int nsites = par ? g.V / 2 : g.V;
   float2* vb = reinterpret_cast<float2*>(V) + (size_t)rhs * n;
   // FIRST (step 0): the stencil reads b and everything is scaled by 1 / ||b|| (linear),
   // v_0 = b / ||b|| is written here (no separate scaling pass); otherwise the input is v_j
@@ -499,23 +502,26 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
     sc = bb > 0 ? (float)(1.0 / bb) : 0.0f;
   }
   float2* wr = reinterpret_cast<float2*>(w) + (size_t)rhs * n;
+  const float2* vst = par ? reinterpret_cast<const float2*>(sin) + (size_t)rhs * n : vin;
   float ar[NVM], ai[NVM];
 #pragma unroll
   for (int q = 0; q < NVM; ++q) { ar[q] = 0.f; ai[q] = 0.f; }
   float ss = 0.f;
   for (int site = blockIdx.x * BT + threadIdx.x; site < nsites; site += gridDim.x * BT) {
     int c[4];
-    stencil_site(g, -1, site, c);
+    // site: the output index (lexicographic, or the checkerboard index with par); ls: the
+    // lattice site the hops start from
+    const int ls = stencil_site(g, par ? 0 : -1, site, c);
     zf acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
-    hop_pair<0, 0, StC64, LL>(g, site, c, vin, 0, false, links, acc);
-    hop_pair<1, 0, StC64, LL>(g, site, c, vin, 0, false, links, acc);
-    hop_pair<2, 0, StC64, LL>(g, site, c, vin, 0, false, links, acc);
-    hop_pair<3, 0, StC64, LL>(g, site, c, vin, 0, false, links, acc);
+    hop_pair<0, 0, StC64, LL>(g, ls, c, vst, 0, par != 0, links, acc);
+    hop_pair<1, 0, StC64, LL>(g, ls, c, vst, 0, par != 0, links, acc);
+    hop_pair<2, 0, StC64, LL>(g, ls, c, vst, 0, par != 0, links, acc);
+    hop_pair<3, 0, StC64, LL>(g, ls, c, vst, 0, par != 0, links, acc);
     zf p[12], x0[12];
     SiteIO<StC64>::load(vin, (size_t)site, x0);
-    const float mk = (float)(-g.kappa);
+    const float mk = par ? (float)g.kappa : (float)(-g.kappa);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       p[k].re = sc * fmaf(mk, acc[k].re, x0[k].re);
@@ -579,42 +585,44 @@ template <int NVM, bool FIRST, int LL, int BT, int MINB>
 void launch_proj_shape(int nv, int V, int nblk, int nrhs, cudaStream_t st, zf* w, zf* V_,
                        size_t fs, size_t n, const float2* L32, const stencil::KGeom& kg, zd* small,
                        SmallLayout L, double* dnorm, ReduceWork& rw, const zf* b0,
-                       const double* beta0, cudaError_t* err) {
-  int nb = (V + BT - 1) / BT;
+                       const double* beta0, const zf* sin, int par, cudaError_t* err) {
+  const int ns = par ? V / 2 : V;
+  int nb = (ns + BT - 1) / BT;
   if (nb > nblk) nb = nblk;
   *err = launch_dep(dslash_proj_kernel<NVM, FIRST, LL, BT, MINB>, dim3(nb, nrhs), BT, 0, st, w,
                     V_, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec,
-                    b0, beta0);
+                    b0, beta0, sin, par);
 }
 
 template <int NVM, bool FIRST, int LL>
 void launch_proj_v(int v, int nv, int nrhs, cudaStream_t st, zf* w, zf* V_, size_t fs, size_t n,
                    const float2* L32, const stencil::KGeom& kg, zd* small, SmallLayout L,
                    double* dnorm, ReduceWork& rw, const zf* b0, const double* beta0,
-                   cudaError_t* err) {
+                   const zf* sin, int par, cudaError_t* err) {
   switch (v) {
-    case 1: launch_proj_shape<NVM, FIRST, LL, 128, 4>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
-    case 2: launch_proj_shape<NVM, FIRST, LL, 128, 5>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
-    default: launch_proj_shape<NVM, FIRST, LL, 256, 2>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, err); break;
+    case 1: launch_proj_shape<NVM, FIRST, LL, 128, 4>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, err); break;
+    case 2: launch_proj_shape<NVM, FIRST, LL, 128, 5>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, err); break;
+    default: launch_proj_shape<NVM, FIRST, LL, 256, 2>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, err); break;
   }
 }
 
 template <int LL>
 int launch_proj(int nv, bool first, int nrhs, cudaStream_t st, zf* w, zf* V, size_t fs,
                 size_t n, const float2* L32, const stencil::KGeom& kg, zd* small, SmallLayout L,
-                double* dnorm, ReduceWork& rw, const zf* b0, const double* beta0) {
+                double* dnorm, ReduceWork& rw, const zf* b0, const double* beta0, const zf* sin,
+                int par) {
   const int nvm = first ? 0 : nv <= 4 ? 4 : nv <= 8 ? 8 : 16;
   cudaError_t err = cudaSuccess;
   auto run = [&](int v) {
-    if (first) launch_proj_v<4, true, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, &err);
-    else if (nvm == 4) launch_proj_v<4, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, &err);
-    else if (nvm == 8) launch_proj_v<8, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, &err);
-    else launch_proj_v<16, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, &err);
+    if (first) launch_proj_v<4, true, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, &err);
+    else if (nvm == 4) launch_proj_v<4, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, &err);
+    else if (nvm == 8) launch_proj_v<8, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, &err);
+    else launch_proj_v<16, false, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, &err);
   };
   // tuning key: a dtype code of its own per (columns class, link layout), parity -2; the
   // kernel is idempotent (it rewrites w, its partials and its Hessenberg column from inputs
   // it does not modify), so the tuner may run it several times
-  int v = tuned_variant(1000 + 10 * nvm + LL, -2, 0, kg.V, nrhs, st, kProjShapes, run);
+  int v = tuned_variant(1000 + 100 * par + 10 * nvm + LL, -2, 0, kg.V, nrhs, st, kProjShapes, run);
   if (v < 0) return fail(MG_ECUDA, "fused stencil autotune failed");
   run(v);
   count_launch();
@@ -630,14 +638,25 @@ int dslash_proj_launch(zf* w, zf* V, size_t fs, size_t n, int nrhs, zd* small,
   stencil::KGeom kg = stencil::to_kgeom(fz.g);
   int nv = j + 1;
   const float2* L32 = static_cast<const float2*>(fz.links);
+  const zf* sin = nullptr;
+  const int par = fz.schur ? 1 : 0;
+  if (par) {
+    // first hop of the Schur operator, t_o = -kappa H_oe x, x = b (first step) or v_j
+    sin = static_cast<const zf*>(fz.odd);
+    const zf* x = b0 ? b0 : V + (size_t)j * fs;
+    WMG_TRY(dslash_launch(MG_C64, fz.odd, x, fz.links, fz.g, 1, 0, nrhs, st, n, n, fz.layout));
+  }
   // algorithmic bytes: per right-hand side the nv basis columns read (v_j, the stencil input,
   // is one of them) and w written -- the first step reads b and writes v_0 and w instead --
-  // and the 36 complex link entries of a site once per launch
-  const double fields = b0 ? 3.0 : (double)(nv + 1);
-  double byts = (double)kg.V * 8.0 * (12.0 * fields * nrhs + 36.0);
-  ProfScope ps("dslash_proj", byts, (1320.0 + 48.0 * (nv + 1)) * kg.V * nrhs, st);
-  if (fz.layout == 2) return launch_proj<2>(nv, b0 != nullptr, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0);
-  return launch_proj<1>(nv, b0 != nullptr, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0);
+  // and the 36 complex link entries of a site once per launch; the Schur form's second hop
+  // reads t_o besides and all 8 links of each even output site
+  const double fields = (b0 ? 3.0 : (double)(nv + 1)) + par;
+  const double nout = par ? kg.V / 2 : kg.V;
+  double byts = nout * 8.0 * (12.0 * fields * nrhs + (par ? 72.0 : 36.0));
+  ProfScope ps(par ? "schur_proj" : "dslash_proj", byts,
+               (1320.0 + 48.0 * (nv + 1)) * nout * nrhs, st);
+  if (fz.layout == 2) return launch_proj<2>(nv, b0 != nullptr, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par);
+  return launch_proj<1>(nv, b0 != nullptr, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par);
 }
 
 template <int NVM>
@@ -767,7 +786,8 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
   E* vj = V + (size_t)j * fs;
   bool fuse = false;
   if constexpr (std::is_same<E, zf>::value)
-    fuse = fused && single_pass && !M && j + 1 <= ST_NV && n == (size_t)fused->g.V * 12;
+    fuse = fused && single_pass && !M && j + 1 <= ST_NV &&
+           n == (size_t)(fused->schur ? fused->g.V / 2 : fused->g.V) * 12;
   if (fuse) {
     // the stencil and the single-pass projections in one kernel
     if constexpr (std::is_same<E, zf>::value)
@@ -822,7 +842,8 @@ int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t 
   WMG_LAUNCH_DEP(init_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
   // the fused first step scales b itself and writes v_0 (see dslash_proj_kernel)
   bool fuse0 = false;
-  if constexpr (std::is_same<E, zf>::value) fuse0 = fused && n == (size_t)fused->g.V * 12;
+  if constexpr (std::is_same<E, zf>::value)
+    fuse0 = fused && n == (size_t)(fused->schur ? fused->g.V / 2 : fused->g.V) * 12;
   if (!fuse0) WMG_TRY(scale_inv_v<E>(V, b, dnorm + nrhs, 1, n, nrhs, st));
   // A fixed number of steps from zero (the smoothers): complex-float bases of up to 16
   // columns orthogonalise with a single classical Gram-Schmidt pass, H[j+1, j] from

@@ -509,7 +509,9 @@ int post_smooth_schur(mg_handle* h, cplx<R>* z, const cplx<R>* r, int nrhs, cuda
   Op<R> Dhat = [h, to, L, lay, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
     return schur_apply<cplx<R>>(out, in, to, L, lay, h->g, 0, nrhs, s2);
   };
-  WMG_TRY(Lvl<R>::posts(h).fixed(Dhat, xe, rh, h->p.post_smooth, st));
+  FusedStencil fz{h->links32L, h->g, h->llay, true, to};   // FP32: hops fused with projections
+  WMG_TRY(Lvl<R>::posts(h).fixed(Dhat, xe, rh, h->p.post_smooth, st, false,
+                                 sizeof(R) == 4 && !h->clov32 ? &fz : nullptr));
   WMG_TRY(dslash_launch(dt, to, xe, L, g, 1, 0, nrhs, st, nh, nh, lay, ro));   // e_o
   cplx<R>* ke = Lvl<R>::ke(h);
   WMG_TRY(eo_join<cplx<R>>(ke, xe, to, g, nrhs, st));
