@@ -188,3 +188,27 @@ def test_least_squares_interpolation_prolongator(cfg, weights):
         assert np.all(svd_bounds.projector_errors(P, Pu) <= bp)
     record("ls_%s_%s" % (cfg["link_seed"], weights), rel_err=worst)
     h.close()
+
+
+def test_anisotropic_configuration_full_size():
+    """The anisotropic 16^3 x 64 workload at full size (2x2x2x4 aggregates: 8192 of them, tiles
+    of 192 rows and up to 40 columns, k = 24, four streams of 16), on 64 supplied complex-float
+    vectors with the mixed form's double-float SVD: sigma of every stream and the projectors of
+    64 aggregates against the oracle within the double-float bound."""
+    cfg = dict(synthetic.WORKLOADS["c3_16^3x64_aniso"])
+    cfg["kappa"] = synthetic.kappa_of(cfg)
+    dims, block, k, r, n_s = cfg["dims"], cfg["block"], cfg["k"], cfg["r"], cfg["n_s"]
+    U = links_for(cfg)
+    vec = synthetic.graded_fields(dims, r * n_s, 2.0, 4002).astype(np.complex64)
+    p = params_for(cfg, setup_dtype="c64", solve_dtype="c64")
+    h = api.Hierarchy(to_dev(U), p, vectors=to_dev(vec))
+    P, _ = h.prolongator()
+    P = P.cpu().numpy()
+    H = h.sigma_history().cpu().numpy()
+    h.close()
+    d = P.shape[0]
+    sub = np.arange(0, d, d // 64)
+    tiles = [icsvd.chiral_split(vec[s * r:(s + 1) * r].astype(np.complex128), dims, block)[sub]
+             for s in range(n_s)]
+    del vec
+    _check("aniso_full_size", P, H, tiles, k, svd_bounds.UDF, sub=sub)
