@@ -126,7 +126,7 @@ def load_peaks():
 # over the launches of one warm-up and one timed step) from one ncu capture of this bench
 # command on its workload, reported as roofline.traffic for that kernel; an entry is removed
 # whenever its kernel changes, until it is captured again.
-NCU_TRAFFIC = {("dslash_proj", "c2_16^3x32_near_critical"): 117.1e6}
+NCU_TRAFFIC = {("galerkin_tc", "c2_16^3x32_near_critical"): 1.6086e9}
 
 
 def kernel_bound(name, alu, peaks, peak_kind):
@@ -188,8 +188,10 @@ def kernel_table(kern, alu, peaks, peak_kind):
         ach = v["flops"] / max(v["launches"], 1e-9) / per_launch_s / 1e12
         roof = {"kernel": name, "bound": bound, "achieved": ach, "peak": pk,
                 "unit": unit, "frac": ach / pk, "peak_source": src,
-                "traffic": None, "avg_launch_us": per_launch_s * 1e6,
-                "algorithmic_flops_per_launch": v["flops"] / max(v["launches"], 1e-9)}
+                "traffic": NCU_TRAFFIC.get((name, WORKLOAD)),
+                "avg_launch_us": per_launch_s * 1e6,
+                "algorithmic_flops_per_launch": v["flops"] / max(v["launches"], 1e-9),
+                "algorithmic_bytes_per_launch": v["bytes"] / max(v["launches"], 1e-9)}
     else:
         ach = v["bytes"] / max(v["launches"], 1e-9) / per_launch_s / 1e9
         roof = {"kernel": name, "bound": bound, "achieved": ach, "peak": pk,
@@ -228,6 +230,52 @@ def anisotropic_leg(api, synthetic, dev, step, reps=2):
         out[tag] = {"seconds": float(np.mean(ts)), "outer": info["outer"],
                     "refinements": info["refinements"], "residual": info["residual"]}
     out["f16_over_fp64_speedup"] = out["fp64"]["seconds"] / out["f16"]["seconds"]
+    out["galerkin_k24"] = galerkin_k24(api, U, cfg, dev)
+    return out
+
+
+def galerkin_k24(api, U, cfg, dev, reps=3):
+    """Double-float Galerkin build (Eq. 5) of the k = 24 hierarchy: the tensor-pipe digit
+    contraction on the setup's own orthonormal prolongator, and the FP32-unit double-float
+    kernel that the build runs instead on Gaussian tiles of the same shape (entries outside
+    the fixed-point range).  Per-launch times from CUDA events around each kernel."""
+    import torch
+    from paper_2505_14399_gb300 import _lib
+    p = api.params(cfg["dims"], cfg["block"], cfg["kappa"], cfg["k"], cfg["r"], cfg["n_s"],
+                   cfg["sweeps"], cfg["tv_seed"], cfg["hop_weight"], cfg["bc"],
+                   setup_dtype="c64", solve_dtype="c64")
+    h = api.Hierarchy(U, p)
+
+    def build():
+        h.coarse_build()
+        torch.cuda.synchronize()
+        _lib.check(_lib.lib().mg_profile_enable(1, 1000), "mg_profile_enable")
+        try:
+            for _ in range(reps):
+                h.coarse_build()
+            torch.cuda.synchronize()
+            kern = json.loads(_lib.lib().mg_profile_report().decode())
+        finally:
+            _lib.lib().mg_profile_enable(0, 0)
+        return kern
+
+    kt = build()
+    g = torch.Generator(device="cpu").manual_seed(11)
+    shape = (h.d, 2, h.k, 6 * h.nd)
+    G = torch.complex(torch.randn(shape, generator=g, dtype=torch.float64),
+                      torch.randn(shape, generator=g, dtype=torch.float64)).to(dev)
+    h.set_prolongator(G)
+    kf = build()
+    h.close()
+    tc, fb = kt["galerkin_tc"], kf.get("galerkin_tc_range_fallback")
+    out = {"k": cfg["k"], "sites": int(np.prod(cfg["dims"])), "block": list(cfg["block"]),
+           "tensor_ms": tc["ms"] / reps, "method_gflop": tc["flops"] / reps / 1e9,
+           "tensor_method_TFLOPs": tc["flops"] / (tc["ms"] * 1e-3) / 1e12,
+           "tensor_issued_TFLOPs": tc.get("issued_flops", 0.0) / (tc["ms"] * 1e-3) / 1e12,
+           "fallback_on_gaussian_tiles": fb is not None}
+    if fb is not None:
+        out["fp32_unit_ms"] = fb["ms"] / reps
+        out["tensor_speedup"] = fb["ms"] / tc["ms"]
     return out
 
 

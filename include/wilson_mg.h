@@ -100,7 +100,7 @@ typedef struct mg_params {
                                 units (~2^-48 relative), 0 native FP64; -1 double-float
                                 only in the mixed forms (SVD: setup_dtype MG_C64;
                                 Galerkin: solve_dtype other than MG_C128).  A double-float
-                                Galerkin with k <= 12 runs its contraction on the tensor
+                                Galerkin with k <= 24 runs its contraction on the tensor
                                 pipe as exact bf16 digit products (same accuracy) when
                                 every entry is in range (orthonormal P, unitary links),
                                 else on the FP32 units                                   */
@@ -290,10 +290,10 @@ int coarse_build(mg_handle* h, void* stream);
  *     (that call allocates the storage of D_c, which this call overwrites); otherwise
  *     MG_EINVAL.
  *   Set-up: the first call on each device looks up the device address of the scratch
- *     array (once, with that device current) and caches it; make that first call before
- *     any stream capture begins.  Like every other device state of the library (handles,
- *     its allocation cache), the cached address belongs to the device's primary context:
- *     a cudaDeviceReset of that device while the library is loaded invalidates it.
+ *     array (once, with that device current) and caches it.  Like every other device
+ *     state of the library (handles, its allocation cache), the cached address belongs to
+ *     the device's primary context: a cudaDeviceReset of that device while the library
+ *     is loaded invalidates it.
  *   Concurrency: the scratch is shared by every handle of the process on a device, so
  *     calls on the same device must not overlap (e.g. from two host threads): two
  *     overlapping calls race on the scratch and both results are undefined.

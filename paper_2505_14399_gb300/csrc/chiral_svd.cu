@@ -46,6 +46,10 @@ __global__ void gather_kernel(TO* tiles, int cmax, int col0, const cplx<R>* __re
 }
 
 constexpr int GT = 256;   // threads per tile CTA
+// threads per Jacobi CTA: a round's work is about (c/2)(c/2 + 1)/2 A blocks and c^2/2 V
+// entries, a few per thread at 128, and 128-thread CTAs keep every tile of a launch resident
+// at once (8 per SM)
+constexpr int JT = 128;
 constexpr int GR = 32;    // rows staged per chunk
 constexpr int MAXC = 64;  // max columns per tile
 
@@ -120,12 +124,14 @@ template <> struct JacOps<zd> {
   static __device__ __forceinline__ zd val(zd v) { return v; }
   static __device__ __forceinline__ zd zero() { return {0, 0}; }
   static __device__ __forceinline__ zd one() { return {1, 0}; }
+  static __device__ __forceinline__ zd cj(zd v) { return {v.re, -v.im}; }
 };
 template <> struct JacOps<zdf> {
   static __device__ __forceinline__ zdf from(zd v) { return zdf_from(v); }
   static __device__ __forceinline__ zd val(zdf v) { return {df_val(v.re), df_val(v.im)}; }
   static __device__ __forceinline__ zdf zero() { return {{0.f, 0.f}, {0.f, 0.f}}; }
   static __device__ __forceinline__ zdf one() { return {{1.f, 0.f}, {0.f, 0.f}}; }
+  static __device__ __forceinline__ zdf cj(zdf v) { return {v.re, df_neg(v.im)}; }
 };
 
 // (xa, xb) <- (c xa - s ph xb, s xa + c ph xb), c and s real, ph a unit phase
@@ -144,7 +150,7 @@ __device__ __forceinline__ void rot_pair(zdf& xa, zdf& xb, df c, df s, zdf ph) {
 }
 
 template <bool DF>
-__global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const zd* G, int c,
+__global__ void __launch_bounds__(JT) jacobi_kernel(double* lam, zd* Vec, const zd* G, int c,
                                                     double rtol) {
   typedef typename std::conditional<DF, zdf, zd>::type T;
   typedef typename std::conditional<DF, df, double>::type TR;
@@ -252,47 +258,66 @@ __global__ void __launch_bounds__(GT) jacobi_kernel(double* lam, zd* Vec, const 
         rotated |= f;
       }
       __syncthreads();
-      // rows: new_a = c A_a - s e^{i phi} A_b ; new_b = s A_a + c e^{i phi} A_b
-      for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
-        int p = e / ce, k = e % ce;
-        if (!rflag[p]) continue;
-        const int a = pa[round * np + p], b = pb[round * np + p];
-        T eph = rph[p];
-        if constexpr (DF) eph.im = df_neg(eph.im);
-        else eph.im = -eph.im;
-        T xa = A[a * ce + k], xb = A[b * ce + k];
-        rot_pair(xa, xb, rcT[p], rsT[p], eph);
-        A[a * ce + k] = xa;
-        A[b * ce + k] = xb;
-      }
-      __syncthreads();
-      // columns: new_a = c M_a - s e^{-i phi} M_b ; new_b = s M_a + c e^{-i phi} M_b
-      for (int e = threadIdx.x; e < np * ce; e += blockDim.x) {
-        int p = e / ce, k = e % ce;
-        if (!rflag[p]) continue;
-        const int a = pa[round * np + p], b = pb[round * np + p];
-        T mph = rph[p];
-        T xa = A[k * ce + a], xb = A[k * ce + b];
-        rot_pair(xa, xb, rcT[p], rsT[p], mph);
-        A[k * ce + a] = xa;
-        A[k * ce + b] = xb;
-        T va = Vv[k * ce + a], vb = Vv[k * ce + b];
-        rot_pair(va, vb, rcT[p], rsT[p], mph);
-        Vv[k * ce + a] = va;
-        Vv[k * ce + b] = vb;
-      }
-      __syncthreads();
-      if constexpr (!DF) {
-        // with the exact FP64 angle the rotated pair's off-diagonal entries are zero
-        for (int p = threadIdx.x; p < np; p += blockDim.x) {
-          if (rflag[p]) {
+      // A <- J^dag A J and V <- V J in one pass.  The pairs of a round are disjoint, so the
+      // 2 x 2 block of A on the rows of pair p and the columns of pair p' is closed under both
+      // rotations: its rows turn with pair p (new_a = c A_a - s e^{i phi} A_b, new_b = s A_a +
+      // c e^{i phi} A_b), then its columns with pair p' (phase e^{-i phi}).  A stays Hermitian,
+      // so only blocks p <= p' are computed and each p < p' block is mirrored (conjugate
+      // transpose) into (p', p); V's columns turn like A's.
+      {
+        const int nblk = np * (np + 1) / 2;
+        for (int e = threadIdx.x; e < nblk + np * ce; e += blockDim.x) {
+          if (e < nblk) {
+            // block (p, p2), p <= p2, from the packed upper-triangle index
+            int p = 0, rem = e;
+            while (rem >= np - p) { rem -= np - p; ++p; }
+            const int p2 = p + rem;
+            const bool fr = rflag[p] != 0, fc = rflag[p2] != 0;
+            if (!fr && !fc) continue;
             const int a = pa[round * np + p], b = pb[round * np + p];
-            A[a * ce + b] = J::zero();
-            A[b * ce + a] = J::zero();
+            const int a2 = pa[round * np + p2], b2 = pb[round * np + p2];
+            T x00 = A[a * ce + a2], x01 = A[a * ce + b2];
+            T x10 = A[b * ce + a2], x11 = A[b * ce + b2];
+            if (fr) {
+              T eph = rph[p];
+              if constexpr (DF) eph.im = df_neg(eph.im);
+              else eph.im = -eph.im;
+              rot_pair(x00, x10, rcT[p], rsT[p], eph);
+              rot_pair(x01, x11, rcT[p], rsT[p], eph);
+            }
+            if (fc) {
+              const T mph = rph[p2];
+              rot_pair(x00, x01, rcT[p2], rsT[p2], mph);
+              rot_pair(x10, x11, rcT[p2], rsT[p2], mph);
+            }
+            if (p == p2) {
+              if constexpr (!DF) {
+                // with the exact FP64 angle the rotated pair's coupling is zero
+                if (fr) x01 = x10 = J::zero();
+              }
+            } else {
+              A[a2 * ce + a] = J::cj(x00);
+              A[b2 * ce + a] = J::cj(x01);
+              A[a2 * ce + b] = J::cj(x10);
+              A[b2 * ce + b] = J::cj(x11);
+            }
+            A[a * ce + a2] = x00;
+            A[a * ce + b2] = x01;
+            A[b * ce + a2] = x10;
+            A[b * ce + b2] = x11;
+          } else {
+            const int ev = e - nblk;
+            const int p = ev / ce, k = ev % ce;
+            if (!rflag[p]) continue;
+            const int a = pa[round * np + p], b = pb[round * np + p];
+            T va = Vv[k * ce + a], vb = Vv[k * ce + b];
+            rot_pair(va, vb, rcT[p], rsT[p], rph[p]);
+            Vv[k * ce + a] = va;
+            Vv[k * ce + b] = vb;
           }
         }
-        __syncthreads();
       }
+      __syncthreads();
     }
     // a barrier that also ORs the flags: every thread takes the same exit decision
     if (!__syncthreads_or(rotated)) break;
@@ -635,8 +660,8 @@ int tile_eig(double* lam, zd* Vec, zd* G, int c, int ntiles, cudaStream_t st, do
               sizeof(int) * (2 * (ce - 1) * np + np) + 64;
   WMG_TRY(smem_attr(df64 ? jacobi_kernel<true> : jacobi_kernel<false>, sh));
   ProfScope ps(df64 ? "svd_jacobi_df64" : "svd_jacobi_fp64", 32.0 * c * c * ntiles, 0.0, st);
-  if (df64) jacobi_kernel<true><<<ntiles, GT, sh, st>>>(lam, Vec, G, c, rtol);
-  else jacobi_kernel<false><<<ntiles, GT, sh, st>>>(lam, Vec, G, c, rtol);
+  if (df64) jacobi_kernel<true><<<ntiles, JT, sh, st>>>(lam, Vec, G, c, rtol);
+  else jacobi_kernel<false><<<ntiles, JT, sh, st>>>(lam, Vec, G, c, rtol);
   WMG_LAUNCHED();
   return MG_OK;
 }

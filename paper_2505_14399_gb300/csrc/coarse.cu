@@ -431,11 +431,8 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, con
   const bool tc = df64 && galerkin_tc_supported(k, B);
   // flops: the method's work, 768 k^2 FP64-equivalent flops per fine site (4 forward hops x
   // 6 rows x (2k)^2 complex multiply-adds); the tensor path also records the bf16 digit-plane
-  // products it issues for them (28 digit pairs of a (2 (2k)) x (2k) x 96 real product per
-  // 8-site batch, padded tiles, about n_d / 8 + 1 batches per CTA)
-  const double t4 = (k + 3) / 4;
-  const double tc_flops = 2.0 * (16 * t4) * (8 * t4) * 96.0 * 28.0 * 4.0 * B.d *
-                          ((double)B.nd / 8.0 + 1.0);
+  // products it issues for them
+  const double tc_flops = tc ? galerkin_tc_issued_flops(k, B) : 0.0;
   ProfScope ps(tc ? "galerkin_tc" : df64 ? "galerkin_df64" : "galerkin_fp64",
                16.0 * (12.0 * B.nd * B.d * k * 5 + 36.0 * B.nd * B.d),
                768.0 * k * k * B.nd * B.d, tc ? tc_flops : 0.0, st);
@@ -449,7 +446,10 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, con
     int h_flag = 0;
     WMG_CUDA(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     WMG_CUDA(cudaStreamSynchronize(st));
-    if (h_flag) WMG_TRY(launch_hop_ne<true>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B));
+    if (h_flag) {
+      ProfScope pf("galerkin_tc_range_fallback", 0.0, 0.0, st);
+      WMG_TRY(launch_hop_ne<true>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B));
+    }
   } else if (df64) {
     WMG_TRY(launch_hop_ne<true>(grid, sh, st, Op, Xpart, P, Pdf, k, links, Ldf, hg, B));
   } else {

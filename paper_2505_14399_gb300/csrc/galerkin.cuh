@@ -24,9 +24,11 @@ __device__ __forceinline__ zdf isigma_df(int mu, int s, zdf p0, zdf p1) {
   return s == 0 ? zdf_ti(p0) : zdf_tmi(p1);
 }
 
-// Whether the tensor-pipe forward-hop kernel handles this k and blocking (2k <= 24, its
+// Whether the tensor-pipe forward-hop kernel handles this k and blocking (2k <= 48, its
 // shared memory fits one CTA).
 bool galerkin_tc_supported(int k, const Blocking& B);
+// bf16 flops that kernel issues for one build (its digit-plane products, padding included).
+double galerkin_tc_issued_flops(int k, const Blocking& B);
 // The forward-hop blocks of the double-float Galerkin build on the tensor pipe (same outputs
 // as the FP32-unit kernel: Y_+mu blocks into Op, in-aggregate partials into Xpart).  Raises
 // *range_flag (device int) if a staged entry is outside the fixed-point range (|v| >= 2 or not

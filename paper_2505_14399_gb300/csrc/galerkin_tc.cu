@@ -16,8 +16,8 @@
 // scaled by their weights (exact) and added to double-float accumulators with error-free
 // two-sums, so the result carries double-float accuracy (~2^-48 relative), not bf16's.
 //
-// The complex product is one real GEMM per digit pair: with K = 48 rows (8 sites x 6 half-
-// spinor rows) per batch, stacked as k' = [re rows | im rows] (96),
+// The complex product is one real GEMM per digit pair: with K = 6 NB rows (NB sites x 6 half-
+// spinor rows) per batch, stacked as k' = [re rows | im rows] (12 NB),
 //     A'[b'][k'] : rows b < 2k = (Ch_re | Ch_im), rows 2k + b = (Ch_im | -Ch_re),
 //     B'[a][k']  : (Pt_re | Pt_im),
 // C'[b'][a] = sum_k' A'[b'][k'] B'[a][k'] gives Re C[a][b] (b' = b) and Im C[a][b] (b' = 2k+b).
@@ -25,6 +25,9 @@
 // planes are stored k'-major (SA[k'][b'], SB[k'][a]) so that staging threads with consecutive
 // columns write consecutive addresses, and read with ldmatrix .trans; every row stride is an
 // odd number of 16-byte units, so the eight rows of an ldmatrix phase hit distinct banks.
+// A batch is NB = 8 sites for 2k <= 24 (two warp groups split its six 16-row k' steps) and
+// NB = 4 for 24 < 2k <= 48 (one warp group, three k' steps), so that the digit planes and the
+// double-buffered raw inputs of one CTA fit its shared memory up to the paper's k = 24.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -38,10 +41,21 @@ namespace wmg {
 namespace {
 
 constexpr int TC_NS = 7;               // digits per value
-constexpr int TC_KB = GNB * 6;         // staged rows per batch (48)
-constexpr int TC_K = 2 * TC_KB;        // stacked real rows (96)
-constexpr int TC_MAXW = 12;            // warps per CTA at most
-constexpr int TC_MAXT4 = 3;            // 2k <= 24 (the digit planes and two raw buffers fit)
+constexpr int TC_MAXT4 = 6;            // 2k <= 48
+
+// Per column-tile count T4 (2k <= 8 T4): sites per batch, stacked rows, warp groups, warps.
+template <int T4>
+struct TcCfg {
+  static constexpr int NB = T4 <= 3 ? 8 : 4;           // fine sites staged per batch
+  static constexpr int KB = NB * 6;                    // staged rows per batch
+  static constexpr int K = 2 * KB;                     // stacked real rows (96 or 48)
+  static constexpr int WG = (K / 16) % 2 == 0 ? 2 : 1; // warp groups (each takes k' steps)
+  static constexpr int NTILES = T4 * T4;
+  // warps per group: at most 12 (two groups) or 16 (one group), tiles spread evenly
+  static constexpr int MAXW = WG == 2 ? 12 : 16;
+  static constexpr int TPW = (NTILES + MAXW - 1) / MAXW;   // tiles per warp
+  static constexpr int NW = (NTILES + TPW - 1) / TPW;
+};
 
 __device__ __forceinline__ void ldm_x4t(unsigned r[4], const __nv_bfloat16* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -57,8 +71,9 @@ __device__ __forceinline__ void ldm_x2t(unsigned r[2], const __nv_bfloat16* p) {
 // Row strides (bf16) of the k'-major digit planes: odd multiples of 8 (16 bytes).
 __host__ __device__ constexpr int tc_lda(int t4) { return 16 * t4 + 8; }
 __host__ __device__ constexpr int tc_ldb(int t4) { return 8 * t4 + ((t4 & 1) ? 0 : 8); }
+__host__ __device__ constexpr int tc_nb(int t4) { return t4 <= 3 ? 8 : 4; }
 __host__ __device__ constexpr size_t tc_smem(int t4) {
-  return sizeof(__nv_bfloat16) * (size_t)TC_NS * TC_K * (tc_lda(t4) + tc_ldb(t4));
+  return sizeof(__nv_bfloat16) * (size_t)TC_NS * 12 * tc_nb(t4) * (tc_lda(t4) + tc_ldb(t4));
 }
 // c += a b, 16x16 (row) x 16x8 (col) bf16, FP32 accumulators
 __device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2]) {
@@ -69,17 +84,30 @@ __device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// The base-256 digits of v (|v| < 2): v = sum_i s[i] 2^{-6-8i}, rounded to nearest at every
-// digit, so |s[i]| <= 128 (+1 when a remainder rounds up).  Exact remainders in double-float.
+// The base-256 digits of v (|v| < 2, normalised: |v.lo| <= ulp(v.hi) / 2): v = sum_i s[i]
+// 2^{-6-8i}, each digit the nearest integer to the high word of the remainder, so |s[i]| <= 128
+// (+1 when a remainder rounds up).  The remainders stay exact and normalised: hi - rint(hi)
+// is exact, and it is either 0 or a multiple of ulp(hi) >= 2 |lo|, so one fast two-sum
+// renormalises (hi - d, lo) (the double-float sum with the zero error terms left out).
 __device__ __forceinline__ void tc_digits(df v, float s[TC_NS]) {
-  df x = {v.hi * 64.0f, v.lo * 64.0f};
+  float hi = v.hi * 64.0f, lo = v.lo * 64.0f;
 #pragma unroll
   for (int i = 0; i < TC_NS; ++i) {
-    float d = rintf(x.hi);
+    const float d = rintf(hi);
     s[i] = d;
-    df r = df_add(x, {-d, 0.0f});
-    x = {r.hi * 256.0f, r.lo * 256.0f};
+    const float r = __fsub_rn(hi, d);
+    const float h2 = __fadd_rn(r, lo);
+    const float l2 = __fsub_rn(lo, __fsub_rn(h2, r));
+    hi = h2 * 256.0f;
+    lo = l2 * 256.0f;
   }
+}
+
+// Two digits (integers, |d| <= 129: at most 8 significant bits, so the low 16 bits of their
+// FP32 words are zero and the high halves are their exact bfloat16 encodings) packed as the
+// bf16 pair (d0 at the lower address, d1 at the higher).
+__device__ __forceinline__ unsigned tc_pack(float d0, float d1) {
+  return __byte_perm(__float_as_uint(d0), __float_as_uint(d1), 0x7632);
 }
 
 // s + e += v with an error-free two-sum (v exact)
@@ -93,9 +121,6 @@ __device__ __forceinline__ void acc_add(dfacc& a, float v) {
 
 __device__ __forceinline__ bool tc_in_range(df v) { return fabsf(v.hi) < 2.0f; }   // false for NaN
 
-__host__ __device__ constexpr int tc_warps(int t4) { return t4 * t4 < TC_MAXW ? t4 * t4 : TC_MAXW; }
-// Two warp groups: both stage; each takes half of the stacked rows k' of every product.
-constexpr int TC_WG = 2;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
@@ -114,27 +139,29 @@ __device__ __forceinline__ void cp_async_wait() {
 // (consecutive columns of one component) spread over the banks.
 __host__ __device__ constexpr int tc_nrp(int t4) { return 8 * t4 + 1; }
 __host__ __device__ constexpr size_t tc_raw_bytes(int t4) {
-  return sizeof(zdf) * 2 * ((size_t)2 * GNB * 6 * tc_nrp(t4) + GNB * 9);
+  return sizeof(zdf) * 2 * ((size_t)2 * tc_nb(t4) * 6 * tc_nrp(t4) + tc_nb(t4) * 9);
 }
 __host__ __device__ inline size_t tc_table_bytes(int nd) { return sizeof(int) * 8 * (size_t)nd + 16; }
 
 template <int T4>
-__global__ void __launch_bounds__(32 * TC_WG * tc_warps(T4), 1)
+__global__ void __launch_bounds__(32 * TcCfg<T4>::WG * TcCfg<T4>::NW, 1)
 galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
                    const zdf* __restrict__ Ldf, HopGeom g, Blocking B, int* range_flag) {
+  using C = TcCfg<T4>;
   constexpr int NR = 8 * T4;                  // columns a (>= 2k)
-  constexpr int NTILES = T4 * T4;
-  constexpr int NW = tc_warps(T4);
-  constexpr int TPW = (NTILES + NW - 1) / NW;   // tiles per warp
+  constexpr int NTILES = C::NTILES;
+  constexpr int NW = C::NW;
+  constexpr int TPW = C::TPW;                 // tiles per warp
+  constexpr int NB = C::NB, KB = C::KB, K = C::K, WG = C::WG;
   constexpr int ND = TC_NS;                   // digit-pair weights d = i + j < NS
   constexpr int LDA = tc_lda(T4), LDB = tc_ldb(T4);
   extern __shared__ __align__(16) unsigned char tc_raw[];
-  __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(tc_raw);   // [NS][TC_K][LDA]
-  __nv_bfloat16* SB = SA + (size_t)TC_NS * TC_K * LDA;             // [NS][TC_K][LDB]
+  __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(tc_raw);   // [NS][K][LDA]
+  __nv_bfloat16* SB = SA + (size_t)TC_NS * K * LDA;                // [NS][K][LDB]
   constexpr int NRP = tc_nrp(T4);
-  zdf* sPy = reinterpret_cast<zdf*>(tc_raw + tc_smem(T4));         // [2][GNB][6][NRP]
-  zdf* sPx = sPy + (size_t)2 * GNB * 6 * NRP;                      // [2][GNB][6][NRP]
-  zdf* sU = sPx + (size_t)2 * GNB * 6 * NRP;                       // [2][GNB][9]
+  zdf* sPy = reinterpret_cast<zdf*>(tc_raw + tc_smem(T4));         // [2][NB][6][NRP]
+  zdf* sPx = sPy + (size_t)2 * NB * 6 * NRP;                       // [2][NB][6][NRP]
+  zdf* sU = sPx + (size_t)2 * NB * 6 * NRP;                        // [2][NB][9]
   const int nd = B.nd;
   int* tx = reinterpret_cast<int*>(tc_raw + tc_smem(T4) + tc_raw_bytes(T4));   // site x
   int* toy = tx + nd;      // P offset of (2 j(y)) k M, y = x + mu
@@ -193,11 +220,16 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
   __syncthreads();
 
   const int pps = 2 * n2k * 6 + 9;   // 16-byte pieces per site (one double-float complex each)
+  // staging assignment: thread -> column pair sq of staged rows srow0, srow0 + srows, ...
+  // (threads beyond srows * k stage nothing)
+  const int srows = blockDim.x / k;
+  const int sq = threadIdx.x % k;
+  const int srow0 = threadIdx.x < srows * k ? threadIdx.x / k : 6 * NB;
   // issue the raw inputs of batch b of pass p into buffer buf (cp.async, one group)
   auto prefetch = [&](int p, int b, int buf) {
     const int* ls = sel + p * nd;
-    const int h0 = b * GNB;
-    const int nb = min(GNB, nsel[p] - h0);
+    const int h0 = b * NB;
+    const int nb = min(NB, nsel[p] - h0);
     for (int q = threadIdx.x; q < nb * pps; q += blockDim.x) {
       int h = q / pps, rem = q - h * pps;
       int l = ls[h0 + h];
@@ -206,16 +238,16 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
       if (rem < n2k * 6) {
         int bcol = rem / 6, part = rem - bcol * 6;
         src = Pdf + (size_t)toy[l] + (size_t)bcol * M + tly[l] * 6 + part;
-        dst = sPy + (((size_t)buf * GNB + h) * 6 + part) * NRP + bcol;
+        dst = sPy + (((size_t)buf * NB + h) * 6 + part) * NRP + bcol;
       } else if (rem < 2 * n2k * 6) {
         rem -= n2k * 6;
         int bcol = rem / 6, part = rem - bcol * 6;
         src = Pdf + (size_t)tox[l] + (size_t)bcol * M + tlx[l] * 6 + part;
-        dst = sPx + (((size_t)buf * GNB + h) * 6 + part) * NRP + bcol;
+        dst = sPx + (((size_t)buf * NB + h) * 6 + part) * NRP + bcol;
       } else {
         int part = rem - 2 * n2k * 6;
         src = Ldf + ((size_t)mu * V + tx[l]) * 9 + part;
-        dst = sU + ((size_t)buf * GNB + h) * 9 + part;
+        dst = sU + ((size_t)buf * NB + h) * 9 + part;
       }
       cp_async16(dst, src);
     }
@@ -231,7 +263,7 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
     for (int t = 0; t < TPW; ++t)
 #pragma unroll
       for (int e = 0; e < 4; ++e) dacc[t][e] = {0.0f, 0.0f};
-    const int nbat = (nsel[pass] + GNB - 1) / GNB;
+    const int nbat = (nsel[pass] + NB - 1) / NB;
     if (nbat > 0) prefetch(pass, 0, 0);
     for (int b = 0; b < nbat; ++b) {
       const int buf = b & 1;
@@ -242,77 +274,85 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
         cp_async_wait<0>();
       }
       __syncthreads();   // batch b's inputs are in; every warp finished batch b - 1's products
-      const int nb = min(GNB, nsel[pass] - b * GNB);
-      const int* ls = sel + pass * nd + b * GNB;
-      if (nb < GNB) {
+      const int nb = min(NB, nsel[pass] - b * NB);
+      const int* ls = sel + pass * nd + b * NB;
+      if (nb < NB) {
         // a short batch: its unused stacked rows k' are zero in every digit plane
-        const int k0 = nb * 6, kn = TC_KB - k0;
+        const int k0 = nb * 6, kn = KB - k0;
         for (int e = threadIdx.x; e < TC_NS * 2 * kn * (LDA + LDB); e += blockDim.x) {
           int col = e % (LDA + LDB), rr = e / (LDA + LDB);
           int i = rr / (2 * kn), q = rr % (2 * kn);
-          int kk = (q < kn) ? k0 + q : TC_KB + k0 + (q - kn);
-          if (col < LDA) SA[((size_t)i * TC_K + kk) * LDA + col] = __float2bfloat16_rn(0.0f);
-          else SB[((size_t)i * TC_K + kk) * LDB + (col - LDA)] = __float2bfloat16_rn(0.0f);
+          int kk = (q < kn) ? k0 + q : KB + k0 + (q - kn);
+          if (col < LDA) SA[((size_t)i * K + kk) * LDA + col] = __float2bfloat16_rn(0.0f);
+          else SB[((size_t)i * K + kk) * LDB + (col - LDA)] = __float2bfloat16_rn(0.0f);
         }
       }
       // stage from shared memory: Ch (spin-projected, transported P(x + mu)) and Pt
-      // (reconstruction-folded P(x)) in double-float, written as digit planes
-      const zdf* py = sPy + (size_t)buf * GNB * 6 * NRP;
-      const zdf* px = sPx + (size_t)buf * GNB * 6 * NRP;
-      const zdf* pu = sU + (size_t)buf * GNB * 9;
-      for (int e = threadIdx.x; e < nb * 6 * n2k; e += blockDim.x) {
-        int h = e / (6 * n2k);
-        int r = (e / n2k) % 6;
-        int bcol = e % n2k;
-        int s = r / 3, cc = r % 3;
-        int beta = bcol / k;
-        // component q of this column at this site: P*[q * NRP]
-        const zdf* Py = py + (size_t)h * 6 * NRP + bcol;
-        const zdf* Px = px + (size_t)h * 6 * NRP + bcol;
-        zdf hv[3];
-#pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2) {
-          if (beta == 0) {
-            hv[c2] = Py[(s * 3 + c2) * NRP];
-          } else {
-            zdf p0 = Py[c2 * NRP], p1 = Py[(3 + c2) * NRP];
-            hv[c2] = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
-          }
-        }
+      // (reconstruction-folded P(x)) in double-float, written as digit planes; a thread takes
+      // the adjacent columns 2q and 2q + 1 of one row, so every digit goes out as a packed
+      // bf16 pair (one 32-bit store)
+      const zdf* py = sPy + (size_t)buf * NB * 6 * NRP;
+      const zdf* px = sPx + (size_t)buf * NB * 6 * NRP;
+      const zdf* pu = sU + (size_t)buf * NB * 9;
+      for (int rr = srow0; rr < nb * 6; rr += srows) {
+        const int h = rr / 6, r = rr - 6 * (rr / 6);
+        const int q = sq;
+        const int s = r / 3, cc = r - 3 * s;
         const zdf* U = pu + h * 9 + cc * 3;
-        zdfacc t{};
+        const zdf u0 = U[0], u1 = U[1], u2 = U[2];
+        const bool neg = tng[ls[h]] != 0;
+        float cr[2][TC_NS], ci[2][TC_NS], tr[2][TC_NS], ti[2][TC_NS];
 #pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2) zdf_fma(t, U[c2], hv[c2]);
-        zdf ch = zdf_norm(t);
-        if (tng[ls[h]]) ch = zdf_neg(ch);
-        zdf pt;
-        if (beta == 0) {
-          pt = Px[(s * 3 + cc) * NRP];
-        } else {
-          zdf p0 = Px[cc * NRP], p1 = Px[(3 + cc) * NRP];
-          pt = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
+        for (int u = 0; u < 2; ++u) {
+          const int bcol = 2 * q + u;
+          const int beta = bcol >= k;
+          // component q' of this column at this site: P*[q' * NRP]
+          const zdf* Py = py + (size_t)h * 6 * NRP + bcol;
+          const zdf* Px = px + (size_t)h * 6 * NRP + bcol;
+          zdf hv[3];
+#pragma unroll
+          for (int c2 = 0; c2 < 3; ++c2) {
+            if (beta == 0) {
+              hv[c2] = Py[(s * 3 + c2) * NRP];
+            } else {
+              zdf p0 = Py[c2 * NRP], p1 = Py[(3 + c2) * NRP];
+              hv[c2] = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
+            }
+          }
+          zdfacc t{};
+          zdf_fma(t, u0, hv[0]);
+          zdf_fma(t, u1, hv[1]);
+          zdf_fma(t, u2, hv[2]);
+          zdf ch = zdf_norm(t);
+          if (neg) ch = zdf_neg(ch);
+          zdf pt;
+          if (beta == 0) {
+            pt = Px[(s * 3 + cc) * NRP];
+          } else {
+            zdf p0 = Px[cc * NRP], p1 = Px[(3 + cc) * NRP];
+            pt = mu < 3 ? isigma_df(mu, s, p0, p1) : zdf_neg(s == 0 ? p0 : p1);
+          }
+          bad |= !(tc_in_range(ch.re) && tc_in_range(ch.im) && tc_in_range(pt.re) &&
+                   tc_in_range(pt.im));
+          tc_digits(ch.re, cr[u]);
+          tc_digits(ch.im, ci[u]);
+          tc_digits(pt.re, tr[u]);
+          tc_digits(pt.im, ti[u]);
         }
-        bad |= !(tc_in_range(ch.re) && tc_in_range(ch.im) && tc_in_range(pt.re) &&
-                 tc_in_range(pt.im));
         const int kk = h * 6 + r;
-        float dr[TC_NS], di[TC_NS];
-        tc_digits(ch.re, dr);
-        tc_digits(ch.im, di);
 #pragma unroll
         for (int i = 0; i < TC_NS; ++i) {
-          __nv_bfloat16* a0 = SA + ((size_t)i * TC_K + kk) * LDA;            // re rows k
-          __nv_bfloat16* a1 = SA + ((size_t)i * TC_K + TC_KB + kk) * LDA;    // im rows k
-          a0[bcol] = __float2bfloat16_rn(dr[i]);
-          a1[bcol] = __float2bfloat16_rn(di[i]);
-          a0[n2k + bcol] = __float2bfloat16_rn(di[i]);
-          a1[n2k + bcol] = __float2bfloat16_rn(-dr[i]);
-        }
-        tc_digits(pt.re, dr);
-        tc_digits(pt.im, di);
-#pragma unroll
-        for (int i = 0; i < TC_NS; ++i) {
-          SB[((size_t)i * TC_K + kk) * LDB + bcol] = __float2bfloat16_rn(dr[i]);
-          SB[((size_t)i * TC_K + TC_KB + kk) * LDB + bcol] = __float2bfloat16_rn(di[i]);
+          __nv_bfloat16* a0 = SA + ((size_t)i * K + kk) * LDA;          // re rows k
+          __nv_bfloat16* a1 = SA + ((size_t)i * K + KB + kk) * LDA;     // im rows k
+          const unsigned pr = tc_pack(cr[0][i], cr[1][i]), pi = tc_pack(ci[0][i], ci[1][i]);
+          *reinterpret_cast<unsigned*>(a0 + 2 * q) = pr;
+          *reinterpret_cast<unsigned*>(a1 + 2 * q) = pi;
+          *reinterpret_cast<unsigned*>(a0 + n2k + 2 * q) = pi;
+          *reinterpret_cast<unsigned*>(a1 + n2k + 2 * q) = pr ^ 0x80008000u;   // -Ch_re
+          *reinterpret_cast<unsigned*>(SB + ((size_t)i * K + kk) * LDB + 2 * q) =
+              tc_pack(tr[0][i], tr[1][i]);
+          *reinterpret_cast<unsigned*>(SB + ((size_t)i * K + KB + kk) * LDB + 2 * q) =
+              tc_pack(ti[0][i], ti[1][i]);
         }
       }
       __syncthreads();
@@ -333,15 +373,15 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
           const __nv_bfloat16* arow = SA + (size_t)(8 * (mq >> 1) + rr) * LDA + 16 * mt + 8 * (mq & 1);
           const __nv_bfloat16* brow = SB + (size_t)(8 * (mq & 1) + rr) * LDB + 8 * nt;
 #pragma unroll 1
-          for (int ks = grp * (TC_K / 16 / TC_WG); ks < (grp + 1) * (TC_K / 16 / TC_WG); ++ks) {
+          for (int ks = grp * (K / 16 / WG); ks < (grp + 1) * (K / 16 / WG); ++ks) {
             unsigned bfr[TC_NS][2];
 #pragma unroll
             for (int i = 0; i < TC_NS; ++i)
-              ldm_x2t(bfr[i], brow + ((size_t)i * TC_K + 16 * ks) * LDB);
+              ldm_x2t(bfr[i], brow + ((size_t)i * K + 16 * ks) * LDB);
 #pragma unroll
             for (int i = 0; i < TC_NS; ++i) {
               unsigned af[4];
-              ldm_x4t(af, arow + ((size_t)i * TC_K + 16 * ks) * LDA);
+              ldm_x4t(af, arow + ((size_t)i * K + 16 * ks) * LDA);
 #pragma unroll
               for (int jd = 0; jd < TC_NS; ++jd)
                 if (i + jd < ND) mma_bf16(acc[i + jd], af, bfr[jd]);
@@ -362,7 +402,7 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
     // second warp group adds its half of the rows to the first group's
     __syncthreads();
     df* sOut = reinterpret_cast<df*>(tc_raw);   // [16 T4][NR]
-    for (int g2 = 0; g2 < TC_WG; ++g2) {
+    for (int g2 = 0; g2 < WG; ++g2) {
       if (grp == g2) {
 #pragma unroll
         for (int tt = 0; tt < TPW; ++tt) {
@@ -397,7 +437,7 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
 template <int T4>
 int launch_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
               const Blocking& B, int* range_flag, cudaStream_t st) {
-  constexpr int NW = tc_warps(T4) * TC_WG;
+  constexpr int NW = TcCfg<T4>::NW * TcCfg<T4>::WG;
   size_t sh = tc_smem(T4) + tc_raw_bytes(T4) + tc_table_bytes(B.nd);
   WMG_TRY(smem_attr(galerkin_tc_kernel<T4>, sh));
   galerkin_tc_kernel<T4><<<dim3(B.d, 4), 32 * NW, sh, st>>>(Op, Xpart, Pdf, k, Ldf, g, B,
@@ -416,13 +456,25 @@ bool galerkin_tc_supported(int k, const Blocking& B) {
   return sh <= (size_t)227 * 1024 - 1024 && (size_t)B.d * 2 * k * B.M < ((size_t)1 << 31);
 }
 
+double galerkin_tc_issued_flops(int k, const Blocking& B) {
+  // bf16 digit-plane products issued: 28 digit pairs of a (16 T4) x (8 T4) x (12 NB) real
+  // product per batch and hop direction, about n_d / NB + 1 batches per CTA
+  const int t4 = (k + 3) / 4;
+  const double nb = tc_nb(t4);
+  return 2.0 * (16.0 * t4) * (8.0 * t4) * (12.0 * nb) * 28.0 * 4.0 * B.d *
+         ((double)B.nd / nb + 1.0);
+}
+
 int galerkin_hops_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
                      const Blocking& B, int* range_flag, cudaStream_t st) {
   switch ((k + 3) / 4) {
     case 1: return launch_tc<1>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
     case 2: return launch_tc<2>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
     case 3: return launch_tc<3>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    default: return fail(MG_EINVAL, "galerkin (tensor pipe): 2k > 24");
+    case 4: return launch_tc<4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 5: return launch_tc<5>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 6: return launch_tc<6>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    default: return fail(MG_EINVAL, "galerkin (tensor pipe): 2k > 48");
   }
 }
 

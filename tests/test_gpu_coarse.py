@@ -1,10 +1,12 @@
 """GPU restriction, prolongation, Galerkin coarse operator (Eq. 5) and coarse apply vs the oracle."""
+import json
+
 import numpy as np
 import pytest
 import torch
 
 from oracle import coarse, icsvd
-from paper_2505_14399_gb300 import api, synthetic
+from paper_2505_14399_gb300 import _lib as L, api, synthetic
 from gpu_common import orthonormal_tiles, rel, random_tiles, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -13,6 +15,12 @@ pytestmark = pytest.mark.gpu
 CASES = [((4, 4, 4, 4), (2, 2, 2, 2), 4),
          ((4, 4, 2, 8), (2, 4, 2, 2), 5),
          ((6, 4, 4, 4), (2, 2, 2, 4), 12)]
+# the tensor-pipe contraction's wider instances: 8 < 2k <= 48 with 4-site staging batches, on
+# the aggregate shapes of the paper's k = 24 configurations (2x2x2x4 and 4^4, ragged batches)
+TC_CASES = CASES + [((4, 4, 4, 4), (2, 2, 2, 2), 14),
+                    ((4, 4, 2, 8), (2, 2, 2, 4), 20),
+                    ((4, 4, 4, 8), (2, 2, 2, 4), 24),
+                    ((8, 8, 4, 8), (4, 4, 4, 4), 24)]
 
 
 def _handle(dims, block, k, seed, kappa=0.125, w=(1, 1, 1, 1 / 3.5), bc=(1, 1, 1, -1),
@@ -45,15 +53,23 @@ def test_restrict_prolong(dims, block, k):
     h.close()
 
 
-@pytest.mark.parametrize("dims,block,k", CASES)
+@pytest.mark.parametrize("dims,block,k", TC_CASES)
 def test_galerkin_tensor_pipe_contraction(dims, block, k):
     """Double-float Galerkin with an orthonormal prolongator and unitary links: every staged
     entry is inside the fixed-point range, so the forward hops run as exact bf16 digit-plane
-    products on the tensor pipe; the operator must still match the FP64 oracle to double-float
-    accuracy."""
+    products on the tensor pipe (checked in the launch record); the operator must still match
+    the FP64 oracle to double-float accuracy."""
     h, U, Pt, (kappa, w, bc) = _handle(dims, block, k, 9, fp64_emulation=1,
                                        tiles=orthonormal_tiles)
-    h.coarse_build()
+    L.check(L.lib().mg_profile_enable(1, 1000), "mg_profile_enable")
+    try:
+        h.coarse_build()
+        torch.cuda.synchronize()
+        kern = json.loads(L.lib().mg_profile_report().decode())
+    finally:
+        L.lib().mg_profile_enable(0, 0)
+    assert kern.get("galerkin_tc", {}).get("launches", 0) == 1, sorted(kern)
+    assert "galerkin_df64" not in kern and "galerkin_tc_range_fallback" not in kern
     X, Y = h.coarse_op()
     Xo, Yo = coarse.galerkin(Pt, U, dims, block, kappa, w, bc)
     assert rel(X.cpu().numpy(), Xo) < 1e-11
