@@ -134,9 +134,10 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Shared memory of one CTA beyond the digit planes: two raw input buffers (P(x + mu) and P(x)
 // column segments of 6 double-float values, U_mu(x)) and the per-site tables.
-// Raw P segments are stored [site][6 components][column], rows padded to 8 T4 + 1 columns so
-// that both the copies (consecutive components of one column) and the staging reads
-// (consecutive columns of one component) spread over the banks.
+// Raw P segments are stored [site][6 components][column slot], rows padded to 8 T4 + 1 slots
+// so that the copies (consecutive components of one column) spread over the banks; column b
+// sits in slot (b odd ? k : 0) + b / 2, so that the staging threads, which take the column
+// pairs (2q, 2q + 1) for consecutive q, read consecutive 16-byte slots.
 __host__ __device__ constexpr int tc_nrp(int t4) { return 8 * t4 + 1; }
 __host__ __device__ constexpr size_t tc_raw_bytes(int t4) {
   return sizeof(zdf) * 2 * ((size_t)2 * tc_nb(t4) * 6 * tc_nrp(t4) + tc_nb(t4) * 9);
@@ -220,6 +221,9 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
   __syncthreads();
 
   const int pps = 2 * n2k * 6 + 9;   // 16-byte pieces per site (one double-float complex each)
+  // q / pps as a multiply-high: with m = ceil(2^32 / pps), floor(q m / 2^32) = floor(q / pps)
+  // whenever q pps < 2^32 (here q < NB pps and pps <= 585)
+  const unsigned pps_m = 0xffffffffu / (unsigned)pps + 1u;
   // staging assignment: thread -> column pair sq of staged rows srow0, srow0 + srows, ...
   // (threads beyond srows * k stage nothing)
   const int srows = blockDim.x / k;
@@ -231,19 +235,19 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
     const int h0 = b * NB;
     const int nb = min(NB, nsel[p] - h0);
     for (int q = threadIdx.x; q < nb * pps; q += blockDim.x) {
-      int h = q / pps, rem = q - h * pps;
+      int h = (int)__umulhi((unsigned)q, pps_m), rem = q - h * pps;
       int l = ls[h0 + h];
       const zdf* src;
       zdf* dst;
       if (rem < n2k * 6) {
         int bcol = rem / 6, part = rem - bcol * 6;
         src = Pdf + (size_t)toy[l] + (size_t)bcol * M + tly[l] * 6 + part;
-        dst = sPy + (((size_t)buf * NB + h) * 6 + part) * NRP + bcol;
+        dst = sPy + (((size_t)buf * NB + h) * 6 + part) * NRP + ((bcol & 1) ? k : 0) + (bcol >> 1);
       } else if (rem < 2 * n2k * 6) {
         rem -= n2k * 6;
         int bcol = rem / 6, part = rem - bcol * 6;
         src = Pdf + (size_t)tox[l] + (size_t)bcol * M + tlx[l] * 6 + part;
-        dst = sPx + (((size_t)buf * NB + h) * 6 + part) * NRP + bcol;
+        dst = sPx + (((size_t)buf * NB + h) * 6 + part) * NRP + ((bcol & 1) ? k : 0) + (bcol >> 1);
       } else {
         int part = rem - 2 * n2k * 6;
         src = Ldf + ((size_t)mu * V + tx[l]) * 9 + part;
@@ -306,9 +310,9 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
         for (int u = 0; u < 2; ++u) {
           const int bcol = 2 * q + u;
           const int beta = bcol >= k;
-          // component q' of this column at this site: P*[q' * NRP]
-          const zdf* Py = py + (size_t)h * 6 * NRP + bcol;
-          const zdf* Px = px + (size_t)h * 6 * NRP + bcol;
+          // component q' of this column at this site: P*[q' * NRP] (slot u k + q)
+          const zdf* Py = py + (size_t)h * 6 * NRP + u * k + q;
+          const zdf* Px = px + (size_t)h * 6 * NRP + u * k + q;
           zdf hv[3];
 #pragma unroll
           for (int c2 = 0; c2 < 3; ++c2) {
