@@ -12,6 +12,7 @@
 //   update   : Phi_s = A V_k (= U_k Sigma_k, Eq. 7), or U_k = A V_k Sigma_k^{-1} at the end
 // An optional second pass (G of A V over all c columns, eig, rotate) restores the
 // accuracy lost by forming A^dag A (its rotations are relative to sigma_i sigma_j).
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -55,33 +56,43 @@ constexpr int MAXC = 64;  // max columns per tile
 
 // G = A^dag A, upper triangle computed, mirrored.  DF: df64 arithmetic (FP32 units,
 // error-free transformations) instead of FP64.  MAXP: column pairs per thread
-// (>= c (c + 1) / 2 / GT), which sets the accumulator registers.
+// (>= pairs / blockDim), which sets the accumulator registers.
+// The first kd columns may be known to be orthogonal with squared norms lamp[t][0..kd-1]
+// (the previous stream's Phi = A V_k, whose Gram matrix is V_k^dag G V_k = Lambda_k): their
+// block is then written as that diagonal and only the pairs (i, j), i <= j, j >= kd are summed.
 template <bool DF, int MAXP>
 __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const void* __restrict__ tiles, int cmax,
-                                                  int c, int M) {
+                                                  int c, int M, int kd, const double* lamp,
+                                                  int cprev) {
   typedef typename std::conditional<DF, zdf, zd>::type T;
   typedef typename std::conditional<DF, zdfacc, zd>::type TA;
   extern __shared__ zd smraw_g[];
   T* sA = reinterpret_cast<T*>(smraw_g);  // [GR][c]
   int t = blockIdx.x;
   const T* A = reinterpret_cast<const T*>(tiles) + (size_t)t * cmax * M;
-  int npairs = c * (c + 1) / 2;
+  const int nth = blockDim.x;
+  const int npairs = c * (c + 1) / 2 - kd * (kd + 1) / 2;
   TA acc[MAXP];
   int pi[MAXP], pj[MAXP];
 #pragma unroll
   for (int q = 0; q < MAXP; ++q) {
     acc[q] = TA{};
-    int p = threadIdx.x + q * GT;
-    // p -> (i, j) with i <= j, row-major over the upper triangle
-    int i = 0, rem = p;
-    while (i < c && rem >= c - i) { rem -= c - i; ++i; }
-    pi[q] = i;
-    pj[q] = i + rem;
+    int p = threadIdx.x + q * nth;
+    // p -> (i, j) with i <= j and j >= kd, column by column (column j holds j + 1 pairs)
+    int j = kd, rem = p;
+    while (j < c && rem >= j + 1) { rem -= j + 1; ++j; }
+    pi[q] = rem;
+    pj[q] = j;
+  }
+  zd* Gt = G + (size_t)t * c * c;
+  for (int e = threadIdx.x; e < kd * kd; e += nth) {
+    const int i = e / kd, j = e % kd;
+    Gt[i * c + j] = i == j ? zd{lamp[(size_t)t * cprev + i], 0.0} : zd{0.0, 0.0};
   }
   for (int r0 = 0; r0 < M; r0 += GR) {
     int nr = min(GR, M - r0);
     __syncthreads();
-    for (int e = threadIdx.x; e < nr * c; e += GT) {
+    for (int e = threadIdx.x; e < nr * c; e += nth) {
       int col = e / nr, rr = e % nr;
       if constexpr (DF) sA[rr * c + col] = zdf_ld(A + (size_t)col * M + r0 + rr);
       else sA[rr * c + col] = A[(size_t)col * M + r0 + rr];
@@ -89,7 +100,7 @@ __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const void* __restrict_
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < MAXP; ++q) {
-      int p = threadIdx.x + q * GT;
+      int p = threadIdx.x + q * nth;
       if (p < npairs) {
         TA a = acc[q];
         for (int rr = 0; rr < nr; ++rr) {
@@ -100,10 +111,9 @@ __global__ void __launch_bounds__(GT) gram_kernel(zd* G, const void* __restrict_
       }
     }
   }
-  zd* Gt = G + (size_t)t * c * c;
 #pragma unroll
   for (int q = 0; q < MAXP; ++q) {
-    int p = threadIdx.x + q * GT;
+    int p = threadIdx.x + q * nth;
     if (p < npairs) {
       zd v;
       if constexpr (DF) v = zdf_result(acc[q]);
@@ -529,7 +539,6 @@ __global__ void __launch_bounds__(GT) ls_weights_kernel(zd* W, const zd* __restr
   zd* Bm = lsm;                  // [k][2k]: B | I, reduced to I | B^-1
   zd* fc = Bm + (size_t)k * 2 * k;   // [k] the pivot column's factors of one elimination step
   __shared__ int piv;
-  __shared__ double pmax;
   const int t = blockIdx.x, w2 = 2 * k;
   const zd* V = Vec + (size_t)t * c * c;   // V[row * c + i]
   for (int e = threadIdx.x; e < k * w2; e += blockDim.x) {
@@ -552,7 +561,6 @@ __global__ void __launch_bounds__(GT) ls_weights_kernel(zd* W, const zd* __restr
         if (v > m) { m = v; p = r; }
       }
       piv = p;
-      pmax = m;
     }
     __syncthreads();
     if (piv != col)
@@ -629,23 +637,31 @@ template int chiral_gather<float>(void*, int, int, const zf*, int, const Blockin
 template int chiral_gather<double>(void*, int, int, const zd*, int, const Blocking&, cudaStream_t, bool);
 
 int tile_gram(zd* G, const void* tiles, int cmax, int c, const Blocking& B, cudaStream_t st,
-              bool df64) {
+              bool df64, int kd, const double* lam_prev, int c_prev) {
   if (c > MAXC) return fail(MG_EINVAL, "tile_gram: more than 64 columns");
+  if (kd < 0 || kd > c || (kd > 0 && (!lam_prev || c_prev < kd)))
+    return fail(MG_EINVAL, "tile_gram: bad known-diagonal block");
   size_t sh = sizeof(zd) * GR * c;
+  const int npairs = c * (c + 1) / 2 - kd * (kd + 1) / 2;
+  // one thread per summed pair where they fit one CTA (whole warps, at least two)
+  const int nth = npairs >= GT ? GT : std::max(64, (npairs + 31) / 32 * 32);
   ProfScope ps(df64 ? "svd_gram_df64" : "svd_gram_fp64", 16.0 * B.M * c * B.d * 2,
-               8.0 * B.M * c * (c + 1) / 2 * B.d * 2, st);
-  int np = (c * (c + 1) / 2 + GT - 1) / GT;
+               8.0 * B.M * npairs * B.d * 2, st);
+  int np = (npairs + nth - 1) / nth;
+#define WMG_GRAM(DFV, MP) \
+  gram_kernel<DFV, MP><<<B.d * 2, nth, sh, st>>>(G, tiles, cmax, c, B.M, kd, lam_prev, c_prev)
   if (df64) {
-    if (np <= 1) gram_kernel<true, 1><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
-    else if (np <= 2) gram_kernel<true, 2><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
-    else if (np <= 4) gram_kernel<true, 4><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
-    else gram_kernel<true, 9><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+    if (np <= 1) WMG_GRAM(true, 1);
+    else if (np <= 2) WMG_GRAM(true, 2);
+    else if (np <= 4) WMG_GRAM(true, 4);
+    else WMG_GRAM(true, 9);
   } else {
-    if (np <= 1) gram_kernel<false, 1><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
-    else if (np <= 2) gram_kernel<false, 2><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
-    else if (np <= 4) gram_kernel<false, 4><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
-    else gram_kernel<false, 9><<<B.d * 2, GT, sh, st>>>(G, tiles, cmax, c, B.M);
+    if (np <= 1) WMG_GRAM(false, 1);
+    else if (np <= 2) WMG_GRAM(false, 2);
+    else if (np <= 4) WMG_GRAM(false, 4);
+    else WMG_GRAM(false, 9);
   }
+#undef WMG_GRAM
   WMG_LAUNCHED();
   return MG_OK;
 }

@@ -272,8 +272,11 @@ template <typename R>
 int chiral_gather(void* tiles, int cmax, int col0, const cplx<R>* fields, int nvec,
                   const Blocking& B, cudaStream_t st, bool df64 = false);
 // G[t][c][c] = A_t^dag A_t over the first c columns (df64: double-float tiles and sums).
+// kd > 0: the first kd columns are the previous stream's Phi = A V_k, orthogonal with squared
+// norms lam_prev[t][0..kd-1] (row stride c_prev): that block is written as the diagonal and
+// only the pairs with a column j >= kd are summed.
 int tile_gram(zd* G, const void* tiles, int cmax, int c, const Blocking& B, cudaStream_t st,
-              bool df64 = false);
+              bool df64 = false, int kd = 0, const double* lam_prev = nullptr, int c_prev = 0);
 // Hermitian eigen-decomposition of every G_t (c x c) by parallel cyclic Jacobi; returns
 // eigenvalues descending in lam[t][c] and eigenvectors in Vec[t][c][c] (column i at
 // Vec[t][*][i], row-major c x c).

@@ -296,13 +296,20 @@ int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr,
   const bool df = p.fp64_emulation > 0 || (p.fp64_emulation < 0 && sizeof(R) == 4);
   // rotate only above the accuracy of the Gram sums (FP64 ~1e-16, double-float ~1e-14)
   const double eig_tol = df ? 1e-13 : 1e-15;
+  const bool refine = p.svd_refine > 0 || (p.svd_refine < 0 && sizeof(R) == 8);
+  int c_prev = 0;
   for (int s = 0; s < p.n_s; ++s) {
     STEP(smooth_stream<R>(h, psi, phi, tmp, gm, s, st, src));
     STEP(chiral_gather<R>(cur, cmax, kk, psi, r, h->B, st, df));
     int c = kk + r;
     int kn = c < k ? c : k;
     bool last = s == p.n_s - 1;
-    STEP(tile_gram(G, cur, cmax, c, h->B, st, df));
+    // single-pass route: the kept columns Phi_{s-1} = A_{s-1} V_k are orthogonal with squared
+    // norms lam (Phi^dag Phi = V_k^dag G V_k = Lambda_k, to the Jacobi tolerance and the
+    // update's c-term rounding), so only their cross products with the new vectors and the new
+    // vectors' own Gram block are summed (the second pass of the refined route recomputes all)
+    const int kd = refine ? 0 : kk;
+    STEP(tile_gram(G, cur, cmax, c, h->B, st, df, kd, lam, c_prev));
     STEP(tile_eig(lam, Vec, G, c, (int)ntile, st, eig_tol, df));
     if (ls_omega) {
       // P = A W with W = Omega V_k B^-1 Sigma_k^-1 (Eq. 9); G is free after the eigensolver
@@ -321,6 +328,7 @@ int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr,
     }
     STEP(tile_sigma(h->hist + (size_t)s * ntile * k, k, lam, c, kn, (int)ntile, st));
     kk = kn;
+    c_prev = c;
   }
   STEP(tile_canonical_phase(cur, cmax, k, h->B, st, df));
   if (df) {

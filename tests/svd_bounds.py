@@ -24,6 +24,13 @@ bound is pinned on the CPU against a plain Gram-route emulation in tests/test_sv
 Unit roundoffs: FP64 sums 2^-53; double-float sums (an unevaluated sum of two floats with
 error-free products and sums) 2^-48.
 
+The single-pass route (double-float) does not sum the Gram block of the kept columns
+Phi_{s-1} = A_{s-1} V_k: it takes it as the diagonal of the previous stream's eigenvalues,
+Phi^dag Phi = V_k^dag G V_k = Lambda_k.  That block is then off by the Jacobi residual (pairs
+are left unrotated below tol sqrt(G_aa G_bb), tol = 1e-13) and by the rounding of Phi's
+c-term sums, both below gamma_M ||A||_F^2 for c << M (c = 20, M = 1536 on the timed
+workload), so the same bound holds.
+
 For test vectors that themselves carry a relative error delta (the FP32 smoother against the
 FP64 one), the tile moves by ||dA||_F <= delta ||A||_F and the same reasoning gives
     || dPi || <= C_v delta sum_t ||A_t||_F sigma_1,t / g_t,   | d sigma | <= C_v delta sum_t ||A_t||_F

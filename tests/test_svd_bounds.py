@@ -12,10 +12,14 @@ from oracle import icsvd
 import svd_bounds
 
 
-def gram_route(stream_tiles, k, gram_dtype):
-    """Algorithm 3 through the Gram matrix, as the library runs it (single pass)."""
+def gram_route(stream_tiles, k, gram_dtype, known_diag=False):
+    """Algorithm 3 through the Gram matrix, as the library runs it (single pass).  known_diag:
+    the Gram block of the kept columns Phi = A V_k is taken as the previous stream's
+    eigenvalues (Phi^dag Phi = Lambda_k) instead of being summed, as the double-float route
+    does."""
     d, _, rows, _ = stream_tiles[0].shape
     Phi = [[np.zeros((rows, 0), dtype=np.complex128) for _ in range(2)] for _ in range(d)]
+    lam_prev = [[None, None] for _ in range(d)]
     hist, P = [], None
     for s, T in enumerate(stream_tiles):
         last = s == len(stream_tiles) - 1
@@ -28,9 +32,13 @@ def gram_route(stream_tiles, k, gram_dtype):
                 A = np.concatenate([Phi[j][a], T[j, a]], axis=1)
                 Al = A.astype(gram_dtype)
                 G = (Al.conj().T @ Al).astype(np.complex128)
+                kd = Phi[j][a].shape[1]
+                if known_diag and kd:
+                    G[:kd, :kd] = np.diag(lam_prev[j][a])
                 lam, V = np.linalg.eigh(G)
                 order = np.argsort(-lam, kind="stable")[:kk]
                 lam, V = lam[order], V[:, order]
+                lam_prev[j][a] = lam
                 sig[j, a] = np.sqrt(np.maximum(lam, 0))
                 B = A @ V
                 if last:
@@ -52,13 +60,14 @@ def graded_tiles(d, rows, r, n_s, decades, seed):
     return out
 
 
+@pytest.mark.parametrize("known_diag", [False, True])
 @pytest.mark.parametrize("gram_dtype,u", [(np.complex128, svd_bounds.U64),
                                           (np.complex64, 2.0 ** -24)])
 @pytest.mark.parametrize("decades", [0.0, 2.0, 4.0])
-def test_gram_route_within_bound(gram_dtype, u, decades):
+def test_gram_route_within_bound(gram_dtype, u, decades, known_diag):
     k, r, n_s = 6, 5, 3
     tiles = graded_tiles(6, 48, r, n_s, decades, 11)
-    P, hist = gram_route(tiles, k, gram_dtype)
+    P, hist = gram_route(tiles, k, gram_dtype, known_diag)
     Pt, S_o, hist_o = icsvd.icsvd_tiles(tiles, k)
     spectra = svd_bounds.stream_spectra(tiles, k)
     bounds = svd_bounds.arithmetic_bounds(spectra, u, 48)
