@@ -194,7 +194,10 @@ class Hierarchy:
     def solve(self, b, tol=1e-10, maxiter=1000, adjoint=False, x=None):
         nrhs = b.numel() // (self.V * 12)
         if x is None:
-            x = torch.empty_like(b)
+            # a host solution follows the pinning of the host right-hand side, so that the
+            # library's device-to-host copy of x runs at the pinned rate
+            pin = (not b.is_cuda) and b.is_pinned()
+            x = torch.empty(b.shape, dtype=b.dtype, device=b.device, pin_memory=pin)
         info = L.MgSolveInfo()
         fn = L.lib().mg_solve_adjoint if adjoint else L.lib().mg_solve
         L.check(fn(self._h, _ptr(x), _ptr(b), int(nrhs), float(tol), int(maxiter),
