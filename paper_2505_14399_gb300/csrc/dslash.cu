@@ -276,7 +276,18 @@ __global__ void su3_deviation_kernel(unsigned long long* out, const zd* __restri
     worst = fmax(worst, sqrt(det.re * det.re + det.im * det.im));
   }
   if (!(worst == worst)) worst = 1e300;   // NaN: not SU(3)
-  atomicMax(out, (unsigned long long)__double_as_longlong(worst));
+  // warp, then CTA maximum: one atomic per CTA (a single address taking one atomic per
+  // thread serialises them)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  __shared__ double wmax[32];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = worst;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = wmax[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  }
 }
 }  // namespace
 

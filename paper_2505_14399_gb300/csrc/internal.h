@@ -349,6 +349,13 @@ template <typename E>
 int eo_split(E* even, E* odd, const E* full, const Geom& g, int nrhs, cudaStream_t st);
 template <typename E>
 int eo_join(E* full, const E* even, const E* odd, const Geom& g, int nrhs, cudaStream_t st);
+// full += join(even, odd) (complex double / float fields)
+template <typename E>
+int eo_join_add(E* full, const E* even, const E* odd, const Geom& g, int nrhs, cudaStream_t st);
+// (even, odd) = split(a - b) of full fields (complex double / float fields)
+template <typename E>
+int eo_split_diff(E* even, E* odd, const E* a, const E* b, const Geom& g, int nrhs,
+                  cudaStream_t st);
 // out = D_hat in = (1 - kappa^2 H_eo H_oe) in on even fields (dagger: D_hat^dag); tmp: odd
 // field per rhs; links in `layout` (dslash_launch)
 template <typename E>

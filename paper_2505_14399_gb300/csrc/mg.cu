@@ -499,9 +499,11 @@ int post_smooth_half(mg_handle* h, GmresV<H>& gm, zf* z, const zf* v, zf* kw, in
 // Post-smoother on the even-odd Schur system (even-odd preconditioning, Sec. 1): with the
 // residual r = v - D z split into r_e, r_o,
 //   r_hat = r_e + kappa H_eo r_o,  e_e = GMRES_post(D_hat, r_hat),  e_o = r_o + kappa H_oe e_e,
-// and z += (e_e, e_o).  (D e)_o = r_o holds exactly for any number of steps.
+// and z += (e_e, e_o).  (D e)_o = r_o holds exactly for any number of steps.  The residual is
+// formed and split by parity in one pass after the stencil, and the accumulation of (e_e, e_o)
+// into z is one pass.
 template <typename R>
-int post_smooth_schur(mg_handle* h, cplx<R>* z, const cplx<R>* r, int nrhs, cudaStream_t st) {
+int post_smooth_schur(mg_handle* h, cplx<R>* z, const cplx<R>* v, int nrhs, cudaStream_t st) {
   const Geom& g = h->g;
   const size_t nh = h->nf / 2;
   cplx<R>* re = static_cast<cplx<R>*>(h->sbuf[0]);
@@ -512,7 +514,10 @@ int post_smooth_schur(mg_handle* h, cplx<R>* z, const cplx<R>* r, int nrhs, cuda
   const void* L = Lvl<R>::links(h);
   const int lay = Lvl<R>::layout(h);
   const int dt = Lvl<R>::dtype;
-  WMG_TRY(eo_split<cplx<R>>(re, ro, r, g, nrhs, st));
+  // (r_e, r_o) = split(v - D z)
+  cplx<R>* kw = Lvl<R>::kw(h);
+  WMG_TRY(fine_op<R>(h, nrhs)(kw, z, st));
+  WMG_TRY(eo_split_diff<cplx<R>>(re, ro, v, kw, g, nrhs, st));
   WMG_TRY(dslash_launch(dt, rh, ro, L, g, 0, 0, nrhs, st, nh, nh, lay, re));   // r_hat
   Op<R> Dhat = [h, to, L, lay, nrhs](cplx<R>* out, const cplx<R>* in, cudaStream_t s2) -> int {
     return schur_apply<cplx<R>>(out, in, to, L, lay, h->g, 0, nrhs, s2);
@@ -521,9 +526,7 @@ int post_smooth_schur(mg_handle* h, cplx<R>* z, const cplx<R>* r, int nrhs, cuda
   WMG_TRY(Lvl<R>::posts(h).fixed(Dhat, xe, rh, h->p.post_smooth, st, false,
                                  sizeof(R) == 4 && !h->clov32 ? &fz : nullptr));
   WMG_TRY(dslash_launch(dt, to, xe, L, g, 1, 0, nrhs, st, nh, nh, lay, ro));   // e_o
-  cplx<R>* ke = Lvl<R>::ke(h);
-  WMG_TRY(eo_join<cplx<R>>(ke, xe, to, g, nrhs, st));
-  WMG_TRY(axpby<R>(z, 1.0, ke, 1.0, h->nf * nrhs, 1, st));                // z += e
+  WMG_TRY(eo_join_add<cplx<R>>(z, xe, to, g, nrhs, st));                  // z += (x_e, e_o)
   return MG_OK;
 }
 
@@ -632,6 +635,8 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
     h->kcycles += 1;
     WMG_TRY(prolong_launch<R>(z, ec, Lvl<R>::P(h), h->k, h->B, nrhs, st));
     if (p.post_smooth > 0) {
+      // the Schur form (Wilson, FP64 / FP32 storage) forms its residual itself
+      if (p.schur_smoother) return post_smooth_schur<R>(h, z, v, nrhs, st);
       Op<R> D = fine_op<R>(h, nrhs);
       WMG_TRY(D(kw, z, st));
       if constexpr (std::is_same<R, float>::value) {
@@ -639,7 +644,6 @@ Op<R> kcycle_op(mg_handle* h, int nrhs) {
         if (p.solve_dtype == MG_BF16) return post_smooth_half<zbf>(h, h->postb, z, v, kw, nrhs, st);
       }
       WMG_TRY(axpby<R>(kw, 1.0, v, -1.0, h->nf * nrhs, 1, st));   // kw = v - D z
-      if (p.schur_smoother) return post_smooth_schur<R>(h, z, kw, nrhs, st);
       FusedStencil fz{h->links32L, h->g, h->llay};   // FP32 Wilson runs fuse the stencil with the projections
       WMG_TRY(Lvl<R>::post(h).fixed(D, ke, kw, p.post_smooth, st, false,
                                     sizeof(R) == 4 && !h->clov32 ? &fz : nullptr));

@@ -62,6 +62,41 @@ __global__ void eo_join_kernel(E* __restrict__ full, const E* __restrict__ even,
   }
 }
 
+// even[rhs][i] = (a - b)[rhs][eo_site(i, 0)], odd[rhs][i] = (a - b)[rhs][eo_site(i, 1)]
+template <typename E>
+__global__ void eo_split_diff_kernel(E* __restrict__ even, E* __restrict__ odd,
+                                     const E* __restrict__ a, const E* __restrict__ b, Dims4 d,
+                                     int Vh, int nrhs) {
+  size_t total = (size_t)nrhs * Vh * 12;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t rhs = e / ((size_t)Vh * 12), rem = e % ((size_t)Vh * 12);
+    int i = (int)(rem / 12), c = (int)(rem % 12);
+    size_t fb = rhs * (size_t)Vh * 24;
+    const size_t se = fb + (size_t)eo_site(d.L, i, 0) * 12 + c;
+    const size_t so = fb + (size_t)eo_site(d.L, i, 1) * 12 + c;
+    even[e] = a[se] - b[se];
+    odd[e] = a[so] - b[so];
+  }
+}
+
+// full[rhs][eo_site(i, 0)] += even[rhs][i], full[rhs][eo_site(i, 1)] += odd[rhs][i]
+template <typename E>
+__global__ void eo_join_add_kernel(E* __restrict__ full, const E* __restrict__ even,
+                                   const E* __restrict__ odd, Dims4 d, int Vh, int nrhs) {
+  size_t total = (size_t)nrhs * Vh * 12;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    size_t rhs = e / ((size_t)Vh * 12), rem = e % ((size_t)Vh * 12);
+    int i = (int)(rem / 12), c = (int)(rem % 12);
+    size_t fb = rhs * (size_t)Vh * 24;
+    E* pe = full + fb + (size_t)eo_site(d.L, i, 0) * 12 + c;
+    E* po = full + fb + (size_t)eo_site(d.L, i, 1) * 12 + c;
+    *pe = *pe + even[e];
+    *po = *po + odd[e];
+  }
+}
+
 unsigned grid_for(size_t n) {
   size_t g = (n + 255) / 256, cap = (size_t)num_sms() * 16;
   return (unsigned)(g < cap ? (g < 1 ? 1 : g) : cap);
@@ -83,6 +118,27 @@ int eo_join(E* full, const E* even, const E* odd, const Geom& g, int nrhs, cudaS
   Dims4 d{{g.L[0], g.L[1], g.L[2], g.L[3]}};
   int Vh = g.V / 2;
   eo_join_kernel<E><<<grid_for((size_t)nrhs * Vh * 12), 256, 0, st>>>(full, even, odd, d, Vh, nrhs);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+template <typename E>
+int eo_join_add(E* full, const E* even, const E* odd, const Geom& g, int nrhs, cudaStream_t st) {
+  Dims4 d{{g.L[0], g.L[1], g.L[2], g.L[3]}};
+  int Vh = g.V / 2;
+  eo_join_add_kernel<E><<<grid_for((size_t)nrhs * Vh * 12), 256, 0, st>>>(full, even, odd, d, Vh,
+                                                                         nrhs);
+  WMG_LAUNCHED();
+  return MG_OK;
+}
+
+template <typename E>
+int eo_split_diff(E* even, E* odd, const E* a, const E* b, const Geom& g, int nrhs,
+                  cudaStream_t st) {
+  Dims4 d{{g.L[0], g.L[1], g.L[2], g.L[3]}};
+  int Vh = g.V / 2;
+  eo_split_diff_kernel<E><<<grid_for((size_t)nrhs * Vh * 12), 256, 0, st>>>(even, odd, a, b, d,
+                                                                           Vh, nrhs);
   WMG_LAUNCHED();
   return MG_OK;
 }
@@ -111,6 +167,10 @@ int schur_apply(E* out, const E* in, E* tmp, const void* links, int layout, cons
 INST_EO(zd)
 INST_EO(zf)
 INST_EO(zh)
+template int eo_join_add<zd>(zd*, const zd*, const zd*, const Geom&, int, cudaStream_t);
+template int eo_join_add<zf>(zf*, const zf*, const zf*, const Geom&, int, cudaStream_t);
+template int eo_split_diff<zd>(zd*, zd*, const zd*, const zd*, const Geom&, int, cudaStream_t);
+template int eo_split_diff<zf>(zf*, zf*, const zf*, const zf*, const Geom&, int, cudaStream_t);
 INST_EO(zbf)
 
 }  // namespace wmg
