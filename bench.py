@@ -626,6 +626,7 @@ def gpu_arm(args):
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(cfg, U, b, info_64["outer"])[0]
+            line["cpu_baseline"]["full_steps_small"] = small_full_steps(api, synthetic, dev, step)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -691,6 +692,46 @@ def cpu_baseline(cfg, U, b, outer_fallback):
                                      "host_cores": rec["host_cores"], "info": rec["info"],
                                      "parts_s": rec["parts_s"]}
     return out, s
+
+
+def small_full_steps(api, synthetic, dev, step):
+    """The two small workloads (4^4 and 8^4) end to end on both sides: the GPU's mixed step
+    (setup + Galerkin + solve, the timed configuration's smoother) and the FP64 oracle's whole
+    step (oracle.full_step, one process per available core), each with its own iteration
+    counts."""
+    import torch
+    from oracle import full_step
+    workers = len(os.sched_getaffinity(0))
+    out = {"cores": workers}
+    for name in ("c1_4^4_haar", "c5_8^4_autograd"):
+        c = dict(synthetic.WORKLOADS[name])
+        c["kappa"] = synthetic.kappa_of(c)
+        Uc = synthetic.make_links(c)
+        bc_ = synthetic.gaussian_rhs(c["dims"], c["rhs_seed"])
+        p = api.params(c["dims"], c["block"], c["kappa"], c["k"], c["r"], c["n_s"], c["sweeps"],
+                       c["tv_seed"], c["hop_weight"], c["bc"], setup_dtype="c64",
+                       solve_dtype="c64", schur_smoother=int(SCHUR_SMOOTHER))
+        Ud = torch.from_numpy(Uc).to(dev)
+        bd = torch.from_numpy(bc_).to(dev)
+        step(p, Ud, bd)   # warm-up
+        ts = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = step(p, Ud, bd)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        info_o, parts = full_step.full_step(Uc, bc_[0], c, c["kappa"], workers,
+                                            schur=SCHUR_SMOOTHER)
+        t_o = float(sum(parts.values()))
+        out[name] = {"gpu_mixed_seconds": float(np.median(ts)), "gpu_outer": info["outer"],
+                     "oracle_seconds": t_o, "oracle_parts_s": parts,
+                     "oracle_outer": info_o["outer"],
+                     "oracle_over_gpu": t_o / float(np.median(ts))}
+    return out
 
 
 def reference_arm(args):
