@@ -883,8 +883,11 @@ int GmresV<E>::solve(const OpV<E>& A, const OpV<E>* M, E* x, const E* b, double 
     return true;
   };
   if (all_done(res.data())) converged = true;
+  bool first = true;
   while (!converged && its < maxiter) {
-    WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, rvec, n, nrhs, rw, st, ip_scale()));
+    // the first cycle's residual is b itself, whose norms are already in dnorm + nrhs
+    if (!first) WMG_TRY(norm2_v<E>(dnorm + nrhs, 1, rvec, n, nrhs, rw, st, ip_scale()));
+    first = false;
     WMG_LAUNCH_DEP(init_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, dnorm + nrhs, dnorm + 2 * nrhs, nrhs);
     WMG_TRY(scale_inv_v<E>(V, rvec, dnorm + nrhs, 1, n, nrhs, st));
     int steps = 0, checked = 0;

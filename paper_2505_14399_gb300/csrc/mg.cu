@@ -695,13 +695,17 @@ int solve_impl(mg_handle* h, zd* x, const zd* b, int nrhs, double tol, int maxit
     double inner = p.inner_tol > 0 ? p.inner_tol : 1e-5;
     status = MG_ENOCONV;
     while (outer < maxiter && refinements < 100) {
-      WMG_TRY(norm2<double>(h->dscal, 1, h->r64, h->nf, nrhs, h->rw, st));
-      WMG_CUDA(cudaMemcpyAsync(h->hscal, h->dscal, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
-      WMG_CUDA(cudaStreamSynchronize(st));
+      // the first pass's residual is b (x = 0): its norms are bn, already in dscal
+      if (refinements > 0) {
+        WMG_TRY(norm2<double>(h->dscal, 1, h->r64, h->nf, nrhs, h->rw, st));
+        WMG_CUDA(cudaMemcpyAsync(h->hscal, h->dscal, nrhs * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+        WMG_CUDA(cudaStreamSynchronize(st));
+      }
       bool done = true;
       double worst = 0;
       for (int r = 0; r < nrhs; ++r) {
-        rn[r] = h->hscal[r];
+        rn[r] = refinements > 0 ? h->hscal[r] : bn[r];
         if (!std::isfinite(rn[r])) return fail(MG_ENAN, "mg_solve: non-finite residual");
         done &= rn[r] <= tol * bn[r];
         worst = std::fmax(worst, rn[r] / (bn[r] > 0 ? bn[r] : 1));
