@@ -162,11 +162,11 @@ class GmresV {
   int alloc(size_t n, int nrhs, int m, bool flexible);
   void release();
   // x = argmin ||b - A x|| over K_m(A, b), x0 = 0 (fixed number of steps, no host sync);
-  // accumulate: x += that minimiser instead (x holds the caller's vector on entry)
+  // accumulate: x += xsign * that minimiser instead (x holds the caller's vector on entry)
   // fused: A is this FP32 fine stencil, applied by one kernel together with each step's
   // projection sweep (complex-float bases only; otherwise ignored)
   int fixed(const OpV<E>& A, E* x, const E* b, int m, cudaStream_t st, bool accumulate = false,
-            const FusedStencil* fused = nullptr);
+            const FusedStencil* fused = nullptr, double xsign = 1.0);
   // Restarted (F)GMRES from x0 = 0 until ||b - A x|| <= rtol ||b|| for every rhs.
   // M == nullptr: plain GMRES.  Returns MG_OK or MG_ENOCONV; *its = iterations.
   // check_every: host convergence check interval in Arnoldi steps; steps taken past

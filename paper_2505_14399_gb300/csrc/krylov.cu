@@ -832,7 +832,7 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
 
 template <typename E>
 int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t st,
-                     bool accumulate, const FusedStencil* fused) {
+                     bool accumulate, const FusedStencil* fused, double xsign) {
   if (steps > m) return fail(MG_EINVAL, "gmres: more steps than allocated");
   SmallLayout L{m};
   size_t fs = n * nrhs;
@@ -853,7 +853,7 @@ int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t 
   for (int j = 0; j < steps; ++j)
     WMG_TRY(arnoldi_step(A, nullptr, j, st, true, fused, fuse0 && j == 0 ? b : nullptr));
   WMG_LAUNCH_DEP(solve_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, steps, nrhs);
-  WMG_TRY(multi_axpy_v<E>(x, V, fs, steps, small + L.y(), L.stride(), 1.0, n, nrhs, st));
+  WMG_TRY(multi_axpy_v<E>(x, V, fs, steps, small + L.y(), L.stride(), xsign, n, nrhs, st));
   return MG_OK;
 }
 

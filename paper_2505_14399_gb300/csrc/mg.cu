@@ -218,28 +218,27 @@ struct SetupSource {
   int smooth;
 };
 
-// b = -D phi ; psi = phi + GMRES_sweeps(D, b)   (Eq. 2) for r fields, in precision R; phi is
-// the stream's Philox field, or the caller's fields when src is given
+// psi = phi + GMRES_sweeps(D, -D phi)   (Eq. 2) for r fields, in precision R; phi is the
+// stream's Philox field, or the caller's fields when src is given.  phi goes straight into
+// psi, and the sum is formed as psi -= GMRES_sweeps(D, D phi): GMRES is odd in its right-hand
+// side (negating b negates every basis vector and the minimiser, exactly), so neither -D phi
+// nor the sum is a pass of its own.  tmp: r fields of scratch.
 template <typename R>
-int smooth_stream(mg_handle* h, cplx<R>* psi, cplx<R>* phi, cplx<R>* tmp, Gmres<R>& gm, int s,
+int smooth_stream(mg_handle* h, cplx<R>* psi, cplx<R>* tmp, Gmres<R>& gm, int s,
                   cudaStream_t st, const SetupSource* src = nullptr) {
   const mg_params& p = h->p;
   int r = p.r;
   if (src) {
     size_t off = (size_t)s * r * h->nf;
     if (src->dtype == MG_C128)
-      WMG_TRY((convert<R, double>(phi, static_cast<const zd*>(src->fields) + off, nullptr, 0,
+      WMG_TRY((convert<R, double>(psi, static_cast<const zd*>(src->fields) + off, nullptr, 0,
                                   h->nf * r, 1, st)));
     else
-      WMG_TRY((convert<R, float>(phi, static_cast<const zf*>(src->fields) + off, nullptr, 0,
+      WMG_TRY((convert<R, float>(psi, static_cast<const zf*>(src->fields) + off, nullptr, 0,
                                  h->nf * r, 1, st)));
-    if (!src->smooth) {
-      WMG_CUDA(cudaMemcpyAsync(psi, phi, h->nf * r * sizeof(cplx<R>), cudaMemcpyDeviceToDevice,
-                               st));
-      return MG_OK;
-    }
+    if (!src->smooth) return MG_OK;
   } else {
-    WMG_TRY(gaussian_fill<R>(phi, p.seed, (unsigned)(s * r), r, h->g.V, st));
+    WMG_TRY(gaussian_fill<R>(psi, p.seed, (unsigned)(s * r), r, h->g.V, st));
   }
   int dt = sizeof(R) == 8 ? MG_C128 : MG_C64;
   const void* L = sizeof(R) == 8 ? (const void*)h->links64L : (const void*)h->links32L;
@@ -250,12 +249,11 @@ int smooth_stream(mg_handle* h, cplx<R>* psi, cplx<R>* phi, cplx<R>* tmp, Gmres<
     if (Cl) WMG_TRY(clover_add<R>(out, in, Cl, h->g.V, r, s2));
     return MG_OK;
   };
-  WMG_TRY(D(tmp, phi, st));
-  WMG_TRY(axpby<R>(tmp, 0.0, tmp, -1.0, h->nf * r, 1, st));   // tmp = -D phi
+  WMG_TRY(D(tmp, psi, st));   // tmp = D phi
   WMG_TRY(gm.alloc(h->nf, r, p.sweeps > 0 ? p.sweeps : 1, false));
   FusedStencil fz{h->links32L, h->g, h->llay};   // FP32 Wilson runs fuse the stencil with the projections
-  WMG_TRY(gm.fixed(D, psi, tmp, p.sweeps, st, false, sizeof(R) == 4 && !Cl ? &fz : nullptr));
-  WMG_TRY(axpby<R>(psi, 1.0, phi, 1.0, h->nf * r, 1, st));     // psi = phi + psi'
+  WMG_TRY(gm.fixed(D, psi, tmp, p.sweeps, st, true, sizeof(R) == 4 && !Cl ? &fz : nullptr,
+                   -1.0));   // psi = phi - GMRES(D, D phi)
   return MG_OK;
 }
 
@@ -270,18 +268,17 @@ int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr,
   size_t ntile = (size_t)h->B.d * 2;
   size_t M = h->B.M;
   size_t fr = h->nf * r;
-  cplx<R>*phi = nullptr, *psi = nullptr, *tmp = nullptr;
+  cplx<R>*psi = nullptr, *tmp = nullptr;
   zd *T0 = nullptr, *T1 = nullptr, *G = nullptr, *Vec = nullptr;
   double* lam = nullptr;
   Gmres<R> gm;
   int status = MG_OK;
   auto cleanup = [&]() {
     cudaStreamSynchronize(st);   // the cached blocks are reused only after their work ends
-    dfree(phi); dfree(psi); dfree(tmp); dfree(T0); dfree(T1); dfree(G); dfree(Vec); dfree(lam);
+    dfree(psi); dfree(tmp); dfree(T0); dfree(T1); dfree(G); dfree(Vec); dfree(lam);
   };
 #define STEP(x) do { status = (x); if (status != MG_OK) { cleanup(); return status; } } while (0)
 #define CSTEP(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { cleanup(); return fail(e_ == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); } } while (0)
-  STEP(dev_alloc(&phi, fr * sizeof(cplx<R>)));
   STEP(dev_alloc(&psi, fr * sizeof(cplx<R>)));
   STEP(dev_alloc(&tmp, fr * sizeof(cplx<R>)));
   STEP(dev_alloc(&T0, ntile * cmax * M * sizeof(zd)));
@@ -299,7 +296,7 @@ int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr,
   const bool refine = p.svd_refine > 0 || (p.svd_refine < 0 && sizeof(R) == 8);
   int c_prev = 0;
   for (int s = 0; s < p.n_s; ++s) {
-    STEP(smooth_stream<R>(h, psi, phi, tmp, gm, s, st, src));
+    STEP(smooth_stream<R>(h, psi, tmp, gm, s, st, src));
     STEP(chiral_gather<R>(cur, cmax, kk, psi, r, h->B, st, df));
     int c = kk + r;
     int kn = c < k ? c : k;
@@ -1148,25 +1145,21 @@ extern "C" int mg_test_vectors(void* out, const void* links, const mg_params* p,
   Staged so;
   WMG_TRY(stage_out_alloc(so, out, fr * sizeof(zd), st));
   if (p->setup_dtype == MG_C128) {
-    zd *phi, *tmp;
-    WMG_CUDA(cudaMallocAsync(&phi, fr * sizeof(zd), st));
+    zd* tmp;
     WMG_CUDA(cudaMallocAsync(&tmp, fr * sizeof(zd), st));
     Gmres<double> gm;
-    int s = smooth_stream<double>(h, (zd*)so.dev, phi, tmp, gm, stream_index, st);
+    int s = smooth_stream<double>(h, (zd*)so.dev, tmp, gm, stream_index, st);
     cudaStreamSynchronize(st);
-    cudaFreeAsync(phi, st);
     cudaFreeAsync(tmp, st);
     WMG_TRY(s);
   } else {
-    zf *phi, *tmp, *psi;
-    WMG_CUDA(cudaMallocAsync(&phi, fr * sizeof(zf), st));
+    zf *tmp, *psi;
     WMG_CUDA(cudaMallocAsync(&tmp, fr * sizeof(zf), st));
     WMG_CUDA(cudaMallocAsync(&psi, fr * sizeof(zf), st));
     Gmres<float> gm;
-    int s = smooth_stream<float>(h, psi, phi, tmp, gm, stream_index, st);
+    int s = smooth_stream<float>(h, psi, tmp, gm, stream_index, st);
     if (s == MG_OK) s = convert<double, float>((zd*)so.dev, psi, nullptr, 0, fr, 1, st);
     cudaStreamSynchronize(st);
-    cudaFreeAsync(phi, st);
     cudaFreeAsync(tmp, st);
     cudaFreeAsync(psi, st);
     WMG_TRY(s);
