@@ -132,7 +132,7 @@ NCU_TRAFFIC = {("galerkin_tc", "c2_16^3x32_near_critical"): 1.5912e9,
 
 def kernel_bound(name, alu, peaks, peak_kind):
     """(bound, peak, unit, source) of a library kernel, by the arithmetic it runs on."""
-    if name.startswith("svd_jacobi") or name == "coarse_gmres":
+    if name.startswith("svd_jacobi") or name in ("coarse_gmres", "cgs_givens"):
         # data-dependent sweep / iteration counts and grid barriers: no fixed algorithmic
         # flop or byte count per launch, so no roofline fraction
         return "latency", None, "TFLOP/s", "none"

@@ -179,10 +179,12 @@ class GmresV {
   bool flexible = false;
 
  private:
-  // b0 (fused first step only): the unscaled right-hand side, scaled and written as v_0 there
+  // b0 (fused first step only): the unscaled right-hand side, scaled and written as v_0 there;
+  // next = false: column j + 1 of the basis is not needed (the last step of a fixed run), so
+  // only the Givens step of column j runs, not the normalised update
   int arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st,
                    bool single_pass = false, const FusedStencil* fused = nullptr,
-                   const E* b0 = nullptr);
+                   const E* b0 = nullptr, bool next = true);
   double ip_scale() const { return VecT<E>::rms ? 1.0 / (double)n : 1.0; }
   E* V = nullptr;         // (m+1) x nrhs x n
   E* Z = nullptr;         // m x nrhs x n

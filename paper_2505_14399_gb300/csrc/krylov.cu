@@ -780,7 +780,8 @@ void GmresV<E>::release() {
 // dnorm layout: [0..nrhs) current ||w||, [nrhs..2nrhs) beta, [2nrhs..3nrhs) residual estimate
 template <typename E>
 int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_t st,
-                            bool single_pass, const FusedStencil* fused, const E* b0) {
+                            bool single_pass, const FusedStencil* fused, const E* b0,
+                            bool next) {
   SmallLayout L{m};
   size_t fs = n * nrhs;
   E* vj = V + (size_t)j * fs;
@@ -819,6 +820,14 @@ int GmresV<E>::arnoldi_step(const OpV<E>& A, const OpV<E>* M, int j, cudaStream_
     ProfScope ps("cgs_update_dot", (j + 3) * fb, (16.0 * (j + 1) + 4.0) * n * nrhs, st);
     WMG_LAUNCH_DEP(cgs_update_dot_kernel<E>, dim3(nb, nrhs), RT, 0, st, w, V, fs, j + 1, small, L, j, n, dnorm, reshist, rw.partial, rw.counter, nb, rw.maxvec, ip_scale());
   }
+  if (!next) {
+    // the Givens step of column j alone (the last CTA of the update kernel)
+    ProfScope ps("cgs_givens", 0.0, 0.0, st);
+    WMG_LAUNCH_DEP(cgs_update_scale_kernel<E>, dim3(1, nrhs), 256, 0, st,
+                   V + (size_t)(j + 1) * fs, w, V, fs, j + 1, small, L, dnorm, n, reshist,
+                   single_pass && streamed ? 1 : 0);
+    return MG_OK;
+  }
   {
   ProfScope ps("cgs_update_scale", (j + 3) * fb, (8.0 * (j + 1) + 2.0) * n * nrhs, st);
   size_t g = (n / 2 + 255) / 256;
@@ -850,8 +859,10 @@ int GmresV<E>::fixed(const OpV<E>& A, E* x, const E* b, int steps, cudaStream_t 
   // Pythagoras.  Over these few steps the basis stays orthogonal to ~eps_32 times the
   // conditioning of the small Krylov basis, which leaves the smoother's approximate
   // minimisation unchanged to FP32 rounding; the tolerance-driven solves keep CGS2.
+  // the last step needs its Hessenberg column and Givens step, not the next basis column
   for (int j = 0; j < steps; ++j)
-    WMG_TRY(arnoldi_step(A, nullptr, j, st, true, fused, fuse0 && j == 0 ? b : nullptr));
+    WMG_TRY(arnoldi_step(A, nullptr, j, st, true, fused, fuse0 && j == 0 ? b : nullptr,
+                         j + 1 < steps));
   WMG_LAUNCH_DEP(solve_kernel, (nrhs + 31) / 32, 32, 0, st, small, L, steps, nrhs);
   WMG_TRY(multi_axpy_v<E>(x, V, fs, steps, small + L.y(), L.stride(), xsign, n, nrhs, st));
   return MG_OK;
