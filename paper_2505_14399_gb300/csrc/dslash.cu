@@ -291,12 +291,83 @@ __global__ void su3_deviation_kernel(unsigned long long* out, const zd* __restri
 }
 }  // namespace
 
+// The same on a double-float copy of the links, in double-float arithmetic on the FP32 units
+// (error-free products and sums, ~2^-48 relative: deviations are resolved far below 1e-9).
+__global__ void su3_deviation_df_kernel(unsigned long long* out, const zdf* __restrict__ L,
+                                        size_t n) {
+  float worst = 0.f;
+  for (size_t l = (size_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (size_t)gridDim.x * blockDim.x) {
+    zdf u[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) u[i] = L[l * 9 + i];
+    // U U^dag - 1: the six entries a <= b of the Hermitian matrix
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b) {
+        zdfacc s{};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) zdf_fmac(s, u[b * 3 + c], u[a * 3 + c]);   // u_ac conj(u_bc)
+        zdf v = zdf_norm(s);
+        if (a == b) v.re = df_add(v.re, {-1.0f, 0.0f});
+        worst = fmaxf(worst, fmaxf(fabsf(v.re.hi), fabsf(v.im.hi)));
+      }
+    // det U - 1 by cofactors of the first row
+    zdfacc t{};
+    zdf_fma(t, u[4], u[8]);
+    zdf_fma(t, zdf_neg(u[5]), u[7]);
+    const zdf c0 = zdf_norm(t);
+    t = zdfacc{};
+    zdf_fma(t, u[3], u[8]);
+    zdf_fma(t, zdf_neg(u[5]), u[6]);
+    const zdf c1 = zdf_norm(t);
+    t = zdfacc{};
+    zdf_fma(t, u[3], u[7]);
+    zdf_fma(t, zdf_neg(u[4]), u[6]);
+    const zdf c2 = zdf_norm(t);
+    t = zdfacc{};
+    zdf_fma(t, u[0], c0);
+    zdf_fma(t, zdf_neg(u[1]), c1);
+    zdf_fma(t, u[2], c2);
+    zdf det = zdf_norm(t);
+    det.re = df_add(det.re, {-1.0f, 0.0f});
+    worst = fmaxf(worst, sqrtf(det.re.hi * det.re.hi + det.im.hi * det.im.hi));
+  }
+  if (!(worst == worst)) worst = 3e38f;   // NaN: not SU(3)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  __shared__ float wmax[32];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = worst;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = wmax[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+    atomicMax(out, (unsigned long long)__double_as_longlong((double)m));
+  }
+}
+
 int su3_deviation(double* dev_out, const zd* links, size_t nlinks, cudaStream_t st) {
   unsigned long long* d = nullptr;
   WMG_CUDA(cudaMallocAsync(&d, sizeof(*d), st));
   WMG_CUDA(cudaMemsetAsync(d, 0, sizeof(*d), st));
   size_t g = (nlinks + 255) / 256, cap = (size_t)num_sms() * 8;
   su3_deviation_kernel<<<(unsigned)(g < cap ? (g < 1 ? 1 : g) : cap), 256, 0, st>>>(d, links, nlinks);
+  WMG_LAUNCHED();
+  unsigned long long bits = 0;
+  WMG_CUDA(cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, st));
+  WMG_CUDA(cudaStreamSynchronize(st));
+  cudaFreeAsync(d, st);
+  std::memcpy(dev_out, &bits, sizeof(double));
+  return MG_OK;
+}
+
+int su3_deviation_df(double* dev_out, const zdf* links, size_t nlinks, cudaStream_t st) {
+  unsigned long long* d = nullptr;
+  WMG_CUDA(cudaMallocAsync(&d, sizeof(*d), st));
+  WMG_CUDA(cudaMemsetAsync(d, 0, sizeof(*d), st));
+  size_t g = (nlinks + 255) / 256, cap = (size_t)num_sms() * 8;
+  su3_deviation_df_kernel<<<(unsigned)(g < cap ? (g < 1 ? 1 : g) : cap), 256, 0, st>>>(d, links, nlinks);
   WMG_LAUNCHED();
   unsigned long long bits = 0;
   WMG_CUDA(cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, st));

@@ -30,6 +30,8 @@ inline int link_to_lanes(cplx<To>* dst, const zd* src, int V, cudaStream_t st, i
 // *dev = the largest deviation of the nlinks 3x3 complex-double links from SU(3):
 // max(|U U^dag - 1|_max, |det U - 1|) (synchronises st).
 int su3_deviation(double* dev, const zd* links, size_t nlinks, cudaStream_t st);
+// the same from a double-float copy of the links, in double-float arithmetic
+int su3_deviation_df(double* dev, const zdf* links, size_t nlinks, cudaStream_t st);
 
 // Autotuned launch shape for a kernel with `nvar` candidate shapes; `run(v)` launches
 // shape v on the caller's arguments.  Returns the chosen shape or -1 on a CUDA error.

@@ -164,11 +164,18 @@ int create_handle(mg_handle** out, const void* links, const mg_params* p, bool n
   WMG_TRY(stage_in(sl, links, lb * sizeof(zd), st));
   WMG_CUDA(cudaMemcpyAsync(h->links64, sl.dev, lb * sizeof(zd), cudaMemcpyDeviceToDevice, st));
   WMG_TRY(link_to_lanes<double>(h->links64L, h->links64, h->g.V, st));
+  // the double-float copy of the links (double-float Galerkin sums) first: the SU(3) check
+  // below runs on it in double-float arithmetic instead of on the FP64 units
+  if (galerkin_df(*p)) {
+    WMG_TRY(dev_alloc(&h->Ldf, lb * sizeof(zdf)));
+    WMG_TRY(to_df(h->Ldf, h->links64, lb, st));
+  }
   // the FP32 / half stencil copies keep two rows per link when the links are SU(3)
   int rows = 3;
   if (p->link_compress != 0) {
     double dev = 0;
-    WMG_TRY(su3_deviation(&dev, h->links64, (size_t)4 * h->g.V, st));
+    if (h->Ldf) WMG_TRY(su3_deviation_df(&dev, h->Ldf, (size_t)4 * h->g.V, st));
+    else WMG_TRY(su3_deviation(&dev, h->links64, (size_t)4 * h->g.V, st));
     if (dev <= 1e-9) rows = 2;
     else if (p->link_compress > 0)
       return fail(MG_EINVAL, "link_compress = 1 needs SU(3) links (deviation " +
@@ -196,8 +203,6 @@ int create_handle(mg_handle** out, const void* links, const mg_params* p, bool n
   WMG_TRY(dev_alloc(&h->PtP, ntile * h->k * h->k * sizeof(zd)));
   if (galerkin_df(*p)) {
     WMG_TRY(dev_alloc(&h->Pdf, ntile * h->k * h->B.M * sizeof(zdf)));
-    WMG_TRY(dev_alloc(&h->Ldf, lb * sizeof(zdf)));
-    WMG_TRY(to_df(h->Ldf, h->links64, lb, st));
   }
   WMG_CUDA(cudaMemsetAsync(h->sigma, 0, ntile * h->k * sizeof(double), st));
   WMG_TRY(dev_alloc(&h->tc_flag, sizeof(int)));

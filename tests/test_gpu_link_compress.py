@@ -64,3 +64,17 @@ def test_auto_keeps_three_rows_for_non_su3_links():
     h = _handle(synthetic.haar_links(DIMS, 77), -1)
     assert L.lib().mg_link_rows(h._h) == 2
     h.close()
+
+
+@pytest.mark.parametrize("solve_dtype", ["c64", "c128"])   # double-float check / FP64 check
+def test_auto_threshold_resolves_1e9(solve_dtype):
+    """The automatic choice resolves deviations from SU(3) around its 1e-9 threshold: one link
+    scaled by 1 + 1e-8 (|U U^dag - 1| ~ 2e-8) keeps three rows, by 1 + 1e-11 two rows -- from
+    the double-float link copy (mixed forms) and from the FP64 links (FP64 form)."""
+    U = synthetic.haar_links(DIMS, 78)
+    for eps, rows in ((1e-8, 3), (1e-11, 2)):
+        Up = U.copy()
+        Up[0, 0] *= 1.0 + eps
+        h = _handle(Up, -1, solve_dtype)
+        assert L.lib().mg_link_rows(h._h) == rows, (eps, solve_dtype)
+        h.close()
