@@ -127,7 +127,7 @@ def load_peaks():
 # command on its workload, reported as roofline.traffic for that kernel; an entry is removed
 # whenever its kernel changes, until it is captured again.
 NCU_TRAFFIC = {("galerkin_tc", "c2_16^3x32_near_critical"): 1.5912e9,
-               ("cgs_update_scale", "c2_16^3x32_near_critical"): 95.26e6}
+               ("dslash_proj", "c2_16^3x32_near_critical"): 506.9e6}
 
 
 def kernel_bound(name, alu, peaks, peak_kind):
