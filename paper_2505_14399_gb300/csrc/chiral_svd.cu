@@ -461,7 +461,11 @@ __global__ void __launch_bounds__(GT) phase_kernel(zd* tiles, int cmax, int k, i
 // The same canonical phase on double-float tiles, in double-float arithmetic: the column sum
 // accumulated error-free on the FP32 units, q = conj(s) / |s| normalised by a Newton
 // reciprocal square root, each entry multiplied by q.
-__global__ void __launch_bounds__(GT) phase_df_kernel(zdf* tiles, int cmax, int k, int M) {
+// OUT: instead of writing the phased columns back, write them as the outputs P [tile][k][M]
+// in complex double, complex float (rounded) and, if Pdf is not null, double-float.
+template <bool OUT>
+__global__ void __launch_bounds__(GT) phase_df_kernel(zdf* tiles, int cmax, int k, int M, zd* P,
+                                                      zf* P32, zdf* Pdf) {
   __shared__ df sh[2][GT / 32];
   __shared__ zdf q;
   int t = blockIdx.x;
@@ -502,26 +506,19 @@ __global__ void __launch_bounds__(GT) phase_df_kernel(zdf* tiles, int cmax, int 
     }
     __syncthreads();
     zdf f = q;
+    const size_t o = ((size_t)t * k + i) * M;
     for (int r = threadIdx.x; r < M; r += blockDim.x) {
       zdf v = col[r];
-      col[r] = {df_dot2(v.re, f.re, df_neg(v.im), f.im), df_dot2(v.re, f.im, v.im, f.re)};
+      zdf w = {df_dot2(v.re, f.re, df_neg(v.im), f.im), df_dot2(v.re, f.im, v.im, f.re)};
+      if (OUT) {
+        P[o + r] = {df_val(w.re), df_val(w.im)};
+        P32[o + r] = {df_to_float(w.re), df_to_float(w.im)};
+        if (Pdf) Pdf[o + r] = w;
+      } else {
+        col[r] = w;
+      }
     }
     __syncthreads();
-  }
-}
-
-// First k columns of double-float tiles -> P (complex double), P32 (complex float, the
-// rounded value) and, when Pdf is given, the double-float copy; outputs [tile][k][M].
-__global__ void tile_outputs_kernel(zd* P, zf* P32, zdf* Pdf, const zdf* __restrict__ tiles,
-                                    int cmax, int k, int M, size_t total) {
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    size_t r = e % M, ti = e / M;
-    size_t t = ti / k, i = ti % k;
-    zdf v = zdf_ld(tiles + (t * cmax + i) * M + r);
-    P[e] = {df_val(v.re), df_val(v.im)};
-    P32[e] = {df_to_float(v.re), df_to_float(v.im)};
-    if (Pdf) Pdf[e] = v;
   }
 }
 
@@ -702,19 +699,15 @@ int tile_update(void* out, int cmax_out, const void* tiles, int cmax, int c, con
 
 int tile_canonical_phase(void* tiles, int cmax, int k, const Blocking& B, cudaStream_t st,
                          bool df64) {
-  if (df64) phase_df_kernel<<<B.d * 2, GT, 0, st>>>((zdf*)tiles, cmax, k, B.M);
+  if (df64) phase_df_kernel<false><<<B.d * 2, GT, 0, st>>>((zdf*)tiles, cmax, k, B.M, nullptr, nullptr, nullptr);
   else phase_kernel<<<B.d * 2, GT, 0, st>>>((zd*)tiles, cmax, k, B.M);
   WMG_LAUNCHED();
   return MG_OK;
 }
 
-int tile_outputs(zd* P, zf* P32, zdf* Pdf, const void* tiles, int cmax, int k, const Blocking& B,
-                 cudaStream_t st) {
-  size_t total = (size_t)B.d * 2 * k * B.M;
-  size_t g = (total + 255) / 256;
-  size_t cap = (size_t)num_sms() * 16;
-  tile_outputs_kernel<<<(unsigned)(g < cap ? g : cap), 256, 0, st>>>(
-      P, P32, Pdf, (const zdf*)tiles, cmax, k, B.M, total);
+int tile_phase_outputs(zd* P, zf* P32, zdf* Pdf, void* tiles, int cmax, int k,
+                       const Blocking& B, cudaStream_t st) {
+  phase_df_kernel<true><<<B.d * 2, GT, 0, st>>>((zdf*)tiles, cmax, k, B.M, P, P32, Pdf);
   WMG_LAUNCHED();
   return MG_OK;
 }

@@ -296,10 +296,11 @@ int tile_update(void* out, int cmax_out, const void* tiles, int cmax, int c, con
 // Multiply every column i < k of every tile by conj(q)/|q|, q = sum of its entries.
 int tile_canonical_phase(void* tiles, int cmax, int k, const Blocking& B, cudaStream_t st,
                          bool df64 = false);
-// The first k columns of double-float tiles as P [tile][k][M] in complex double, complex
-// float (rounded) and, if Pdf is not null, double-float.
-int tile_outputs(zd* P, zf* P32, zdf* Pdf, const void* tiles, int cmax, int k, const Blocking& B,
-                 cudaStream_t st);
+// For double-float tiles, the canonical phase of every column applied on the way to the
+// outputs: the first k columns as P [tile][k][M] in complex double, complex float (rounded)
+// and, if Pdf is not null, double-float (the tiles keep their unphased values).
+int tile_phase_outputs(zd* P, zf* P32, zdf* Pdf, void* tiles, int cmax, int k,
+                       const Blocking& B, cudaStream_t st);
 // Eq. 9 weights: W[t][row][i] = omega_row (V_k B^-1)[row][i] / sqrt(lam_i), B = V_k^dag Omega V_k,
 // so that A W is the least-squares interpolation prolongator (leading dimension c, i < k)
 int tile_ls_weights(zd* W, const zd* Vec, const double* lam, const double* omega, int c, int k,

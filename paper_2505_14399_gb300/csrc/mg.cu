@@ -332,13 +332,13 @@ int run_setup(mg_handle* h, cudaStream_t st, const SetupSource* src = nullptr,
     kk = kn;
     c_prev = c;
   }
-  STEP(tile_canonical_phase(cur, cmax, k, h->B, st, df));
   if (df) {
-    // double-float tiles: P, its FP32 copy and (for the double-float Galerkin) its
-    // double-float copy in one pass
-    STEP(tile_outputs(h->P64, h->P32, h->Pdf, cur, cmax, k, h->B, st));
+    // double-float tiles: the canonical phase, P, its FP32 copy and (for the double-float
+    // Galerkin) its double-float copy in one pass
+    STEP(tile_phase_outputs(h->P64, h->P32, h->Pdf, cur, cmax, k, h->B, st));
     h->pdf_ready = h->Pdf != nullptr;
   } else {
+    STEP(tile_canonical_phase(cur, cmax, k, h->B, st, df));
     CSTEP(cudaMemcpy2DAsync(h->P64, (size_t)k * M * sizeof(zd), cur, (size_t)cmax * M * sizeof(zd),
                             (size_t)k * M * sizeof(zd), ntile, cudaMemcpyDeviceToDevice, st));
     STEP((convert<float, double>(h->P32, h->P64, nullptr, 0, ntile * k * M, 1, st)));
