@@ -43,19 +43,35 @@ restrict_kernel(cplx<R>* vc, const cplx<R>* __restrict__ v, const cplx<R>* __res
     sv[row] = vr[(size_t)s * 12 + (2 * alpha + sp) * 3 + c];
   }
   __syncthreads();
+  // warp work items (column i, half h of the rows): 2k items spread evenly over the warps
+  // (k = 12: three per warp), each lane with two independent accumulators; the two halves of
+  // a column meet in shared memory
+  cplx<R>* sred = sv + B.M;   // [2k]
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const cplx<R>* Pt = P + (size_t)t * k * B.M;
-  for (int i = wid; i < k; i += nw) {
+  const int half_rows = (B.M + 1) / 2;
+  for (int it = wid; it < 2 * k; it += nw) {
+    const int i = it >> 1, r0 = (it & 1) * half_rows;
+    const int r1 = min(B.M, r0 + half_rows);
     const cplx<R>* col = Pt + (size_t)i * B.M;
-    cplx<R> acc = {0, 0};
-    for (int row = lane; row < B.M; row += 32) cfmac(acc, col[row], sv[row]);
+    cplx<R> a0 = {0, 0}, a1 = {0, 0};
+    int row = r0 + lane;
+    for (; row + 32 < r1; row += 64) {
+      cfmac(a0, col[row], sv[row]);
+      cfmac(a1, col[row + 32], sv[row + 32]);
+    }
+    for (; row < r1; row += 32) cfmac(a0, col[row], sv[row]);
+    a0 += a1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      acc.re += __shfl_down_sync(0xffffffffu, acc.re, o);
-      acc.im += __shfl_down_sync(0xffffffffu, acc.im, o);
+      a0.re += __shfl_down_sync(0xffffffffu, a0.re, o);
+      a0.im += __shfl_down_sync(0xffffffffu, a0.im, o);
     }
-    if (lane == 0) vc[(size_t)rhs * B.d * 2 * k + (size_t)t * k + i] = acc;
+    if (lane == 0) sred[it] = a0;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x)
+    vc[(size_t)rhs * B.d * 2 * k + (size_t)t * k + i] = sred[2 * i] + sred[2 * i + 1];
 }
 
 template <typename R>
@@ -351,7 +367,7 @@ template <typename R>
 int restrict_launch(cplx<R>* vc, const cplx<R>* v, const cplx<R>* P, int k, const Blocking& B,
                     int nrhs, cudaStream_t st) {
   dim3 grid(B.d * 2, nrhs);
-  size_t sh = sizeof(cplx<R>) * B.M;
+  size_t sh = sizeof(cplx<R>) * (B.M + 2 * k);   // v's aggregate rows, half-column sums
   if (sh > 200 * 1024) return fail(MG_EINVAL, "restrict: aggregate too large");
   WMG_TRY(smem_attr(restrict_kernel<R>, sh));
   ProfScope ps("restrict", (double)sizeof(cplx<R>) * (12.0 * B.nd * B.d * (k + nrhs) + 2.0 * B.d * k * nrhs),
