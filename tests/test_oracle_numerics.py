@@ -69,6 +69,22 @@ def test_gmres_minimises_over_krylov_space():
     assert np.abs(x - K @ y).max() < 1e-9 * np.abs(x).max()
 
 
+def test_gmres_fixed_is_odd_in_the_right_hand_side():
+    """GMRES_m(D, -b) = -GMRES_m(D, b) bit for bit (every Arnoldi quantity changes sign or
+    not at all, and sign changes are exact), so the test vectors of Eq. 2 equal
+    phi - GMRES_m(D, D phi) exactly: the form the library evaluates them in."""
+    dims = (4, 4, 4, 4)
+    U = synthetic.haar_links(dims, 31)
+    phi = synthetic.gaussian_rhs(dims, 32)[0].reshape(-1)
+    D = lambda v: wilson.dslash(v, U, dims, 0.125, (1, 1, 1, 1), (1, 1, 1, -1)).reshape(-1)
+    Dphi = D(phi)
+    for m in (1, 3, 5):
+        xp = krylov.gmres_fixed(D, Dphi, m)
+        xn = krylov.gmres_fixed(D, -Dphi, m)
+        assert np.array_equal(xn, -xp)
+        assert np.array_equal(phi + xn, phi - xp)
+
+
 def test_gmres_tol_and_fgmres():
     A, b = _rand_system(60, 4, shift=2.0)
     x, its, res = krylov.gmres_tol(lambda v: A @ v, b, 1e-10, 10, 500)
