@@ -8,9 +8,9 @@
 //
 // Persistence: with WMG_AUTOTUNE_CACHE=<file> the choices are also kept in that file, one JSON
 // object per line ({"device": ..., "dtype": ..., "parity": ..., "dagger": ..., "volume": ...,
-// "nrhs": ..., "variant": ..., "ms": ...}); the file is read once per process and every new
-// choice is appended, so later processes on the same kind of GPU skip the timing.  Entries of
-// other device names are ignored.
+// "nrhs": ..., "variant": ..., "ms": ..., "all_ms": [every candidate's time]}); the file is
+// read once per process and every new choice is appended, so later processes on the same
+// kind of GPU skip the timing.  Entries of other device names are ignored.
 #include <cstdio>
 #include <cstdlib>
 #include <map>
@@ -18,6 +18,7 @@
 #include <sstream>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -69,16 +70,18 @@ void load_cache_file() {
 }
 
 // caller holds g_mu
-void append_cache_file(const Key& k, int var, float ms) {
+void append_cache_file(const Key& k, int var, float ms, const std::vector<float>& all) {
   const char* path = std::getenv("WMG_AUTOTUNE_CACHE");
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
   std::fprintf(f,
                "{\"device\":\"%s\",\"dtype\":%d,\"parity\":%d,\"dagger\":%d,\"volume\":%d,"
-               "\"nrhs\":%d,\"variant\":%d,\"ms\":%.6g}\n",
+               "\"nrhs\":%d,\"variant\":%d,\"ms\":%.6g,\"all_ms\":[",
                device_name().c_str(), std::get<0>(k), std::get<1>(k), std::get<2>(k),
                std::get<3>(k), std::get<4>(k), var, ms);
+  for (size_t i = 0; i < all.size(); ++i) std::fprintf(f, i ? ",%.6g" : "%.6g", all[i]);
+  std::fprintf(f, "]}\n");
   std::fclose(f);
 }
 }  // namespace
@@ -110,6 +113,7 @@ int tuned_variant(int dtype, int parity, int dagger, int V, int nrhs, cudaStream
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1;
   int best = 0;
   float best_ms = 1e30f;
+  std::vector<float> all;
   for (int v = 0; v < nvar; ++v) {
     run(v);
     cudaEventRecord(e0, st);
@@ -123,6 +127,7 @@ int tuned_variant(int dtype, int parity, int dagger, int V, int nrhs, cudaStream
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     count_launch(4);
+    all.push_back(ms / 3.0f);
     if (ms < best_ms) {
       best_ms = ms;
       best = v;
@@ -132,7 +137,7 @@ int tuned_variant(int dtype, int parity, int dagger, int V, int nrhs, cudaStream
   cudaEventDestroy(e1);
   std::lock_guard<std::mutex> lk(g_mu);
   g_cache[key] = std::make_pair(best, best_ms / 3.0f);
-  append_cache_file(key, best, best_ms / 3.0f);
+  append_cache_file(key, best, best_ms / 3.0f, all);
   return best;
 }
 

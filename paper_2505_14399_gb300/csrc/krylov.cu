@@ -474,9 +474,9 @@ stream_cgs_kernel(zf* w, const zf* __restrict__ V, size_t vstride, int nv, size_
 // lane-contiguous links), h_i = V_i^dag w for i < nv = j + 1, ||w||^2, and in the last CTA
 // H[j+1, j]^2 = ||w||^2 - ||h||^2 as in stream_cgs_kernel<2>.  The basis reads at each
 // thread's own site do not depend on the stencil, so they overlap its latency-bound hops,
-// and w is not read back.  One thread per site and rhs row (blockIdx.y), a grid-stride
-// over BT-site blocks; BT and the register budget (MINB resident CTAs) are launch shapes the
-// autotuner picks per (columns, link layout, volume, rhs).
+// and w is not read back.  One thread per site and rhs row (blockIdx.y); BT and the register
+// budget (MINB resident CTAs) are launch shapes the autotuner picks per (columns, link
+// layout, volume, rhs).
 template <int NVM, bool FIRST, int LL, int BT, int MINB>
 __global__ void __launch_bounds__(BT, MINB)
 dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
@@ -507,7 +507,10 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
 #pragma unroll
   for (int q = 0; q < NVM; ++q) { ar[q] = 0.f; ai[q] = 0.f; }
   float ss = 0.f;
-  for (int site = blockIdx.x * BT + threadIdx.x; site < nsites; site += gridDim.x * BT) {
+  // one site per thread (the launcher sizes the grid to cover every site): with no loop the
+  // projection accumulators are not live across the stencil's hops, which need the registers
+  const int site = blockIdx.x * BT + threadIdx.x;
+  if (site < nsites) {
     int c[4];
     // site: the output index (lexicographic, or the checkerboard index with par); ls: the
     // lattice site the hops start from
@@ -576,10 +579,9 @@ dslash_proj_kernel(zf* w, zf* V, size_t vstride, int nv, size_t n,
 }
 
 // launch shapes of the fused kernel: threads per CTA and resident CTAs per SM asked of the
-// register allocator (register cap 64K / (BT MINB)): 256 x 2 and 128 x 4 (128 registers),
-// 128 x 5 (102).  (128 x 6, 85 registers, spilled 250-330 bytes per thread and doubled the
-// kernel's DRAM writes; it is not a candidate.)
-constexpr int kProjShapes = 3;
+// register allocator (register cap 64K / (BT MINB), allocated in steps of 8): 256 x 2 and
+// 128 x 4 (128 registers), 128 x 5 (96), 128 x 6 (80; spills 12-64 bytes per thread).
+constexpr int kProjShapes = 4;
 
 template <int NVM, bool FIRST, int LL, int BT, int MINB>
 void launch_proj_shape(int nv, int V, int nblk, int nrhs, cudaStream_t st, zf* w, zf* V_,
@@ -587,8 +589,7 @@ void launch_proj_shape(int nv, int V, int nblk, int nrhs, cudaStream_t st, zf* w
                        SmallLayout L, double* dnorm, ReduceWork& rw, const zf* b0,
                        const double* beta0, const zf* sin, int par, cudaError_t* err) {
   const int ns = par ? V / 2 : V;
-  int nb = (ns + BT - 1) / BT;
-  if (nb > nblk) nb = nblk;
+  const int nb = (ns + BT - 1) / BT;   // one site per thread; launch_proj checked nb <= nblk
   *err = launch_dep(dslash_proj_kernel<NVM, FIRST, LL, BT, MINB>, dim3(nb, nrhs), BT, 0, st, w,
                     V_, fs, nv, n, L32, kg, small, L, dnorm, rw.partial, rw.counter, rw.maxvec,
                     b0, beta0, sin, par);
@@ -602,6 +603,7 @@ void launch_proj_v(int v, int nv, int nrhs, cudaStream_t st, zf* w, zf* V_, size
   switch (v) {
     case 1: launch_proj_shape<NVM, FIRST, LL, 128, 4>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, err); break;
     case 2: launch_proj_shape<NVM, FIRST, LL, 128, 5>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, err); break;
+    case 3: launch_proj_shape<NVM, FIRST, LL, 128, 6>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, err); break;
     default: launch_proj_shape<NVM, FIRST, LL, 256, 2>(nv, kg.V, rw.cap, nrhs, st, w, V_, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, err); break;
   }
 }
@@ -612,6 +614,11 @@ int launch_proj(int nv, bool first, int nrhs, cudaStream_t st, zf* w, zf* V, siz
                 double* dnorm, ReduceWork& rw, const zf* b0, const double* beta0, const zf* sin,
                 int par) {
   const int nvm = first ? 0 : nv <= 4 ? 4 : nv <= 8 ? 8 : 16;
+  // every shape takes one site per thread, so its grid (at least 128 threads per CTA) must
+  // fit the partial slots of the reduction workspace
+  const int ns = par ? kg.V / 2 : kg.V;
+  if ((ns + 127) / 128 > rw.cap)
+    return fail(MG_EINVAL, "dslash_proj: reduction workspace holds too few CTA partials");
   cudaError_t err = cudaSuccess;
   auto run = [&](int v) {
     if (first) launch_proj_v<4, true, LL>(v, nv, nrhs, st, w, V, fs, n, L32, kg, small, L, dnorm, rw, b0, beta0, sin, par, &err);

@@ -41,6 +41,8 @@ def test_cache_file_round_trip(tmp_path):
     lines = [json.loads(l) for l in open(path)]
     assert len(lines) == 1 and lines[0]["volume"] == 8 ** 4 and lines[0]["nrhs"] == 1
     assert first["launches"] > 1                 # the shapes were timed, then the call launched
+    times = lines[0]["all_ms"]                   # every candidate's time, the winner the fastest
+    assert len(times) > 1 and times[lines[0]["variant"]] == min(times)
     second = _run(path)
     assert second["launches"] == 1               # read from the file: only the call itself
     assert second["report"][0]["variant"] == lines[0]["variant"] == first["report"][0]["variant"]

@@ -1,5 +1,5 @@
 """Every launch shape of the smoother's fused stencil + projection kernel (one thread per site
-at three register caps), forced one at a time through
+at four register caps), forced one at a time through
 WMG_DSLASH_VARIANT in a child process: the mixed-precision K-cycle solve with the post-smoother
 on the full system and on the even-odd Schur system reaches a true residual of 1e-10 against
 the oracle's operator, with the same outer iteration count (within one) for every shape."""
@@ -51,7 +51,7 @@ def _run(variant):
 
 
 def test_every_fused_shape_solves():
-    its = [_run(v) for v in range(3)]
+    its = [_run(v) for v in range(4)]
     for schur in ("0", "1"):
         counts = [d[schur] for d in its]
         assert max(counts) - min(counts) <= 1, (schur, counts)
