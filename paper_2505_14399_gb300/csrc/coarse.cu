@@ -448,17 +448,19 @@ int galerkin_build(zd* Op, zd* Xpart, const zd* P, zdf* Pdf, zd* PtP, int k, con
   // flops: the method's work, 768 k^2 FP64-equivalent flops per fine site (4 forward hops x
   // 6 rows x (2k)^2 complex multiply-adds); the tensor path also records the bf16 digit-plane
   // products it issues for them
-  const double tc_flops = tc ? galerkin_tc_issued_flops(k, B) : 0.0;
+  if (tc && !range_flag) return fail(MG_EINVAL, "galerkin: no range flag");
+  int tc_nb = 0;
+  if (tc) WMG_TRY(galerkin_tc_batch(&tc_nb, Op, Xpart, Pdf, k, Ldf, hg, B, range_flag, st));
+  const double tc_flops = tc ? galerkin_tc_issued_flops(k, B, tc_nb) : 0.0;
   ProfScope ps(tc ? "galerkin_tc" : df64 ? "galerkin_df64" : "galerkin_fp64",
                16.0 * (12.0 * B.nd * B.d * k * 5 + 36.0 * B.nd * B.d),
                768.0 * k * k * B.nd * B.d, tc ? tc_flops : 0.0, st);
   if (tc) {
     // tensor pipe (exact digit-plane products); entries outside its fixed-point range (links
     // that are not unitary, a prolongator that is not orthonormal) fall back to the FP32 units
-    if (!range_flag) return fail(MG_EINVAL, "galerkin: no range flag");
     int* flag = range_flag;
     WMG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
-    WMG_TRY(galerkin_hops_tc(Op, Xpart, Pdf, k, Ldf, hg, B, flag, st));
+    WMG_TRY(galerkin_hops_tc(Op, Xpart, Pdf, k, Ldf, hg, B, tc_nb, flag, st));
     int h_flag = 0;
     WMG_CUDA(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     WMG_CUDA(cudaStreamSynchronize(st));

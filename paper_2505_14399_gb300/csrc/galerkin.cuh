@@ -27,13 +27,19 @@ __device__ __forceinline__ zdf isigma_df(int mu, int s, zdf p0, zdf p1) {
 // Whether the tensor-pipe forward-hop kernel handles this k and blocking (2k <= 48, its
 // shared memory fits one CTA).
 bool galerkin_tc_supported(int k, const Blocking& B);
-// bf16 flops that kernel issues for one build (its digit-plane products, padding included).
-double galerkin_tc_issued_flops(int k, const Blocking& B);
+// bf16 flops that kernel issues for one build at nb sites per batch (its digit-plane
+// products, padding included).
+double galerkin_tc_issued_flops(int k, const Blocking& B, int nb);
+// Sites per staging batch of the tensor-pipe kernel for this build (8 or 4; autotuned where
+// both fit, which runs the kernel on these arguments).
+int galerkin_tc_batch(int* nb, zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf,
+                      const HopGeom& g, const Blocking& B, int* range_flag, cudaStream_t st);
 // The forward-hop blocks of the double-float Galerkin build on the tensor pipe (same outputs
-// as the FP32-unit kernel: Y_+mu blocks into Op, in-aggregate partials into Xpart).  Raises
-// *range_flag (device int) if a staged entry is outside the fixed-point range (|v| >= 2 or not
-// finite), in which case the caller rebuilds with the FP32-unit kernel.
+// as the FP32-unit kernel: Y_+mu blocks into Op, in-aggregate partials into Xpart), nb sites
+// per staging batch.  Raises *range_flag (device int) if a staged entry is outside the
+// fixed-point range (|v| >= 2 or not finite), in which case the caller rebuilds with the
+// FP32-unit kernel.
 int galerkin_hops_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
-                     const Blocking& B, int* range_flag, cudaStream_t st);
+                     const Blocking& B, int nb, int* range_flag, cudaStream_t st);
 
 }  // namespace wmg

@@ -43,10 +43,11 @@ namespace {
 
 constexpr int TC_MAXT4 = 6;            // 2k <= 48
 
-// Per column-tile count T4 (2k <= 8 T4): sites per batch, stacked rows, warp groups, warps.
-template <int T4>
+// Per column-tile count T4 (2k <= 8 T4) and sites per batch NB_ (8 or 4): stacked rows, warp
+// groups, warps.
+template <int T4, int NB_>
 struct TcCfg {
-  static constexpr int NB = T4 <= 3 ? 8 : 4;           // fine sites staged per batch
+  static constexpr int NB = NB_;                       // fine sites staged per batch
   static constexpr int KB = NB * 6;                    // staged rows per batch
   static constexpr int K = 2 * KB;                     // stacked real rows (96 or 48)
   static constexpr int WG = (K / 16) % 2 == 0 ? 2 : 1; // warp groups (each takes k' steps)
@@ -55,14 +56,16 @@ struct TcCfg {
   static constexpr int MAXW = WG == 2 ? 12 : 16;
   static constexpr int TPW = (NTILES + MAXW - 1) / MAXW;   // tiles per warp
   static constexpr int NW = (NTILES + TPW - 1) / TPW;
+  // resident CTAs per SM asked of the register allocator: two for 4-site batches of 2k <= 24
+  // (about 100 KB of shared memory each), whose staging and products then overlap
+  static constexpr int MINB = (NB == 4 && T4 <= 3) ? 2 : 1;
 };
 
 // Row strides (bf16) of the k'-major digit planes: odd multiples of 8 (16 bytes).
 __host__ __device__ constexpr int tc_lda(int t4) { return 16 * t4 + 8; }
 __host__ __device__ constexpr int tc_ldb(int t4) { return 8 * t4 + ((t4 & 1) ? 0 : 8); }
-__host__ __device__ constexpr int tc_nb(int t4) { return t4 <= 3 ? 8 : 4; }
-__host__ __device__ constexpr size_t tc_smem(int t4) {
-  return sizeof(__nv_bfloat16) * (size_t)TC_NS * 12 * tc_nb(t4) * (tc_lda(t4) + tc_ldb(t4));
+__host__ __device__ constexpr size_t tc_smem(int t4, int nb) {
+  return sizeof(__nv_bfloat16) * (size_t)TC_NS * 12 * nb * (tc_lda(t4) + tc_ldb(t4));
 }
 
 
@@ -73,16 +76,19 @@ __host__ __device__ constexpr size_t tc_smem(int t4) {
 // sits in slot (b odd ? k : 0) + b / 2, so that the staging threads, which take the column
 // pairs (2q, 2q + 1) for consecutive q, read consecutive 16-byte slots.
 __host__ __device__ constexpr int tc_nrp(int t4) { return 8 * t4 + 1; }
-__host__ __device__ constexpr size_t tc_raw_bytes(int t4) {
-  return sizeof(zdf) * 2 * ((size_t)2 * tc_nb(t4) * 6 * tc_nrp(t4) + tc_nb(t4) * 9);
+__host__ __device__ constexpr size_t tc_raw_bytes(int t4, int nb) {
+  return sizeof(zdf) * 2 * ((size_t)2 * nb * 6 * tc_nrp(t4) + nb * 9);
 }
 __host__ __device__ inline size_t tc_table_bytes(int nd) { return sizeof(int) * 8 * (size_t)nd + 16; }
-
-template <int T4>
-__global__ void __launch_bounds__(32 * TcCfg<T4>::WG * TcCfg<T4>::NW, 1)
+__host__ __device__ inline size_t tc_cta_bytes(int t4, int nb, int nd) {
+  return tc_smem(t4, nb) + tc_raw_bytes(t4, nb) + tc_table_bytes(nd);
+}
+template <int T4, int NB_>
+__global__ void __launch_bounds__(32 * TcCfg<T4, NB_>::WG * TcCfg<T4, NB_>::NW,
+                                  TcCfg<T4, NB_>::MINB)
 galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
                    const zdf* __restrict__ Ldf, HopGeom g, Blocking B, int* range_flag) {
-  using C = TcCfg<T4>;
+  using C = TcCfg<T4, NB_>;
   constexpr int NR = 8 * T4;                  // columns a (>= 2k)
   constexpr int NTILES = C::NTILES;
   constexpr int NW = C::NW;
@@ -94,11 +100,11 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
   __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(tc_raw);   // [NS][K][LDA]
   __nv_bfloat16* SB = SA + (size_t)TC_NS * K * LDA;                // [NS][K][LDB]
   constexpr int NRP = tc_nrp(T4);
-  zdf* sPy = reinterpret_cast<zdf*>(tc_raw + tc_smem(T4));         // [2][NB][6][NRP]
+  zdf* sPy = reinterpret_cast<zdf*>(tc_raw + tc_smem(T4, NB));     // [2][NB][6][NRP]
   zdf* sPx = sPy + (size_t)2 * NB * 6 * NRP;                       // [2][NB][6][NRP]
   zdf* sU = sPx + (size_t)2 * NB * 6 * NRP;                        // [2][NB][9]
   const int nd = B.nd;
-  int* tx = reinterpret_cast<int*>(tc_raw + tc_smem(T4) + tc_raw_bytes(T4));   // site x
+  int* tx = reinterpret_cast<int*>(tc_raw + tc_smem(T4, NB) + tc_raw_bytes(T4, NB));   // site x
   int* toy = tx + nd;      // P offset of (2 j(y)) k M, y = x + mu
   int* tox = toy + nd;     // P offset of (2 j(x)) k M
   int* tly = tox + nd;     // local site of y, x
@@ -114,7 +120,7 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
   const size_t V = (size_t)B.nd * B.d;
   const int lane = threadIdx.x & 31;
   const int wid = (threadIdx.x >> 5) % NW, grp = (threadIdx.x >> 5) / NW;   // tile slot, k' half
-  const size_t plane16 = tc_smem(T4) / 16;   // 16-byte chunks of SA + SB
+  const size_t plane16 = tc_smem(T4, NB) / 16;   // 16-byte chunks of SA + SB
   bool bad = false;
 
   // ---- per-site tables of this aggregate, and the two passes' site lists
@@ -372,48 +378,86 @@ galerkin_tc_kernel(zd* Op, zd* Xpart, const zdf* __restrict__ Pdf, int k,
   if (bad) atomicExch(range_flag, 1);
 }
 
-template <int T4>
+template <int T4, int NB>
 int launch_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
               const Blocking& B, int* range_flag, cudaStream_t st) {
-  constexpr int NW = TcCfg<T4>::NW * TcCfg<T4>::WG;
-  size_t sh = tc_smem(T4) + tc_raw_bytes(T4) + tc_table_bytes(B.nd);
-  WMG_TRY(smem_attr(galerkin_tc_kernel<T4>, sh));
-  galerkin_tc_kernel<T4><<<dim3(B.d, 4), 32 * NW, sh, st>>>(Op, Xpart, Pdf, k, Ldf, g, B,
-                                                            range_flag);
+  constexpr int NW = TcCfg<T4, NB>::NW * TcCfg<T4, NB>::WG;
+  size_t sh = tc_cta_bytes(T4, NB, B.nd);
+  WMG_TRY(smem_attr(galerkin_tc_kernel<T4, NB>, sh));
+  if (TcCfg<T4, NB>::MINB > 1)   // room for two CTAs: the largest shared-memory carveout
+    WMG_CUDA(cudaFuncSetAttribute(galerkin_tc_kernel<T4, NB>,
+                                  cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
+  galerkin_tc_kernel<T4, NB><<<dim3(B.d, 4), 32 * NW, sh, st>>>(Op, Xpart, Pdf, k, Ldf, g, B,
+                                                                range_flag);
   WMG_LAUNCHED();
   return MG_OK;
 }
+
+constexpr size_t kTcSmemMax = (size_t)227 * 1024 - 1024;
 
 }  // namespace
 
 bool galerkin_tc_supported(int k, const Blocking& B) {
   if (k < 1 || (k + 3) / 4 > TC_MAXT4) return false;
-  // shared memory of one CTA, and tile offsets that fit an int
+  // shared memory of one CTA at 4 sites per batch, and tile offsets that fit an int
   const int t4 = (k + 3) / 4;
-  size_t sh = tc_smem(t4) + tc_raw_bytes(t4) + tc_table_bytes(B.nd);
-  return sh <= (size_t)227 * 1024 - 1024 && (size_t)B.d * 2 * k * B.M < ((size_t)1 << 31);
+  return tc_cta_bytes(t4, 4, B.nd) <= kTcSmemMax &&
+         (size_t)B.d * 2 * k * B.M < ((size_t)1 << 31);
 }
 
-double galerkin_tc_issued_flops(int k, const Blocking& B) {
+double galerkin_tc_issued_flops(int k, const Blocking& B, int nb) {
   // bf16 digit-plane products issued: 28 digit pairs of a (16 T4) x (8 T4) x (12 NB) real
   // product per batch and hop direction, about n_d / NB + 1 batches per CTA
   const int t4 = (k + 3) / 4;
-  const double nb = tc_nb(t4);
   return 2.0 * (16.0 * t4) * (8.0 * t4) * (12.0 * nb) * 28.0 * 4.0 * B.d *
          ((double)B.nd / nb + 1.0);
 }
 
 int galerkin_hops_tc(zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf, const HopGeom& g,
-                     const Blocking& B, int* range_flag, cudaStream_t st) {
+                     const Blocking& B, int nb, int* range_flag, cudaStream_t st) {
+  if (nb == 8) {
+    switch ((k + 3) / 4) {
+      case 1: return launch_tc<1, 8>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+      case 2: return launch_tc<2, 8>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+      case 3: return launch_tc<3, 8>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+      default: return fail(MG_EINVAL, "galerkin (tensor pipe): 8-site batches need 2k <= 24");
+    }
+  }
+  if (nb != 4) return fail(MG_EINVAL, "galerkin (tensor pipe): batches of 4 or 8 sites");
   switch ((k + 3) / 4) {
-    case 1: return launch_tc<1>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    case 2: return launch_tc<2>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    case 3: return launch_tc<3>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    case 4: return launch_tc<4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    case 5: return launch_tc<5>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
-    case 6: return launch_tc<6>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 1: return launch_tc<1, 4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 2: return launch_tc<2, 4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 3: return launch_tc<3, 4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 4: return launch_tc<4, 4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 5: return launch_tc<5, 4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
+    case 6: return launch_tc<6, 4>(Op, Xpart, Pdf, k, Ldf, g, B, range_flag, st);
     default: return fail(MG_EINVAL, "galerkin (tensor pipe): 2k > 48");
   }
+}
+
+int galerkin_tc_batch(int* nb, zd* Op, zd* Xpart, const zdf* Pdf, int k, const zdf* Ldf,
+                      const HopGeom& g, const Blocking& B, int* range_flag, cudaStream_t st) {
+  // 8-site batches (one CTA per SM: the staging and the products of a CTA alternate) or
+  // 4-site batches (two CTAs per SM whose phases overlap, twice the per-batch folds): the
+  // autotuner times both on the live arguments where both fit (2k <= 24); the kernel is
+  // idempotent (it rewrites its outputs from inputs it does not modify; the range flag, which
+  // the caller clears before its own launch, can only be raised)
+  const int t4 = (k + 3) / 4;
+  if (t4 > 3 || tc_cta_bytes(t4, 8, B.nd) > kTcSmemMax) {
+    *nb = 4;
+    return MG_OK;
+  }
+  int err = MG_OK;
+  auto run = [&](int v) {
+    int e = galerkin_hops_tc(Op, Xpart, Pdf, k, Ldf, g, B, v == 0 ? 8 : 4, range_flag, st);
+    if (e != MG_OK) err = e;
+  };
+  int v = tuned_variant(2000 + t4, -3, 0, B.d * B.nd, k, st, 2, run);
+  if (err != MG_OK) return err;
+  if (v < 0) return fail(MG_ECUDA, "galerkin (tensor pipe): autotune failed");
+  *nb = v == 0 ? 8 : 4;
+  return MG_OK;
 }
 
 }  // namespace wmg

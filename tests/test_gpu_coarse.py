@@ -77,6 +77,42 @@ def test_galerkin_tensor_pipe_contraction(dims, block, k):
     h.close()
 
 
+BATCH_CHILD = r"""
+import json, sys
+import numpy as np
+sys.path.insert(0, "tests")
+from gpu_common import orthonormal_tiles, rel
+from test_gpu_coarse import _handle, CASES
+from oracle import coarse
+out = []
+for dims, block, k in CASES:
+    h, U, Pt, (kappa, w, bc) = _handle(dims, block, k, 9, fp64_emulation=1,
+                                       tiles=orthonormal_tiles)
+    h.coarse_build()
+    X, Y = h.coarse_op()
+    Xo, Yo = coarse.galerkin(Pt, U, dims, block, kappa, w, bc)
+    out.append(max(rel(X.cpu().numpy(), Xo), rel(Y.cpu().numpy(), Yo)))
+    h.close()
+print(json.dumps(out))
+"""
+
+
+@pytest.mark.parametrize("variant,nb", [(0, 8), (1, 4)])
+def test_galerkin_tensor_pipe_batch_sizes(variant, nb):
+    """For 2k <= 24 the tensor-pipe kernel has two staging batch sizes (8 sites, one CTA per
+    SM; 4 sites, two CTAs per SM), of which the autotuner keeps the faster; each, forced in a
+    child process, must match the FP64 oracle to double-float accuracy."""
+    import os, subprocess, sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, WMG_DSLASH_VARIANT=str(variant), PYTHONPATH=root)
+    env.pop("WMG_AUTOTUNE_CACHE", None)
+    r = subprocess.run([sys.executable, "-c", BATCH_CHILD], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    errs = json.loads(r.stdout.strip().splitlines()[-1])
+    assert len(errs) == len(CASES) and max(errs) < 1e-11, (nb, errs)
+
+
 @pytest.mark.parametrize("dims,block,k", CASES)
 def test_galerkin_double_float_contraction(dims, block, k):
     """Galerkin contraction in double-float arithmetic on FP32 units vs the FP64 oracle: Gaussian
