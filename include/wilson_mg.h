@@ -143,8 +143,9 @@ const char* mg_last_error(void);
 /* Number of kernels this library has launched since load (diagnostic counter). */
 long long mg_kernel_launches(void);
 
-/* JSON list of the launch shapes the autotuner has chosen so far (library-owned string,
- * valid until the next call). */
+/* JSON list of the launch shapes the autotuner has chosen so far, one object per problem key
+ * ("kernel": "dslash" | "dslash_proj" | "galerkin_tc", the key fields, "variant", "ms");
+ * library-owned string, valid until the next call. */
 const char* mg_autotune_report(void);
 
 /* Per-kernel timing: enable = 1 brackets every subsequent instrumented launch with CUDA

@@ -149,7 +149,11 @@ const char* tune_report() {
   for (auto& kv : g_cache) {
     if (!first) os << ",";
     first = false;
-    os << "{\"kernel\":\"dslash\",\"dtype\":" << std::get<0>(kv.first)
+    // key ranges: stencil dtype codes below 1000, the fused stencil + projections 1000-1999,
+    // the tensor-pipe Galerkin from 2000
+    const int dt = std::get<0>(kv.first);
+    const char* kern = dt >= 2000 ? "galerkin_tc" : dt >= 1000 ? "dslash_proj" : "dslash";
+    os << "{\"kernel\":\"" << kern << "\",\"dtype\":" << dt
        << ",\"parity\":" << std::get<1>(kv.first) << ",\"dagger\":" << std::get<2>(kv.first)
        << ",\"volume\":" << std::get<3>(kv.first) << ",\"nrhs\":" << std::get<4>(kv.first)
        << ",\"variant\":" << kv.second.first << ",\"ms\":" << kv.second.second << "}";
