@@ -18,6 +18,7 @@ import pytest
 import oracle.adjoint
 import oracle.clover
 import oracle.coarse
+import oracle.critical_kappa
 import oracle.icsvd
 import oracle.krylov
 import oracle.mg
@@ -262,6 +263,41 @@ MUTANTS = [
     ("gradient_generator_not_daggered", oracle.adjoint, "grad_link_angles",
      [("dUd = np.conj(np.swapaxes(dU, 1, 2))", "dUd = np.swapaxes(dU, 1, 2)")],
      [_link_gradient_fd]),
+    # Gaussian draws (Box-Muller of the Philox uniforms)
+    ("box_muller_radius_unscaled", oracle.philox, "gaussian_field",
+     [("rho = np.sqrt(-2.0 * np.log(1.0 - ua))", "rho = np.sqrt(-np.log(1.0 - ua))")],
+     [TN.test_gaussian_moments]),
+    ("box_muller_half_circle", oracle.philox, "gaussian_field",
+     [("th = 2.0 * np.pi * ub", "th = np.pi * ub")], [TN.test_gaussian_moments]),
+    # the test vectors of one stream and the streams of Algorithm 3
+    ("test_vector_ids_shifted", oracle.icsvd, "test_vectors",
+     [("ids = np.arange(stream * r, stream * r + r)",
+       "ids = np.arange(stream * r + 1, stream * r + r + 1)")],
+     [TN.test_test_vectors_follow_eq2]),
+    ("icsvd_streams_repeat_the_first", oracle.icsvd, "icsvd",
+     [("test_vectors(links, dims, kappa, w, bc, seed, r, s, sweeps, clover)",
+       "test_vectors(links, dims, kappa, w, bc, seed, r, 0, sweeps, clover)")],
+     [TN.test_icsvd_without_truncation_keeps_every_stream]),
+    # prolongation from the per-site blocks of P
+    ("prolong_conjugates_p", oracle.coarse, "prolong",
+     [("np.einsum('xra,xa->xr', Ps, vc[coarse])", "np.einsum('xra,xa->xr', Ps.conj(), vc[coarse])")],
+     [GAL_A]),
+    ("site_prolongator_swaps_chirality", oracle.coarse, "site_prolongator",
+     [("Ps[:, 2 * a:2 * a + 2, :, a, :] = T[coarse, a, local]",
+       "Ps[:, 2 * a:2 * a + 2, :, 1 - a, :] = T[coarse, a, local]")], [GAL_A]),
+    # restarted GMRES to a tolerance
+    ("gmres_tol_basis_not_normalised", oracle.krylov, "gmres_tol",
+     [("V.append(w / H[j + 1, j])", "V.append(w)")], [TN.test_gmres_tol_and_fgmres]),
+    # even-odd split and join
+    ("schur_join_parities_swapped", oracle.schur, "join",
+     [("out[par == 0] = np.asarray(ve)", "out[par == 1] = np.asarray(ve)"),
+      ("out[par == 1] = np.asarray(vo)", "out[par == 0] = np.asarray(vo)")],
+     [TS.test_schur_solve_reconstructs_the_full_solution]),
+    # the near-critical hopping parameter of the synthetic workloads
+    ("hermitian_part_not_halved", oracle.critical_kappa, "hermitian_part_lmax",
+     [("return 0.5 * (h + hd)", "return h + hd")], [TW.test_kappa_crit_bound_on_free_field]),
+    ("hermitian_part_smallest_eigenvalue", oracle.critical_kappa, "hermitian_part_lmax",
+     [("which='LA'", "which='SA'")], [TW.test_kappa_crit_bound_on_free_field]),
 ]
 
 

@@ -256,6 +256,33 @@ def test_test_vectors_follow_eq2():
         assert np.abs(corr - K @ y).max() < 1e-8 * np.abs(corr).max()
 
 
+def test_icsvd_without_truncation_keeps_every_stream():
+    """Algorithm 3 with k = n_s r (nothing truncated): the final singular values of each
+    chirality's tile are those of all n_s r smoothed test vectors at once (a library SVD of
+    vectors built here from their definition: Philox ids 0 .. n_s r - 1, Eq. 2's Krylov
+    minimiser by least squares on the dense operator), so every stream's own vectors -- ids
+    s r .. s r + r - 1 -- enter the basis."""
+    dims, block = (2, 2, 2, 2), (2, 2, 2, 2)          # one aggregate: rows (site, spin, colour)
+    U = synthetic.haar_links(dims, 11)
+    w, bc, kappa = (1, 1, 1, 1), (1, 1, 1, -1), 0.12
+    r, n_s, sweeps, seed = 2, 3, 3, 5
+    _, S, _ = icsvd.icsvd(U, dims, kappa, w, bc, block, n_s * r, r, n_s, sweeps, seed)
+    V = wilson.volume(dims)
+    D = wilson.dense_dirac(U, dims, kappa, w, bc)
+    phi = philox.gaussian_vectors(seed, np.arange(n_s * r), V)
+    psi = []
+    for i in range(n_s * r):
+        p = phi[i].reshape(-1)
+        K = np.stack([np.linalg.matrix_power(D, j) @ (-D @ p) for j in range(sweeps)], axis=1)
+        y = np.linalg.lstsq(D @ K, -D @ p, rcond=None)[0]
+        psi.append((p + K @ y).reshape(V, 4, 3))
+    psi = np.stack(psi)
+    for a in range(2):
+        tile = np.moveaxis(psi[:, :, 2 * a:2 * a + 2, :], 0, -1).reshape(6 * V, n_s * r)
+        ref = np.linalg.svd(tile, compute_uv=False)
+        assert np.abs(S[0, a] - ref).max() < 1e-10 * ref[0]
+
+
 # ----------------------------------------------------------------------------- Galerkin
 @pytest.mark.parametrize("dims,block", [((4, 4, 2, 2), (2, 2, 2, 2)),      # coarse extent 2 and 1
                                         ((6, 2, 2, 4), (2, 2, 1, 2))])     # extent 3, block 1
