@@ -25,9 +25,11 @@
 // planes are stored k'-major (SA[k'][b'], SB[k'][a]) so that staging threads with consecutive
 // columns write consecutive addresses, and read with ldmatrix .trans; every row stride is an
 // odd number of 16-byte units, so the eight rows of an ldmatrix phase hit distinct banks.
-// A batch is NB = 8 sites for 2k <= 24 (two warp groups split its six 16-row k' steps) and
-// NB = 4 for 24 < 2k <= 48 (one warp group, three k' steps), so that the digit planes and the
-// double-buffered raw inputs of one CTA fit its shared memory up to the paper's k = 24.
+// A batch is NB = 4 sites (one warp group, three k' steps) or, for 2k <= 24, NB = 8 sites (two
+// warp groups split its six 16-row k' steps; the digit planes and the double-buffered raw
+// inputs of one CTA then take ~195 KB, one CTA per SM).  At 4 sites a CTA fits its shared
+// memory up to the paper's k = 24, and for 2k <= 24 two CTAs share an SM, so one CTA's staging
+// overlaps the other's products; the autotuner picks between the two where both fit.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -67,7 +69,6 @@ __host__ __device__ constexpr int tc_ldb(int t4) { return 8 * t4 + ((t4 & 1) ? 0
 __host__ __device__ constexpr size_t tc_smem(int t4, int nb) {
   return sizeof(__nv_bfloat16) * (size_t)TC_NS * 12 * nb * (tc_lda(t4) + tc_ldb(t4));
 }
-
 
 // Shared memory of one CTA beyond the digit planes: two raw input buffers (P(x + mu) and P(x)
 // column segments of 6 double-float values, U_mu(x)) and the per-site tables.
