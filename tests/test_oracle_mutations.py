@@ -298,6 +298,18 @@ MUTANTS = [
      [("return 0.5 * (h + hd)", "return h + hd")], [TW.test_kappa_crit_bound_on_free_field]),
     ("hermitian_part_smallest_eigenvalue", oracle.critical_kappa, "hermitian_part_lmax",
      [("which='LA'", "which='SA'")], [TW.test_kappa_crit_bound_on_free_field]),
+    # the clover term added to the Wilson-Dirac operator, the level-l prolongation, and the
+    # two-level solve's operator / preconditioner roles
+    ("clover_term_subtracted", oracle.clover, "dslash",
+     [("return out + np.einsum('xrc,xc->xr', C, psi.reshape(-1, 12))",
+       "return out - np.einsum('xrc,xc->xr', C, psi.reshape(-1, 12))")],
+     [TC.test_galerkin_with_clover_equals_dense_product]),
+    ("level_prolong_conjugates_p", oracle.multilevel, "prolong",
+     [("np.einsum('jna,ja->jn', Ps, vc[agg])", "np.einsum('jna,ja->jn', Ps.conj(), vc[agg])")],
+     [TM.test_level1_kcycle_with_exact_coarsest_solve_is_coarse_grid_correction]),
+    ("two_level_solve_roles_swapped", oracle.mg, "TwoLevel.solve",
+     [("fgmres(self.D, self.kcycle,", "fgmres(self.kcycle, self.D,")],
+     [TN.test_two_level_solve_matches_direct_solve]),
 ]
 
 
