@@ -7,7 +7,8 @@
 // Every staged double-float entry v satisfies |v| < 2 (|P| <= 1 entrywise for orthonormal
 // columns; |U h| <= sqrt(3) for unitary U and |h| <= 1), so it is written exactly enough as
 // fixed-point digits in base 256,
-//     v = sum_{i < NS} s_i 2^{-6-8i},  s_i integers, |s_i| <= 129,  NS = 7 (error < 2^-55),
+//     v = sum_{i < NS} s_i 2^{-6-8i},  s_i integers, |s_i| <= 129,  NS = 7
+// (error at most 2^-55 (1 + 2^-16)),
 // each digit exact in bfloat16.  A product of digit planes is an integer matrix product:
 // bf16 x bf16 tensor-core MMAs with FP32 accumulation are exact while the partial sums stay
 // below 2^24, which holds for one staging batch (<= 7 digit pairs x 96 stacked rows x 129^2).

@@ -2,7 +2,7 @@
 // the Galerkin forward-hop kernel and the SVD basis update.
 //
 // A double-float value v with |v| < 2 is written as 7 base-256 digits,
-//     v = sum_{i < 7} s_i 2^{-6-8i},  s_i integers, |s_i| <= 129  (remainder below 2^-55),
+//     v = sum_{i < 7} s_i 2^{-6-8i},  s_i integers, |s_i| <= 129  (remainder at most 2^-55 (1 + 2^-16)),
 // each digit exact in bfloat16.  The product of two such expansions is a sum of integer digit
 // products: bf16 x bf16 MMAs with FP32 accumulation are exact while the partial sums stay
 // below 2^24, the digit pairs (i, j) with i + j = d share one FP32 accumulator of weight
