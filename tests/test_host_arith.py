@@ -65,3 +65,15 @@ def test_digit_split_is_exact():
         v = Fraction(float(hi)) + Fraction(float(lo))
         expansion = sum(Fraction(int(d)) * Fraction(1, 2 ** (6 + 8 * i)) for i, d in enumerate(ds))
         assert abs(v - expansion) <= Fraction(1, 2 ** 55) * (1 + Fraction(1, 2 ** 16)), x
+
+
+def test_digit_products_accumulate_exactly_in_fp32():
+    """One staging batch's FP32 accumulator of weight d sums at most 7 digit pairs (i + j = d)
+    over the 12 NB stacked rows, each product at most 129^2 in magnitude: below 2^24, so every
+    partial sum of integers is exact in FP32 (NB = 8 and 4)."""
+    for nb in (8, 4):
+        assert 7 * (12 * nb) * 129 ** 2 < 2 ** 24
+    # the fold's weights 2^(-12-8d), d < 7, are FP32 numbers (normal, exact powers of two)
+    for d in range(7):
+        w = F(2.0) ** F(-12 - 8 * d)
+        assert float(w) == 2.0 ** (-12 - 8 * d) and np.isfinite(w) and w > np.finfo(F).tiny
